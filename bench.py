@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ghost-point multigrid solver.
+
+Workload (the 3D Poisson problem the headline metric is quoted on): ellipsoid
+phi = x^2/0.36 + y^2/0.25 + z^2/0.16 - 1 in [-1,1]^3, N = 256 (257^3 nodes),
+manufactured u = exp(x+y+z) sin(pi z), Dirichlet data on the curved boundary,
+FP64, V(2,1) cycles from u = 0 to ||r||_2 / ||r0||_2 <= 1e-10.
+
+One step = one whole solve through the C ABI: hierarchy creation from phi
+and f (classification, ghost projection / stencils / Delta tau, band,
+coarsest inverse), evaluation of g at the projection points, and the
+V-cycles with their residual checks.  Metric: V-cycles per second over the
+timed steps (set-up time included).  Inputs are resident in HBM and L2 is
+flushed before every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the plain CPU oracle (single thread) on the same
+workload, each step a bounded sample (one V-cycle plus the amortised
+set-up).  Multi-GPU runs are independent replicas (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2207_14208_gb300 import workloads as W  # noqa: E402
+
+METRIC = "V-cycles/s at 256^3 (3D ellipsoid Poisson, FP64, V(2,1) solve to 1e-10)"
+UNIT = "V-cycles/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--N", type=int, default=256)
+    p.add_argument("--rtol", type=float, default=1e-10)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ distributed
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, ws: int) -> float:
+    """Max of a float over all ranks (the timing rule: slowest rank)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(items, ws, rank):
+    """Independent problems split across replicas with no collective."""
+    return [x for i, x in enumerate(items) if i % ws == rank]
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), "bcmg_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def u_exact_torch(Q):
+    import torch
+    x, y, z = Q[:, 0], Q[:, 1], Q[:, 2]
+    return torch.exp(x + y + z) * torch.sin(math.pi * z)
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+# ------------------------------------------------------------ our arm
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2207_14208_gb300 import bcmg
+    from paper_2207_14208_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    B.build()
+    N = args.N
+    d = 3
+    phi_h = W.phi_ellipsoid(N)
+    f_h, us_h = W.manufactured(d, N)
+    phi = torch.from_numpy(phi_h).cuda()
+    f = torch.from_numpy(f_h).cuda()
+    u = torch.zeros_like(phi)
+    flush = torch.empty(512 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(profile=False):
+        s = bcmg.Solver(d, N, phi, f, profile=int(profile))
+        Q = s.ghost_points()
+        s.set_boundary_values(u_exact_torch(Q).contiguous())
+        u.zero_()
+        cycles, rel = s.solve(u, args.rtol, 200)
+        return s, cycles, rel
+
+    for _ in range(args.warmup):
+        s, c, rel = step()
+        s.close()
+    torch.cuda.synchronize()
+
+    # timed steps: events on the caller's stream bracket all library work
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = bcmg.kernel_launches()
+    times, cycles, rels, prof = [], [], [], []
+    for _ in range(args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s, c, rel = step(profile=True)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        cycles.append(c)
+        rels.append(rel)
+        prof.append(s.profile())
+        s.close()
+    torch.cuda.synchronize()
+    launches = bcmg.kernel_launches() - launches0
+    clk = clocks.stop()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    total_ms = sum(times)
+    total_ms_max = max_over_ranks(total_ms, ws)
+    total_cycles = sum(cycles) * ws
+    value = total_cycles / (total_ms_max / 1e3)
+
+    # roofline of the dominant kernel: the finest-level red/black sweep
+    s = bcmg.Solver(d, N, phi, f)
+    info = s.info(0)
+    s.close()
+    sweep_ms = sum(p["smooth_ms"] for p in prof) / max(1, sum(p["smooth_launches"] for p in prof))
+    n_int = info["n_interior"]
+    alg_bytes = 12.0 * n_int  # per colour sweep: F, new u and one neighbour value per updated node
+    achieved_gbs = alg_bytes / (sweep_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (analytic level set and manufactured solution)",
+        "config": {"workload": "3D ellipsoid Poisson N=256 (257^3), FP64 V(2,1) solve to 1e-10",
+                   "N": N, "cycles_per_solve": cycles[0], "final_rel_residual": max(rels),
+                   "interior_nodes": n_int, "ghosts": info["n_ghost"],
+                   "step": "create hierarchy + g(Q) + solve", "l2": "flushed (512 MiB write) before every step",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "k_smooth<3> (finest level, one colour)",
+                     "achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
+                     "peak_source": peak_kind, "traffic": None, "sweep_us": sweep_ms * 1e3,
+                     "alg_bytes_per_launch": alg_bytes},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = run_e2e(args, d, N, phi_h, f_h)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, d, N, phi_h, f_h, cycles[0])
+    return out
+
+
+def run_e2e(args, d, N, phi_h, f_h, steps=3):
+    """Same metric through the public API with host buffers: H2D of phi and
+    f, creation, Q to host, g(Q) on the host, H2D of g, solve, D2H of u."""
+    import torch
+    from paper_2207_14208_gb300 import bcmg
+    phi_p = torch.from_numpy(phi_h).pin_memory()
+    f_p = torch.from_numpy(f_h).pin_memory()
+    u_p = torch.empty_like(phi_p).pin_memory()
+    tot_c, tot_t, h2d, d2h = 0, 0.0, 0, 0
+    for it in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phi = phi_p.cuda(non_blocking=True)
+        f = f_p.cuda(non_blocking=True)
+        s = bcmg.Solver(d, N, phi, f)
+        Q = s.ghost_points().cpu().numpy()
+        g = torch.from_numpy(W.g_at(d, Q)).pin_memory().cuda(non_blocking=True)
+        s.set_boundary_values(g)
+        u = torch.zeros_like(phi)
+        c, rel = s.solve(u, args.rtol, 200)
+        u_p.copy_(u)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s.close()
+        if it > 0:
+            tot_c += c
+            tot_t += t1 - t0
+            h2d = phi_h.nbytes + f_h.nbytes + g.numel() * 8
+            d2h = Q.nbytes + u_p.numel() * 8
+    return {"value": tot_c / tot_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps}
+
+
+def oracle_sample(d, N, phi_h, f_h, ncyc):
+    """Oracle hierarchy set-up, then ncyc V-cycles: (setup_s, per_cycle_s)."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle(d, N, phi_h)
+    o.set_rhs(f_h, W.g_at(d, o.ghosts(0)["Q"]))
+    u = np.zeros(o.nn(0))
+    o.vcycle(u, 0)  # factor the coarsest system (part of set-up)
+    t1 = time.perf_counter()
+    per = []
+    for _ in range(ncyc):
+        a = time.perf_counter()
+        u = o.vcycle(u, 1)
+        o.norms(u)
+        per.append(time.perf_counter() - a)
+    return o, t1 - t0, per
+
+
+def cpu_baseline(args, d, N, phi_h, f_h, cycles_per_solve):
+    """One complete solve of the same workload by the oracle (single thread):
+    set-up, then V-cycles with residual checks to the same tolerance."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.Oracle(d, N, phi_h)
+    o.set_rhs(f_h, W.g_at(d, o.ghosts(0)["Q"]))
+    u, c, _ = o.solve(np.zeros(o.nn(0)), args.rtol, 200)
+    t = time.perf_counter() - t0
+    return {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one complete oracle solve at N=%d: set-up + %d V-cycles to %.0e, %.1f s "
+                      "(1 of %d host cores)" % (N, c, args.rtol, t, os.cpu_count() or 0)}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    d, N = 3, args.N
+    phi_h = W.phi_ellipsoid(N)
+    f_h, _ = W.manufactured(d, N)
+    import oracle
+    o, setup_s, _ = oracle_sample(d, N, phi_h, f_h, 0)
+    cycles_per_solve = 16  # the cycle count of the GPU solve at this workload (same algorithm)
+    u = np.zeros(o.nn(0))
+    for _ in range(args.warmup):
+        u = o.vcycle(u, 1)
+    times = []
+    for _ in range(args.steps):
+        a = time.perf_counter()
+        u = o.vcycle(u, 1)
+        o.norms(u)
+        times.append(time.perf_counter() - a + setup_s / cycles_per_solve)
+    t = statistics.mean(times)
+    value = 1.0 / t
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic level set and manufactured solution)",
+            "config": {"workload": "3D ellipsoid Poisson N=256 (257^3), FP64 V(2,1) solve to 1e-10", "N": N},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step one oracle V-cycle + residual norms plus 1/%d of the "
+                                       "oracle set-up (%.2f s)" % (cycles_per_solve, setup_s)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_info()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,196 @@
+/*
+ * bcmg.h -- C ABI of the GB300 (sm_103a) ghost-point Boundary Condition
+ * MultiGrid solver.
+ *
+ * Method: Coco, Mazza and Semplice, "A ghost-point smoothing strategy for
+ * geometric multigrid on curved boundaries" (arXiv 2207.14208).  The solver
+ * treats -Lap u = f in Omega = {phi < 0} inside D = [-1,1]^d (d = 2 or 3)
+ * with Dirichlet data g on the curved boundary by the ghost-point method of
+ * Sec. 3.3 and relaxes every ghost equation with the distance-dependent
+ * fictitious-time step Delta tau_OPT(theta~) of eq. DtauOptTheta.
+ *
+ * Grid and layout (Sec. 3 and Sec. 4 set-up): N cells per axis, n = N + 1
+ * nodes per axis, x_i = -1 + i h, h = 2/N.  Every grid array passed through
+ * this ABI is dense FP64 with n^d entries, x fastest: index i + n j + n^2 k.
+ *
+ * Node classes: INTERIOR (phi < 0, not on the box boundary), GHOST (phi >= 0
+ * with an interior axis neighbour), BOXDIR (phi < 0 on the box boundary: an
+ * eliminated Dirichlet node whose value is read from u), INACTIVE.
+ *
+ * Conventions of every entry point:
+ *  - the return value is a status (BCMG_OK = 0 or one of the codes below);
+ *    nothing throws across the ABI; bcmg_last_error() gives a message for
+ *    the calling thread's last failure;
+ *  - "_dev" pointers are CUDA device pointers, "_host" pointers host memory;
+ *    the caller owns every pointer it passes; the handle owns everything else;
+ *  - work is stream-ordered on the stream given at creation; entry points
+ *    that return host data (counts, norms, host copies) synchronise it;
+ *  - a call that reads or writes caller arrays must not overlap on the GPU
+ *    with another call on the same handle (calls on one handle are ordered).
+ */
+#ifndef BCMG_H
+#define BCMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BCMG_OK 0
+#define BCMG_EINVAL 1     /* bad argument (null pointer, size, level) */
+#define BCMG_ENOMEM 2     /* device or host allocation failed */
+#define BCMG_ECUDA 3      /* a CUDA runtime call failed */
+#define BCMG_EGEOM 4      /* no interior node, or singular / oversized coarsest system */
+#define BCMG_ENOCONV 5    /* solve hit max_cycles before rtol */
+#define BCMG_ENONFINITE 6 /* NaN or Inf in the residual */
+#define BCMG_ETIMEOUT 7   /* reserved for bounded device-side waits */
+
+#define BCMG_CLASS_INACTIVE 0
+#define BCMG_CLASS_INTERIOR 1
+#define BCMG_CLASS_GHOST 2
+#define BCMG_CLASS_BOXDIR 3
+
+#define BCMG_DTAU_EXP 0   /* G0 = exp(-p theta): Remark exptheta2D (default) */
+#define BCMG_DTAU_POLY 1  /* G0 of eqs. G / G3D with coefficients eq. coeff */
+#define BCMG_DTAU_CONST 2 /* one Delta tau for every ghost (Remark dtau) */
+
+typedef struct bcmg_h *bcmg_handle;
+
+typedef struct {
+    int nu1;           /* pre-smoothing steps (Sec. 3.1: 2) */
+    int nu2;           /* post-smoothing steps (Sec. 3.1: 1) */
+    int dtau_mode;     /* BCMG_DTAU_* */
+    double dtau_const; /* Delta tau when dtau_mode == BCMG_DTAU_CONST */
+    int ext_sweeps;    /* pseudo-time sweeps of the normal extension (4) */
+    int min_coarse;    /* coarsening stops before N_l / 2 < min_coarse (8) */
+    int max_levels;    /* upper bound on the number of levels (24) */
+    int use_graph;     /* replay the V-cycle from a captured CUDA graph (1) */
+    int profile;       /* time every finest-level smoothing sweep with CUDA
+                          events during bcmg_solve (0) */
+} bcmg_opts;
+
+/* Fill *opts with the defaults above. */
+void bcmg_default_opts(bcmg_opts *opts);
+
+/* Build the level hierarchy (Sec. 2.1 re-discretisation, Sec. 3.3 geometry):
+ * per level the node classes from phi injected to the level, the ghost list
+ * with projection points Q = G - eta h n (phi(Q) = 0), upwind 3^d stencils,
+ * quadratic interpolation weights and Delta tau_OPT(eta) (eq. DtauOptTheta),
+ * the inactive band that receives normal extensions, and the inverse of the
+ * coarsest system.
+ *   dim      2 or 3
+ *   N        cells per axis, N >= 4
+ *   phi_dev  n^dim level-set values (read during the call only)
+ *   f_dev    n^dim right-hand side of -Lap u = f (interior values are
+ *            copied; may be NULL for f = 0)
+ *   opts     NULL for the defaults
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ *   out      receives the handle
+ * Errors: EINVAL, ENOMEM, ECUDA, EGEOM (no interior node on the finest grid,
+ * or the coarsest system is singular or has more than 4096 unknowns). */
+int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
+                               const bcmg_opts *opts, void *stream, bcmg_handle *out);
+
+/* Release every resource of the handle (NULL is accepted). */
+int bcmg_destroy(bcmg_handle h);
+
+/* Number of ghost points on the finest level. */
+int bcmg_ghost_count(bcmg_handle h, int64_t *n);
+
+/* Projection points Q of the finest-level ghosts (Sec. 3.3), ghost-list order
+ * (increasing node index), written as count x dim FP64 (x, y[, z]) to the
+ * device buffer Q_dev.  The caller evaluates its boundary data there. */
+int bcmg_ghost_points(bcmg_handle h, double *Q_dev);
+
+/* Dirichlet values g(Q) for the finest-level ghosts (eq. BCh right-hand
+ * side), count FP64 values in ghost-list order, device pointer. */
+int bcmg_set_boundary_values(bcmg_handle h, const double *g_dev);
+
+/* Replace the interior right-hand side f (n^dim, device; NULL = 0). */
+int bcmg_set_rhs(bcmg_handle h, const double *f_dev);
+
+/* ncycles V(nu1, nu2) cycles (Sec. 2.1, gamma = 1) on u_dev (n^dim, device,
+ * in/out).  Interior and ghost nodes are updated; BOXDIR values are read as
+ * eliminated Dirichlet data; every other node of u is left untouched. */
+int bcmg_vcycle(bcmg_handle h, double *u_dev, int ncycles);
+
+/* V-cycles until ||r||_2 <= rtol ||r^(0)||_2 (r stacked over interior and
+ * ghost rows, Sec. 2.2) or max_cycles.  cycles_done and final_rel_res may be
+ * NULL.  Returns ENOCONV if max_cycles is reached, ENONFINITE on NaN/Inf. */
+int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *cycles_done,
+               double *final_rel_res);
+
+/* Residual norms of u_dev on the finest level into out_host[4]:
+ * ||r_I||_2, ||r_G||_2, ||r_I||_inf, ||r_G||_inf (unscaled residuals). */
+int bcmg_residual_norm(bcmg_handle h, const double *u_dev, double *out_host);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *bcmg_last_error(void);
+
+/* Kernels this process launched through the library so far (each replayed
+ * CUDA-graph node counts once per replay). */
+int64_t bcmg_kernel_launches(void);
+
+/* With opts.profile = 1: out_host[0] = summed device time (ms) of the
+ * finest-level red/black interior sweeps run by bcmg_solve on this handle,
+ * out_host[1] = their number (CUDA events recorded on the launching stream,
+ * read after each cycle). */
+int bcmg_profile_read(bcmg_handle h, double *out_host);
+
+/* ---- introspection (host copies, synchronous) ----------------------- */
+
+int bcmg_num_levels(bcmg_handle h, int *levels);
+
+/* out_host[10]: N, n, n^dim, interior, ghost, band, boxdir, clamped (eta
+ * forced to 1), stencil fall-backs, active unknowns of the coarsest system
+ * (0 on other levels). */
+int bcmg_level_info(bcmg_handle h, int level, int64_t *out_host);
+
+/* n^dim node classes (BCMG_CLASS_*) of a level. */
+int bcmg_get_class(bcmg_handle h, int level, uint8_t *cls_host);
+
+/* Ghost list of a level (ng entries; the vector fields hold 3 per ghost,
+ * unused axes 0): node index, eta, outward normal n, local coordinates xi of
+ * Q in the stencil, stencil direction s (+1: stencil towards -x_a), degree q
+ * per axis, Delta tau, and Q.  Any output pointer may be NULL. */
+int bcmg_get_ghosts(bcmg_handle h, int level, int64_t *idx, double *eta, double *n3, double *xi3,
+                    int32_t *s3, int32_t *q3, double *dtau, double *Q3);
+
+/* Band node indices of a level (increasing). */
+int bcmg_get_band(bcmg_handle h, int level, int64_t *idx_host);
+
+/* ---- stage operators on caller arrays of one level (device, n_l^dim) --
+ * These run the same kernels as the V-cycle; they exist so that every step
+ * of the cycle can be called and checked on its own. */
+
+/* nsteps smoothing steps: red then black Gauss-Seidel on interior nodes
+ * (eq. GSLEX_2D in red-black order), then the simultaneous fictitious-time
+ * relaxation of every ghost (eq. rel with Delta tau of eq. DtauOptTheta). */
+int bcmg_smooth(bcmg_handle h, int level, double *u_dev, const double *F_dev, int nsteps);
+
+/* r = F - A u on interior (eq. Laph) and ghost (eq. BCh) rows; other nodes
+ * of r are left untouched. */
+int bcmg_residual(bcmg_handle h, int level, const double *u_dev, const double *F_dev,
+                  double *r_dev);
+
+/* Extend ghost values of a into the band along the normal (Sec. 3.3.2). */
+int bcmg_extend(bcmg_handle h, int level, double *a_dev);
+
+/* Class-aware restriction (Sec. 3.3.2) of r on level `level` to F on
+ * level + 1 (interior and ghost coarse nodes written, others untouched). */
+int bcmg_restrict(bcmg_handle h, int level, const double *r_fine_dev, double *F_coarse_dev);
+
+/* u_fine += multilinear interpolation of e_coarse (level + 1) on the fine
+ * interior and ghost nodes (Sec. 3.3.2). */
+int bcmg_prolong(bcmg_handle h, int level, const double *e_coarse_dev, double *u_fine_dev);
+
+/* Exact correction on the coarsest level: u += A^-1 (F - A u). */
+int bcmg_coarsest_solve(bcmg_handle h, double *u_dev, const double *F_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCMG_H */

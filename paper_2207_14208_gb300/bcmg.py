@@ -1,0 +1,257 @@
+"""Thin ctypes binding of the GB300 BCMG C ABI (``include/bcmg.h``).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libbcmg.so``.  Tensors are PyTorch CUDA tensors (float64,
+contiguous, n^d entries, x fastest); work is ordered on the current PyTorch
+stream.  If the library has not been built, loading raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbcmg.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bcmg.h")
+
+OK, EINVAL, ENOMEM, ECUDA, EGEOM, ENOCONV, ENONFINITE, ETIMEOUT = range(8)
+INACTIVE, INTERIOR, GHOST, BOXDIR = 0, 1, 2, 3
+DTAU_EXP, DTAU_POLY, DTAU_CONST = 0, 1, 2
+
+_lib = None
+_lock = threading.Lock()
+
+
+class BcmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("bcmg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("dtau_mode", C.c_int),
+                ("dtau_const", C.c_double), ("ext_sweeps", C.c_int), ("min_coarse", C.c_int),
+                ("max_levels", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int)]
+
+
+def declared_functions():
+    """Names of the functions declared in include/bcmg.h."""
+    text = open(HEADER).read()
+    return re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(bcmg_[a-z_0-9]+)\s*\(", text, re.M)
+
+
+def load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("BCMG CUDA library missing (%s); build it with "
+                               "paper_2207_14208_gb300.build.build()" % LIB_PATH)
+        lib = C.CDLL(LIB_PATH)
+        vp, i32, i64, f64 = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "bcmg_default_opts": (None, [vp]),
+            "bcmg_create_grid_hierarchy": (i32, [i32, i64, vp, vp, vp, vp, vp]),
+            "bcmg_destroy": (i32, [vp]),
+            "bcmg_ghost_count": (i32, [vp, vp]),
+            "bcmg_ghost_points": (i32, [vp, vp]),
+            "bcmg_set_boundary_values": (i32, [vp, vp]),
+            "bcmg_set_rhs": (i32, [vp, vp]),
+            "bcmg_vcycle": (i32, [vp, vp, i32]),
+            "bcmg_solve": (i32, [vp, vp, f64, i32, vp, vp]),
+            "bcmg_residual_norm": (i32, [vp, vp, vp]),
+            "bcmg_last_error": (C.c_char_p, []),
+            "bcmg_kernel_launches": (i64, []),
+            "bcmg_profile_read": (i32, [vp, vp]),
+            "bcmg_num_levels": (i32, [vp, vp]),
+            "bcmg_level_info": (i32, [vp, i32, vp]),
+            "bcmg_get_class": (i32, [vp, i32, vp]),
+            "bcmg_get_ghosts": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "bcmg_get_band": (i32, [vp, i32, vp]),
+            "bcmg_smooth": (i32, [vp, i32, vp, vp, i32]),
+            "bcmg_residual": (i32, [vp, i32, vp, vp, vp]),
+            "bcmg_extend": (i32, [vp, i32, vp]),
+            "bcmg_restrict": (i32, [vp, i32, vp, vp]),
+            "bcmg_prolong": (i32, [vp, i32, vp, vp]),
+            "bcmg_coarsest_solve": (i32, [vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise BcmgError(rc, load().bcmg_last_error().decode())
+
+
+def kernel_launches() -> int:
+    return int(load().bcmg_kernel_launches())
+
+
+def _dptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().bcmg_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """A BCMG hierarchy on the current CUDA device.
+
+    phi, f: CUDA float64 tensors with (N+1)^dim entries (x fastest)."""
+
+    def __init__(self, dim: int, N: int, phi, f=None, **opts):
+        self.lib = load()
+        self.dim, self.N = dim, N
+        self.n = N + 1
+        self.nn = self.n ** dim
+        if phi.numel() != self.nn:
+            raise ValueError("phi must have (N+1)^dim entries")
+        o = default_opts(**opts)
+        h = C.c_void_p()
+        fp = _dptr(f) if f is not None else None
+        _check(self.lib.bcmg_create_grid_hierarchy(dim, N, _dptr(phi), fp, C.byref(o), _stream(),
+                                                   C.byref(h)))
+        self.h = h
+        self.levels = self._num_levels()
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.bcmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- problem data ------------------------------------------------
+    def ghost_count(self) -> int:
+        n = C.c_int64()
+        _check(self.lib.bcmg_ghost_count(self.h, C.byref(n)))
+        return n.value
+
+    def ghost_points(self):
+        import torch
+        ng = self.ghost_count()
+        Q = torch.empty((max(ng, 1), self.dim), dtype=torch.float64, device="cuda")
+        _check(self.lib.bcmg_ghost_points(self.h, _dptr(Q)))
+        return Q[:ng]
+
+    def set_boundary_values(self, g):
+        _check(self.lib.bcmg_set_boundary_values(self.h, _dptr(g)))
+
+    def set_rhs(self, f):
+        _check(self.lib.bcmg_set_rhs(self.h, _dptr(f) if f is not None else None))
+
+    # ---- cycles ------------------------------------------------------
+    def vcycle(self, u, ncycles: int = 1):
+        _check(self.lib.bcmg_vcycle(self.h, _dptr(u), ncycles))
+
+    def solve(self, u, rtol: float = 1e-10, max_cycles: int = 100, raise_noconv: bool = True):
+        c = C.c_int()
+        rel = C.c_double()
+        rc = self.lib.bcmg_solve(self.h, _dptr(u), float(rtol), int(max_cycles), C.byref(c), C.byref(rel))
+        if rc != OK and not (rc == ENOCONV and not raise_noconv):
+            _check(rc)
+        return c.value, rel.value
+
+    def profile(self) -> dict:
+        """Summed device time of the finest-level sweeps timed during solve()
+        (needs profile=1 at creation)."""
+        out = np.zeros(2)
+        _check(self.lib.bcmg_profile_read(self.h, _hptr(out)))
+        return {"smooth_ms": float(out[0]), "smooth_launches": int(out[1])}
+
+    def residual_norm(self, u) -> np.ndarray:
+        out = np.zeros(4)
+        _check(self.lib.bcmg_residual_norm(self.h, _dptr(u), _hptr(out)))
+        return out
+
+    # ---- introspection -----------------------------------------------
+    def _num_levels(self) -> int:
+        v = C.c_int()
+        _check(self.lib.bcmg_num_levels(self.h, C.byref(v)))
+        return v.value
+
+    def info(self, l: int = 0) -> dict:
+        out = np.zeros(10, dtype=np.int64)
+        _check(self.lib.bcmg_level_info(self.h, l, _hptr(out)))
+        keys = ["N", "n", "nn", "n_interior", "n_ghost", "n_band", "n_boxdir", "n_clamped",
+                "n_fallback", "n_active"]
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def cls(self, l: int = 0) -> np.ndarray:
+        out = np.zeros(self.info(l)["nn"], dtype=np.uint8)
+        _check(self.lib.bcmg_get_class(self.h, l, _hptr(out)))
+        return out
+
+    def ghosts(self, l: int = 0) -> dict:
+        ng = self.info(l)["n_ghost"]
+        idx = np.zeros(ng, dtype=np.int64)
+        eta = np.zeros(ng)
+        n3 = np.zeros((ng, 3))
+        xi3 = np.zeros((ng, 3))
+        s3 = np.zeros((ng, 3), dtype=np.int32)
+        q3 = np.zeros((ng, 3), dtype=np.int32)
+        dt = np.zeros(ng)
+        Q3 = np.zeros((ng, 3))
+        _check(self.lib.bcmg_get_ghosts(self.h, l, _hptr(idx), _hptr(eta), _hptr(n3), _hptr(xi3),
+                                        _hptr(s3), _hptr(q3), _hptr(dt), _hptr(Q3)))
+        d = self.dim
+        return dict(idx=idx, eta=eta, n=n3[:, :d], xi=xi3[:, :d], s=s3[:, :d], q=q3[:, :d],
+                    dtau=dt, Q=Q3[:, :d])
+
+    def band(self, l: int = 0) -> np.ndarray:
+        out = np.zeros(max(self.info(l)["n_band"], 1), dtype=np.int64)
+        _check(self.lib.bcmg_get_band(self.h, l, _hptr(out)))
+        return out[: self.info(l)["n_band"]]
+
+    # ---- stage operators (device tensors of one level) -------------------
+    def smooth(self, l, u, F, nsteps=1):
+        _check(self.lib.bcmg_smooth(self.h, l, _dptr(u), _dptr(F), nsteps))
+
+    def residual(self, l, u, F, r):
+        _check(self.lib.bcmg_residual(self.h, l, _dptr(u), _dptr(F), _dptr(r)))
+
+    def extend(self, l, a):
+        _check(self.lib.bcmg_extend(self.h, l, _dptr(a)))
+
+    def restrict(self, l, rf, Fc):
+        _check(self.lib.bcmg_restrict(self.h, l, _dptr(rf), _dptr(Fc)))
+
+    def prolong(self, l, ec, uf):
+        _check(self.lib.bcmg_prolong(self.h, l, _dptr(ec), _dptr(uf)))
+
+    def coarsest_solve(self, u, F):
+        _check(self.lib.bcmg_coarsest_solve(self.h, _dptr(u), _dptr(F)))

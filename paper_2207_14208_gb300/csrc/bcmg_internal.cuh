@@ -1,0 +1,136 @@
+// Internal declarations of the GB300 BCMG library (not part of the C ABI).
+//
+// Data layout in HBM, per level l (N_l = N >> l cells, n_l = N_l + 1 nodes per
+// axis, dense x-fastest arrays of n_l^d entries):
+//   cls  uint8 node class (INACTIVE / INTERIOR / GHOST / BOXDIR)
+//   u    FP64 solution (level 0: internal copy) or correction e (l > 0)
+//   F    FP64 right-hand side: f on interior rows, g on ghost rows (level 0),
+//        restricted residuals on coarse levels
+//   r    FP64 residual (interior, ghost, then extended into the band)
+// Work lists (compacted once at set-up, sorted by node index):
+//   win  64-node windows of one x-row that hold interior nodes: base index,
+//        (j, k) and a 64-bit interior mask; one warp per window
+//   ghost list: index, direction/degree code, xi per axis (SoA), Delta tau
+//   band list: index, up to d upwind sources (band position or ghost index)
+//        with normalised weights (SoA)
+//   coarsest level: active list and the dense inverse of its system
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bcmg.h"
+
+namespace bcmg {
+
+enum : uint8_t { CL_INACTIVE = 0, CL_INTERIOR = 1, CL_GHOST = 2, CL_BOXDIR = 3 };
+
+constexpr int kWin = 64;          // nodes per interior window (one warp, 2 per lane)
+constexpr int kWarpsPerBlock = 8; // window kernels: 256 threads
+constexpr int kMaxCoarse = 4096;  // largest coarsest system inverted densely
+constexpr int32_t kNoRef = INT32_MIN;
+
+struct Win {
+    uint32_t base;  // linear index of the window's first node (i0 = 64 m)
+    uint32_t jk;    // j | k << 16
+    uint64_t mask;  // bit t: node base + t is INTERIOR
+};
+
+struct Level {
+    int d = 0, N = 0, n = 0;
+    int64_t nn = 0;
+    int64_t st[3] = {0, 0, 0};
+    double h = 0.0;
+    uint8_t *cls = nullptr;
+    int64_t nint = 0, nbox = 0, ng = 0, nb = 0, nclamp = 0, nfall = 0, nact = 0;
+    int64_t nwin = 0;
+    Win *win = nullptr;
+    // ghosts (SoA)
+    uint32_t *gidx = nullptr;
+    uint16_t *gcode = nullptr;  // bit a: s_a = -1; bits 3+2a..4+2a: degree q_a
+    double *gxi = nullptr;      // 3 * ng, axis-major
+    double *gdt = nullptr;
+    double *geta = nullptr;
+    double *gn = nullptr;  // 3 * ng, axis-major
+    double *gQ = nullptr;  // ng * d, point-major (x, y[, z])
+    // band (SoA)
+    uint32_t *bidx = nullptr;
+    int32_t *bref = nullptr;  // 3 * nb, axis-major: >= 0 band position,
+                              // < 0 -(ghost node index) - 1, kNoRef none
+    double *bw = nullptr;     // 3 * nb, axis-major, normalised weights
+    // boxdir list (finest level only)
+    uint32_t *boxidx = nullptr;
+    // arrays
+    double *u = nullptr, *F = nullptr, *r = nullptr;
+    double *gtmp = nullptr;  // ng
+    double *bbuf = nullptr;  // 2 * nb
+    // coarsest
+    uint32_t *act = nullptr;
+    double *Ainv = nullptr;
+    double *crhs = nullptr;
+    // set-up only: phi of this level (finest: caller's array)
+    const double *phi = nullptr;
+};
+
+struct Handle {
+    int d = 0;
+    int64_t N = 0;
+    bcmg_opts o{};
+    cudaStream_t user = nullptr;  // caller's stream
+    cudaStream_t st = nullptr;    // library stream (graph capture, all work)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<Level> L;
+    double *u0 = nullptr;        // finest-level working copy of u
+    double *npart = nullptr;     // norm partials
+    double *nout = nullptr;      // 4 norms (device)
+    double *nhost = nullptr;     // pinned copy of the 4 norms
+    cudaGraphExec_t vgraph = nullptr;
+    cudaGraphExec_t ngraph = nullptr;  // V-cycle followed by norms
+    int64_t vgraph_kernels = 0, ngraph_kernels = 0;
+    bool capturing = false;
+    int64_t captured = 0;
+    std::vector<void *> allocs;
+    std::vector<void *> temps;  // set-up scratch, freed when creation ends
+    // profiling of the finest-level sweeps (opts.profile)
+    std::vector<cudaEvent_t> pev;
+    int pev_next = 0, pev_pairs = 0;
+    double prof_ms = 0.0;
+    int64_t prof_n = 0;
+};
+
+// record a timing event of the finest-level sweep profile (no-op otherwise)
+void profile_mark(Handle &H, const Level &L);
+
+// ---- error handling -------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+void check_cuda(cudaError_t e, const char *what);
+void *dalloc(Handle &H, size_t bytes, bool temp = false);  // zero-filled; temp: freed after set-up
+void count_launch(Handle &H);
+int64_t launches_total();
+
+// ---- set-up (setup.cu) -------------------------------------------------
+void setup_level(Handle &H, Level &L, int level_index);
+int64_t compact_flags(Handle &H, const uint8_t *flags, int64_t n, uint32_t **out, bool temp = false);
+void setup_coarsest(Handle &H, Level &L);
+double dtau_of(int d, int mode, double cst, double theta);
+
+// ---- cycle kernels (cycle.cu) -----------------------------------------
+void smooth(Handle &H, Level &L, double *u, const double *F, int nsteps);
+void residual(Handle &H, Level &L, const double *u, const double *F, double *r);
+void extend(Handle &H, Level &L, double *a);
+void restrict_to(Handle &H, Level &Lf, Level &Lc, const double *rf, double *Fc, double *uc_zero);
+void prolong(Handle &H, Level &Lf, Level &Lc, const double *ec, double *uf);
+void coarsest_correct(Handle &H, Level &L, double *u, const double *F);
+void norms(Handle &H, Level &L, const double *r, double *out4);
+void vcycle_enqueue(Handle &H, int l, double *u);
+void copy_active(Handle &H, const double *src, double *dst, bool with_boxdir);
+void scatter_ghost_values(Handle &H, Level &L, const double *g, double *F);
+void set_interior_rhs(Handle &H, Level &L, const double *f, double *F);
+
+}  // namespace bcmg

@@ -1,0 +1,554 @@
+// C ABI of the GB300 BCMG library: handle life cycle, argument checks,
+// stream ordering, CUDA-graph replay of the V-cycle, and error reporting.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "bcmg_internal.cuh"
+
+namespace bcmg {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<int64_t> g_launches{0};
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+}  // namespace
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+        throw Error{e == cudaErrorMemoryAllocation ? BCMG_ENOMEM : BCMG_ECUDA, m};
+    }
+}
+
+void *dalloc(Handle &H, size_t bytes, bool temp) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 8;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        throw Error{BCMG_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+    }
+    (temp ? H.temps : H.allocs).push_back(p);
+    check_cuda(cudaMemsetAsync(p, 0, bytes, H.st), "cudaMemsetAsync");
+    return p;
+}
+
+void count_launch(Handle &H) {
+    if (H.capturing) H.captured++;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+int64_t launches_total() { return g_launches.load(); }
+
+void profile_mark(Handle &H, const Level &L) {
+    if (!H.o.profile || H.L.empty() || &L != &H.L[0]) return;
+    if (H.pev_next >= (int)H.pev.size()) return;
+    check_cuda(cudaEventRecordWithFlags(H.pev[H.pev_next], H.st, H.capturing ? cudaEventRecordExternal : 0),
+               "profile event");
+    H.pev_next++;
+}
+
+namespace {
+
+void free_temps(Handle &H) {
+    for (void *p : H.temps) cudaFree(p);
+    H.temps.clear();
+}
+
+void destroy(Handle *H) {
+    if (!H) return;
+    if (H->st) cudaStreamSynchronize(H->st);
+    if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
+    if (H->ngraph) cudaGraphExecDestroy(H->ngraph);
+    free_temps(*H);
+    for (void *p : H->allocs) cudaFree(p);
+    if (H->nhost) cudaFreeHost(H->nhost);
+    for (cudaEvent_t e : H->pev) cudaEventDestroy(e);
+    if (H->ev_in) cudaEventDestroy(H->ev_in);
+    if (H->ev_out) cudaEventDestroy(H->ev_out);
+    if (H->st) cudaStreamDestroy(H->st);
+    delete H;
+}
+
+// order the library stream after the caller's stream, and back
+void enter(Handle &H) {
+    check_cuda(cudaEventRecord(H.ev_in, H.user), "cudaEventRecord(in)");
+    check_cuda(cudaStreamWaitEvent(H.st, H.ev_in, 0), "cudaStreamWaitEvent(in)");
+}
+
+void leave(Handle &H) {
+    check_cuda(cudaEventRecord(H.ev_out, H.st), "cudaEventRecord(out)");
+    check_cuda(cudaStreamWaitEvent(H.user, H.ev_out, 0), "cudaStreamWaitEvent(out)");
+}
+
+// Capture fn() on the library stream into an executable graph.
+template <class Fn>
+cudaGraphExec_t capture(Handle &H, int64_t *kernels, Fn fn) {
+    cudaGraph_t g = nullptr;
+    check_cuda(cudaStreamBeginCapture(H.st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    H.capturing = true;
+    H.captured = 0;
+    H.pev_next = 0;
+    try {
+        fn();
+    } catch (...) {
+        H.capturing = false;
+        cudaStreamEndCapture(H.st, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    H.capturing = false;
+    H.pev_pairs = H.pev_next / 2;
+    check_cuda(cudaStreamEndCapture(H.st, &g), "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    check_cuda(e, "cudaGraphInstantiate");
+    *kernels = H.captured;
+    return ex;
+}
+
+void run_vcycle(Handle &H) {
+    if (H.o.use_graph) {
+        if (!H.vgraph) H.vgraph = capture(H, &H.vgraph_kernels, [&] { vcycle_enqueue(H, 0, H.u0); });
+        check_cuda(cudaGraphLaunch(H.vgraph, H.st), "cudaGraphLaunch(vcycle)");
+        g_launches.fetch_add(H.vgraph_kernels, std::memory_order_relaxed);
+    } else {
+        vcycle_enqueue(H, 0, H.u0);
+    }
+}
+
+void enqueue_norms(Handle &H) {
+    Level &L = H.L[0];
+    residual(H, L, H.u0, L.F, L.r);
+    norms(H, L, L.r, H.nout);
+}
+
+// add the device time of the profiled sweeps of the last completed cycle
+void profile_collect(Handle &H) {
+    if (!H.o.profile) return;
+    for (int p = 0; p < H.pev_pairs; ++p) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, H.pev[2 * p], H.pev[2 * p + 1]) == cudaSuccess) {
+            H.prof_ms += ms;
+            H.prof_n++;
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
+}
+
+// V-cycle + residual norms of the result (one graph)
+void run_vcycle_norms(Handle &H) {
+    if (!H.o.use_graph) H.pev_next = 0;
+    if (H.o.use_graph) {
+        if (!H.ngraph)
+            H.ngraph = capture(H, &H.ngraph_kernels, [&] {
+                vcycle_enqueue(H, 0, H.u0);
+                enqueue_norms(H);
+            });
+        check_cuda(cudaGraphLaunch(H.ngraph, H.st), "cudaGraphLaunch(vcycle+norms)");
+        g_launches.fetch_add(H.ngraph_kernels, std::memory_order_relaxed);
+    } else {
+        vcycle_enqueue(H, 0, H.u0);
+        enqueue_norms(H);
+        H.pev_pairs = H.pev_next / 2;
+    }
+}
+
+void fetch_norms(Handle &H, double out[4]) {
+    check_cuda(cudaMemcpyAsync(H.nhost, H.nout, 4 * sizeof(double), cudaMemcpyDeviceToHost, H.st), "norms D2H");
+    check_cuda(cudaStreamSynchronize(H.st), "norms sync");
+    for (int i = 0; i < 4; ++i) out[i] = H.nhost[i];
+}
+
+Handle *checked(bcmg_handle h) {
+    if (!h) throw Error{BCMG_EINVAL, "null handle"};
+    return reinterpret_cast<Handle *>(h);
+}
+
+Level &level_of(Handle &H, int l) {
+    if (l < 0 || l >= (int)H.L.size()) throw Error{BCMG_EINVAL, "level out of range"};
+    return H.L[l];
+}
+
+template <class Fn>
+int guarded(Fn fn) {
+    try {
+        fn();
+        g_last_error.clear();
+        return BCMG_OK;
+    } catch (const Error &e) {
+        return fail(e.code, e.msg);
+    } catch (const std::bad_alloc &) {
+        return fail(BCMG_ENOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(BCMG_ECUDA, "unexpected exception");
+    }
+}
+
+}  // namespace
+}  // namespace bcmg
+
+using namespace bcmg;
+
+extern "C" {
+
+void bcmg_default_opts(bcmg_opts *o) {
+    if (!o) return;
+    o->nu1 = 2;
+    o->nu2 = 1;
+    o->dtau_mode = BCMG_DTAU_EXP;
+    o->dtau_const = 1.75;
+    o->ext_sweeps = 4;
+    o->min_coarse = 8;
+    o->max_levels = 24;
+    o->use_graph = 1;
+    o->profile = 0;
+}
+
+int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
+                               const bcmg_opts *opts, void *stream, bcmg_handle *out) {
+    if (!out) return fail(BCMG_EINVAL, "out is null");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(BCMG_EINVAL, "dim must be 2 or 3");
+    if (N < 4 || N > 65534) return fail(BCMG_EINVAL, "N must be in [4, 65534]");
+    double nn_d = std::pow((double)(N + 1), dim);
+    if (nn_d >= 4294967295.0) return fail(BCMG_EINVAL, "grid has 2^32 nodes or more");
+    if (!phi_dev) return fail(BCMG_EINVAL, "phi is null");
+    Handle *H = nullptr;
+    int rc = guarded([&] {
+        H = new Handle();
+        H->d = dim;
+        H->N = N;
+        if (opts) H->o = *opts;
+        else bcmg_default_opts(&H->o);
+        if (H->o.nu1 < 0 || H->o.nu2 < 0 || H->o.ext_sweeps < 1 || H->o.min_coarse < 2 ||
+            H->o.max_levels < 1 || H->o.dtau_mode < 0 || H->o.dtau_mode > 2)
+            throw Error{BCMG_EINVAL, "invalid options"};
+        H->user = (cudaStream_t)stream;
+        check_cuda(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking), "cudaStreamCreate");
+        check_cuda(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        check_cuda(cudaEventCreateWithFlags(&H->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+        if (H->o.profile) {
+            H->pev.resize(4 * (size_t)(H->o.nu1 + H->o.nu2), nullptr);
+            for (auto &e : H->pev) check_cuda(cudaEventCreate(&e), "cudaEventCreate(profile)");
+        }
+        enter(*H);
+        // levels: N_l = N / 2^l while N_l is even, N_l / 2 >= min_coarse and
+        // the coarser level still has interior nodes (Sec. 2.1)
+        int64_t Nl = N;
+        for (int l = 0; l < H->o.max_levels; ++l) {
+            Level L;
+            L.d = dim;
+            L.N = (int)Nl;
+            L.n = (int)Nl + 1;
+            L.h = 2.0 / (double)Nl;
+            L.nn = 1;
+            for (int a = 0; a < dim; ++a) {
+                L.st[a] = L.nn;
+                L.nn *= L.n;
+            }
+            if (l == 0) L.phi = phi_dev;
+            H->L.push_back(L);
+            setup_level(*H, H->L.back(), l);
+            if (H->L.back().nint == 0) {
+                if (l == 0) throw Error{BCMG_EGEOM, "no interior node on the finest grid"};
+                H->L.pop_back();
+                break;
+            }
+            if (Nl % 2 != 0 || Nl / 2 < H->o.min_coarse) break;
+            Nl /= 2;
+        }
+        setup_coarsest(*H, H->L.back());
+        Level &L0 = H->L[0];
+        H->u0 = (double *)dalloc(*H, sizeof(double) * L0.nn);
+        int64_t nparts = (L0.nwin + kWarpsPerBlock - 1) / kWarpsPerBlock + (L0.ng + 255) / 256 + 1;
+        H->npart = (double *)dalloc(*H, sizeof(double) * 4 * nparts);
+        H->nout = (double *)dalloc(*H, sizeof(double) * 4);
+        check_cuda(cudaMallocHost((void **)&H->nhost, 4 * sizeof(double)), "cudaMallocHost");
+        set_interior_rhs(*H, L0, f_dev, L0.F);
+        for (auto &L : H->L) L.phi = nullptr;
+        check_cuda(cudaStreamSynchronize(H->st), "create sync");
+        free_temps(*H);
+        leave(*H);
+    });
+    if (rc != BCMG_OK) {
+        std::string keep = g_last_error;
+        destroy(H);
+        g_last_error = keep;
+        return rc;
+    }
+    *out = reinterpret_cast<bcmg_handle>(H);
+    return BCMG_OK;
+}
+
+int bcmg_destroy(bcmg_handle h) {
+    destroy(reinterpret_cast<Handle *>(h));
+    return BCMG_OK;
+}
+
+int bcmg_ghost_count(bcmg_handle h, int64_t *n) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!n) throw Error{BCMG_EINVAL, "n is null"};
+        *n = H.L[0].ng;
+    });
+}
+
+int bcmg_ghost_points(bcmg_handle h, double *Q_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!Q_dev) throw Error{BCMG_EINVAL, "Q is null"};
+        enter(H);
+        Level &L = H.L[0];
+        if (L.ng > 0)
+            check_cuda(cudaMemcpyAsync(Q_dev, L.gQ, sizeof(double) * L.ng * H.d, cudaMemcpyDeviceToDevice, H.st),
+                       "ghost points copy");
+        leave(H);
+    });
+}
+
+int bcmg_set_boundary_values(bcmg_handle h, const double *g_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!g_dev) throw Error{BCMG_EINVAL, "g is null"};
+        enter(H);
+        scatter_ghost_values(H, H.L[0], g_dev, H.L[0].F);
+        leave(H);
+    });
+}
+
+int bcmg_set_rhs(bcmg_handle h, const double *f_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        enter(H);
+        set_interior_rhs(H, H.L[0], f_dev, H.L[0].F);
+        leave(H);
+    });
+}
+
+int bcmg_vcycle(bcmg_handle h, double *u_dev, int ncycles) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!u_dev || ncycles < 0) throw Error{BCMG_EINVAL, "bad u or ncycles"};
+        enter(H);
+        copy_active(H, u_dev, H.u0, true);
+        for (int c = 0; c < ncycles; ++c) run_vcycle(H);
+        copy_active(H, H.u0, u_dev, false);
+        leave(H);
+    });
+}
+
+int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *cycles_done,
+               double *final_rel_res) {
+    int status = BCMG_OK;
+    int rc = guarded([&] {
+        Handle &H = *checked(h);
+        if (!u_dev || max_cycles < 0 || !(rtol >= 0.0)) throw Error{BCMG_EINVAL, "bad u, rtol or max_cycles"};
+        enter(H);
+        copy_active(H, u_dev, H.u0, true);
+        enqueue_norms(H);
+        double nr[4];
+        fetch_norms(H, nr);
+        const double r0 = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
+        double rel = (r0 > 0.0) ? 1.0 : 0.0;
+        int c = 0;
+        if (!std::isfinite(r0)) status = BCMG_ENONFINITE;
+        while (status == BCMG_OK && r0 > 0.0 && c < max_cycles) {
+            run_vcycle_norms(H);
+            fetch_norms(H, nr);
+            profile_collect(H);
+            ++c;
+            const double rn = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
+            rel = rn / r0;
+            if (!std::isfinite(rn)) status = BCMG_ENONFINITE;
+            else if (rel <= rtol) break;
+        }
+        if (status == BCMG_OK && r0 > 0.0 && rel > rtol) status = BCMG_ENOCONV;
+        copy_active(H, H.u0, u_dev, false);
+        leave(H);
+        if (cycles_done) *cycles_done = c;
+        if (final_rel_res) *final_rel_res = rel;
+    });
+    if (rc != BCMG_OK) return rc;
+    if (status == BCMG_ENOCONV) return fail(status, "max_cycles reached before rtol");
+    if (status == BCMG_ENONFINITE) return fail(status, "non-finite residual");
+    return BCMG_OK;
+}
+
+int bcmg_residual_norm(bcmg_handle h, const double *u_dev, double *out_host) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!u_dev || !out_host) throw Error{BCMG_EINVAL, "null pointer"};
+        enter(H);
+        copy_active(H, u_dev, H.u0, true);
+        enqueue_norms(H);
+        fetch_norms(H, out_host);
+        leave(H);
+    });
+}
+
+const char *bcmg_last_error(void) { return g_last_error.c_str(); }
+
+int64_t bcmg_kernel_launches(void) { return launches_total(); }
+
+int bcmg_profile_read(bcmg_handle h, double *out_host) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!out_host) throw Error{BCMG_EINVAL, "null pointer"};
+        out_host[0] = H.prof_ms;
+        out_host[1] = (double)H.prof_n;
+    });
+}
+
+int bcmg_num_levels(bcmg_handle h, int *levels) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!levels) throw Error{BCMG_EINVAL, "null pointer"};
+        *levels = (int)H.L.size();
+    });
+}
+
+int bcmg_level_info(bcmg_handle h, int level, int64_t *out) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        if (!out) throw Error{BCMG_EINVAL, "null pointer"};
+        int64_t v[10] = {L.N, L.n, L.nn, L.nint, L.ng, L.nb, L.nbox, L.nclamp, L.nfall, L.nact};
+        std::memcpy(out, v, sizeof(v));
+    });
+}
+
+int bcmg_get_class(bcmg_handle h, int level, uint8_t *cls_host) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        if (!cls_host) throw Error{BCMG_EINVAL, "null pointer"};
+        check_cuda(cudaMemcpyAsync(cls_host, L.cls, L.nn, cudaMemcpyDeviceToHost, H.st), "class copy");
+        check_cuda(cudaStreamSynchronize(H.st), "class sync");
+    });
+}
+
+int bcmg_get_ghosts(bcmg_handle h, int level, int64_t *idx, double *eta, double *n3, double *xi3, int32_t *s3,
+                    int32_t *q3, double *dtau, double *Q3) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        const int64_t ng = L.ng;
+        const int d = H.d;
+        std::vector<uint32_t> gi(ng);
+        std::vector<uint16_t> gc(ng);
+        std::vector<double> xi(3 * ng), nn(3 * ng), et(ng), dt(ng), Q(d * ng);
+        if (ng > 0) {
+            check_cuda(cudaMemcpyAsync(gi.data(), L.gidx, 4 * ng, cudaMemcpyDeviceToHost, H.st), "g");
+            check_cuda(cudaMemcpyAsync(gc.data(), L.gcode, 2 * ng, cudaMemcpyDeviceToHost, H.st), "g");
+            check_cuda(cudaMemcpyAsync(xi.data(), L.gxi, 8 * 3 * ng, cudaMemcpyDeviceToHost, H.st), "g");
+            check_cuda(cudaMemcpyAsync(nn.data(), L.gn, 8 * 3 * ng, cudaMemcpyDeviceToHost, H.st), "g");
+            check_cuda(cudaMemcpyAsync(et.data(), L.geta, 8 * ng, cudaMemcpyDeviceToHost, H.st), "g");
+            check_cuda(cudaMemcpyAsync(dt.data(), L.gdt, 8 * ng, cudaMemcpyDeviceToHost, H.st), "g");
+            check_cuda(cudaMemcpyAsync(Q.data(), L.gQ, 8 * d * ng, cudaMemcpyDeviceToHost, H.st), "g");
+        }
+        check_cuda(cudaStreamSynchronize(H.st), "ghost sync");
+        for (int64_t g = 0; g < ng; ++g) {
+            if (idx) idx[g] = gi[g];
+            if (eta) eta[g] = et[g];
+            if (dtau) dtau[g] = dt[g];
+            for (int a = 0; a < 3; ++a) {
+                const bool on = a < d;
+                if (n3) n3[3 * g + a] = on ? nn[a * ng + g] : 0.0;
+                if (xi3) xi3[3 * g + a] = on ? xi[a * ng + g] : 0.0;
+                if (s3) s3[3 * g + a] = on ? (((gc[g] >> a) & 1) ? -1 : 1) : 0;
+                if (q3) q3[3 * g + a] = on ? ((gc[g] >> (3 + 2 * a)) & 3) : 0;
+                if (Q3) Q3[3 * g + a] = on ? Q[g * d + a] : 0.0;
+            }
+        }
+    });
+}
+
+int bcmg_get_band(bcmg_handle h, int level, int64_t *idx_host) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        if (!idx_host) throw Error{BCMG_EINVAL, "null pointer"};
+        std::vector<uint32_t> b(L.nb);
+        if (L.nb > 0)
+            check_cuda(cudaMemcpyAsync(b.data(), L.bidx, 4 * L.nb, cudaMemcpyDeviceToHost, H.st), "band copy");
+        check_cuda(cudaStreamSynchronize(H.st), "band sync");
+        for (int64_t i = 0; i < L.nb; ++i) idx_host[i] = b[i];
+    });
+}
+
+int bcmg_smooth(bcmg_handle h, int level, double *u_dev, const double *F_dev, int nsteps) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        if (!u_dev || !F_dev || nsteps < 0) throw Error{BCMG_EINVAL, "bad argument"};
+        enter(H);
+        smooth(H, L, u_dev, F_dev, nsteps);
+        leave(H);
+    });
+}
+
+int bcmg_residual(bcmg_handle h, int level, const double *u_dev, const double *F_dev, double *r_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        if (!u_dev || !F_dev || !r_dev) throw Error{BCMG_EINVAL, "bad argument"};
+        enter(H);
+        residual(H, L, u_dev, F_dev, r_dev);
+        leave(H);
+    });
+}
+
+int bcmg_extend(bcmg_handle h, int level, double *a_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        if (!a_dev) throw Error{BCMG_EINVAL, "bad argument"};
+        enter(H);
+        extend(H, L, a_dev);
+        leave(H);
+    });
+}
+
+int bcmg_restrict(bcmg_handle h, int level, const double *r_fine_dev, double *F_coarse_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (level < 0 || level + 1 >= (int)H.L.size()) throw Error{BCMG_EINVAL, "level out of range"};
+        if (!r_fine_dev || !F_coarse_dev) throw Error{BCMG_EINVAL, "bad argument"};
+        enter(H);
+        restrict_to(H, H.L[level], H.L[level + 1], r_fine_dev, F_coarse_dev, nullptr);
+        leave(H);
+    });
+}
+
+int bcmg_prolong(bcmg_handle h, int level, const double *e_coarse_dev, double *u_fine_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (level < 0 || level + 1 >= (int)H.L.size()) throw Error{BCMG_EINVAL, "level out of range"};
+        if (!e_coarse_dev || !u_fine_dev) throw Error{BCMG_EINVAL, "bad argument"};
+        enter(H);
+        prolong(H, H.L[level], H.L[level + 1], e_coarse_dev, u_fine_dev);
+        leave(H);
+    });
+}
+
+int bcmg_coarsest_solve(bcmg_handle h, double *u_dev, const double *F_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!u_dev || !F_dev) throw Error{BCMG_EINVAL, "bad argument"};
+        enter(H);
+        coarsest_correct(H, H.L.back(), u_dev, F_dev);
+        leave(H);
+    });
+}
+
+}  // extern "C"
