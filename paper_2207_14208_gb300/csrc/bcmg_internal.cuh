@@ -61,6 +61,12 @@ struct Level {
     int32_t *bref = nullptr;  // 3 * nb, axis-major: >= 0 band position,
                               // < 0 -(ghost node index) - 1, kNoRef none
     double *bw = nullptr;     // 3 * nb, axis-major, normalised weights
+    // the K extension sweeps from zero are a fixed linear map from ghost
+    // values to band values: CSR rows (per band node) of (ghost node, weight)
+    int64_t ne = 0;
+    int64_t *eoff = nullptr;  // nb + 1
+    uint32_t *eg = nullptr;
+    double *ew = nullptr;
     // boxdir list (finest level only)
     uint32_t *boxidx = nullptr;
     // arrays
@@ -113,12 +119,13 @@ void check_cuda(cudaError_t e, const char *what);
 void *dalloc(Handle &H, size_t bytes, bool temp = false);  // zero-filled; temp: freed after set-up
 void count_launch(Handle &H);
 int64_t launches_total();
+void add_launches(int64_t n);
+int report(int code, const std::string &msg);  // sets the thread's last error
 
 // ---- set-up (setup.cu) -------------------------------------------------
-void setup_level(Handle &H, Level &L, int level_index);
-int64_t compact_flags(Handle &H, const uint8_t *flags, int64_t n, uint32_t **out, bool temp = false);
-void setup_coarsest(Handle &H, Level &L);
+void setup_hierarchy(Handle &H, const double *phi0);
 double dtau_of(int d, int mode, double cst, double theta);
+bool ext_csr_ok(int d, int K);
 
 // ---- cycle kernels (cycle.cu) -----------------------------------------
 void smooth(Handle &H, Level &L, double *u, const double *F, int nsteps);

@@ -30,10 +30,12 @@ void check_cuda(cudaError_t e, const char *what) {
 void *dalloc(Handle &H, size_t bytes, bool temp) {
     void *p = nullptr;
     if (bytes == 0) bytes = 8;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    // stream-ordered allocation from the device's default pool (which keeps
+    // freed memory for reuse, so repeated create/destroy stays cheap)
+    cudaError_t e = cudaMallocAsync(&p, bytes, H.st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        throw Error{BCMG_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+        throw Error{BCMG_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
     }
     (temp ? H.temps : H.allocs).push_back(p);
     check_cuda(cudaMemsetAsync(p, 0, bytes, H.st), "cudaMemsetAsync");
@@ -47,6 +49,14 @@ void count_launch(Handle &H) {
 
 int64_t launches_total() { return g_launches.load(); }
 
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int report(int code, const std::string &msg) {
+    if (code == BCMG_OK) g_last_error.clear();
+    else g_last_error = msg;
+    return code;
+}
+
 void profile_mark(Handle &H, const Level &L) {
     if (!H.o.profile || H.L.empty() || &L != &H.L[0]) return;
     if (H.pev_next >= (int)H.pev.size()) return;
@@ -58,8 +68,17 @@ void profile_mark(Handle &H, const Level &L) {
 namespace {
 
 void free_temps(Handle &H) {
-    for (void *p : H.temps) cudaFree(p);
+    for (void *p : H.temps) cudaFreeAsync(p, H.st);
     H.temps.clear();
+}
+
+void keep_pool_memory() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
 }
 
 void destroy(Handle *H) {
@@ -67,8 +86,11 @@ void destroy(Handle *H) {
     if (H->st) cudaStreamSynchronize(H->st);
     if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
     if (H->ngraph) cudaGraphExecDestroy(H->ngraph);
-    free_temps(*H);
-    for (void *p : H->allocs) cudaFree(p);
+    if (H->st) {
+        free_temps(*H);
+        for (void *p : H->allocs) cudaFreeAsync(p, H->st);
+        cudaStreamSynchronize(H->st);
+    }
     if (H->nhost) cudaFreeHost(H->nhost);
     for (cudaEvent_t e : H->pev) cudaEventDestroy(e);
     if (H->ev_in) cudaEventDestroy(H->ev_in);
@@ -234,6 +256,7 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
             H->o.max_levels < 1 || H->o.dtau_mode < 0 || H->o.dtau_mode > 2)
             throw Error{BCMG_EINVAL, "invalid options"};
         H->user = (cudaStream_t)stream;
+        keep_pool_memory();
         check_cuda(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking), "cudaStreamCreate");
         check_cuda(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming), "cudaEventCreate");
         check_cuda(cudaEventCreateWithFlags(&H->ev_out, cudaEventDisableTiming), "cudaEventCreate");
@@ -244,30 +267,7 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         enter(*H);
         // levels: N_l = N / 2^l while N_l is even, N_l / 2 >= min_coarse and
         // the coarser level still has interior nodes (Sec. 2.1)
-        int64_t Nl = N;
-        for (int l = 0; l < H->o.max_levels; ++l) {
-            Level L;
-            L.d = dim;
-            L.N = (int)Nl;
-            L.n = (int)Nl + 1;
-            L.h = 2.0 / (double)Nl;
-            L.nn = 1;
-            for (int a = 0; a < dim; ++a) {
-                L.st[a] = L.nn;
-                L.nn *= L.n;
-            }
-            if (l == 0) L.phi = phi_dev;
-            H->L.push_back(L);
-            setup_level(*H, H->L.back(), l);
-            if (H->L.back().nint == 0) {
-                if (l == 0) throw Error{BCMG_EGEOM, "no interior node on the finest grid"};
-                H->L.pop_back();
-                break;
-            }
-            if (Nl % 2 != 0 || Nl / 2 < H->o.min_coarse) break;
-            Nl /= 2;
-        }
-        setup_coarsest(*H, H->L.back());
+        setup_hierarchy(*H, phi_dev);
         Level &L0 = H->L[0];
         H->u0 = (double *)dalloc(*H, sizeof(double) * L0.nn);
         int64_t nparts = (L0.nwin + kWarpsPerBlock - 1) / kWarpsPerBlock + (L0.ng + 255) / 256 + 1;

@@ -62,32 +62,34 @@ __device__ __forceinline__ void lagrange(int q, double xi, double w[3]) {
     }
 }
 
-// B u~ at a ghost: the (tri/bi)quadratic interpolant on ST_G at Q (eq. BCh)
+// B u~ at a ghost: the (tri/bi)quadratic interpolant on ST_G at Q (eq. BCh).
+// Fully unrolled with compile-time stencil offsets (weights stay in
+// registers); nodes beyond an axis' degree are never loaded.
 template <int D>
 __device__ __forceinline__ double ghost_B(int64_t X, uint16_t code, const double *__restrict__ gxi, int64_t ng,
                                           int64_t g, const double *u, const G2 &G) {
-    double w[3][3];
-    int64_t off[3];
-    int q[3] = {0, 0, 0};
-    const int64_t st[3] = {1, G.sy, G.sz};
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        q[a] = (code >> (3 + 2 * a)) & 3;
-        off[a] = ((code >> a) & 1) ? st[a] : -st[a];  // offset per stencil step
-        lagrange(q[a], gxi[(int64_t)a * ng + g], w[a]);
-    }
+    const int qx = (code >> 3) & 3, qy = (code >> 5) & 3, qz = (D == 3) ? ((code >> 7) & 3) : 0;
+    const int64_t ox = (code & 1) ? 1 : -1;
+    const int64_t oy = (code & 2) ? G.sy : -G.sy;
+    const int64_t oz = (D == 3) ? ((code & 4) ? G.sz : -G.sz) : 0;
+    double wx[3], wy[3], wz[3] = {1.0, 0.0, 0.0};
+    lagrange(qx, gxi[g], wx);
+    lagrange(qy, gxi[ng + g], wy);
+    if (D == 3) lagrange(qz, gxi[2 * ng + g], wz);
     double B = 0.0;
-    if (D == 3) {
-        for (int o2 = 0; o2 <= q[2]; ++o2)
-            for (int o1 = 0; o1 <= q[1]; ++o1) {
-                double w12 = w[2][o2] * w[1][o1];
-                int64_t Y = X + o2 * off[2] + o1 * off[1];
-                for (int o0 = 0; o0 <= q[0]; ++o0) B = fma(w12 * w[0][o0], u[Y + o0 * off[0]], B);
+#pragma unroll
+    for (int o2 = 0; o2 < (D == 3 ? 3 : 1); ++o2) {
+        if (o2 > qz) break;
+#pragma unroll
+        for (int o1 = 0; o1 < 3; ++o1) {
+            if (o1 > qy) break;
+            const double wyz = wz[o2] * wy[o1];
+            const int64_t Y = X + o2 * oz + o1 * oy;
+#pragma unroll
+            for (int o0 = 0; o0 < 3; ++o0) {
+                if (o0 > qx) break;
+                B = fma(wyz * wx[o0], u[Y + o0 * ox], B);
             }
-    } else {
-        for (int o1 = 0; o1 <= q[1]; ++o1) {
-            int64_t Y = X + o1 * off[1];
-            for (int o0 = 0; o0 <= q[0]; ++o0) B = fma(w[1][o1] * w[0][o0], u[Y + o0 * off[0]], B);
         }
     }
     return B;
@@ -191,6 +193,18 @@ __global__ void k_extend(const uint32_t *__restrict__ bidx, const int32_t *__res
     else out[b] = v;
 }
 
+// All K sweeps at once: band value = sum over the precomputed (ghost, weight)
+// row of the band node (the expansion of the sweeps started from zero).
+__global__ void k_extend_csr(const uint32_t *__restrict__ bidx, const int64_t *__restrict__ eoff,
+                             const uint32_t *__restrict__ eg, const double *__restrict__ ew, int64_t nb,
+                             double *a) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    double v = 0.0;
+    for (int64_t j = eoff[b]; j < eoff[b + 1]; ++j) v = fma(ew[j], a[eg[j]], v);
+    a[bidx[b]] = v;
+}
+
 // ------------------------------------------------------------ restriction
 // Coarse interior: FW of the fine interior residual if all 3^d fine
 // neighbours are interior, else their FW-weight average over the interior
@@ -198,11 +212,17 @@ __global__ void k_extend(const uint32_t *__restrict__ bidx, const int32_t *__res
 template <int D>
 __device__ __forceinline__ double restrict_at(const int ic[3], bool interior, const uint8_t *__restrict__ clsf,
                                               const double *__restrict__ rf, const G2 &Gf) {
-    double fw = 0.0, wsum = 0.0;
+    // FW weights as integers (1, 2, 4[, 8]) / 4^d: scaling by a power of two
+    // is exact, so sum(w_int r) / sum(w_int) equals the weighted mean, and the
+    // FW case is sum(w_int r) * 4^-d.
+    double fw = 0.0;
+    int wsum = 0;
     bool all = true;
-    const int oz0 = (D == 3) ? -1 : 0, oz1 = (D == 3) ? 1 : 0;
-    for (int oz = oz0; oz <= oz1; ++oz)
+#pragma unroll
+    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
+#pragma unroll
         for (int oy = -1; oy <= 1; ++oy)
+#pragma unroll
             for (int ox = -1; ox <= 1; ++ox) {
                 const int y0 = 2 * ic[0] + ox, y1 = 2 * ic[1] + oy, y2 = 2 * ic[2] + oz;
                 if (y0 < 0 || y0 > Gf.N || y1 < 0 || y1 > Gf.N || (D == 3 && (y2 < 0 || y2 > Gf.N))) {
@@ -216,12 +236,12 @@ __device__ __forceinline__ double restrict_at(const int ic[3], bool interior, co
                     all = false;
                     continue;
                 }
-                const double wfw = (ox == 0 ? 0.5 : 0.25) * (oy == 0 ? 0.5 : 0.25) * (D == 3 ? (oz == 0 ? 0.5 : 0.25) : 1.0);
-                fw = fma(wfw, rf[Y], fw);
-                wsum += wfw;
+                const int wi = (ox == 0 ? 2 : 1) * (oy == 0 ? 2 : 1) * ((D == 3 && oz == 0) ? 2 : 1);
+                fw = fma((double)wi, rf[Y], fw);
+                wsum += wi;
             }
-    if (all) return fw;
-    return wsum > 0.0 ? fw / wsum : 0.0;
+    if (all) return fw * (D == 3 ? (1.0 / 64.0) : (1.0 / 16.0));
+    return wsum > 0 ? fw / (double)wsum : 0.0;
 }
 
 template <int D>
@@ -483,6 +503,10 @@ void residual(Handle &H, Level &L, const double *u, const double *F, double *r) 
 
 void extend(Handle &H, Level &L, double *a) {
     if (L.nb == 0) return;
+    if (L.eoff) {
+        LAUNCH(k_extend_csr, nblk(L.nb, 256), 256, L.bidx, L.eoff, L.eg, L.ew, L.nb, a);
+        return;
+    }
     const int K = std::max(H.o.ext_sweeps, 1);
     double *b0 = L.bbuf, *b1 = L.bbuf + L.nb;
     const double *in = nullptr;

@@ -182,11 +182,21 @@ __device__ double grad_a(const Geo &G, const double *phi, int64_t lin, const int
     return __dmul_rn(0.5, __dsub_rn(phi[lin + s], phi[lin - s]));
 }
 
-// multilinear interpolation of grid phi at an index-space point
-__device__ double interp_phi(const Geo &G, const double *phi, const double p[3]) {
+// multilinear interpolation of grid phi at an index-space point.  The corner
+// values of the last cell are kept in registers (every point of one ghost's
+// bisection lies in the same cell or two), so the serial bisection chain
+// does not wait on global loads.
+struct CellCache {
+    int64_t c[3] = {-1, -1, -1};
+    double v[8];
+};
+
+__device__ double interp_phi(const Geo &G, const double *phi, const double p[3], CellCache &cc) {
     int64_t c[3] = {0, 0, 0};
     double t[3] = {0.0, 0.0, 0.0};
-    for (int a = 0; a < G.d; ++a) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= G.d) break;
         double f = floor(p[a]);
         int64_t ci = (int64_t)f;
         if (ci < 0) ci = 0;
@@ -194,16 +204,32 @@ __device__ double interp_phi(const Geo &G, const double *phi, const double p[3])
         c[a] = ci;
         t[a] = __dsub_rn(p[a], (double)ci);
     }
+    if (c[0] != cc.c[0] || c[1] != cc.c[1] || c[2] != cc.c[2]) {
+#pragma unroll
+        for (int corner = 0; corner < 8; ++corner) {
+            if (corner >= (1 << G.d)) break;
+            int64_t idx = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (a < G.d) idx += (c[a] + ((corner >> a) & 1)) * G.st[a];
+            cc.v[corner] = phi[idx];
+        }
+        cc.c[0] = c[0];
+        cc.c[1] = c[1];
+        cc.c[2] = c[2];
+    }
     double val = 0.0;
-    for (int corner = 0; corner < (1 << G.d); ++corner) {
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        if (corner >= (1 << G.d)) break;
         double w = 1.0;
-        int64_t idx = 0;
-        for (int a = 0; a < G.d; ++a) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a >= G.d) break;
             int b = (corner >> a) & 1;
             w = __dmul_rn(w, b ? t[a] : __dsub_rn(1.0, t[a]));
-            idx += (c[a] + b) * G.st[a];
         }
-        val = __dadd_rn(val, __dmul_rn(w, phi[idx]));
+        val = __dadd_rn(val, __dmul_rn(w, cc.v[corner]));
     }
     return val;
 }
@@ -291,12 +317,13 @@ __global__ void k_ghost_setup(const uint32_t *__restrict__ gidx, int64_t ng, con
     // eta in [0, 1] with phi(G - eta h n) = 0 by bisection on the
     // multilinear interpolant (64 halvings)
     double eta;
+    CellCache cc;
     if (phi[lin] == 0.0) {
         eta = 0.0;
     } else {
         double p1[3];
         for (int a = 0; a < 3; ++a) p1[a] = (a < d) ? __dsub_rn((double)ix[a], n[a]) : (double)ix[a];
-        if (interp_phi(G, phi, p1) >= 0.0) {
+        if (interp_phi(G, phi, p1, cc) >= 0.0) {
             eta = 1.0;
             atomicAdd(out.nclamp, 1ull);
         } else {
@@ -306,7 +333,7 @@ __global__ void k_ghost_setup(const uint32_t *__restrict__ gidx, int64_t ng, con
                 double pm[3];
                 for (int a = 0; a < 3; ++a)
                     pm[a] = (a < d) ? __dsub_rn((double)ix[a], __dmul_rn(mid, n[a])) : (double)ix[a];
-                if (interp_phi(G, phi, pm) >= 0.0) lo = mid;
+                if (interp_phi(G, phi, pm, cc) >= 0.0) lo = mid;
                 else hi = mid;
             }
             eta = __dmul_rn(0.5, __dadd_rn(lo, hi));
@@ -426,6 +453,95 @@ __global__ void k_band_setup(const uint32_t *__restrict__ bidx, int64_t nb, cons
     for (int a = 0; a < 3; ++a) {
         bref[(int64_t)a * nb + b] = ref[a];
         bw[(int64_t)a * nb + b] = (den > 0.0 && ref[a] != kNoRef) ? w[a] / den : 0.0;
+    }
+}
+
+// The K Jacobi sweeps of the extension, started from zero, expand into a sum
+// over upwind paths of length <= K that end at a ghost: value(b) =
+// sum_paths (product of the normalised weights) * a[ghost].  Enumerate the
+// paths (depth-first, fixed order), merge equal ghosts in a stable order.
+constexpr int kExtMaxItems = 128;
+
+__device__ int ext_paths(int64_t b, const int32_t *__restrict__ bref, const double *__restrict__ bw, int64_t nb,
+                         int d, int K, uint32_t *g, double *w) {
+    int64_t st_node[16];
+    int st_depth[16];
+    double st_w[16];
+    int sp = 0, cnt = 0;
+    st_node[0] = b;
+    st_depth[0] = 1;
+    st_w[0] = 1.0;
+    sp = 1;
+    while (sp > 0) {
+        --sp;
+        const int64_t x = st_node[sp];
+        const int j = st_depth[sp];
+        const double W = st_w[sp];
+        // push band sources in reverse axis order so that axis 0 is visited first
+        for (int ax = d - 1; ax >= 0; --ax) {
+            const int32_t ref = bref[(int64_t)ax * nb + x];
+            if (ref == kNoRef || ref < 0 || j >= K) continue;
+            if (sp < 16) {
+                st_node[sp] = ref;
+                st_depth[sp] = j + 1;
+                st_w[sp] = W * bw[(int64_t)ax * nb + x];
+                ++sp;
+            }
+        }
+        for (int ax = 0; ax < d; ++ax) {
+            const int32_t ref = bref[(int64_t)ax * nb + x];
+            if (ref == kNoRef || ref >= 0) continue;
+            if (cnt < kExtMaxItems) {
+                g[cnt] = (uint32_t)(-(int64_t)ref - 1);
+                w[cnt] = W * bw[(int64_t)ax * nb + x];
+                ++cnt;
+            }
+        }
+    }
+    // stable insertion sort by ghost node, then merge equal nodes
+    for (int i = 1; i < cnt; ++i)
+        for (int k = i; k > 0 && g[k] < g[k - 1]; --k) {
+            uint32_t tg = g[k];
+            g[k] = g[k - 1];
+            g[k - 1] = tg;
+            double tw = w[k];
+            w[k] = w[k - 1];
+            w[k - 1] = tw;
+        }
+    int m = 0;
+    for (int i = 0; i < cnt; ++i) {
+        if (m > 0 && g[m - 1] == g[i]) {
+            w[m - 1] += w[i];
+        } else {
+            g[m] = g[i];
+            w[m] = w[i];
+            ++m;
+        }
+    }
+    return m;
+}
+
+__global__ void k_ext_count(const int32_t *__restrict__ bref, const double *__restrict__ bw, int64_t nb, int d,
+                            int K, int64_t *__restrict__ counts) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    uint32_t g[kExtMaxItems];
+    double w[kExtMaxItems];
+    counts[b] = ext_paths(b, bref, bw, nb, d, K, g, w);
+}
+
+__global__ void k_ext_fill(const int32_t *__restrict__ bref, const double *__restrict__ bw, int64_t nb, int d,
+                           int K, const int64_t *__restrict__ off, uint32_t *__restrict__ eg,
+                           double *__restrict__ ew) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    uint32_t g[kExtMaxItems];
+    double w[kExtMaxItems];
+    const int m = ext_paths(b, bref, bw, nb, d, K, g, w);
+    const int64_t o = off[b];
+    for (int i = 0; i < m; ++i) {
+        eg[o + i] = g[i];
+        ew[o + i] = w[i];
     }
 }
 
@@ -560,133 +676,296 @@ inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 double dtau_of(int d, int mode, double cst, double theta) { return dtau_formula(d, mode, cst, theta); }
 
-int64_t compact_flags(Handle &H, const uint8_t *flags, int64_t n, uint32_t **out, bool temp) {
-    int64_t nblk = (n + kCompactTile - 1) / kCompactTile;
-    if (nblk == 0) nblk = 1;
-    int64_t *counts = (int64_t *)dalloc(H, sizeof(int64_t) * nblk, true);
-    k_count<<<(unsigned)nblk, kCompactThreads, 0, H.st>>>(flags, n, counts);
-    count_launch(H);
-    check_cuda(cudaGetLastError(), "k_count");
-    std::vector<int64_t> hc(nblk);
-    check_cuda(cudaMemcpyAsync(hc.data(), counts, sizeof(int64_t) * nblk, cudaMemcpyDeviceToHost, H.st),
-               "compact counts");
-    check_cuda(cudaStreamSynchronize(H.st), "compact sync");
-    int64_t total = 0;
-    for (int64_t i = 0; i < nblk; ++i) {
-        int64_t c = hc[i];
-        hc[i] = total;
-        total += c;
-    }
-    check_cuda(cudaMemcpyAsync(counts, hc.data(), sizeof(int64_t) * nblk, cudaMemcpyHostToDevice, H.st),
-               "compact offsets");
-    *out = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(total, 1), temp);
-    k_scatter<<<(unsigned)nblk, kCompactThreads, 0, H.st>>>(flags, n, counts, *out);
-    count_launch(H);
-    check_cuda(cudaGetLastError(), "k_scatter");
-    check_cuda(cudaStreamSynchronize(H.st), "compact sync 2");
-    return total;
+// the path expansion fits the per-thread buffers: at most d (d^K - 1)/(d - 1)
+// ghost terms and a depth-first stack of (d - 1)(K - 1) + d entries
+bool ext_csr_ok(int d, int K) {
+    double pk = std::pow((double)d, (double)K);
+    return K >= 1 && d * (pk - 1.0) / (d - 1.0) <= kExtMaxItems && (d - 1) * (K - 1) + d <= 16;
 }
 
-void setup_level(Handle &H, Level &L, int li) {
-    Geo G = geo_of(L);
+// ------------------------------------------------------------ batched compaction
+// Many flag arrays are compacted with one device->host round trip: block
+// counts of every array land in one buffer, the host scans them, offsets go
+// back in one copy, then every array is scattered.
+namespace {
+
+struct CompactItem {
+    const uint8_t *flags;
+    int64_t n, nblk, base;
+    uint32_t **out;  // nullptr: count only
+    bool temp;
+    int64_t total;
+};
+
+thread_local int64_t *t_pinned = nullptr;
+thread_local size_t t_pinned_n = 0;
+
+int64_t *pinned_scratch(size_t n) {
+    if (n > t_pinned_n) {
+        if (t_pinned) cudaFreeHost(t_pinned);
+        t_pinned = nullptr;
+        t_pinned_n = 0;
+        size_t want = std::max<size_t>(n, 1 << 16);
+        check_cuda(cudaMallocHost((void **)&t_pinned, want * sizeof(int64_t)), "cudaMallocHost(scratch)");
+        t_pinned_n = want;
+    }
+    return t_pinned;
+}
+
+void run_compaction(Handle &H, std::vector<CompactItem> &items) {
+    int64_t B = 0;
+    for (auto &it : items) {
+        it.nblk = std::max<int64_t>((it.n + kCompactTile - 1) / kCompactTile, 1);
+        it.base = B;
+        B += it.nblk;
+    }
+    if (B == 0) return;
+    int64_t *counts = (int64_t *)dalloc(H, sizeof(int64_t) * B, true);
+    for (auto &it : items) {
+        k_count<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, counts + it.base);
+        count_launch(H);
+    }
+    check_cuda(cudaGetLastError(), "k_count");
+    int64_t *hc = pinned_scratch((size_t)B);
+    check_cuda(cudaMemcpyAsync(hc, counts, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, H.st), "counts D2H");
+    check_cuda(cudaStreamSynchronize(H.st), "compaction sync");
+    for (auto &it : items) {
+        int64_t tot = 0;
+        for (int64_t b = 0; b < it.nblk; ++b) {
+            int64_t c = hc[it.base + b];
+            hc[it.base + b] = tot;
+            tot += c;
+        }
+        it.total = tot;
+    }
+    check_cuda(cudaMemcpyAsync(counts, hc, sizeof(int64_t) * B, cudaMemcpyHostToDevice, H.st), "offsets H2D");
+    for (auto &it : items) {
+        if (!it.out) continue;
+        *it.out = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(it.total, 1), it.temp);
+        k_scatter<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, counts + it.base, *it.out);
+        count_launch(H);
+    }
+    check_cuda(cudaGetLastError(), "k_scatter");
+    // the pinned offsets are read by the H2D copy: keep them until it is done
+    check_cuda(cudaStreamSynchronize(H.st), "compaction sync 2");
+}
+
+struct LevelScratch {
+    uint8_t *wflags = nullptr, *fint = nullptr, *fbox = nullptr, *fghost = nullptr, *fact = nullptr, *fband = nullptr;
+    uint64_t *masks = nullptr;
+    uint32_t *wids = nullptr;
+    int64_t nwall = 0;
+    int wpr = 0;
+    int64_t nint = 0;
+    unsigned long long *cnt = nullptr;  // clamp / fall-back counters
+    int64_t *ecnt = nullptr;
+};
+
+}  // namespace
+
+// Build every level of the hierarchy (Sec. 2.1 re-discretisation, Sec. 3.3
+// geometry).  Four host synchronisations in total.
+void setup_hierarchy(Handle &H, const double *phi0) {
     const int T = 256;
-    // phi of this level by injection from the finer level
-    if (li > 0) {
-        Level &Lf = H.L[li - 1];
-        double *phic = (double *)dalloc(H, sizeof(double) * L.nn, true);
-        k_inject<<<nblocks(L.nn, T), T, 0, H.st>>>(Lf.phi, geo_of(Lf), G, phic);
-        count_launch(H);
-        check_cuda(cudaGetLastError(), "k_inject");
-        L.phi = phic;
+    // candidate levels: N_l = N / 2^l while N_l is even and N_l / 2 >= min_coarse
+    {
+        int64_t Nl = H.N;
+        for (int l = 0; l < H.o.max_levels; ++l) {
+            Level L;
+            L.d = H.d;
+            L.N = (int)Nl;
+            L.n = (int)Nl + 1;
+            L.h = 2.0 / (double)Nl;
+            L.nn = 1;
+            for (int a = 0; a < H.d; ++a) {
+                L.st[a] = L.nn;
+                L.nn *= L.n;
+            }
+            H.L.push_back(L);
+            if (Nl % 2 != 0 || Nl / 2 < H.o.min_coarse) break;
+            Nl /= 2;
+        }
     }
-    L.cls = (uint8_t *)dalloc(H, L.nn);
-    k_classify<<<nblocks(L.nn, T), T, 0, H.st>>>(L.phi, G, L.nn, L.cls);
-    count_launch(H);
-    check_cuda(cudaGetLastError(), "k_classify");
-
-    uint8_t *flags = (uint8_t *)dalloc(H, (size_t)L.nn + 1, true);
-    // interior windows
-    int wpr = (L.n + kWin - 1) / kWin;
-    int64_t rows = L.nn / L.n;
-    int64_t nwall = rows * wpr;
-    uint64_t *masks = (uint64_t *)dalloc(H, sizeof(uint64_t) * nwall, true);
-    k_win_mask<<<nblocks(nwall, T), T, 0, H.st>>>(L.cls, G, nwall, wpr, masks, flags);
-    count_launch(H);
-    check_cuda(cudaGetLastError(), "k_win_mask");
-    uint32_t *ids = nullptr;
-    L.nwin = compact_flags(H, flags, nwall, &ids, true);
-    L.win = (Win *)dalloc(H, sizeof(Win) * (size_t)std::max<int64_t>(L.nwin, 1));
-    if (L.nwin > 0) {
-        k_make_win<<<nblocks(L.nwin, T), T, 0, H.st>>>(ids, L.nwin, masks, G, wpr, L.win);
+    const int nc = (int)H.L.size();
+    std::vector<LevelScratch> S(nc);
+    // phase A: phi by injection, classes, window masks and class flags
+    for (int l = 0; l < nc; ++l) {
+        Level &L = H.L[l];
+        LevelScratch &s = S[l];
+        Geo G = geo_of(L);
+        if (l == 0) {
+            L.phi = phi0;
+        } else {
+            double *phic = (double *)dalloc(H, sizeof(double) * L.nn, true);
+            k_inject<<<nblocks(L.nn, T), T, 0, H.st>>>(H.L[l - 1].phi, geo_of(H.L[l - 1]), G, phic);
+            count_launch(H);
+            L.phi = phic;
+        }
+        L.cls = (uint8_t *)dalloc(H, L.nn);
+        k_classify<<<nblocks(L.nn, T), T, 0, H.st>>>(L.phi, G, L.nn, L.cls);
         count_launch(H);
-        check_cuda(cudaGetLastError(), "k_make_win");
+        s.wpr = (L.n + kWin - 1) / kWin;
+        s.nwall = (L.nn / L.n) * s.wpr;
+        s.masks = (uint64_t *)dalloc(H, sizeof(uint64_t) * s.nwall, true);
+        s.wflags = (uint8_t *)dalloc(H, (size_t)s.nwall, true);
+        k_win_mask<<<nblocks(s.nwall, T), T, 0, H.st>>>(L.cls, G, s.nwall, s.wpr, s.masks, s.wflags);
+        count_launch(H);
+        s.fint = (uint8_t *)dalloc(H, (size_t)L.nn, true);
+        s.fbox = (uint8_t *)dalloc(H, (size_t)L.nn, true);
+        s.fghost = (uint8_t *)dalloc(H, (size_t)L.nn, true);
+        s.fact = (uint8_t *)dalloc(H, (size_t)L.nn, true);
+        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_INTERIOR, CL_INTERIOR, s.fint);
+        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_BOXDIR, CL_BOXDIR, s.fbox);
+        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_GHOST, CL_GHOST, s.fghost);
+        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_INTERIOR, CL_GHOST, s.fact);
+        for (int i = 0; i < 4; ++i) count_launch(H);
+        check_cuda(cudaGetLastError(), "classification");
     }
-    // counts of interior / boxdir nodes
-    k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_INTERIOR, CL_INTERIOR, flags);
-    count_launch(H);
-    uint32_t *tmpidx = nullptr;
-    L.nint = compact_flags(H, flags, L.nn, &tmpidx, true);
-    k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_BOXDIR, CL_BOXDIR, flags);
-    count_launch(H);
-    L.nbox = compact_flags(H, flags, L.nn, &L.boxidx);
-    if (L.nint == 0) return;
-
-    // ghost list and per-ghost geometry
-    k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_GHOST, CL_GHOST, flags);
-    count_launch(H);
-    L.ng = compact_flags(H, flags, L.nn, &L.gidx);
-    int64_t ng1 = std::max<int64_t>(L.ng, 1);
-    L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1);
-    L.gxi = (double *)dalloc(H, sizeof(double) * 3 * ng1);
-    L.gn = (double *)dalloc(H, sizeof(double) * 3 * ng1);
-    L.gdt = (double *)dalloc(H, sizeof(double) * ng1);
-    L.geta = (double *)dalloc(H, sizeof(double) * ng1);
-    L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
-    L.gtmp = (double *)dalloc(H, sizeof(double) * ng1);
-    unsigned long long *cnt = (unsigned long long *)dalloc(H, 2 * sizeof(unsigned long long), true);
-    if (L.ng > 0) {
-        GhostOut go{L.gcode, L.gxi, L.gdt, L.geta, L.gn, L.gQ, cnt, cnt + 1};
-        k_ghost_setup<<<nblocks(L.ng, 128), 128, 0, H.st>>>(L.gidx, L.ng, L.phi, L.cls, G, H.o.dtau_mode,
-                                                            H.o.dtau_const, go);
-        count_launch(H);
-        check_cuda(cudaGetLastError(), "k_ghost_setup");
+    // round 1: counts of every list on every candidate level (one sync)
+    {
+        std::vector<CompactItem> items;
+        for (int l = 0; l < nc; ++l) {
+            Level &L = H.L[l];
+            LevelScratch &s = S[l];
+            items.push_back({s.wflags, s.nwall, 0, 0, &s.wids, true, 0});
+            items.push_back({s.fint, L.nn, 0, 0, nullptr, true, 0});
+            items.push_back({s.fbox, L.nn, 0, 0, l == 0 ? &L.boxidx : nullptr, false, 0});
+            items.push_back({s.fghost, L.nn, 0, 0, &L.gidx, false, 0});
+        }
+        run_compaction(H, items);
+        for (int l = 0; l < nc; ++l) {
+            Level &L = H.L[l];
+            L.nwin = items[4 * l + 0].total;
+            L.nint = items[4 * l + 1].total;
+            L.nbox = items[4 * l + 2].total;
+            L.ng = items[4 * l + 3].total;
+        }
     }
-    unsigned long long hcnt[2] = {0, 0};
-    check_cuda(cudaMemcpyAsync(hcnt, cnt, sizeof(hcnt), cudaMemcpyDeviceToHost, H.st), "ghost counts");
-    // band: inactive nodes within Chebyshev distance 2 of a ghost
-    check_cuda(cudaMemsetAsync(flags, 0, (size_t)L.nn, H.st), "band memset");
-    if (L.ng > 0) {
-        k_band_mark<<<nblocks(L.ng, T), T, 0, H.st>>>(L.gidx, L.ng, L.cls, G, flags);
-        count_launch(H);
-        check_cuda(cudaGetLastError(), "k_band_mark");
+    if (H.L[0].nint == 0) throw Error{BCMG_EGEOM, "no interior node on the finest grid"};
+    int keep = nc;
+    for (int l = 1; l < nc; ++l)
+        if (H.L[l].nint == 0) {
+            keep = l;
+            break;
+        }
+    H.L.resize(keep);
+    S.resize(keep);
+    // phase B: windows, ghost geometry, band marks
+    for (int l = 0; l < keep; ++l) {
+        Level &L = H.L[l];
+        LevelScratch &s = S[l];
+        Geo G = geo_of(L);
+        L.win = (Win *)dalloc(H, sizeof(Win) * (size_t)std::max<int64_t>(L.nwin, 1));
+        if (L.nwin > 0) {
+            k_make_win<<<nblocks(L.nwin, T), T, 0, H.st>>>(s.wids, L.nwin, s.masks, G, s.wpr, L.win);
+            count_launch(H);
+        }
+        int64_t ng1 = std::max<int64_t>(L.ng, 1);
+        L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1);
+        L.gxi = (double *)dalloc(H, sizeof(double) * 3 * ng1);
+        L.gn = (double *)dalloc(H, sizeof(double) * 3 * ng1);
+        L.gdt = (double *)dalloc(H, sizeof(double) * ng1);
+        L.geta = (double *)dalloc(H, sizeof(double) * ng1);
+        L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
+        L.gtmp = (double *)dalloc(H, sizeof(double) * ng1);
+        s.cnt = (unsigned long long *)dalloc(H, 2 * sizeof(unsigned long long), true);
+        s.fband = s.fint;  // reuse: cleared below
+        check_cuda(cudaMemsetAsync(s.fband, 0, (size_t)L.nn, H.st), "band memset");
+        if (L.ng > 0) {
+            GhostOut go{L.gcode, L.gxi, L.gdt, L.geta, L.gn, L.gQ, s.cnt, s.cnt + 1};
+            k_ghost_setup<<<nblocks(L.ng, 128), 128, 0, H.st>>>(L.gidx, L.ng, L.phi, L.cls, G, H.o.dtau_mode,
+                                                                H.o.dtau_const, go);
+            k_band_mark<<<nblocks(L.ng, T), T, 0, H.st>>>(L.gidx, L.ng, L.cls, G, s.fband);
+            count_launch(H);
+            count_launch(H);
+        }
+        check_cuda(cudaGetLastError(), "ghost set-up");
     }
-    L.nb = compact_flags(H, flags, L.nn, &L.bidx);
-    L.nclamp = (int64_t)hcnt[0];
-    L.nfall = (int64_t)hcnt[1];
-    int64_t nb1 = std::max<int64_t>(L.nb, 1);
-    L.bref = (int32_t *)dalloc(H, sizeof(int32_t) * 3 * nb1);
-    L.bw = (double *)dalloc(H, sizeof(double) * 3 * nb1);
-    L.bbuf = (double *)dalloc(H, sizeof(double) * 2 * nb1);
-    if (L.nb > 0) {
-        k_band_setup<<<nblocks(L.nb, T), T, 0, H.st>>>(L.bidx, L.nb, L.phi, L.cls, G, L.bref, L.bw);
-        count_launch(H);
-        check_cuda(cudaGetLastError(), "k_band_setup");
+    // round 2: band lists on every level and the coarsest active list (one sync)
+    {
+        std::vector<CompactItem> items;
+        for (int l = 0; l < keep; ++l) items.push_back({S[l].fband, H.L[l].nn, 0, 0, &H.L[l].bidx, false, 0});
+        Level &Lc = H.L[keep - 1];
+        items.push_back({S[keep - 1].fact, Lc.nn, 0, 0, &Lc.act, false, 0});
+        run_compaction(H, items);
+        for (int l = 0; l < keep; ++l) H.L[l].nb = items[l].total;
+        Lc.nact = items[keep].total;
+    }
+    if (H.L[keep - 1].nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
+    // phase C: band sources and the expansion counts of the extension
+    const bool csr = ext_csr_ok(H.d, H.o.ext_sweeps);
+    int64_t ebase_total = 0;
+    std::vector<int64_t> ebase(keep, 0);
+    for (int l = 0; l < keep; ++l) {
+        ebase[l] = ebase_total;
+        ebase_total += H.L[l].nb;
+    }
+    int64_t *ecnt = csr ? (int64_t *)dalloc(H, sizeof(int64_t) * (size_t)std::max<int64_t>(ebase_total, 1), true)
+                        : nullptr;
+    for (int l = 0; l < keep; ++l) {
+        Level &L = H.L[l];
+        Geo G = geo_of(L);
+        int64_t nb1 = std::max<int64_t>(L.nb, 1);
+        L.bref = (int32_t *)dalloc(H, sizeof(int32_t) * 3 * nb1);
+        L.bw = (double *)dalloc(H, sizeof(double) * 3 * nb1);
+        L.bbuf = (double *)dalloc(H, sizeof(double) * 2 * nb1);
+        if (L.nb > 0) {
+            k_band_setup<<<nblocks(L.nb, T), T, 0, H.st>>>(L.bidx, L.nb, L.phi, L.cls, G, L.bref, L.bw);
+            count_launch(H);
+            if (csr) {
+                k_ext_count<<<nblocks(L.nb, 128), 128, 0, H.st>>>(L.bref, L.bw, L.nb, L.d, H.o.ext_sweeps,
+                                                                 ecnt + ebase[l]);
+                count_launch(H);
+            }
+        }
+        check_cuda(cudaGetLastError(), "band set-up");
+    }
+    // round 3: extension row lengths, clamp / fall-back counters (one sync)
+    {
+        size_t ncnt = (size_t)ebase_total + 2 * keep;
+        int64_t *hc = pinned_scratch(ncnt + 1);
+        if (csr && ebase_total > 0)
+            check_cuda(cudaMemcpyAsync(hc, ecnt, sizeof(int64_t) * ebase_total, cudaMemcpyDeviceToHost, H.st),
+                       "ext counts");
+        for (int l = 0; l < keep; ++l)
+            check_cuda(cudaMemcpyAsync(hc + ebase_total + 2 * l, S[l].cnt, 2 * sizeof(int64_t),
+                                       cudaMemcpyDeviceToHost, H.st),
+                       "ghost counters");
+        check_cuda(cudaStreamSynchronize(H.st), "set-up sync 3");
+        for (int l = 0; l < keep; ++l) {
+            Level &L = H.L[l];
+            L.nclamp = hc[ebase_total + 2 * l];
+            L.nfall = hc[ebase_total + 2 * l + 1];
+            if (!csr || L.nb == 0) continue;
+            int64_t tot = 0;
+            int64_t *c = hc + ebase[l];
+            for (int64_t b = 0; b < L.nb; ++b) {
+                int64_t v = c[b];
+                c[b] = tot;
+                tot += v;
+            }
+            L.ne = tot;
+            L.eoff = (int64_t *)dalloc(H, sizeof(int64_t) * (L.nb + 1));
+            check_cuda(cudaMemcpyAsync(L.eoff, c, sizeof(int64_t) * L.nb, cudaMemcpyHostToDevice, H.st), "eoff");
+            check_cuda(cudaMemcpyAsync(L.eoff + L.nb, &tot, sizeof(int64_t), cudaMemcpyHostToDevice, H.st), "eoff");
+            L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * std::max<int64_t>(tot, 1));
+            L.ew = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(tot, 1));
+            k_ext_fill<<<nblocks(L.nb, 128), 128, 0, H.st>>>(L.bref, L.bw, L.nb, L.d, H.o.ext_sweeps, L.eoff, L.eg,
+                                                             L.ew);
+            count_launch(H);
+        }
+        check_cuda(cudaGetLastError(), "ext fill");
     }
     // level arrays
-    if (li > 0) L.u = (double *)dalloc(H, sizeof(double) * L.nn);
-    L.F = (double *)dalloc(H, sizeof(double) * L.nn);
-    L.r = (double *)dalloc(H, sizeof(double) * L.nn);
-    check_cuda(cudaStreamSynchronize(H.st), "setup_level sync");
-}
-
-void setup_coarsest(Handle &H, Level &L) {
+    for (int l = 0; l < keep; ++l) {
+        Level &L = H.L[l];
+        if (l > 0) L.u = (double *)dalloc(H, sizeof(double) * L.nn);
+        L.F = (double *)dalloc(H, sizeof(double) * L.nn);
+        L.r = (double *)dalloc(H, sizeof(double) * L.nn);
+    }
+    // coarsest: dense system and its Gauss-Jordan inverse
+    Level &L = H.L[keep - 1];
     Geo G = geo_of(L);
-    const int T = 256;
-    uint8_t *flags = (uint8_t *)dalloc(H, (size_t)L.nn + 1, true);
-    k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_INTERIOR, CL_GHOST, flags);
-    count_launch(H);
-    L.nact = compact_flags(H, flags, L.nn, &L.act);
-    if (L.nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
     int64_t n = L.nact;
     double *A = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
     L.Ainv = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1));
@@ -695,20 +974,20 @@ void setup_coarsest(Handle &H, Level &L) {
     int *sing = (int *)dalloc(H, sizeof(int), true);
     k_assemble<<<nblocks(n, 128), 128, 0, H.st>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.ng, G, A);
     count_launch(H);
-    check_cuda(cudaGetLastError(), "k_assemble");
     k_identity<<<nblocks(n * n, T), T, 0, H.st>>>(L.Ainv, n);
     count_launch(H);
     for (int64_t k = 0; k < n; ++k) {
         k_gj_pivot<<<1, 1024, 0, H.st>>>(A, L.Ainv, n, k, col, sing);
-        count_launch(H);
         k_gj_elim<<<nblocks(n * n, T), T, 0, H.st>>>(A, L.Ainv, n, k, col);
+        count_launch(H);
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "gauss-jordan");
-    int hs = 0;
-    check_cuda(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, H.st), "singular flag");
-    check_cuda(cudaStreamSynchronize(H.st), "coarsest sync");
-    if (hs) throw Error{BCMG_EGEOM, "coarsest system is singular"};
+    int *hs = (int *)pinned_scratch(1);
+    check_cuda(cudaMemcpyAsync(hs, sing, sizeof(int), cudaMemcpyDeviceToHost, H.st), "singular flag");
+    check_cuda(cudaStreamSynchronize(H.st), "set-up sync 4");
+    if (*hs) throw Error{BCMG_EGEOM, "coarsest system is singular"};
+    for (auto &Lv : H.L) Lv.phi = nullptr;
 }
 
 }  // namespace bcmg
