@@ -139,6 +139,26 @@ int64_t bcmg_kernel_launches(void);
  * read after each cycle). */
 int bcmg_profile_read(bcmg_handle h, double *out_host);
 
+/* Residual norms for callers that cannot allocate device memory (code that
+ * runs inside a stream capture, plugins whose host owns every allocation,
+ * processes that forbid cudaMalloc after start-up).  The paper has no
+ * counterpart: this is a service of the library, not a step of the method.
+ *   r_dev    count FP64 residual values (device), e.g. from bcmg_residual
+ *   cls_dev  count node classes (device, BCMG_CLASS_*), e.g. from
+ *            bcmg_get_class; only INTERIOR and GHOST entries are summed
+ *   count    number of entries, 1 <= count <= 33554432 (the capacity of the
+ *            library's fixed scratch); larger counts return BCMG_EINVAL
+ *   out_dev  4 FP64 (device): ||r_I||_2, ||r_G||_2, ||r_I||_inf, ||r_G||_inf
+ *   stream   cudaStream_t the two kernels are launched on (NULL = legacy)
+ * Allocates nothing: the per-block partial sums live in a fixed 128 KiB
+ * __device__ array that every device loading the library keeps until the
+ * process exits.  The first call on each device resolves that array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU race; order
+ * them (same stream or events).  Asynchronous: returns after the launches. */
+int bcmg_residual_norms_static(const double *r_dev, const uint8_t *cls_dev, int64_t count, double *out_dev,
+                               void *stream);
+
 /* ---- introspection (host copies, synchronous) ----------------------- */
 
 int bcmg_num_levels(bcmg_handle h, int *levels);

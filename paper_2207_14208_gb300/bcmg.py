@@ -69,6 +69,7 @@ def load():
             "bcmg_last_error": (C.c_char_p, []),
             "bcmg_kernel_launches": (i64, []),
             "bcmg_profile_read": (i32, [vp, vp]),
+            "bcmg_residual_norms_static": (i32, [vp, vp, i64, vp, vp]),
             "bcmg_num_levels": (i32, [vp, vp]),
             "bcmg_level_info": (i32, [vp, i32, vp]),
             "bcmg_get_class": (i32, [vp, i32, vp]),
@@ -96,6 +97,20 @@ def _check(rc):
 
 def kernel_launches() -> int:
     return int(load().bcmg_kernel_launches())
+
+
+def residual_norms_static(r, cls, out):
+    """Norms of a residual without any device allocation by the library
+    (bcmg_residual_norms_static): r float64 and cls uint8 CUDA tensors of the
+    same length, out a float64 CUDA tensor of 4 entries.  Asynchronous on the
+    current stream."""
+    import torch
+    if not (isinstance(cls, torch.Tensor) and cls.is_cuda and cls.dtype == torch.uint8 and cls.is_contiguous()):
+        raise TypeError("cls must be a contiguous CUDA uint8 tensor")
+    if cls.numel() != r.numel() or out.numel() < 4:
+        raise ValueError("size mismatch")
+    _check(load().bcmg_residual_norms_static(_dptr(r), C.c_void_p(cls.data_ptr()), r.numel(), _dptr(out),
+                                             _stream()))
 
 
 def _dptr(t):

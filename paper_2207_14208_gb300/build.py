@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libbcmg.so")
-SOURCES = ["setup.cu", "cycle.cu", "capi.cu"]
+SOURCES = ["setup.cu", "cycle.cu", "capi.cu", "static_norms.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
