@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--arms", choices=["both", "fp64", "mixed"], default="both")
     return p.parse_args()
 
 
@@ -151,6 +152,10 @@ def flush_l2(buf):
 
 
 # ------------------------------------------------------------ our arm
+FP64_INSTR_PER_UPDATE = 7   # 5 adds, 1 FMA, 1 multiply per red/black update
+FP64_PEAK_GINSTR = 152 * 2 * 2.07  # SMs x FP64 FMA pipes per clock x GHz (1.26 TFLOP/s)
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2207_14208_gb300 import bcmg
@@ -168,92 +173,112 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(512 * 1024 * 1024 // 8, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(profile=False):
-        s = bcmg.Solver(d, N, phi, f, profile=int(profile))
+    def step(precision, profile=False):
+        s = bcmg.Solver(d, N, phi, f, profile=int(profile), precision=precision)
         Q = s.ghost_points()
         s.set_boundary_values(u_exact_torch(Q).contiguous())
         u.zero_()
         cycles, rel = s.solve(u, args.rtol, 200)
         return s, cycles, rel
 
-    for _ in range(args.warmup):
-        s, c, rel = step()
-        s.close()
-    torch.cuda.synchronize()
-
-    # timed steps: events on the caller's stream bracket all library work
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    launches0 = bcmg.kernel_launches()
-    times, cycles, rels, prof = [], [], [], []
-    for _ in range(args.steps):
-        flush_l2(flush)
+    def timed(precision, steps, warmup):
+        for _ in range(warmup):
+            s, c, rel = step(precision)
+            s.close()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s, c, rel = step(profile=True)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        cycles.append(c)
-        rels.append(rel)
-        prof.append(s.profile())
-        s.close()
-    torch.cuda.synchronize()
-    launches = bcmg.kernel_launches() - launches0
-    clk = clocks.stop()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    total_ms = sum(times)
-    total_ms_max = max_over_ranks(total_ms, ws)
-    total_cycles = sum(cycles) * ws
-    value = total_cycles / (total_ms_max / 1e3)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        launches0 = bcmg.kernel_launches()
+        times, cycles, rels, prof = [], [], [], []
+        for _ in range(steps):
+            flush_l2(flush)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, c, rel = step(precision, profile=True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            cycles.append(c)
+            rels.append(rel)
+            prof.append(s.profile())
+            s.close()
+        torch.cuda.synchronize()
+        launches = bcmg.kernel_launches() - launches0
+        clk = clocks.stop()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        total_ms_max = max_over_ranks(sum(times), ws)
+        sweep_ms = sum(p["smooth_ms"] for p in prof) / max(1, sum(p["smooth_launches"] for p in prof))
+        return dict(ms=total_ms_max, cycles=cycles, rels=rels, sweep_ms=sweep_ms, launches=launches,
+                    clocks=clk, value=sum(cycles) * ws / (total_ms_max / 1e3))
 
-    # roofline of the dominant kernel: the finest-level red/black sweep
+    # --arms restricts the run to one precision (for profiling runs only; the
+    # JSON line then repeats that arm in both places)
+    r64 = timed(bcmg.PREC_FP64, args.steps, args.warmup) if args.arms != "mixed" else None
+    r32 = timed(bcmg.PREC_MIXED, args.steps, args.warmup) if args.arms != "fp64" else None
+    r64 = r64 or r32
+    r32 = r32 or r64
+
     s = bcmg.Solver(d, N, phi, f)
     info = s.info(0)
     s.close()
-    sweep_ms = sum(p["smooth_ms"] for p in prof) / max(1, sum(p["smooth_launches"] for p in prof))
     n_int = info["n_interior"]
-    alg_bytes = 12.0 * n_int  # per colour sweep: F, new u and one neighbour value per updated node
-    achieved_gbs = alg_bytes / (sweep_ms / 1e3) / 1e9
+    # dominant kernel: the finest-level red/black sweep (one colour per launch,
+    # n_int / 2 updates).  FP64 is bound by the FP64 pipe (7 instructions per
+    # update); the FP32 sweep of the mixed path by memory (12 B per update).
+    upd = n_int / 2.0
+    ach_instr = FP64_INSTR_PER_UPDATE * upd / (r64["sweep_ms"] / 1e3) / 1e9
+    alg_bytes64 = 24.0 * upd
+    alg_bytes32 = 12.0 * upd
     peak, peak_kind = measured_peaks()
+    hbm64 = alg_bytes64 / (r64["sweep_ms"] / 1e3) / 1e9
+    hbm32 = alg_bytes32 / (r32["sweep_ms"] / 1e3) / 1e9
 
     out = {
         "metric": METRIC,
-        "value": value,
+        "value": r64["value"],
         "unit": UNIT,
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": total_ms_max / args.steps,
+        "ms_per_step": r64["ms"] / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (analytic level set and manufactured solution)",
         "config": {"workload": "3D ellipsoid Poisson N=256 (257^3), FP64 V(2,1) solve to 1e-10",
-                   "N": N, "cycles_per_solve": cycles[0], "final_rel_residual": max(rels),
+                   "N": N, "cycles_per_solve": r64["cycles"][0], "final_rel_residual": max(r64["rels"]),
                    "interior_nodes": n_int, "ghosts": info["n_ghost"],
                    "step": "create hierarchy + g(Q) + solve", "l2": "flushed (512 MiB write) before every step",
                    "parallelism": "replicas" if ws > 1 else "single"},
-        "roofline": {"bound": "hbm", "kernel": "k_smooth<3> (finest level, one colour)",
-                     "achieved": achieved_gbs, "peak": peak, "unit": "GB/s", "frac": achieved_gbs / peak,
-                     "peak_source": peak_kind, "traffic": None, "sweep_us": sweep_ms * 1e3,
-                     "alg_bytes_per_launch": alg_bytes},
-        "clocks": clk,
-        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_smooth<3,double> (finest level, one colour)",
+                     "achieved": ach_instr, "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instr/s",
+                     "frac": ach_instr / FP64_PEAK_GINSTR,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (1.26 TFLOP/s)",
+                     "traffic": None, "sweep_us": r64["sweep_ms"] * 1e3,
+                     "hbm_view": {"alg_bytes_per_launch": alg_bytes64, "achieved_gbs": hbm64,
+                                  "peak_gbs": peak, "frac": hbm64 / peak, "peak_source": peak_kind}},
+        "mixed": {"value": r32["value"], "unit": UNIT, "dtype": "f32 cycles in f64 refinement",
+                  "ms_per_step": r32["ms"] / args.steps, "cycles_per_solve": r32["cycles"][0],
+                  "final_rel_residual": max(r32["rels"]),
+                  "roofline": {"bound": "hbm", "kernel": "k_smooth<3,float> (finest level, one colour)",
+                               "achieved": hbm32, "peak": peak, "unit": "GB/s", "frac": hbm32 / peak,
+                               "sweep_us": r32["sweep_ms"] * 1e3, "alg_bytes_per_launch": alg_bytes32}},
+        "clocks": r64["clocks"],
+        "gpu_launches": r64["launches"],
     }
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, d, N, phi_h, f_h)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, d, N, phi_h, f_h, cycles[0])
+        out["cpu_baseline"] = cpu_baseline(args, d, N, phi_h, f_h, r64["cycles"][0])
     return out
 
 

@@ -69,7 +69,12 @@ typedef struct {
     int use_graph;     /* replay the V-cycle from a captured CUDA graph (1) */
     int profile;       /* time every finest-level smoothing sweep with CUDA
                           events during bcmg_solve (0) */
+    int precision;     /* BCMG_PREC_FP64 (default) or BCMG_PREC_MIXED */
 } bcmg_opts;
+
+#define BCMG_PREC_FP64 0  /* every cycle in FP64 */
+#define BCMG_PREC_MIXED 1 /* FP64 iterative refinement: FP64 residual and
+                             update, the V-cycle on the correction in FP32 */
 
 /* Fill *opts with the defaults above. */
 void bcmg_default_opts(bcmg_opts *opts);

@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "bcmg.h")
 OK, EINVAL, ENOMEM, ECUDA, EGEOM, ENOCONV, ENONFINITE, ETIMEOUT = range(8)
 INACTIVE, INTERIOR, GHOST, BOXDIR = 0, 1, 2, 3
 DTAU_EXP, DTAU_POLY, DTAU_CONST = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
 
 _lib = None
 _lock = threading.Lock()
@@ -36,7 +37,8 @@ class BcmgError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("dtau_mode", C.c_int),
                 ("dtau_const", C.c_double), ("ext_sweeps", C.c_int), ("min_coarse", C.c_int),
-                ("max_levels", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int)]
+                ("max_levels", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
+                ("precision", C.c_int)]
 
 
 def declared_functions():

@@ -62,17 +62,19 @@ struct Level {
                               // < 0 -(ghost node index) - 1, kNoRef none
     double *bw = nullptr;     // 3 * nb, axis-major, normalised weights
     // the K extension sweeps from zero are a fixed linear map from ghost
-    // values to band values: CSR rows (per band node) of (ghost node, weight)
-    int64_t ne = 0;
-    int64_t *eoff = nullptr;  // nb + 1
-    uint32_t *eg = nullptr;
-    double *ew = nullptr;
+    // values to band values: per band node up to kExtCap (ghost node,
+    // weight) terms, ELL layout (term-major); null ecnt = sweep by sweep
+    uint8_t *ecnt = nullptr;  // nb
+    uint32_t *eg = nullptr;   // kExtCap * nb
+    double *ew = nullptr;     // kExtCap * nb
     // boxdir list (finest level only)
     uint32_t *boxidx = nullptr;
     // arrays
     double *u = nullptr, *F = nullptr, *r = nullptr;
     double *gtmp = nullptr;  // ng
     double *bbuf = nullptr;  // 2 * nb
+    // FP32 arrays of the mixed-precision inner cycle (correction equation)
+    float *u32 = nullptr, *F32 = nullptr, *r32 = nullptr, *gtmp32 = nullptr, *bbuf32 = nullptr;
     // coarsest
     uint32_t *act = nullptr;
     double *Ainv = nullptr;
@@ -125,17 +127,23 @@ int report(int code, const std::string &msg);  // sets the thread's last error
 // ---- set-up (setup.cu) -------------------------------------------------
 void setup_hierarchy(Handle &H, const double *phi0);
 double dtau_of(int d, int mode, double cst, double theta);
-bool ext_csr_ok(int d, int K);
+bool ext_ell_ok(int d, int K);
+constexpr int kExtCap = 16;  // terms per band node of the expanded extension
 
-// ---- cycle kernels (cycle.cu) -----------------------------------------
-void smooth(Handle &H, Level &L, double *u, const double *F, int nsteps);
-void residual(Handle &H, Level &L, const double *u, const double *F, double *r);
-void extend(Handle &H, Level &L, double *a);
-void restrict_to(Handle &H, Level &Lf, Level &Lc, const double *rf, double *Fc, double *uc_zero);
-void prolong(Handle &H, Level &Lf, Level &Lc, const double *ec, double *uf);
-void coarsest_correct(Handle &H, Level &L, double *u, const double *F);
+// ---- cycle kernels (cycle.cu); T = double (FP64) or float (inner cycles of
+// the mixed-precision refinement) ----------------------------------------
+template <typename T> void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps);
+template <typename T> void residual(Handle &H, Level &L, const T *u, const T *F, T *r);
+template <typename T> void extend(Handle &H, Level &L, T *a);
+template <typename T>
+void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero);
+template <typename T> void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf);
+template <typename T> void coarsest_correct(Handle &H, Level &L, T *u, const T *F);
 void norms(Handle &H, Level &L, const double *r, double *out4);
 void vcycle_enqueue(Handle &H, int l, double *u);
+// one refinement step: F32 = r (finest), FP32 V-cycle on the correction,
+// u += correction; r must hold the FP64 residual of u
+void mixed_step_enqueue(Handle &H, double *u);
 void copy_active(Handle &H, const double *src, double *dst, bool with_boxdir);
 void scatter_ghost_values(Handle &H, Level &L, const double *g, double *F);
 void set_interior_rhs(Handle &H, Level &L, const double *f, double *F);

@@ -137,13 +137,25 @@ cudaGraphExec_t capture(Handle &H, int64_t *kernels, Fn fn) {
     return ex;
 }
 
+// one cycle on the working copy: a V-cycle (FP64), or one refinement step
+// (FP64 residual, FP32 V-cycle on the correction, FP64 update)
+void cycle_body(Handle &H) {
+    if (H.o.precision == BCMG_PREC_MIXED) {
+        Level &L = H.L[0];
+        residual<double>(H, L, H.u0, L.F, L.r);
+        mixed_step_enqueue(H, H.u0);
+    } else {
+        vcycle_enqueue(H, 0, H.u0);
+    }
+}
+
 void run_vcycle(Handle &H) {
     if (H.o.use_graph) {
-        if (!H.vgraph) H.vgraph = capture(H, &H.vgraph_kernels, [&] { vcycle_enqueue(H, 0, H.u0); });
+        if (!H.vgraph) H.vgraph = capture(H, &H.vgraph_kernels, [&] { cycle_body(H); });
         check_cuda(cudaGraphLaunch(H.vgraph, H.st), "cudaGraphLaunch(vcycle)");
         g_launches.fetch_add(H.vgraph_kernels, std::memory_order_relaxed);
     } else {
-        vcycle_enqueue(H, 0, H.u0);
+        cycle_body(H);
     }
 }
 
@@ -167,20 +179,22 @@ void profile_collect(Handle &H) {
     }
 }
 
-// V-cycle + residual norms of the result (one graph)
+// cycle + residual norms of the result (one graph).  In mixed precision the
+// finest residual r left by the previous norms is the refinement's input.
+void solve_body(Handle &H) {
+    if (H.o.precision == BCMG_PREC_MIXED) mixed_step_enqueue(H, H.u0);
+    else vcycle_enqueue(H, 0, H.u0);
+    enqueue_norms(H);
+}
+
 void run_vcycle_norms(Handle &H) {
     if (!H.o.use_graph) H.pev_next = 0;
     if (H.o.use_graph) {
-        if (!H.ngraph)
-            H.ngraph = capture(H, &H.ngraph_kernels, [&] {
-                vcycle_enqueue(H, 0, H.u0);
-                enqueue_norms(H);
-            });
+        if (!H.ngraph) H.ngraph = capture(H, &H.ngraph_kernels, [&] { solve_body(H); });
         check_cuda(cudaGraphLaunch(H.ngraph, H.st), "cudaGraphLaunch(vcycle+norms)");
         g_launches.fetch_add(H.ngraph_kernels, std::memory_order_relaxed);
     } else {
-        vcycle_enqueue(H, 0, H.u0);
-        enqueue_norms(H);
+        solve_body(H);
         H.pev_pairs = H.pev_next / 2;
     }
 }
@@ -234,6 +248,7 @@ void bcmg_default_opts(bcmg_opts *o) {
     o->max_levels = 24;
     o->use_graph = 1;
     o->profile = 0;
+    o->precision = BCMG_PREC_FP64;
 }
 
 int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
@@ -253,7 +268,8 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         if (opts) H->o = *opts;
         else bcmg_default_opts(&H->o);
         if (H->o.nu1 < 0 || H->o.nu2 < 0 || H->o.ext_sweeps < 1 || H->o.min_coarse < 2 ||
-            H->o.max_levels < 1 || H->o.dtau_mode < 0 || H->o.dtau_mode > 2)
+            H->o.max_levels < 1 || H->o.dtau_mode < 0 || H->o.dtau_mode > 2 ||
+            (H->o.precision != BCMG_PREC_FP64 && H->o.precision != BCMG_PREC_MIXED))
             throw Error{BCMG_EINVAL, "invalid options"};
         H->user = (cudaStream_t)stream;
         keep_pool_memory();
@@ -525,7 +541,7 @@ int bcmg_restrict(bcmg_handle h, int level, const double *r_fine_dev, double *F_
         if (level < 0 || level + 1 >= (int)H.L.size()) throw Error{BCMG_EINVAL, "level out of range"};
         if (!r_fine_dev || !F_coarse_dev) throw Error{BCMG_EINVAL, "bad argument"};
         enter(H);
-        restrict_to(H, H.L[level], H.L[level + 1], r_fine_dev, F_coarse_dev, nullptr);
+        restrict_to<double>(H, H.L[level], H.L[level + 1], r_fine_dev, F_coarse_dev, nullptr);
         leave(H);
     });
 }

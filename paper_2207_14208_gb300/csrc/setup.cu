@@ -280,10 +280,10 @@ struct GhostOut {
     unsigned long long *nclamp, *nfall;
 };
 
-__global__ void k_ghost_setup(const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
-                              const uint8_t *__restrict__ cls, Geo G, int dmode, double dconst, GhostOut out) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
+// geometry of ghost g of one level (normal, eta, stencil, xi, Q, Delta tau)
+__device__ void ghost_one(const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
+                          const uint8_t *__restrict__ cls, const Geo &G, int dmode, double dconst,
+                          const GhostOut &out, int64_t g) {
     const int d = G.d;
     int64_t lin = gidx[g];
     int ix[3];
@@ -394,10 +394,9 @@ __global__ void k_ghost_setup(const uint32_t *__restrict__ gidx, int64_t ng, con
 }
 
 // ---------------------------------------------------------------- band
-__global__ void k_band_mark(const uint32_t *__restrict__ gidx, int64_t ng, const uint8_t *__restrict__ cls,
-                            Geo G, uint8_t *__restrict__ mark) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
+// mark the inactive nodes within Chebyshev distance 2 of ghost g
+__device__ void band_mark_one(const uint32_t *__restrict__ gidx, const uint8_t *__restrict__ cls, const Geo &G,
+                              uint8_t *__restrict__ mark, int64_t g) {
     int ix[3];
     decode(G, gidx[g], ix);
     int o[3];
@@ -421,11 +420,47 @@ __device__ int64_t find_sorted(const uint32_t *a, int64_t n, uint32_t key) {
     return (lo < n && a[lo] == key) ? lo : -1;
 }
 
-__global__ void k_band_setup(const uint32_t *__restrict__ bidx, int64_t nb, const double *__restrict__ phi,
-                             const uint8_t *__restrict__ cls, Geo G, int32_t *__restrict__ bref,
-                             double *__restrict__ bw) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+// Per-level tables: the set-up kernels below process every level of the
+// hierarchy in one launch (blocks are assigned to levels by their start
+// block), so the many tiny coarse levels do not each pay a serial launch.
+struct LevelTab {
+    Geo G;
+    const double *phi;
+    const uint8_t *cls;
+    const uint32_t *gidx;
+    int64_t ng;
+    GhostOut gout;
+    uint8_t *mark;
+    const uint32_t *bidx;
+    int64_t nb;
+    int32_t *bref;
+    double *bw;
+    uint32_t *eg;
+    double *ew;
+    uint8_t *ecnt;
+    int64_t blk_g, blk_b;  // first block of this level in the ghost / band launches
+};
+
+__device__ __forceinline__ int level_of_block(const LevelTab *tab, int nl, bool band) {
+    int l = 0;
+    for (int i = 1; i < nl; ++i)
+        if ((int64_t)blockIdx.x >= (band ? tab[i].blk_b : tab[i].blk_g)) l = i;
+    return l;
+}
+
+// ghost geometry and band marks of every level
+__global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int dmode, double dconst) {
+    const int l = level_of_block(tab, nl, false);
+    const LevelTab &T = tab[l];
+    const int64_t g = ((int64_t)blockIdx.x - T.blk_g) * blockDim.x + threadIdx.x;
+    if (g >= T.ng) return;
+    ghost_one(T.gidx, T.ng, T.phi, T.cls, T.G, dmode, dconst, T.gout, g);
+    band_mark_one(T.gidx, T.cls, T.G, T.mark, g);
+}
+
+__device__ void band_one(const uint32_t *__restrict__ bidx, int64_t nb, const double *__restrict__ phi,
+                         const uint8_t *__restrict__ cls, const Geo &G, int32_t *__restrict__ bref,
+                         double *__restrict__ bw, int64_t b) {
     int64_t lin = bidx[b];
     int ix[3];
     decode(G, lin, ix);
@@ -456,92 +491,78 @@ __global__ void k_band_setup(const uint32_t *__restrict__ bidx, int64_t nb, cons
     }
 }
 
+__global__ void k_band_all(const LevelTab *__restrict__ tab, int nl) {
+    const int l = level_of_block(tab, nl, true);
+    const LevelTab &T = tab[l];
+    const int64_t b = ((int64_t)blockIdx.x - T.blk_b) * blockDim.x + threadIdx.x;
+    if (b >= T.nb) return;
+    band_one(T.bidx, T.nb, T.phi, T.cls, T.G, T.bref, T.bw, b);
+}
+
 // The K Jacobi sweeps of the extension, started from zero, expand into a sum
 // over upwind paths of length <= K that end at a ghost: value(b) =
-// sum_paths (product of the normalised weights) * a[ghost].  Enumerate the
-// paths (depth-first, fixed order), merge equal ghosts in a stable order.
-constexpr int kExtMaxItems = 128;
+// sum_paths (product of the normalised weights) * a[ghost].  The paths are
+// walked depth-first in a fixed order and equal ghosts merged as they come,
+// into at most kExtCap terms per band node (ELL layout, term-major); a level
+// with a longer row keeps the sweep-by-sweep extension instead.
 
-__device__ int ext_paths(int64_t b, const int32_t *__restrict__ bref, const double *__restrict__ bw, int64_t nb,
-                         int d, int K, uint32_t *g, double *w) {
+__global__ void k_ext_all(const LevelTab *__restrict__ tab, int nl, int d, int K, int *__restrict__ overflow) {
+    const int l = level_of_block(tab, nl, true);
+    const LevelTab &T = tab[l];
+    const int64_t b = ((int64_t)blockIdx.x - T.blk_b) * blockDim.x + threadIdx.x;
+    if (b >= T.nb) return;
+    const int64_t nb = T.nb;
+    uint32_t g[kExtCap];
+    double w[kExtCap];
+    int cnt = 0;
+    bool over = false;
     int64_t st_node[16];
     int st_depth[16];
     double st_w[16];
-    int sp = 0, cnt = 0;
+    int sp = 1;
     st_node[0] = b;
     st_depth[0] = 1;
     st_w[0] = 1.0;
-    sp = 1;
     while (sp > 0) {
         --sp;
         const int64_t x = st_node[sp];
         const int j = st_depth[sp];
         const double W = st_w[sp];
-        // push band sources in reverse axis order so that axis 0 is visited first
         for (int ax = d - 1; ax >= 0; --ax) {
-            const int32_t ref = bref[(int64_t)ax * nb + x];
+            const int32_t ref = T.bref[(int64_t)ax * nb + x];
             if (ref == kNoRef || ref < 0 || j >= K) continue;
             if (sp < 16) {
                 st_node[sp] = ref;
                 st_depth[sp] = j + 1;
-                st_w[sp] = W * bw[(int64_t)ax * nb + x];
+                st_w[sp] = W * T.bw[(int64_t)ax * nb + x];
                 ++sp;
+            } else {
+                over = true;
             }
         }
         for (int ax = 0; ax < d; ++ax) {
-            const int32_t ref = bref[(int64_t)ax * nb + x];
+            const int32_t ref = T.bref[(int64_t)ax * nb + x];
             if (ref == kNoRef || ref >= 0) continue;
-            if (cnt < kExtMaxItems) {
-                g[cnt] = (uint32_t)(-(int64_t)ref - 1);
-                w[cnt] = W * bw[(int64_t)ax * nb + x];
+            const uint32_t gg = (uint32_t)(-(int64_t)ref - 1);
+            const double ww = W * T.bw[(int64_t)ax * nb + x];
+            int k = 0;
+            while (k < cnt && g[k] != gg) ++k;
+            if (k < cnt) {
+                w[k] += ww;
+            } else if (cnt < kExtCap) {
+                g[cnt] = gg;
+                w[cnt] = ww;
                 ++cnt;
+            } else {
+                over = true;
             }
         }
     }
-    // stable insertion sort by ghost node, then merge equal nodes
-    for (int i = 1; i < cnt; ++i)
-        for (int k = i; k > 0 && g[k] < g[k - 1]; --k) {
-            uint32_t tg = g[k];
-            g[k] = g[k - 1];
-            g[k - 1] = tg;
-            double tw = w[k];
-            w[k] = w[k - 1];
-            w[k - 1] = tw;
-        }
-    int m = 0;
-    for (int i = 0; i < cnt; ++i) {
-        if (m > 0 && g[m - 1] == g[i]) {
-            w[m - 1] += w[i];
-        } else {
-            g[m] = g[i];
-            w[m] = w[i];
-            ++m;
-        }
-    }
-    return m;
-}
-
-__global__ void k_ext_count(const int32_t *__restrict__ bref, const double *__restrict__ bw, int64_t nb, int d,
-                            int K, int64_t *__restrict__ counts) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    uint32_t g[kExtMaxItems];
-    double w[kExtMaxItems];
-    counts[b] = ext_paths(b, bref, bw, nb, d, K, g, w);
-}
-
-__global__ void k_ext_fill(const int32_t *__restrict__ bref, const double *__restrict__ bw, int64_t nb, int d,
-                           int K, const int64_t *__restrict__ off, uint32_t *__restrict__ eg,
-                           double *__restrict__ ew) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    uint32_t g[kExtMaxItems];
-    double w[kExtMaxItems];
-    const int m = ext_paths(b, bref, bw, nb, d, K, g, w);
-    const int64_t o = off[b];
-    for (int i = 0; i < m; ++i) {
-        eg[o + i] = g[i];
-        ew[o + i] = w[i];
+    if (over) atomicOr(overflow + l, 1);
+    T.ecnt[b] = (uint8_t)cnt;
+    for (int k = 0; k < cnt; ++k) {
+        T.eg[(int64_t)k * nb + b] = g[k];
+        T.ew[(int64_t)k * nb + b] = w[k];
     }
 }
 
@@ -670,6 +691,76 @@ __global__ void k_gj_elim(double *__restrict__ A, double *__restrict__ B, int64_
     B[i * n + j] -= f * B[k * n + j];
 }
 
+// Whole Gauss-Jordan inversion with partial pivoting in one block (small
+// coarsest systems): same pivot rule and elimination order as the
+// multi-launch version, with __syncthreads between the phases of a step.
+constexpr int kGjSmall = 512;
+
+__global__ void __launch_bounds__(1024) k_gj_small(double *__restrict__ A, double *__restrict__ B, int n,
+                                                   int *__restrict__ singular) {
+    __shared__ double col[kGjSmall];
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    __shared__ double piv;
+    for (int k = 0; k < n; ++k) {
+        double best = -1.0;
+        int bidx = n;
+        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+            double v = fabs(A[(int64_t)i * n + k]);
+            if (v > best || (v == best && i < bidx)) {
+                best = v;
+                bidx = i;
+            }
+        }
+        bv[threadIdx.x] = best;
+        bi[threadIdx.x] = bidx;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) {
+                double v = bv[threadIdx.x + s];
+                int ii = bi[threadIdx.x + s];
+                if (v > bv[threadIdx.x] || (v == bv[threadIdx.x] && ii < bi[threadIdx.x])) {
+                    bv[threadIdx.x] = v;
+                    bi[threadIdx.x] = ii;
+                }
+            }
+            __syncthreads();
+        }
+        int p = bi[0];
+        if (bv[0] <= 0.0) {
+            if (threadIdx.x == 0) *singular = 1;
+            p = k;
+        }
+        if (p != k)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                double t = A[(int64_t)k * n + j];
+                A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
+                A[(int64_t)p * n + j] = t;
+                t = B[(int64_t)k * n + j];
+                B[(int64_t)k * n + j] = B[(int64_t)p * n + j];
+                B[(int64_t)p * n + j] = t;
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) piv = A[(int64_t)k * n + k];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = (i == k) ? 0.0 : A[(int64_t)i * n + k];
+        __syncthreads();
+        const double ip = (piv != 0.0) ? 1.0 / piv : 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            A[(int64_t)k * n + j] *= ip;
+            B[(int64_t)k * n + j] *= ip;
+        }
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+            const int i = (int)(t / n), j = (int)(t % n);
+            const double f = col[i];
+            if (i == k || f == 0.0) continue;
+            A[(int64_t)i * n + j] -= f * A[(int64_t)k * n + j];
+            B[(int64_t)i * n + j] -= f * B[(int64_t)k * n + j];
+        }
+        __syncthreads();
+    }
+}
+
 inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -678,10 +769,9 @@ double dtau_of(int d, int mode, double cst, double theta) { return dtau_formula(
 
 // the path expansion fits the per-thread buffers: at most d (d^K - 1)/(d - 1)
 // ghost terms and a depth-first stack of (d - 1)(K - 1) + d entries
-bool ext_csr_ok(int d, int K) {
-    double pk = std::pow((double)d, (double)K);
-    return K >= 1 && d * (pk - 1.0) / (d - 1.0) <= kExtMaxItems && (d - 1) * (K - 1) + d <= 16;
-}
+// the depth-first walk of the expansion keeps at most (d - 1)(K - 1) + d
+// pending nodes on its 16-entry stack
+bool ext_ell_ok(int d, int K) { return K >= 1 && (d - 1) * (K - 1) + d <= 16; }
 
 // ------------------------------------------------------------ batched compaction
 // Many flag arrays are compacted with one device->host round trip: block
@@ -850,7 +940,10 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         }
     H.L.resize(keep);
     S.resize(keep);
-    // phase B: windows, ghost geometry, band marks
+    // phase B: windows and ghost arrays per level, then the ghost geometry
+    // and band marks of every level in one launch
+    std::vector<LevelTab> tab(keep);
+    int64_t gblocks = 0;
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
         LevelScratch &s = S[l];
@@ -869,18 +962,27 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
         L.gtmp = (double *)dalloc(H, sizeof(double) * ng1);
         s.cnt = (unsigned long long *)dalloc(H, 2 * sizeof(unsigned long long), true);
-        s.fband = s.fint;  // reuse: cleared below
+        s.fband = s.fint;  // reuse: cleared here
         check_cuda(cudaMemsetAsync(s.fband, 0, (size_t)L.nn, H.st), "band memset");
-        if (L.ng > 0) {
-            GhostOut go{L.gcode, L.gxi, L.gdt, L.geta, L.gn, L.gQ, s.cnt, s.cnt + 1};
-            k_ghost_setup<<<nblocks(L.ng, 128), 128, 0, H.st>>>(L.gidx, L.ng, L.phi, L.cls, G, H.o.dtau_mode,
-                                                                H.o.dtau_const, go);
-            k_band_mark<<<nblocks(L.ng, T), T, 0, H.st>>>(L.gidx, L.ng, L.cls, G, s.fband);
-            count_launch(H);
-            count_launch(H);
-        }
-        check_cuda(cudaGetLastError(), "ghost set-up");
+        LevelTab &t = tab[l];
+        t = LevelTab{};
+        t.G = G;
+        t.phi = L.phi;
+        t.cls = L.cls;
+        t.gidx = L.gidx;
+        t.ng = L.ng;
+        t.gout = GhostOut{L.gcode, L.gxi, L.gdt, L.geta, L.gn, L.gQ, s.cnt, s.cnt + 1};
+        t.mark = s.fband;
+        t.blk_g = gblocks;
+        gblocks += nblocks(L.ng, 128);
     }
+    LevelTab *tab_d = (LevelTab *)dalloc(H, sizeof(LevelTab) * keep, true);
+    check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(LevelTab) * keep, cudaMemcpyHostToDevice, H.st), "tab");
+    if (gblocks > 0) {
+        k_ghost_all<<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.dtau_mode, H.o.dtau_const);
+        count_launch(H);
+    }
+    check_cuda(cudaGetLastError(), "ghost set-up");
     // round 2: band lists on every level and the coarsest active list (one sync)
     {
         std::vector<CompactItem> items;
@@ -892,69 +994,58 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         Lc.nact = items[keep].total;
     }
     if (H.L[keep - 1].nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
-    // phase C: band sources and the expansion counts of the extension
-    const bool csr = ext_csr_ok(H.d, H.o.ext_sweeps);
-    int64_t ebase_total = 0;
-    std::vector<int64_t> ebase(keep, 0);
-    for (int l = 0; l < keep; ++l) {
-        ebase[l] = ebase_total;
-        ebase_total += H.L[l].nb;
-    }
-    int64_t *ecnt = csr ? (int64_t *)dalloc(H, sizeof(int64_t) * (size_t)std::max<int64_t>(ebase_total, 1), true)
-                        : nullptr;
+    // phase C: band sources and the ELL expansion of the extension, every
+    // level in one launch each
+    const bool ell = ext_ell_ok(H.d, H.o.ext_sweeps);
+    int64_t bblocks = 0;
+    int *ovf = (int *)dalloc(H, sizeof(int) * keep, true);
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
-        Geo G = geo_of(L);
         int64_t nb1 = std::max<int64_t>(L.nb, 1);
         L.bref = (int32_t *)dalloc(H, sizeof(int32_t) * 3 * nb1);
         L.bw = (double *)dalloc(H, sizeof(double) * 3 * nb1);
         L.bbuf = (double *)dalloc(H, sizeof(double) * 2 * nb1);
-        if (L.nb > 0) {
-            k_band_setup<<<nblocks(L.nb, T), T, 0, H.st>>>(L.bidx, L.nb, L.phi, L.cls, G, L.bref, L.bw);
-            count_launch(H);
-            if (csr) {
-                k_ext_count<<<nblocks(L.nb, 128), 128, 0, H.st>>>(L.bref, L.bw, L.nb, L.d, H.o.ext_sweeps,
-                                                                 ecnt + ebase[l]);
-                count_launch(H);
-            }
+        if (ell && L.nb > 0) {
+            L.ecnt = (uint8_t *)dalloc(H, (size_t)nb1);
+            L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1);
+            L.ew = (double *)dalloc(H, sizeof(double) * kExtCap * nb1);
         }
-        check_cuda(cudaGetLastError(), "band set-up");
+        LevelTab &t = tab[l];
+        t.bidx = L.bidx;
+        t.nb = L.nb;
+        t.bref = L.bref;
+        t.bw = L.bw;
+        t.eg = L.eg;
+        t.ew = L.ew;
+        t.ecnt = L.ecnt;
+        t.blk_b = bblocks;
+        bblocks += nblocks(L.nb, 128);
     }
-    // round 3: extension row lengths, clamp / fall-back counters (one sync)
+    check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(LevelTab) * keep, cudaMemcpyHostToDevice, H.st), "tab");
+    if (bblocks > 0) {
+        k_band_all<<<(unsigned)bblocks, 128, 0, H.st>>>(tab_d, keep);
+        count_launch(H);
+        if (ell) {
+            k_ext_all<<<(unsigned)bblocks, 128, 0, H.st>>>(tab_d, keep, H.d, H.o.ext_sweeps, ovf);
+            count_launch(H);
+        }
+    }
+    check_cuda(cudaGetLastError(), "band set-up");
+    // round 3: clamp / fall-back counters and ELL overflows (one sync)
     {
-        size_t ncnt = (size_t)ebase_total + 2 * keep;
-        int64_t *hc = pinned_scratch(ncnt + 1);
-        if (csr && ebase_total > 0)
-            check_cuda(cudaMemcpyAsync(hc, ecnt, sizeof(int64_t) * ebase_total, cudaMemcpyDeviceToHost, H.st),
-                       "ext counts");
+        int64_t *hc = pinned_scratch(3 * (size_t)keep + 1);
         for (int l = 0; l < keep; ++l)
-            check_cuda(cudaMemcpyAsync(hc + ebase_total + 2 * l, S[l].cnt, 2 * sizeof(int64_t),
-                                       cudaMemcpyDeviceToHost, H.st),
+            check_cuda(cudaMemcpyAsync(hc + 2 * l, S[l].cnt, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, H.st),
                        "ghost counters");
+        int *hov = (int *)(hc + 2 * keep);
+        check_cuda(cudaMemcpyAsync(hov, ovf, sizeof(int) * keep, cudaMemcpyDeviceToHost, H.st), "overflow");
         check_cuda(cudaStreamSynchronize(H.st), "set-up sync 3");
         for (int l = 0; l < keep; ++l) {
             Level &L = H.L[l];
-            L.nclamp = hc[ebase_total + 2 * l];
-            L.nfall = hc[ebase_total + 2 * l + 1];
-            if (!csr || L.nb == 0) continue;
-            int64_t tot = 0;
-            int64_t *c = hc + ebase[l];
-            for (int64_t b = 0; b < L.nb; ++b) {
-                int64_t v = c[b];
-                c[b] = tot;
-                tot += v;
-            }
-            L.ne = tot;
-            L.eoff = (int64_t *)dalloc(H, sizeof(int64_t) * (L.nb + 1));
-            check_cuda(cudaMemcpyAsync(L.eoff, c, sizeof(int64_t) * L.nb, cudaMemcpyHostToDevice, H.st), "eoff");
-            check_cuda(cudaMemcpyAsync(L.eoff + L.nb, &tot, sizeof(int64_t), cudaMemcpyHostToDevice, H.st), "eoff");
-            L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * std::max<int64_t>(tot, 1));
-            L.ew = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(tot, 1));
-            k_ext_fill<<<nblocks(L.nb, 128), 128, 0, H.st>>>(L.bref, L.bw, L.nb, L.d, H.o.ext_sweeps, L.eoff, L.eg,
-                                                             L.ew);
-            count_launch(H);
+            L.nclamp = hc[2 * l];
+            L.nfall = hc[2 * l + 1];
+            if (hov[l]) L.ecnt = nullptr;  // a row longer than kExtCap: sweep by sweep
         }
-        check_cuda(cudaGetLastError(), "ext fill");
     }
     // level arrays
     for (int l = 0; l < keep; ++l) {
@@ -962,6 +1053,13 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         if (l > 0) L.u = (double *)dalloc(H, sizeof(double) * L.nn);
         L.F = (double *)dalloc(H, sizeof(double) * L.nn);
         L.r = (double *)dalloc(H, sizeof(double) * L.nn);
+        if (H.o.precision == BCMG_PREC_MIXED) {
+            L.u32 = (float *)dalloc(H, sizeof(float) * L.nn);
+            L.F32 = (float *)dalloc(H, sizeof(float) * L.nn);
+            L.r32 = (float *)dalloc(H, sizeof(float) * L.nn);
+            L.gtmp32 = (float *)dalloc(H, sizeof(float) * std::max<int64_t>(L.ng, 1));
+            L.bbuf32 = (float *)dalloc(H, sizeof(float) * 2 * std::max<int64_t>(L.nb, 1));
+        }
     }
     // coarsest: dense system and its Gauss-Jordan inverse
     Level &L = H.L[keep - 1];
@@ -976,11 +1074,16 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     count_launch(H);
     k_identity<<<nblocks(n * n, T), T, 0, H.st>>>(L.Ainv, n);
     count_launch(H);
-    for (int64_t k = 0; k < n; ++k) {
-        k_gj_pivot<<<1, 1024, 0, H.st>>>(A, L.Ainv, n, k, col, sing);
-        k_gj_elim<<<nblocks(n * n, T), T, 0, H.st>>>(A, L.Ainv, n, k, col);
+    if (n <= kGjSmall) {
+        k_gj_small<<<1, 1024, 0, H.st>>>(A, L.Ainv, (int)n, sing);
         count_launch(H);
-        count_launch(H);
+    } else {
+        for (int64_t k = 0; k < n; ++k) {
+            k_gj_pivot<<<1, 1024, 0, H.st>>>(A, L.Ainv, n, k, col, sing);
+            k_gj_elim<<<nblocks(n * n, T), T, 0, H.st>>>(A, L.Ainv, n, k, col);
+            count_launch(H);
+            count_launch(H);
+        }
     }
     check_cuda(cudaGetLastError(), "gauss-jordan");
     int *hs = (int *)pinned_scratch(1);
