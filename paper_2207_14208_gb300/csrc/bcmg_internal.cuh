@@ -7,9 +7,9 @@
 //   F    FP64 right-hand side: f on interior rows, g on ghost rows (level 0),
 //        restricted residuals on coarse levels
 //   r    FP64 residual (interior, ghost, then extended into the band)
-// Work lists (compacted once at set-up, sorted by node index):
-//   win  64-node windows of one x-row that hold interior nodes: base index,
-//        (j, k) and a 64-bit interior mask; one warp per window
+// Work lists (compacted once at set-up):
+//   ilist interior node indices, red nodes ((i + j + k) even) first, then
+//        black, each colour in increasing index order; one thread per node
 //   ghost list: index, direction/degree code, xi per axis (SoA), Delta tau
 //   band list: index, up to d upwind sources (band position or ghost index)
 //        with normalised weights (SoA)
@@ -28,16 +28,14 @@ namespace bcmg {
 
 enum : uint8_t { CL_INACTIVE = 0, CL_INTERIOR = 1, CL_GHOST = 2, CL_BOXDIR = 3 };
 
-constexpr int kWin = 64;          // nodes per interior window (one warp, 2 per lane)
-constexpr int kWarpsPerBlock = 8; // window kernels: 256 threads
-constexpr int kMaxCoarse = 4096;  // largest coarsest system inverted densely
+constexpr int kMaxCoarse = 4096;   // largest coarsest system inverted densely
+#ifndef BCMG_TAIL_NODES
+#define BCMG_TAIL_NODES 8192
+#endif
+constexpr int kTailNodes = BCMG_TAIL_NODES;  // coarse levels up to this many interior +
+                                             // ghost + band nodes run in the cluster tail
+constexpr int kTailCoarse = 1024;  // largest coarsest system the tail inverts
 constexpr int32_t kNoRef = INT32_MIN;
-
-struct Win {
-    uint32_t base;  // linear index of the window's first node (i0 = 64 m)
-    uint32_t jk;    // j | k << 16
-    uint64_t mask;  // bit t: node base + t is INTERIOR
-};
 
 struct Level {
     int d = 0, N = 0, n = 0;
@@ -46,8 +44,8 @@ struct Level {
     double h = 0.0;
     uint8_t *cls = nullptr;
     int64_t nint = 0, nbox = 0, ng = 0, nb = 0, nclamp = 0, nfall = 0, nact = 0;
-    int64_t nwin = 0;
-    Win *win = nullptr;
+    int64_t nred = 0;            // red interior nodes (head of ilist)
+    uint32_t *ilist = nullptr;  // nint interior node indices, red then black
     // ghosts (SoA)
     uint32_t *gidx = nullptr;
     uint16_t *gcode = nullptr;  // bit a: s_a = -1; bits 3+2a..4+2a: degree q_a
@@ -56,6 +54,10 @@ struct Level {
     double *geta = nullptr;
     double *gn = nullptr;  // 3 * ng, axis-major
     double *gQ = nullptr;  // ng * d, point-major (x, y[, z])
+    // interpolation weights of B at each ghost: 3^d terms (o2 * 3 + o1) * 3
+    // + o0, term-major (gw[term * ng + g]); FP32 copy for the mixed cycle
+    double *gw = nullptr;
+    float *gw32 = nullptr;
     // band (SoA)
     uint32_t *bidx = nullptr;
     int32_t *bref = nullptr;  // 3 * nb, axis-major: >= 0 band position,
@@ -98,6 +100,12 @@ struct Handle {
     cudaGraphExec_t vgraph = nullptr;
     cudaGraphExec_t ngraph = nullptr;  // V-cycle followed by norms
     int64_t vgraph_kernels = 0, ngraph_kernels = 0;
+    // coarse end of the V-cycle on one thread-block cluster: first level (-1:
+    // none), cluster size
+    // and the per-level tables of the FP64 and FP32 cycles
+    int tail_start = -1, tail_cluster = 0;
+    void *tail64 = nullptr, *tail32 = nullptr;
+    int nsm = 152;  // SMs of the device (block sizes of the FP64 kernels)
     bool capturing = false;
     int64_t captured = 0;
     std::vector<void *> allocs;
@@ -128,7 +136,7 @@ int report(int code, const std::string &msg);  // sets the thread's last error
 void setup_hierarchy(Handle &H, const double *phi0);
 double dtau_of(int d, int mode, double cst, double theta);
 bool ext_ell_ok(int d, int K);
-constexpr int kExtCap = 16;  // terms per band node of the expanded extension
+constexpr int kExtCap = 32;  // terms per band node of the expanded extension
 
 // ---- cycle kernels (cycle.cu); T = double (FP64) or float (inner cycles of
 // the mixed-precision refinement) ----------------------------------------
@@ -139,7 +147,11 @@ template <typename T>
 void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero);
 template <typename T> void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf);
 template <typename T> void coarsest_correct(Handle &H, Level &L, T *u, const T *F);
-void norms(Handle &H, Level &L, const double *r, double *out4);
+// finest-level residual r = F - A u and its four norms (out4, device)
+void residual_norms(Handle &H, const double *u, double *out4);
+int64_t norm_parts(const Level &L);  // block partials residual_norms writes
+// ghost weights of every level; the levels of the cluster tail and their tables
+void setup_cycle(Handle &H);
 void vcycle_enqueue(Handle &H, int l, double *u);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,
 // u += correction; r must hold the FP64 residual of u

@@ -160,9 +160,7 @@ void run_vcycle(Handle &H) {
 }
 
 void enqueue_norms(Handle &H) {
-    Level &L = H.L[0];
-    residual(H, L, H.u0, L.F, L.r);
-    norms(H, L, L.r, H.nout);
+    residual_norms(H, H.u0, H.nout);
 }
 
 // add the device time of the profiled sweeps of the last completed cycle
@@ -286,8 +284,8 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         setup_hierarchy(*H, phi_dev);
         Level &L0 = H->L[0];
         H->u0 = (double *)dalloc(*H, sizeof(double) * L0.nn);
-        int64_t nparts = (L0.nwin + kWarpsPerBlock - 1) / kWarpsPerBlock + (L0.ng + 255) / 256 + 1;
-        H->npart = (double *)dalloc(*H, sizeof(double) * 4 * nparts);
+        H->npart = (double *)dalloc(*H, sizeof(double) * 4 * (norm_parts(L0) + 1));
+        setup_cycle(*H);
         H->nout = (double *)dalloc(*H, sizeof(double) * 4);
         check_cuda(cudaMallocHost((void **)&H->nhost, 4 * sizeof(double)), "cudaMallocHost");
         set_interior_rhs(*H, L0, f_dev, L0.F);

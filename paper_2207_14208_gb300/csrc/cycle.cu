@@ -1,11 +1,19 @@
 // Multigrid cycle kernels of the GB300 BCMG library (arXiv 2207.14208).
 //
-// Interior work runs over the compacted 64-node windows (one warp per
-// window, coalesced x-rows, no class reads); ghost and band work over their
-// compacted lists.  Every cycle kernel is templated on the value type: FP64
-// for the plain cycle, FP32 for the inner cycle of the mixed-precision
-// refinement (whose outer residual and update stay FP64).  None of them is a
-// dense contraction, so no tensor-core path is used.
+// Interior work runs over compacted per-colour lists of interior nodes (red
+// then black, increasing index), so every lane of a warp does useful work:
+// on GB300 the FP64 pipe executes whole warp instructions, so idle lanes
+// would cost FP64 throughput.  Ghost and band work runs over their compacted
+// lists.  Every cycle kernel is templated on the value type: FP64 for the
+// plain cycle, FP32 for the inner cycle of the mixed-precision refinement.
+// GB300 executes FP64 at 2 FMA per clock per SM, so FP64 work is spread over
+// all SMs (block sizes shrink on small levels) and kept short (the ghost
+// interpolation weights are tabulated once).  The coarse end of the V-cycle
+// runs as one kernel on a thread-block cluster, its phases separated by the
+// hardware cluster barrier.  None of these kernels is a dense contraction,
+// so no tensor-core path is used.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "bcmg_internal.cuh"
@@ -34,14 +42,42 @@ G2 g2_of(const Level &L) {
 }
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-inline unsigned wblk(int64_t nwin) { return (unsigned)((nwin + kWarpsPerBlock - 1) / kWarpsPerBlock); }
-constexpr int kT = kWarpsPerBlock * 32;
+constexpr int kT = 256;           // largest block of the grid kernels
+constexpr int kTailThreads = 512; // threads per CTA of the cluster tail
+
+// block size for n independent work items: the largest of 256, 128, 64 that
+// still gives every SM about four blocks (FP64 work is spread, not queued)
+int bs_for(const Handle &H, int64_t n) {
+    int bs = kT;
+    while (bs > 64 && (int64_t)nblk(n, bs) < 4 * (int64_t)H.nsm) bs >>= 1;
+    return bs;
+}
+
+// Programmatic dependent launch: every cycle kernel is launched with
+// programmatic stream serialisation, so its CTAs may be scheduled while its
+// predecessor drains; each kernel first waits (griddepcontrol.wait, a
+// hardware dependency wait that returns once the preceding grid has completed
+// and its writes are visible) and then allows its own successor to be
+// scheduled.  Nothing is read or written before the wait.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 template <typename K, typename... A>
 void launch(Handle &H, const char *name, K kern, unsigned grid, unsigned block, A... args) {
     if (grid == 0) return;
-    kern<<<grid, block, 0, H.st>>>(args...);
-    check_cuda(cudaGetLastError(), name);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = H.st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    check_cuda(cudaLaunchKernelEx(&cfg, kern, args...), name);
     count_launch(H);
 }
 
@@ -64,37 +100,44 @@ __device__ __forceinline__ void lagrange(int q, T xi, T w[3]) {
     }
 }
 
-// B u~ at a ghost: the (tri/bi)quadratic interpolant on ST_G at Q (eq. BCh).
-// Fully unrolled with compile-time stencil offsets (weights stay in
-// registers); nodes beyond an axis' degree are never loaded.
+__device__ __forceinline__ void coords(uint32_t X, uint32_t n, int D, int ic[3]) {
+    const uint32_t q = X / n;
+    ic[0] = (int)(X - q * n);
+    if (D == 3) {
+        const uint32_t q2 = q / n;
+        ic[1] = (int)(q - q2 * n);
+        ic[2] = (int)q2;
+    } else {
+        ic[1] = (int)q;
+        ic[2] = 0;
+    }
+}
+
+// B u~ at a ghost: the (tri/bi)quadratic interpolant on ST_G at Q (eq. BCh),
+// with the tensor-product Lagrange weights tabulated per ghost (gw, term
+// (o2 * 3 + o1) * 3 + o0, term-major).  Branch-free: every term's loads are
+// predicated on the term lying within the stencil's degrees, so all of them
+// are in flight together; one partial sum per stencil row.
 template <int D, typename T>
-__device__ __forceinline__ T ghost_B(int64_t X, uint16_t code, const double *__restrict__ gxi, int64_t ng,
-                                     int64_t g, const T *u, const G2 &G) {
+__device__ __forceinline__ T ghost_B(int64_t X, uint16_t code, const T *gw, int64_t ng, int64_t g, const T *u,
+                                     const G2 &G) {
     const int qx = (code >> 3) & 3, qy = (code >> 5) & 3, qz = (D == 3) ? ((code >> 7) & 3) : 0;
     const int64_t ox = (code & 1) ? 1 : -1;
     const int64_t oy = (code & 2) ? G.sy : -G.sy;
     const int64_t oz = (D == 3) ? ((code & 4) ? G.sz : -G.sz) : 0;
-    T wx[3], wy[3], wz[3] = {T(1), T(0), T(0)};
-    lagrange<T>(qx, (T)gxi[g], wx);
-    lagrange<T>(qy, (T)gxi[ng + g], wy);
-    if (D == 3) lagrange<T>(qz, (T)gxi[2 * ng + g], wz);
-    T B = T(0);
+    constexpr int NT = (D == 3) ? 27 : 9;
+    T w[NT], v[NT];
 #pragma unroll
-    for (int o2 = 0; o2 < (D == 3 ? 3 : 1); ++o2) {
-        if (o2 > qz) break;
-#pragma unroll
-        for (int o1 = 0; o1 < 3; ++o1) {
-            if (o1 > qy) break;
-            const T wyz = wz[o2] * wy[o1];
-            const int64_t Y = X + o2 * oz + o1 * oy;
-#pragma unroll
-            for (int o0 = 0; o0 < 3; ++o0) {
-                if (o0 > qx) break;
-                B = fma(wyz * wx[o0], u[Y + o0 * ox], B);
-            }
-        }
+    for (int k = 0; k < NT; ++k) {
+        const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+        const bool p = o0 <= qx && o1 <= qy && o2 <= qz;
+        w[k] = p ? gw[(int64_t)k * ng + g] : T(0);
+        v[k] = p ? u[X + o2 * oz + o1 * oy + o0 * ox] : T(0);
     }
-    return B;
+    T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < NT; ++k) acc[(k / 3) % 3] = fma(w[k], v[k], acc[(k / 3) % 3]);
+    return (acc[0] + acc[1]) + acc[2];
 }
 
 template <int D, typename T>
@@ -104,85 +147,245 @@ __device__ __forceinline__ T nbr_sum(const T *u, int64_t X, const G2 &G) {
     return s;
 }
 
-// ------------------------------------------------------------ smoothing
-// One colour of red-black Gauss-Seidel on interior nodes (eq. GSLEX_2D in
-// red-black order): u_X = (sum of 2d neighbours + h^2 F_X) / (2d).
+// ------------------------------------------------------------ per-node steps
+// red-black Gauss-Seidel update of interior node X (eq. GSLEX_2D in
+// red-black order): u_X = (sum of 2d neighbours + h^2 F_X) / (2d)
 template <int D, typename T>
-__global__ void __launch_bounds__(kT) k_smooth(const Win *__restrict__ win, int64_t nwin, T *u,
-                                               const T *__restrict__ F, G2 G, int color) {
-    int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= nwin) return;
-    const int lane = threadIdx.x & 31;
-    const Win W = win[w];
-    const int par = ((W.jk & 0xffffu) + (W.jk >> 16)) & 1;
-    const int t = 2 * lane + ((color ^ par) & 1);
-    if (!((W.mask >> t) & 1ull)) return;
-    const int64_t X = (int64_t)W.base + t;
+__device__ __forceinline__ void smooth_at(int64_t X, T *u, const T *F, const G2 &G) {
     const T s = nbr_sum<D, T>(u, X, G);
     u[X] = fma((T)G.h2, F[X], s) * (T)G.inv2d;
 }
 
-// Fictitious-time relaxation of all ghosts from the same u (eq. rel with
-// eq. DtauOptTheta; the ghost block of P is diag(1/Delta tau)): new values go
-// to tmp, then k_ghost_scatter writes them.
+// fictitious-time relaxation of ghost g (eq. rel with eq. DtauOptTheta)
 template <int D, typename T>
-__global__ void k_ghost_relax(const uint32_t *__restrict__ gidx, const uint16_t *__restrict__ gcode,
-                              const double *__restrict__ gxi, const double *__restrict__ gdt, int64_t ng,
-                              const T *u, const T *__restrict__ F, T *__restrict__ tmp, G2 G) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
+__device__ __forceinline__ T ghost_new(int64_t g, const uint32_t *gidx, const uint16_t *gcode, const T *gw,
+                                       const double *gdt, int64_t ng, const T *u, const T *F, const G2 &G) {
     const int64_t X = gidx[g];
-    const T B = ghost_B<D, T>(X, gcode[g], gxi, ng, g, u, G);
-    tmp[g] = fma((T)gdt[g], F[X] - B, u[X]);
+    const T B = ghost_B<D, T>(X, gcode[g], gw, ng, g, u, G);
+    return fma((T)gdt[g], F[X] - B, u[X]);
 }
 
-template <typename T>
-__global__ void k_ghost_scatter(const uint32_t *__restrict__ gidx, int64_t ng, const T *__restrict__ tmp,
-                                T *__restrict__ u) {
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    u[gidx[g]] = tmp[g];
-}
-
-// ------------------------------------------------------------ residual
-// r = F - A u on interior rows (eq. Laph) and ghost rows (eq. BCh).
+// interior residual (eq. Laph)
 template <int D, typename T>
-__global__ void __launch_bounds__(kT) k_residual(const Win *__restrict__ win, int64_t nwin, unsigned wblocks,
-                                                 const uint32_t *__restrict__ gidx,
-                                                 const uint16_t *__restrict__ gcode,
-                                                 const double *__restrict__ gxi, int64_t ng,
-                                                 const T *__restrict__ u, const T *__restrict__ F,
-                                                 T *__restrict__ r, G2 G) {
-    if (blockIdx.x < wblocks) {
-        int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-        if (w >= nwin) return;
-        const int lane = threadIdx.x & 31;
-        const Win W = win[w];
+__device__ __forceinline__ T residual_int(int64_t X, const T *u, const T *F, const G2 &G) {
+    const T s = nbr_sum<D, T>(u, X, G);
+    return F[X] - (T(2 * D) * u[X] - s) * (T)G.ih2;
+}
+
+// Restriction (Sec. 2.1 eq. coarseFW, Sec. 3.3.2): FW if all 3^d fine
+// neighbours belong to the coarse node's class family, else the FW-weight
+// average over the family members.  FW weights are the integers 1, 2, 4
+// (, 8) over 4^d; scaling by a power of two is exact.  All 3^d class and
+// residual loads are issued before any of them is used.
+template <int D, typename T>
+__device__ __forceinline__ T restrict_at(const int ic[3], bool interior, const uint8_t *clsf, const T *rf,
+                                         const G2 &Gf) {
+    constexpr int NT = (D == 3) ? 27 : 9;
+    uint8_t c[NT];
+    T v[NT];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = lane + 32 * h;
-            if (!((W.mask >> t) & 1ull)) continue;
-            const int64_t X = (int64_t)W.base + t;
-            const T s = nbr_sum<D, T>(u, X, G);
-            r[X] = F[X] - (T(2 * D) * u[X] - s) * (T)G.ih2;
-        }
-        return;
+    for (int k = 0; k < NT; ++k) {
+        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
+        const int y0 = 2 * ic[0] + ox, y1 = 2 * ic[1] + oy, y2 = 2 * ic[2] + oz;
+        const bool in = y0 >= 0 && y0 <= Gf.N && y1 >= 0 && y1 <= Gf.N && (D == 2 || (y2 >= 0 && y2 <= Gf.N));
+        const int64_t Y = (int64_t)y0 + (int64_t)y1 * Gf.sy + (int64_t)y2 * Gf.sz;
+        c[k] = in ? clsf[Y] : (uint8_t)CL_BOXDIR;  // outside the grid: never in a family
+        v[k] = in ? rf[Y] : T(0);
     }
-    int64_t g = (int64_t)(blockIdx.x - wblocks) * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    const int64_t X = gidx[g];
-    r[X] = F[X] - ghost_B<D, T>(X, gcode[g], gxi, ng, g, u, G);
+    T fw = T(0);
+    int wsum = 0;
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
+        const bool fam = interior ? (c[k] == CL_INTERIOR) : (c[k] == CL_GHOST || c[k] == CL_INACTIVE);
+        const int wi = (ox == 0 ? 2 : 1) * (oy == 0 ? 2 : 1) * ((D == 3 && oz == 0) ? 2 : 1);
+        all = all && fam;
+        if (fam) {
+            fw = fma((T)wi, v[k], fw);
+            wsum += wi;
+        }
+    }
+    if (all) return fw * (D == 3 ? T(1.0 / 64.0) : T(1.0 / 16.0));
+    return wsum > 0 ? fw / (T)wsum : T(0);
 }
 
-// ------------------------------------------------------------ band extension
-// One explicit pseudo-time sweep of dr/dsigma + dr/dn = 0 with upwind
-// differences at the largest stable step: each band value becomes the
-// normalised |n_a|-weighted mean of its upwind ghost / band sources.
+// multilinear prolongation at fine node iy (Sec. 2.1, 3.2, 3.3.2): the 2^k
+// coarse neighbours (k = number of odd coordinates) all weigh 2^-k, so their
+// sum is scaled once; the corner loads are predicated, not branched
+template <int D, typename T>
+__device__ __forceinline__ T prolong_at(const int iy[3], const T *ec, const G2 &Gc) {
+    const int t0 = iy[0] & 1, t1 = iy[1] & 1, t2 = (D == 3) ? (iy[2] & 1) : 0;
+    const int64_t C0 = (int64_t)(iy[0] >> 1) + (int64_t)(iy[1] >> 1) * Gc.sy +
+                       (D == 3 ? (int64_t)(iy[2] >> 1) * Gc.sz : 0);
+    constexpr int NC = (D == 3) ? 8 : 4;
+    T c[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
+        const bool p = b0 <= t0 && b1 <= t1 && b2 <= t2;
+        c[k] = p ? ec[C0 + b0 + b1 * Gc.sy + b2 * Gc.sz] : T(0);
+    }
+    T v = c[0];
+    if (t0) v += c[1];
+    if (t1) {
+        v += c[2];
+        if (t0) v += c[3];
+    }
+    if (D == 3 && t2) {
+        v += c[4];
+        if (t0) v += c[5];
+        if (t1) {
+            v += c[6];
+            if (t0) v += c[7];
+        }
+    }
+    const int k = t0 + t1 + t2;
+    const T scale = k == 0 ? T(1) : k == 1 ? T(0.5) : k == 2 ? T(0.25) : T(0.125);
+    return v * scale;
+}
+
+// band value: the expanded extension (ELL terms of the band node), eight
+// terms per round with predicated loads so that their gathers overlap
 template <typename T>
-__global__ void k_extend(const uint32_t *__restrict__ bidx, const int32_t *__restrict__ bref,
-                         const double *__restrict__ bw, int64_t nb, int d, T *a, const T *__restrict__ in,
-                         T *__restrict__ out, int last) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ T extend_at(int64_t b, const uint8_t *ecnt, const uint32_t *eg, const double *ew,
+                                       int64_t nb, const T *a) {
+    T v = T(0);
+    const int c = ecnt[b];
+    for (int k0 = 0; k0 < c; k0 += 8) {
+        T w[8], x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool p = k0 + j < c;
+            const int64_t e = (int64_t)(k0 + j) * nb + b;
+            w[j] = p ? (T)ew[e] : T(0);
+            x[j] = p ? a[eg[e]] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (k0 + j < c) v = fma(w[j], x[j], v);
+    }
+    return v;
+}
+
+// ------------------------------------------------------------ grid kernels
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_smooth(const uint32_t *__restrict__ list, int64_t n, T *u,
+                                               const T *__restrict__ F, G2 G) {
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) smooth_at<D, T>(list[i], u, F, G);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_ghost_relax(const uint32_t *__restrict__ gidx,
+                                                    const uint16_t *__restrict__ gcode, const T *__restrict__ gw,
+                                                    const double *__restrict__ gdt, int64_t ng, const T *u,
+                                                    const T *__restrict__ F, T *__restrict__ tmp, G2 G) {
+    pdl_begin();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) tmp[g] = ghost_new<D, T>(g, gidx, gcode, gw, gdt, ng, u, F, G);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT) k_ghost_scatter(const uint32_t *__restrict__ gidx, int64_t ng,
+                                                      const T *__restrict__ tmp, T *__restrict__ u) {
+    pdl_begin();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) u[gidx[g]] = tmp[g];
+}
+
+// the block's norm partials (sum r^2, max|r|) of one row class, reduced in
+// a fixed order (warp shuffles, then the block's warps); every thread calls it
+__device__ __forceinline__ void block_partials(double s2, double mx, double *part, int64_t slot, bool interior) {
+    __shared__ double sh[2][kT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+        sh[0][warp] = s2;
+        sh[1][warp] = mx;
+    }
+    __syncthreads();
+    if (warp != 0) return;
+    const int nw = blockDim.x >> 5;
+    s2 = lane < nw ? sh[0][lane] : 0.0;
+    mx = lane < nw ? sh[1][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+        double *p = part + slot * 4;
+        p[0] = interior ? s2 : 0.0;
+        p[1] = interior ? 0.0 : s2;
+        p[2] = interior ? mx : 0.0;
+        p[3] = interior ? 0.0 : mx;
+    }
+}
+
+// r = F - A u on the interior rows (eq. Laph); with part != null also the
+// block's norm partials (slot = block)
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict__ ilist, int64_t nint,
+                                                     const T *__restrict__ u, const T *__restrict__ F,
+                                                     T *__restrict__ r, G2 G, double *__restrict__ part) {
+    pdl_begin();
+    double s2 = 0.0, mx = 0.0;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nint) {
+        const int64_t X = ilist[i];
+        const T v = residual_int<D, T>(X, u, F, G);
+        r[X] = v;
+        s2 = (double)v * (double)v;
+        mx = fabs((double)v);
+    }
+    if (part) block_partials(s2, mx, part, blockIdx.x, true);
+}
+
+// r = g - B u on the ghost rows (eq. BCh); norm partials at slot0 + block
+template <int D, typename T>
+__global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__ gidx,
+                                                    const uint16_t *__restrict__ gcode, const T *__restrict__ gw,
+                                                    int64_t ng, const T *__restrict__ u, const T *__restrict__ F,
+                                                    T *__restrict__ r, G2 G, double *__restrict__ part,
+                                                    int64_t slot0) {
+    pdl_begin();
+    double s2 = 0.0, mx = 0.0;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < ng) {
+        const int64_t X = gidx[g];
+        const T v = F[X] - ghost_B<D, T>(X, gcode[g], gw, ng, g, u, G);
+        r[X] = v;
+        s2 = (double)v * (double)v;
+        mx = fabs((double)v);
+    }
+    if (part) block_partials(s2, mx, part, slot0 + blockIdx.x, false);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kT) k_extend_ell(const uint32_t *__restrict__ bidx,
+                                                   const uint8_t *__restrict__ ecnt,
+                                                   const uint32_t *__restrict__ eg, const double *__restrict__ ew,
+                                                   int64_t nb, T *a) {
+    pdl_begin();
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) a[bidx[b]] = extend_at<T>(b, ecnt, eg, ew, nb, a);
+}
+
+// One explicit pseudo-time sweep of dr/dsigma + dr/dn = 0 with upwind
+// differences at the largest stable step (used when a band node's expanded
+// extension has more than kExtCap terms).
+template <typename T>
+__global__ void __launch_bounds__(kT) k_extend(const uint32_t *__restrict__ bidx, const int32_t *__restrict__ bref,
+                                               const double *__restrict__ bw, int64_t nb, int d, T *a,
+                                               const T *__restrict__ in, T *__restrict__ out, int last) {
+    pdl_begin();
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     T v = T(0);
     for (int ax = 0; ax < d; ++ax) {
@@ -197,151 +400,59 @@ __global__ void k_extend(const uint32_t *__restrict__ bidx, const int32_t *__res
     else out[b] = v;
 }
 
-// All K sweeps at once: band value = sum over the precomputed (ghost, weight)
-// terms of the band node (the expansion of the sweeps started from zero),
-// ELL layout with the terms of one slot contiguous across band nodes.
-template <typename T>
-__global__ void k_extend_ell(const uint32_t *__restrict__ bidx, const uint8_t *__restrict__ ecnt,
-                             const uint32_t *__restrict__ eg, const double *__restrict__ ew, int64_t nb, T *a) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    T v = T(0);
-    const int c = ecnt[b];
-    for (int k = 0; k < c; ++k) v = fma((T)ew[(int64_t)k * nb + b], a[eg[(int64_t)k * nb + b]], v);
-    a[bidx[b]] = v;
-}
-
-// ------------------------------------------------------------ restriction
-// Coarse interior: FW of the fine interior residual if all 3^d fine
-// neighbours are interior, else their FW-weight average over the interior
-// ones.  Coarse ghost: the same with ghost/inactive (extended) fine nodes.
+// F_c from the fine residual on coarse interior nodes (first iblocks) and
+// coarse ghosts; uc (the coarse correction) is zeroed on the same nodes
 template <int D, typename T>
-__device__ __forceinline__ T restrict_at(const int ic[3], bool interior, const uint8_t *__restrict__ clsf,
-                                         const T *__restrict__ rf, const G2 &Gf) {
-    // FW weights as integers (1, 2, 4[, 8]) / 4^d: scaling by a power of two
-    // is exact, so sum(w_int r) / sum(w_int) equals the weighted mean, and the
-    // FW case is sum(w_int r) * 4^-d.
-    T fw = T(0);
-    int wsum = 0;
-    bool all = true;
-#pragma unroll
-    for (int oz = (D == 3 ? -1 : 0); oz <= (D == 3 ? 1 : 0); ++oz)
-#pragma unroll
-        for (int oy = -1; oy <= 1; ++oy)
-#pragma unroll
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int y0 = 2 * ic[0] + ox, y1 = 2 * ic[1] + oy, y2 = 2 * ic[2] + oz;
-                if (y0 < 0 || y0 > Gf.N || y1 < 0 || y1 > Gf.N || (D == 3 && (y2 < 0 || y2 > Gf.N))) {
-                    all = false;
-                    continue;
-                }
-                const int64_t Y = (int64_t)y0 + (int64_t)y1 * Gf.sy + (int64_t)y2 * Gf.sz;
-                const uint8_t c = clsf[Y];
-                const bool fam = interior ? (c == CL_INTERIOR) : (c == CL_GHOST || c == CL_INACTIVE);
-                if (!fam) {
-                    all = false;
-                    continue;
-                }
-                const int wi = (ox == 0 ? 2 : 1) * (oy == 0 ? 2 : 1) * ((D == 3 && oz == 0) ? 2 : 1);
-                fw = fma((T)wi, rf[Y], fw);
-                wsum += wi;
-            }
-    if (all) return fw * (D == 3 ? T(1.0 / 64.0) : T(1.0 / 16.0));
-    return wsum > 0 ? fw / (T)wsum : T(0);
-}
-
-template <int D, typename T>
-__global__ void __launch_bounds__(kT) k_restrict(const Win *__restrict__ win, int64_t nwin, unsigned wblocks,
-                                                 const uint32_t *__restrict__ gidx, int64_t ng,
-                                                 const uint8_t *__restrict__ clsf, const T *__restrict__ rf,
-                                                 T *__restrict__ Fc, T *__restrict__ uc, G2 Gf, G2 Gc) {
-    if (blockIdx.x < wblocks) {
-        int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-        if (w >= nwin) return;
-        const int lane = threadIdx.x & 31;
-        const Win W = win[w];
-        const int j = W.jk & 0xffffu, k = W.jk >> 16;
-        const int i0 = (int)((int64_t)W.base - (int64_t)j * Gc.sy - (int64_t)k * Gc.sz);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = lane + 32 * h;
-            if (!((W.mask >> t) & 1ull)) continue;
-            const int ic[3] = {i0 + t, j, k};
-            const int64_t Xc = (int64_t)W.base + t;
-            Fc[Xc] = restrict_at<D, T>(ic, true, clsf, rf, Gf);
-            if (uc) uc[Xc] = T(0);
-        }
-        return;
+__global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ ilist_c, int64_t nint_c,
+                                                 unsigned iblocks, const uint32_t *__restrict__ gidx_c,
+                                                 int64_t ng_c, const uint8_t *__restrict__ clsf,
+                                                 const T *__restrict__ rf, T *__restrict__ Fc, T *__restrict__ uc,
+                                                 G2 Gf, G2 Gc) {
+    pdl_begin();
+    uint32_t Xc;
+    bool interior;
+    if (blockIdx.x < iblocks) {
+        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= nint_c) return;
+        Xc = ilist_c[i];
+        interior = true;
+    } else {
+        const int64_t g = (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
+        if (g >= ng_c) return;
+        Xc = gidx_c[g];
+        interior = false;
     }
-    int64_t g = (int64_t)(blockIdx.x - wblocks) * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    const uint32_t Xc = gidx[g];
-    const uint32_t n = (uint32_t)Gc.n;
     int ic[3];
-    ic[0] = (int)(Xc % n);
-    ic[1] = (int)((Xc / n) % n);
-    ic[2] = (D == 3) ? (int)(Xc / (n * n)) : 0;
-    Fc[Xc] = restrict_at<D, T>(ic, false, clsf, rf, Gf);
+    coords(Xc, (uint32_t)Gc.n, D, ic);
+    Fc[Xc] = restrict_at<D, T>(ic, interior, clsf, rf, Gf);
     if (uc) uc[Xc] = T(0);
 }
 
-// ------------------------------------------------------------ prolongation
 template <int D, typename T>
-__device__ __forceinline__ T prolong_at(const int iy[3], const T *__restrict__ ec, const G2 &Gc) {
-    int lo[3] = {0, 0, 0}, two[3] = {0, 0, 0};
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        lo[a] = iy[a] >> 1;
-        two[a] = iy[a] & 1;
-    }
-    T v = T(0);
-    for (int b2 = 0; b2 <= two[2]; ++b2)
-        for (int b1 = 0; b1 <= two[1]; ++b1)
-            for (int b0 = 0; b0 <= two[0]; ++b0) {
-                const T w = (two[0] ? T(0.5) : T(1)) * (two[1] ? T(0.5) : T(1)) * (two[2] ? T(0.5) : T(1));
-                const int64_t C = (int64_t)(lo[0] + b0) + (int64_t)(lo[1] + b1) * Gc.sy + (int64_t)(lo[2] + b2) * Gc.sz;
-                v = fma(w, ec[C], v);
-            }
-    return v;
-}
-
-template <int D, typename T>
-__global__ void __launch_bounds__(kT) k_prolong(const Win *__restrict__ win, int64_t nwin, unsigned wblocks,
+__global__ void __launch_bounds__(kT) k_prolong(const uint32_t *__restrict__ ilist, int64_t nint, unsigned iblocks,
                                                 const uint32_t *__restrict__ gidx, int64_t ng,
                                                 const T *__restrict__ ec, T *__restrict__ uf, G2 Gf, G2 Gc) {
-    if (blockIdx.x < wblocks) {
-        int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-        if (w >= nwin) return;
-        const int lane = threadIdx.x & 31;
-        const Win W = win[w];
-        const int j = W.jk & 0xffffu, k = W.jk >> 16;
-        const int i0 = (int)((int64_t)W.base - (int64_t)j * Gf.sy - (int64_t)k * Gf.sz);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = lane + 32 * h;
-            if (!((W.mask >> t) & 1ull)) continue;
-            const int iy[3] = {i0 + t, j, k};
-            const int64_t X = (int64_t)W.base + t;
-            uf[X] += prolong_at<D, T>(iy, ec, Gc);
-        }
-        return;
+    pdl_begin();
+    uint32_t X;
+    if (blockIdx.x < iblocks) {
+        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= nint) return;
+        X = ilist[i];
+    } else {
+        const int64_t g = (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
+        if (g >= ng) return;
+        X = gidx[g];
     }
-    int64_t g = (int64_t)(blockIdx.x - wblocks) * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    const uint32_t X = gidx[g];
-    const uint32_t n = (uint32_t)Gf.n;
     int iy[3];
-    iy[0] = (int)(X % n);
-    iy[1] = (int)((X / n) % n);
-    iy[2] = (D == 3) ? (int)(X / (n * n)) : 0;
+    coords(X, (uint32_t)Gf.n, D, iy);
     uf[X] += prolong_at<D, T>(iy, ec, Gc);
 }
 
-// ------------------------------------------------------------ coarsest
 template <typename T>
 __global__ void k_coarse_gather(const uint32_t *__restrict__ act, int64_t nact, const T *__restrict__ r,
                                 double *__restrict__ rhs) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_begin();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < nact) rhs[j] = (double)r[act[j]];
 }
 
@@ -350,7 +461,8 @@ template <typename T>
 __global__ void __launch_bounds__(kT) k_coarse_gemv(const uint32_t *__restrict__ act, int64_t nact,
                                                     const double *__restrict__ Ainv,
                                                     const double *__restrict__ rhs, T *__restrict__ u) {
-    int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (i >= nact) return;
     const int lane = threadIdx.x & 31;
     double s = 0.0;
@@ -360,56 +472,11 @@ __global__ void __launch_bounds__(kT) k_coarse_gemv(const uint32_t *__restrict__
     if (lane == 0) u[act[i]] += (T)s;
 }
 
-// ------------------------------------------------------------ norms
-// Per-block partial sums (sum r_I^2, sum r_G^2, max|r_I|, max|r_G|) in a
-// fixed tree order; a single block then reduces the partials in block order.
-__global__ void __launch_bounds__(kT) k_norm_partial(const Win *__restrict__ win, int64_t nwin, unsigned wblocks,
-                                                     const uint32_t *__restrict__ gidx, int64_t ng,
-                                                     const double *__restrict__ r, double *__restrict__ part) {
-    __shared__ double sh[4][kT];
-    double sI = 0.0, sG = 0.0, mI = 0.0, mG = 0.0;
-    if (blockIdx.x < wblocks) {
-        int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-        if (w < nwin) {
-            const int lane = threadIdx.x & 31;
-            const Win W = win[w];
-            for (int h = 0; h < 2; ++h) {
-                const int t = lane + 32 * h;
-                if ((W.mask >> t) & 1ull) {
-                    const double v = r[(int64_t)W.base + t];
-                    sI = fma(v, v, sI);
-                    mI = fmax(mI, fabs(v));
-                }
-            }
-        }
-    } else {
-        int64_t g = (int64_t)(blockIdx.x - wblocks) * blockDim.x + threadIdx.x;
-        if (g < ng) {
-            const double v = r[gidx[g]];
-            sG = v * v;
-            mG = fabs(v);
-        }
-    }
-    sh[0][threadIdx.x] = sI;
-    sh[1][threadIdx.x] = sG;
-    sh[2][threadIdx.x] = mI;
-    sh[3][threadIdx.x] = mG;
-    __syncthreads();
-    for (int s = kT / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
-            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
-            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + s]);
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x < 4) part[(int64_t)blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
-}
-
+// reduce the residual kernel's block partials in block order (deterministic)
 __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ part, int64_t nparts,
                                                      double *__restrict__ out) {
-    __shared__ double sh[4][1024];
+    pdl_begin();
+    __shared__ double sh[4][32];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t i = threadIdx.x; i < nparts; i += blockDim.x) {
         a[0] += part[i * 4 + 0];
@@ -417,120 +484,253 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ 
         a[2] = fmax(a[2], part[i * 4 + 2]);
         a[3] = fmax(a[3], part[i * 4 + 3]);
     }
-    for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
-            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
-            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + s]);
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a[0] += __shfl_down_sync(0xffffffffu, a[0], o);
+        a[1] += __shfl_down_sync(0xffffffffu, a[1], o);
+        a[2] = fmax(a[2], __shfl_down_sync(0xffffffffu, a[2], o));
+        a[3] = fmax(a[3], __shfl_down_sync(0xffffffffu, a[3], o));
     }
-    if (threadIdx.x == 0) {
-        out[0] = sqrt(sh[0][0]);
-        out[1] = sqrt(sh[1][0]);
-        out[2] = sh[2][0];
-        out[3] = sh[3][0];
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) sh[q][warp] = a[q];
+    __syncthreads();
+    if (warp != 0) return;
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < 4; ++q) a[q] = lane < nw ? sh[q][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a[0] += __shfl_down_sync(0xffffffffu, a[0], o);
+        a[1] += __shfl_down_sync(0xffffffffu, a[1], o);
+        a[2] = fmax(a[2], __shfl_down_sync(0xffffffffu, a[2], o));
+        a[3] = fmax(a[3], __shfl_down_sync(0xffffffffu, a[3], o));
+    }
+    if (lane == 0) {
+        out[0] = sqrt(a[0]);
+        out[1] = sqrt(a[1]);
+        out[2] = a[2];
+        out[3] = a[3];
+    }
+}
+
+// tensor-product Lagrange weights of every ghost's interpolation stencil
+// (eq. BCh), all levels in one launch; FP32 copies for the mixed cycle
+struct GwTab {
+    const uint16_t *gcode;
+    const double *gxi;
+    int64_t ng;
+    double *gw;
+    float *gw32;
+    int64_t blk;  // first block of this level
+};
+
+__global__ void __launch_bounds__(kT) k_ghost_weights(const GwTab *__restrict__ tab, int nl, int d) {
+    pdl_begin();
+    int l = 0;
+    for (int i = 1; i < nl; ++i)
+        if ((int64_t)blockIdx.x >= tab[i].blk) l = i;
+    const GwTab &t = tab[l];
+    const int64_t g = ((int64_t)blockIdx.x - t.blk) * blockDim.x + threadIdx.x;
+    if (g >= t.ng) return;
+    const uint16_t code = t.gcode[g];
+    double w[3][3];
+    for (int a = 0; a < 3; ++a) {
+        if (a < d) lagrange<double>((code >> (3 + 2 * a)) & 3, t.gxi[(int64_t)a * t.ng + g], w[a]);
+        else {
+            w[a][0] = 1.0;
+            w[a][1] = 0.0;
+            w[a][2] = 0.0;
+        }
+    }
+    const int n2 = d == 3 ? 3 : 1;
+    for (int o2 = 0; o2 < n2; ++o2)
+        for (int o1 = 0; o1 < 3; ++o1)
+            for (int o0 = 0; o0 < 3; ++o0) {
+                const double v = __dmul_rn(__dmul_rn(w[2][o2], w[1][o1]), w[0][o0]);
+                const int64_t k = (int64_t)((o2 * 3 + o1) * 3 + o0) * t.ng + g;
+                t.gw[k] = v;
+                if (t.gw32) t.gw32[k] = (float)v;
+            }
+}
+
+// ------------------------------------------------------------ coarse tail
+// Levels tail[0..nl-1] (the last one is the coarsest) of the V-cycle in one
+// launch on one thread-block cluster: the same per-node steps as the grid
+// kernels, every thread of the cluster striding over each phase's nodes, the
+// phases separated by the cluster barrier (release / acquire at cluster
+// scope, so global writes of one CTA are seen by the others).  Every thread
+// reaches every barrier.
+template <typename T>
+struct TailLevel {
+    G2 g;
+    const uint32_t *ilist;
+    int64_t nred, nint;
+    const uint32_t *gidx;
+    const uint16_t *gcode;
+    const T *gw;
+    const double *gdt;
+    int64_t ng;
+    const uint32_t *bidx;
+    const uint8_t *ecnt;
+    const uint32_t *eg;
+    const double *ew;
+    int64_t nb;
+    const uint8_t *cls;
+    T *u, *F, *r, *gtmp;
+    const uint32_t *act;
+    int64_t nact;
+    const double *Ainv;
+    double *crhs;
+};
+
+namespace cg = cooperative_groups;
+
+struct TailCtx {
+    int64_t tid, nthr;
+};
+
+__device__ __forceinline__ void tail_sync() { cg::this_cluster().sync(); }
+
+template <int D, typename T>
+__device__ void tail_smooth(const TailCtx &c, const TailLevel<T> &A, int nsteps) {
+    for (int s = 0; s < nsteps; ++s) {
+        for (int64_t i = c.tid; i < A.nred; i += c.nthr) smooth_at<D, T>(A.ilist[i], A.u, A.F, A.g);
+        tail_sync();
+        for (int64_t i = A.nred + c.tid; i < A.nint; i += c.nthr) smooth_at<D, T>(A.ilist[i], A.u, A.F, A.g);
+        tail_sync();
+        for (int64_t g = c.tid; g < A.ng; g += c.nthr)
+            A.gtmp[g] = ghost_new<D, T>(g, A.gidx, A.gcode, A.gw, A.gdt, A.ng, A.u, A.F, A.g);
+        tail_sync();
+        for (int64_t g = c.tid; g < A.ng; g += c.nthr) A.u[A.gidx[g]] = A.gtmp[g];
+        tail_sync();
+    }
+}
+
+template <int D, typename T>
+__device__ void tail_residual(const TailCtx &c, const TailLevel<T> &A) {
+    for (int64_t i = c.tid; i < A.nint; i += c.nthr) {
+        const int64_t X = A.ilist[i];
+        A.r[X] = residual_int<D, T>(X, A.u, A.F, A.g);
+    }
+    for (int64_t g = c.tid; g < A.ng; g += c.nthr) {
+        const int64_t X = A.gidx[g];
+        A.r[X] = A.F[X] - ghost_B<D, T>(X, A.gcode[g], A.gw, A.ng, g, A.u, A.g);
+    }
+    tail_sync();
+}
+
+template <typename T>
+__device__ void tail_extend(const TailCtx &c, const TailLevel<T> &A, T *a) {
+    for (int64_t b = c.tid; b < A.nb; b += c.nthr) a[A.bidx[b]] = extend_at<T>(b, A.ecnt, A.eg, A.ew, A.nb, a);
+    tail_sync();
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ tl, int nl, int nu1,
+                                                       int nu2) {
+    pdl_begin();
+    TailCtx c;
+    c.tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // the grid is one cluster
+    c.nthr = (int64_t)gridDim.x * blockDim.x;
+    for (int l = 0; l + 1 < nl; ++l) {
+        const TailLevel<T> &A = tl[l], &B = tl[l + 1];
+        tail_smooth<D, T>(c, A, nu1);
+        tail_residual<D, T>(c, A);
+        tail_extend<T>(c, A, A.r);
+        for (int64_t i = c.tid; i < B.nint + B.ng; i += c.nthr) {
+            const bool interior = i < B.nint;
+            const uint32_t Xc = interior ? B.ilist[i] : B.gidx[i - B.nint];
+            int ic[3];
+            coords(Xc, (uint32_t)B.g.n, D, ic);
+            B.F[Xc] = restrict_at<D, T>(ic, interior, A.cls, A.r, A.g);
+            B.u[Xc] = T(0);
+        }
+        tail_sync();
+    }
+    {
+        const TailLevel<T> &C = tl[nl - 1];
+        tail_residual<D, T>(c, C);
+        for (int64_t j = c.tid; j < C.nact; j += c.nthr) C.crhs[j] = (double)C.r[C.act[j]];
+        tail_sync();
+        const int lane = threadIdx.x & 31;
+        for (int64_t i = c.tid >> 5; i < C.nact; i += c.nthr >> 5) {
+            double s = 0.0;
+            for (int64_t j = lane; j < C.nact; j += 32) s = fma(C.Ainv[i * C.nact + j], C.crhs[j], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (lane == 0) C.u[C.act[i]] += (T)s;
+        }
+        tail_sync();
+    }
+    for (int l = nl - 2; l >= 0; --l) {
+        const TailLevel<T> &A = tl[l], &B = tl[l + 1];
+        tail_extend<T>(c, B, B.u);
+        for (int64_t i = c.tid; i < A.nint + A.ng; i += c.nthr) {
+            const uint32_t X = (i < A.nint) ? A.ilist[i] : A.gidx[i - A.nint];
+            int iy[3];
+            coords(X, (uint32_t)A.g.n, D, iy);
+            A.u[X] += prolong_at<D, T>(iy, B.u, B.g);
+        }
+        tail_sync();
+        tail_smooth<D, T>(c, A, nu2);
     }
 }
 
 // ------------------------------------------------------------ mixed precision
 // Start of one refinement step on the finest level: the FP32 right-hand side
 // is the FP64 residual rounded to FP32, the FP32 correction starts at zero.
-__global__ void __launch_bounds__(kT) k_ir_begin(const Win *__restrict__ win, int64_t nwin, unsigned wblocks,
+__global__ void __launch_bounds__(kT) k_ir_begin(const uint32_t *__restrict__ ilist, int64_t nint,
                                                  const uint32_t *__restrict__ gidx, int64_t ng,
                                                  const double *__restrict__ r, float *__restrict__ F32,
                                                  float *__restrict__ e32) {
-    if (blockIdx.x < wblocks) {
-        int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-        if (w >= nwin) return;
-        const int lane = threadIdx.x & 31;
-        const Win W = win[w];
-        for (int h = 0; h < 2; ++h) {
-            const int t = lane + 32 * h;
-            if ((W.mask >> t) & 1ull) {
-                const int64_t X = (int64_t)W.base + t;
-                F32[X] = (float)r[X];
-                e32[X] = 0.0f;
-            }
-        }
-        return;
-    }
-    int64_t g = (int64_t)(blockIdx.x - wblocks) * blockDim.x + threadIdx.x;
-    if (g < ng) {
-        const int64_t X = gidx[g];
-        F32[X] = (float)r[X];
-        e32[X] = 0.0f;
-    }
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nint + ng) return;
+    const int64_t X = (i < nint) ? ilist[i] : gidx[i - nint];
+    F32[X] = (float)r[X];
+    e32[X] = 0.0f;
 }
 
 // End of a refinement step: u += e on interior and ghost nodes (FP64).
-__global__ void __launch_bounds__(kT) k_ir_update(const Win *__restrict__ win, int64_t nwin, unsigned wblocks,
+__global__ void __launch_bounds__(kT) k_ir_update(const uint32_t *__restrict__ ilist, int64_t nint,
                                                   const uint32_t *__restrict__ gidx, int64_t ng,
                                                   const float *__restrict__ e32, double *__restrict__ u) {
-    if (blockIdx.x < wblocks) {
-        int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-        if (w >= nwin) return;
-        const int lane = threadIdx.x & 31;
-        const Win W = win[w];
-        for (int h = 0; h < 2; ++h) {
-            const int t = lane + 32 * h;
-            if ((W.mask >> t) & 1ull) {
-                const int64_t X = (int64_t)W.base + t;
-                u[X] += (double)e32[X];
-            }
-        }
-        return;
-    }
-    int64_t g = (int64_t)(blockIdx.x - wblocks) * blockDim.x + threadIdx.x;
-    if (g < ng) {
-        const int64_t X = gidx[g];
-        u[X] += (double)e32[X];
-    }
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nint + ng) return;
+    const int64_t X = (i < nint) ? ilist[i] : gidx[i - nint];
+    u[X] += (double)e32[X];
 }
 
 // ------------------------------------------------------------ data movement
-__global__ void __launch_bounds__(kT) k_copy_active(const Win *__restrict__ win, int64_t nwin, unsigned wblocks,
-                                                    const uint32_t *__restrict__ gidx, int64_t ng, unsigned gblocks,
+__global__ void __launch_bounds__(kT) k_copy_active(const uint32_t *__restrict__ ilist, int64_t nint,
+                                                    const uint32_t *__restrict__ gidx, int64_t ng,
                                                     const uint32_t *__restrict__ box, int64_t nbox,
                                                     const double *__restrict__ src, double *__restrict__ dst) {
-    if (blockIdx.x < wblocks) {
-        int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-        if (w >= nwin) return;
-        const int lane = threadIdx.x & 31;
-        const Win W = win[w];
-        for (int h = 0; h < 2; ++h) {
-            const int t = lane + 32 * h;
-            if ((W.mask >> t) & 1ull) dst[(int64_t)W.base + t] = src[(int64_t)W.base + t];
-        }
-        return;
-    }
-    if (blockIdx.x < wblocks + gblocks) {
-        int64_t g = (int64_t)(blockIdx.x - wblocks) * blockDim.x + threadIdx.x;
-        if (g < ng) dst[gidx[g]] = src[gidx[g]];
-        return;
-    }
-    int64_t b = (int64_t)(blockIdx.x - wblocks - gblocks) * blockDim.x + threadIdx.x;
-    if (b < nbox) dst[box[b]] = src[box[b]];
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nint + ng + nbox) return;
+    int64_t X;
+    if (i < nint) X = ilist[i];
+    else if (i < nint + ng) X = gidx[i - nint];
+    else X = box[i - nint - ng];
+    dst[X] = src[X];
 }
 
 __global__ void k_scatter_ghosts(const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ g,
                                  double *__restrict__ F) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ng) F[gidx[i]] = g[i];
 }
 
-__global__ void __launch_bounds__(kT) k_set_interior(const Win *__restrict__ win, int64_t nwin,
+__global__ void __launch_bounds__(kT) k_set_interior(const uint32_t *__restrict__ ilist, int64_t nint,
                                                      const double *__restrict__ f, double *__restrict__ F) {
-    int64_t w = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    if (w >= nwin) return;
-    const int lane = threadIdx.x & 31;
-    const Win W = win[w];
-    for (int h = 0; h < 2; ++h) {
-        const int t = lane + 32 * h;
-        if ((W.mask >> t) & 1ull) F[(int64_t)W.base + t] = f ? f[(int64_t)W.base + t] : 0.0;
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nint) {
+        const int64_t X = ilist[i];
+        F[X] = f ? f[X] : 0.0;
     }
 }
 
@@ -542,6 +742,7 @@ template <> struct Arr<double> {
     static double *r(Level &L) { return L.r; }
     static double *gtmp(Level &L) { return L.gtmp; }
     static double *bbuf(Level &L) { return L.bbuf; }
+    static const double *gw(const Level &L) { return L.gw; }
 };
 template <> struct Arr<float> {
     static float *u(Level &L) { return L.u32; }
@@ -549,13 +750,21 @@ template <> struct Arr<float> {
     static float *r(Level &L) { return L.r32; }
     static float *gtmp(Level &L) { return L.gtmp32; }
     static float *bbuf(Level &L) { return L.bbuf32; }
+    static const float *gw(const Level &L) { return L.gw32; }
 };
+
+template <typename T>
+void run_tail(Handle &H);
 
 template <typename T>
 void vcycle_t(Handle &H, int l, T *u) {
     Level &A = H.L[l];
     if (l == (int)H.L.size() - 1) {
         coarsest_correct<T>(H, A, u, Arr<T>::F(A));
+        return;
+    }
+    if (l > 0 && l == H.tail_start) {
+        run_tail<T>(H);
         return;
     }
     Level &B = H.L[l + 1];
@@ -569,6 +778,89 @@ void vcycle_t(Handle &H, int l, T *u) {
     smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu2);
 }
 
+template <typename T>
+TailLevel<T> tail_level(Level &L) {
+    TailLevel<T> t;
+    t.g = g2_of(L);
+    t.ilist = L.ilist;
+    t.nred = L.nred;
+    t.nint = L.nint;
+    t.gidx = L.gidx;
+    t.gcode = L.gcode;
+    t.gw = Arr<T>::gw(L);
+    t.gdt = L.gdt;
+    t.ng = L.ng;
+    t.bidx = L.bidx;
+    t.ecnt = L.ecnt;
+    t.eg = L.eg;
+    t.ew = L.ew;
+    t.nb = L.nb;
+    t.cls = L.cls;
+    t.u = Arr<T>::u(L);
+    t.F = Arr<T>::F(L);
+    t.r = Arr<T>::r(L);
+    t.gtmp = Arr<T>::gtmp(L);
+    t.act = L.act;
+    t.nact = L.nact;
+    t.Ainv = L.Ainv;
+    t.crhs = L.crhs;
+    return t;
+}
+
+template <typename T>
+using TailKernel = void (*)(const TailLevel<T> *, int, int, int);
+
+template <typename T>
+TailKernel<T> tail_kernel(int d) {
+    return d == 3 ? k_tail<3, T> : k_tail<2, T>;
+}
+
+cudaLaunchConfig_t tail_config(Handle &H, int csize, cudaLaunchAttribute *at, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)csize, 1, 1);
+    cfg.blockDim = dim3(kTailThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = H.st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 2 : 1;
+    return cfg;
+}
+
+// largest cluster (16, else 8) of kTailThreads-thread CTAs that the device
+// can place; 0 if none
+template <typename T>
+int tail_cluster_size(Handle &H) {
+    TailKernel<T> k = tail_kernel<T>(H.d);
+    for (int cs : {16, 8}) {
+        if (cs > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaLaunchAttribute at[2];
+        cudaLaunchConfig_t cfg = tail_config(H, cs, at, false);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n >= 1) return cs;
+        (void)cudaGetLastError();
+    }
+    return 0;
+}
+
+template <typename T>
+void run_tail(Handle &H) {
+    const int nl = (int)H.L.size() - H.tail_start;
+    const TailLevel<T> *tab = (const TailLevel<T> *)(sizeof(T) == 8 ? H.tail64 : H.tail32);
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = tail_config(H, H.tail_cluster, at, true);
+    check_cuda(cudaLaunchKernelEx(&cfg, tail_kernel<T>(H.d), tab, nl, H.o.nu1, H.o.nu2), "k_tail");
+    count_launch(H);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ host wrappers
@@ -577,43 +869,66 @@ template <typename T>
 void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps) {
     const G2 G = g2_of(L);
     T *tmp = Arr<T>::gtmp(L);
+    const T *gw = Arr<T>::gw(L);
     // the timed sweeps are the finest-level ones of the solve's working precision
     const bool prof = (sizeof(T) == 8) == (H.o.precision == BCMG_PREC_FP64);
+    const int64_t nblack = L.nint - L.nred;
+    const int bg = bs_for(H, L.ng);
     for (int s = 0; s < nsteps; ++s) {
         for (int c = 0; c < 2; ++c) {
+            const uint32_t *list = L.ilist + (c ? L.nred : 0);
+            const int64_t n = c ? nblack : L.nred;
+            const int bs = bs_for(H, n);
             if (prof) profile_mark(H, L);
-            if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, wblk(L.nwin), kT, L.win, L.nwin, u, F, G, c);
-            else launch(H, "k_smooth", k_smooth<2, T>, wblk(L.nwin), kT, L.win, L.nwin, u, F, G, c);
+            if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, G);
+            else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, G);
             if (prof) profile_mark(H, L);
         }
         if (L.d == 3)
-            launch(H, "k_ghost_relax", k_ghost_relax<3, T>, nblk(L.ng, 128), 128, L.gidx, L.gcode, L.gxi, L.gdt,
-                   L.ng, (const T *)u, F, tmp, G);
+            launch(H, "k_ghost_relax", k_ghost_relax<3, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
+                   (const uint16_t *)L.gcode, gw, (const double *)L.gdt, L.ng, (const T *)u, F, tmp, G);
         else
-            launch(H, "k_ghost_relax", k_ghost_relax<2, T>, nblk(L.ng, 128), 128, L.gidx, L.gcode, L.gxi, L.gdt,
-                   L.ng, (const T *)u, F, tmp, G);
-        launch(H, "k_ghost_scatter", k_ghost_scatter<T>, nblk(L.ng, 256), 256, L.gidx, L.ng, (const T *)tmp, u);
+            launch(H, "k_ghost_relax", k_ghost_relax<2, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
+                   (const uint16_t *)L.gcode, gw, (const double *)L.gdt, L.ng, (const T *)u, F, tmp, G);
+        launch(H, "k_ghost_scatter", k_ghost_scatter<T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, L.ng,
+               (const T *)tmp, u);
     }
+}
+
+// interior rows, then ghost rows (separate kernels: the ghost stencil's
+// registers would otherwise limit the occupancy of the interior rows);
+// returns the number of norm partials written
+template <typename T>
+static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, double *part) {
+    const G2 G = g2_of(L);
+    const int bi = bs_for(H, L.nint), bg = bs_for(H, L.ng);
+    const int64_t ni = nblk(L.nint, bi);
+    const T *gw = Arr<T>::gw(L);
+    if (L.d == 3) {
+        launch(H, "k_residual_int", k_residual_int<3, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
+               r, G, part);
+        launch(H, "k_residual_gh", k_residual_gh<3, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
+               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni);
+    } else {
+        launch(H, "k_residual_int", k_residual_int<2, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
+               r, G, part);
+        launch(H, "k_residual_gh", k_residual_gh<2, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
+               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni);
+    }
+    return ni + nblk(L.ng, bg);
 }
 
 template <typename T>
 void residual(Handle &H, Level &L, const T *u, const T *F, T *r) {
-    const G2 G = g2_of(L);
-    const unsigned wb = wblk(L.nwin);
-    const unsigned grid = wb + nblk(L.ng, kT);
-    if (L.d == 3)
-        launch(H, "k_residual", k_residual<3, T>, grid, kT, L.win, L.nwin, wb, L.gidx, L.gcode, L.gxi, L.ng, u, F,
-               r, G);
-    else
-        launch(H, "k_residual", k_residual<2, T>, grid, kT, L.win, L.nwin, wb, L.gidx, L.gcode, L.gxi, L.ng, u, F,
-               r, G);
+    residual_impl<T>(H, L, u, F, r, nullptr);
 }
 
 template <typename T>
 void extend(Handle &H, Level &L, T *a) {
     if (L.nb == 0) return;
+    const int bs = bs_for(H, L.nb);
     if (L.ecnt) {
-        launch(H, "k_extend_ell", k_extend_ell<T>, nblk(L.nb, 256), 256, (const uint32_t *)L.bidx,
+        launch(H, "k_extend_ell", k_extend_ell<T>, nblk(L.nb, bs), bs, (const uint32_t *)L.bidx,
                (const uint8_t *)L.ecnt, (const uint32_t *)L.eg, (const double *)L.ew, L.nb, a);
         return;
     }
@@ -623,7 +938,8 @@ void extend(Handle &H, Level &L, T *a) {
     for (int k = 0; k < K; ++k) {
         const int last = (k == K - 1);
         T *out = (k % 2 == 0) ? b0 : b1;
-        launch(H, "k_extend", k_extend<T>, nblk(L.nb, 256), 256, L.bidx, L.bref, L.bw, L.nb, L.d, a, in, out, last);
+        launch(H, "k_extend", k_extend<T>, nblk(L.nb, bs), bs, (const uint32_t *)L.bidx, (const int32_t *)L.bref,
+               (const double *)L.bw, L.nb, L.d, a, in, out, last);
         in = out;
     }
 }
@@ -631,42 +947,50 @@ void extend(Handle &H, Level &L, T *a) {
 template <typename T>
 void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero) {
     const G2 Gf = g2_of(Lf), Gc = g2_of(Lc);
-    const unsigned wb = wblk(Lc.nwin);
-    const unsigned grid = wb + nblk(Lc.ng, kT);
+    const int bs = bs_for(H, Lc.nint + Lc.ng);
+    const unsigned ib = nblk(Lc.nint, bs);
+    const unsigned grid = ib + nblk(Lc.ng, bs);
     if (Lf.d == 3)
-        launch(H, "k_restrict", k_restrict<3, T>, grid, kT, Lc.win, Lc.nwin, wb, Lc.gidx, Lc.ng,
-               (const uint8_t *)Lf.cls, rf, Fc, uc_zero, Gf, Gc);
+        launch(H, "k_restrict", k_restrict<3, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint8_t *)Lf.cls, rf, Fc, uc_zero, Gf, Gc);
     else
-        launch(H, "k_restrict", k_restrict<2, T>, grid, kT, Lc.win, Lc.nwin, wb, Lc.gidx, Lc.ng,
-               (const uint8_t *)Lf.cls, rf, Fc, uc_zero, Gf, Gc);
+        launch(H, "k_restrict", k_restrict<2, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint8_t *)Lf.cls, rf, Fc, uc_zero, Gf, Gc);
 }
 
 template <typename T>
 void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf) {
     const G2 Gf = g2_of(Lf), Gc = g2_of(Lc);
-    const unsigned wb = wblk(Lf.nwin);
-    const unsigned grid = wb + nblk(Lf.ng, kT);
+    const int bs = bs_for(H, Lf.nint + Lf.ng);
+    const unsigned ib = nblk(Lf.nint, bs);
+    const unsigned grid = ib + nblk(Lf.ng, bs);
     if (Lf.d == 3)
-        launch(H, "k_prolong", k_prolong<3, T>, grid, kT, Lf.win, Lf.nwin, wb, Lf.gidx, Lf.ng, ec, uf, Gf, Gc);
+        launch(H, "k_prolong", k_prolong<3, T>, grid, bs, (const uint32_t *)Lf.ilist, Lf.nint, ib,
+               (const uint32_t *)Lf.gidx, Lf.ng, ec, uf, Gf, Gc);
     else
-        launch(H, "k_prolong", k_prolong<2, T>, grid, kT, Lf.win, Lf.nwin, wb, Lf.gidx, Lf.ng, ec, uf, Gf, Gc);
+        launch(H, "k_prolong", k_prolong<2, T>, grid, bs, (const uint32_t *)Lf.ilist, Lf.nint, ib,
+               (const uint32_t *)Lf.gidx, Lf.ng, ec, uf, Gf, Gc);
 }
 
 template <typename T>
 void coarsest_correct(Handle &H, Level &L, T *u, const T *F) {
     residual<T>(H, L, u, F, Arr<T>::r(L));
-    launch(H, "k_coarse_gather", k_coarse_gather<T>, nblk(L.nact, 256), 256, L.act, L.nact,
+    launch(H, "k_coarse_gather", k_coarse_gather<T>, nblk(L.nact, 64), 64, (const uint32_t *)L.act, L.nact,
            (const T *)Arr<T>::r(L), L.crhs);
-    launch(H, "k_coarse_gemv", k_coarse_gemv<T>, wblk(L.nact), kT, L.act, L.nact, (const double *)L.Ainv,
-           (const double *)L.crhs, u);
+    launch(H, "k_coarse_gemv", k_coarse_gemv<T>, nblk(L.nact, 2), 64, (const uint32_t *)L.act, L.nact,
+           (const double *)L.Ainv, (const double *)L.crhs, u);
 }
 
-void norms(Handle &H, Level &L, const double *r, double *out4) {
-    const unsigned wb = wblk(L.nwin);
-    const unsigned grid = wb + nblk(L.ng, kT);
-    launch(H, "k_norm_partial", k_norm_partial, grid, kT, L.win, L.nwin, wb, L.gidx, L.ng, r, H.npart);
-    launch(H, "k_norm_final", k_norm_final, 1u, 1024u, (const double *)H.npart, (int64_t)grid, out4);
+// residual of the finest level and its four norms (one fused pass + a
+// single-block reduction of the block partials)
+void residual_norms(Handle &H, const double *u, double *out4) {
+    Level &L = H.L[0];
+    const int64_t parts = residual_impl<double>(H, L, u, L.F, L.r, H.npart);
+    launch(H, "k_norm_final", k_norm_final, 1u, 1024u, (const double *)H.npart, parts, out4);
 }
+
+// an upper bound of the block partials residual_norms writes (64-thread blocks)
+int64_t norm_parts(const Level &L) { return (int64_t)nblk(L.nint, 64) + nblk(L.ng, 64); }
 
 // V(nu1, nu2) cycle from level l down (Sec. 2.1 with gamma = 1); u is the
 // level's unknown (finest: the working copy, coarse: the correction).
@@ -674,29 +998,86 @@ void vcycle_enqueue(Handle &H, int l, double *u) { vcycle_t<double>(H, l, u); }
 
 void mixed_step_enqueue(Handle &H, double *u) {
     Level &L = H.L[0];
-    const unsigned wb = wblk(L.nwin);
-    const unsigned grid = wb + nblk(L.ng, kT);
-    launch(H, "k_ir_begin", k_ir_begin, grid, kT, L.win, L.nwin, wb, L.gidx, L.ng, (const double *)L.r, L.F32,
-           L.u32);
+    const unsigned grid = nblk(L.nint + L.ng, kT);
+    launch(H, "k_ir_begin", k_ir_begin, grid, kT, (const uint32_t *)L.ilist, L.nint, (const uint32_t *)L.gidx, L.ng,
+           (const double *)L.r, L.F32, L.u32);
     vcycle_t<float>(H, 0, L.u32);
-    launch(H, "k_ir_update", k_ir_update, grid, kT, L.win, L.nwin, wb, L.gidx, L.ng, (const float *)L.u32, u);
+    launch(H, "k_ir_update", k_ir_update, grid, kT, (const uint32_t *)L.ilist, L.nint, (const uint32_t *)L.gidx,
+           L.ng, (const float *)L.u32, u);
+}
+
+// Cycle tables made once after the hierarchy: the ghost interpolation
+// weights of every level (one launch), then the levels of the cluster tail
+// and their tables.  The tail holds the coarse levels whose interior +
+// ghost + band nodes fit kTailNodes and whose extension is expanded (ELL),
+// down to a coarsest level of at most kTailCoarse unknowns; it needs a level
+// above the coarsest and never starts at level 0.
+void setup_cycle(Handle &H) {
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&H.nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    const int L = (int)H.L.size();
+    const bool mixed = H.o.precision == BCMG_PREC_MIXED;
+    const int nterm = H.d == 3 ? 27 : 9;
+    std::vector<GwTab> gt(L);
+    int64_t blocks = 0;
+    for (int l = 0; l < L; ++l) {
+        Level &A = H.L[l];
+        const size_t n1 = (size_t)std::max<int64_t>(A.ng, 1) * nterm;
+        A.gw = (double *)dalloc(H, sizeof(double) * n1);
+        if (mixed) A.gw32 = (float *)dalloc(H, sizeof(float) * n1);
+        gt[l] = GwTab{A.gcode, A.gxi, A.ng, A.gw, A.gw32, blocks};
+        blocks += nblk(A.ng, kT);
+    }
+    if (blocks > 0) {
+        GwTab *gt_d = (GwTab *)dalloc(H, sizeof(GwTab) * L, true);
+        check_cuda(cudaMemcpyAsync(gt_d, gt.data(), sizeof(GwTab) * L, cudaMemcpyHostToDevice, H.st), "gw table");
+        launch(H, "k_ghost_weights", k_ghost_weights, (unsigned)blocks, kT, (const GwTab *)gt_d, L, H.d);
+    }
+
+    H.tail_start = -1;
+    int lt = L - 1;
+    while (lt - 1 >= 1) {
+        const Level &A = H.L[lt - 1];
+        if (A.nint + A.ng + A.nb > kTailNodes || (A.nb > 0 && !A.ecnt)) break;
+        --lt;
+    }
+    if (lt >= L - 1 || lt < 1) return;
+    const Level &C = H.L[L - 1];
+    if (C.nint + C.ng + C.nb > kTailNodes || (C.nb > 0 && !C.ecnt) || C.nact > kTailCoarse) return;
+    const int cs = tail_cluster_size<double>(H);
+    if (cs == 0 || (mixed && tail_cluster_size<float>(H) < cs)) return;
+    H.tail_cluster = cs;
+    H.tail_start = lt;
+    const int nl = L - lt;
+    std::vector<TailLevel<double>> t64;
+    for (int l = lt; l < L; ++l) t64.push_back(tail_level<double>(H.L[l]));
+    H.tail64 = dalloc(H, sizeof(TailLevel<double>) * nl);
+    check_cuda(cudaMemcpyAsync(H.tail64, t64.data(), sizeof(TailLevel<double>) * nl, cudaMemcpyHostToDevice, H.st),
+               "tail table");
+    if (mixed) {
+        std::vector<TailLevel<float>> t32;
+        for (int l = lt; l < L; ++l) t32.push_back(tail_level<float>(H.L[l]));
+        H.tail32 = dalloc(H, sizeof(TailLevel<float>) * nl);
+        check_cuda(cudaMemcpyAsync(H.tail32, t32.data(), sizeof(TailLevel<float>) * nl, cudaMemcpyHostToDevice,
+                                   H.st),
+                   "tail table");
+    }
 }
 
 void copy_active(Handle &H, const double *src, double *dst, bool with_boxdir) {
     Level &L = H.L[0];
-    const unsigned wb = wblk(L.nwin), gb = nblk(L.ng, kT);
     const int64_t nbox = with_boxdir ? L.nbox : 0;
-    const unsigned grid = wb + gb + nblk(nbox, kT);
-    launch(H, "k_copy_active", k_copy_active, grid, kT, L.win, L.nwin, wb, L.gidx, L.ng, gb,
-           (const uint32_t *)L.boxidx, nbox, src, dst);
+    launch(H, "k_copy_active", k_copy_active, nblk(L.nint + L.ng + nbox, kT), kT, (const uint32_t *)L.ilist, L.nint,
+           (const uint32_t *)L.gidx, L.ng, (const uint32_t *)L.boxidx, nbox, src, dst);
 }
 
 void scatter_ghost_values(Handle &H, Level &L, const double *g, double *F) {
-    launch(H, "k_scatter_ghosts", k_scatter_ghosts, nblk(L.ng, 256), 256, L.gidx, L.ng, g, F);
+    launch(H, "k_scatter_ghosts", k_scatter_ghosts, nblk(L.ng, kT), kT, (const uint32_t *)L.gidx, L.ng, g, F);
 }
 
 void set_interior_rhs(Handle &H, Level &L, const double *f, double *F) {
-    launch(H, "k_set_interior", k_set_interior, wblk(L.nwin), kT, L.win, L.nwin, f, F);
+    launch(H, "k_set_interior", k_set_interior, nblk(L.nint, kT), kT, (const uint32_t *)L.ilist, L.nint, f, F);
 }
 
 template void smooth<double>(Handle &, Level &, double *, const double *, int);

@@ -1,4 +1,4 @@
-// Hierarchy set-up on the GPU: per-level node classes, interior windows,
+// Hierarchy set-up on the GPU: per-level node classes, interior lists,
 // ghost projection / stencil / Delta tau, band lists and the coarsest-level
 // inverse (arXiv 2207.14208, Sec. 3.3 geometry, Sec. 3.2-4.1 BLFA).
 //
@@ -31,12 +31,15 @@ Geo geo_of(const Level &L) {
     return g;
 }
 
+// node indices are below 2^32 (checked at creation): 32-bit division
 __device__ __forceinline__ void decode(const Geo &G, int64_t lin, int ix[3]) {
-    uint64_t v = (uint64_t)lin;
+    uint32_t v = (uint32_t)lin;
+    const uint32_t n = (uint32_t)G.n;
     ix[0] = ix[1] = ix[2] = 0;
     for (int a = 0; a < G.d; ++a) {
-        ix[a] = (int)(v % (uint64_t)G.n);
-        v /= (uint64_t)G.n;
+        const uint32_t q = v / n;
+        ix[a] = (int)(v - q * n);
+        v = q;
     }
 }
 
@@ -94,84 +97,60 @@ __global__ void k_scatter(const uint8_t *__restrict__ flags, int64_t n, const in
 }
 
 // ---------------------------------------------------------------- classes
-__global__ void k_inject(const double *__restrict__ phif, Geo Gf, Geo Gc, double *__restrict__ phic) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nn = 1;
-    for (int a = 0; a < Gc.d; ++a) nn *= Gc.n;
-    if (c >= nn) return;
-    int ic[3];
-    decode(Gc, c, ic);
-    int iy[3] = {2 * ic[0], 2 * ic[1], 2 * ic[2]};
-    phic[c] = phif[lin_of(Gf, iy)];
+// coarse phi by injection: one thread per coarse node on a (x-blocks, j, k) grid
+__global__ void __launch_bounds__(128) k_inject(const double *__restrict__ phif, Geo Gf, Geo Gc,
+                                                double *__restrict__ phic) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i > Gc.N) return;
+    phic[(int64_t)i + (int64_t)j * Gc.st[1] + (int64_t)k * Gc.st[2]] =
+        phif[2 * (int64_t)i + 2 * (int64_t)j * Gf.st[1] + 2 * (int64_t)k * Gf.st[2]];
 }
 
-__device__ __forceinline__ bool interior_at(const Geo &G, const double *phi, const int ix[3]) {
-    for (int a = 0; a < G.d; ++a)
-        if (ix[a] == 0 || ix[a] == G.N) return false;
-    return phi[lin_of(G, ix)] < 0.0;
+// x < 0.0 decided on the IEEE bit pattern (sign set, not -0, not NaN), so
+// the test runs on the integer pipe instead of the FP64 pipe
+__device__ __forceinline__ bool neg_d(double x) {
+    const long long b = __double_as_longlong(x);
+    const long long m = b & 0x7fffffffffffffffLL;
+    return b < 0 && m != 0 && m <= 0x7ff0000000000000LL;
 }
 
-__global__ void k_classify(const double *__restrict__ phi, Geo G, int64_t nn, uint8_t *__restrict__ cls) {
-    int64_t lin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (lin >= nn) return;
-    int ix[3];
-    decode(G, lin, ix);
-    bool edge = false;
-    for (int a = 0; a < G.d; ++a)
-        if (ix[a] == 0 || ix[a] == G.N) edge = true;
-    uint8_t c;
-    if (phi[lin] < 0.0) {
+// Node classes of one level (Sec. 3.3) and the flags of every list the
+// set-up compacts, one thread per node on a (x-blocks, j, k) grid (no index
+// division): red / black interior, box-edge Dirichlet, ghost, active.
+template <int D>
+__global__ void __launch_bounds__(128) k_classify(const double *__restrict__ phi, Geo G, uint8_t *__restrict__ cls,
+                                                  uint8_t *__restrict__ fred, uint8_t *__restrict__ fblack,
+                                                  uint8_t *__restrict__ fbox, uint8_t *__restrict__ fghost,
+                                                  uint8_t *__restrict__ fact) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = (D == 3) ? blockIdx.z : 0;
+    if (i > G.N) return;
+    const int64_t sy = G.st[1], sz = (D == 3) ? G.st[2] : 0;
+    const int64_t lin = (int64_t)i + (int64_t)j * sy + (int64_t)k * sz;
+    const bool edge = i == 0 || i == G.N || j == 0 || j == G.N || (D == 3 && (k == 0 || k == G.N));
+    uint8_t c = CL_INACTIVE;
+    if (neg_d(phi[lin])) {
         c = edge ? CL_BOXDIR : CL_INTERIOR;
     } else {
-        c = CL_INACTIVE;
-        for (int a = 0; a < G.d; ++a)
+        // a neighbour is interior if it is off the box edge with phi < 0
+        const int ix[3] = {i, j, k};
+        const int64_t st[3] = {1, sy, sz};
+        for (int a = 0; a < D; ++a)
             for (int dir = -1; dir <= 1; dir += 2) {
-                int iy[3] = {ix[0], ix[1], ix[2]};
-                iy[a] += dir;
-                if (in_grid(G, iy) && interior_at(G, phi, iy)) c = CL_GHOST;
+                int ok = 1;
+                for (int b2 = 0; b2 < D; ++b2) {
+                    const int v = ix[b2] + (b2 == a ? dir : 0);
+                    ok &= (v > 0 && v < G.N) ? 1 : 0;
+                }
+                if (ok && neg_d(phi[lin + dir * st[a]])) c = CL_GHOST;
             }
     }
     cls[lin] = c;
-}
-
-__global__ void k_flag_class(const uint8_t *__restrict__ cls, int64_t nn, uint8_t want, uint8_t want2,
-                             uint8_t *__restrict__ flags) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    uint8_t c = cls[i];
-    flags[i] = (c == want || c == want2) ? 1 : 0;
-}
-
-// one thread per 64-node window of an x-row: interior mask
-__global__ void k_win_mask(const uint8_t *__restrict__ cls, Geo G, int64_t nwall, int wpr,
-                           uint64_t *__restrict__ masks, uint8_t *__restrict__ flags) {
-    int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nwall) return;
-    int64_t row = w / wpr;
-    int m = (int)(w % wpr);
-    int64_t base = row * G.n + (int64_t)m * kWin;
-    int cnt = min(kWin, G.n - m * kWin);
-    uint64_t mask = 0;
-    for (int t = 0; t < cnt; ++t)
-        if (cls[base + t] == CL_INTERIOR) mask |= (1ull << t);
-    masks[w] = mask;
-    flags[w] = mask ? 1 : 0;
-}
-
-__global__ void k_make_win(const uint32_t *__restrict__ ids, int64_t nw, const uint64_t *__restrict__ masks,
-                           Geo G, int wpr, Win *__restrict__ win) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nw) return;
-    int64_t w = ids[i];
-    int64_t row = w / wpr;
-    int m = (int)(w % wpr);
-    int j = (G.d > 1) ? (int)(row % G.n) : 0;
-    int k = (G.d > 2) ? (int)(row / G.n) : 0;
-    Win x;
-    x.base = (uint32_t)(row * G.n + (int64_t)m * kWin);
-    x.jk = (uint32_t)j | ((uint32_t)k << 16);
-    x.mask = masks[w];
-    win[i] = x;
+    const int par = (i + j + k) & 1;
+    fred[lin] = (c == CL_INTERIOR && par == 0) ? 1 : 0;
+    fblack[lin] = (c == CL_INTERIOR && par == 1) ? 1 : 0;
+    fbox[lin] = (c == CL_BOXDIR) ? 1 : 0;
+    fghost[lin] = (c == CL_GHOST) ? 1 : 0;
+    fact[lin] = (c == CL_INTERIOR || c == CL_GHOST) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- ghosts
@@ -691,74 +670,136 @@ __global__ void k_gj_elim(double *__restrict__ A, double *__restrict__ B, int64_
     B[i * n + j] -= f * B[k * n + j];
 }
 
-// Whole Gauss-Jordan inversion with partial pivoting in one block (small
-// coarsest systems): same pivot rule and elimination order as the
-// multi-launch version, with __syncthreads between the phases of a step.
-constexpr int kGjSmall = 512;
+// Small coarsest systems (n <= kLuSmall): LU factorisation with partial
+// pivoting (largest |a_ik|, lowest row on ties) of the whole matrix in the
+// shared memory of one block, then the columns of the inverse by forward and
+// back substitution, one warp per column spread over many SMs (FP64 work on
+// one SM is the scarce resource).  PA = LU; row k of the factor holds
+// l_k0..l_k,k-1 and u_kk..u_k,n-1; perm[k] is the row swapped into k.
+constexpr int kLuSmall = 144;
 
-__global__ void __launch_bounds__(1024) k_gj_small(double *__restrict__ A, double *__restrict__ B, int n,
-                                                   int *__restrict__ singular) {
-    __shared__ double col[kGjSmall];
-    __shared__ double bv[1024];
-    __shared__ int bi[1024];
-    __shared__ double piv;
+__global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A, int n, double *__restrict__ LU,
+                                                   int *__restrict__ perm, int *__restrict__ singular) {
+    extern __shared__ double S[];  // n * n
+    __shared__ long long bv[32];
+    __shared__ int bi[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) S[t] = A[t];
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
-        double best = -1.0;
+        // pivot search on the bit patterns of |a_ik| (for non-negative
+        // doubles integer order is numeric order; no FP64 compares): per
+        // thread, per warp, then across warps, lowest row on ties
+        long long best = -1;
         int bidx = n;
         for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-            double v = fabs(A[(int64_t)i * n + k]);
-            if (v > best || (v == best && i < bidx)) {
+            const long long v = __double_as_longlong(S[i * n + k]) & 0x7fffffffffffffffLL;
+            if (v > best) {
                 best = v;
                 bidx = i;
             }
         }
-        bv[threadIdx.x] = best;
-        bi[threadIdx.x] = bidx;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long v = __shfl_down_sync(0xffffffffu, best, o);
+            const int ii = __shfl_down_sync(0xffffffffu, bidx, o);
+            if (v > best || (v == best && ii < bidx)) {
+                best = v;
+                bidx = ii;
+            }
+        }
+        if (lane == 0) {
+            bv[warp] = best;
+            bi[warp] = bidx;
+        }
         __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                double v = bv[threadIdx.x + s];
-                int ii = bi[threadIdx.x + s];
-                if (v > bv[threadIdx.x] || (v == bv[threadIdx.x] && ii < bi[threadIdx.x])) {
-                    bv[threadIdx.x] = v;
-                    bi[threadIdx.x] = ii;
+        if (warp == 0) {
+            best = lane < nw ? bv[lane] : -1;
+            bidx = lane < nw ? bi[lane] : n;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long v = __shfl_down_sync(0xffffffffu, best, o);
+                const int ii = __shfl_down_sync(0xffffffffu, bidx, o);
+                if (v > best || (v == best && ii < bidx)) {
+                    best = v;
+                    bidx = ii;
                 }
             }
-            __syncthreads();
+            if (lane == 0) {
+                bv[0] = best;
+                bi[0] = bidx;
+            }
         }
+        __syncthreads();
         int p = bi[0];
-        if (bv[0] <= 0.0) {
-            if (threadIdx.x == 0) *singular = 1;
-            p = k;
+        const bool sing = bv[0] <= 0;  // zero column (or nothing left)
+        if (sing) p = k;
+        if (threadIdx.x == 0) {
+            perm[k] = p;
+            if (sing) *singular = 1;
         }
         if (p != k)
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                double t = A[(int64_t)k * n + j];
-                A[(int64_t)k * n + j] = A[(int64_t)p * n + j];
-                A[(int64_t)p * n + j] = t;
-                t = B[(int64_t)k * n + j];
-                B[(int64_t)k * n + j] = B[(int64_t)p * n + j];
-                B[(int64_t)p * n + j] = t;
+                const double t = S[k * n + j];
+                S[k * n + j] = S[p * n + j];
+                S[p * n + j] = t;
             }
         __syncthreads();
-        if (threadIdx.x == 0) piv = A[(int64_t)k * n + k];
-        for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = (i == k) ? 0.0 : A[(int64_t)i * n + k];
+        const double ukk = S[k * n + k];
+        const double inv = sing ? 0.0 : 1.0 / ukk;
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * n + k] *= inv;
         __syncthreads();
-        const double ip = (piv != 0.0) ? 1.0 / piv : 0.0;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            A[(int64_t)k * n + j] *= ip;
-            B[(int64_t)k * n + j] *= ip;
-        }
-        __syncthreads();
-        for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
-            const int i = (int)(t / n), j = (int)(t % n);
-            const double f = col[i];
-            if (i == k || f == 0.0) continue;
-            A[(int64_t)i * n + j] -= f * A[(int64_t)k * n + j];
-            B[(int64_t)i * n + j] -= f * B[(int64_t)k * n + j];
+        // rank-1 update of the trailing block: rows by warp, columns by lane
+        for (int i = k + 1 + warp; i < n; i += nw) {
+            const double l = S[i * n + k];
+            for (int j = k + 1 + lane; j < n; j += 32) S[i * n + j] -= l * S[k * n + j];
         }
         __syncthreads();
     }
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) LU[t] = S[t];
+}
+
+// column j of A^-1: solve L U x = P e_j, one warp per column; the block
+// first copies the factor into shared memory (every step of the sequential
+// substitutions then reads shared memory, not L2)
+constexpr int kLuColsPerBlock = 8;
+
+__global__ void __launch_bounds__(32 * kLuColsPerBlock) k_lu_inverse(const double *__restrict__ LU, int n,
+                                                                     const int *__restrict__ perm,
+                                                                     double *__restrict__ Ainv) {
+    extern __shared__ double sm[];  // n * n factor, then kLuColsPerBlock * n vectors
+    double *F = sm;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) F[t] = LU[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * kLuColsPerBlock + w;
+    if (j >= n) return;  // whole warps leave together, after the block barrier
+    double *x = sm + n * n + w * n;
+    for (int i = lane; i < n; i += 32) x[i] = (i == j) ? 1.0 : 0.0;
+    __syncwarp();
+    if (lane == 0)
+        for (int k = 0; k < n; ++k) {
+            const int p = perm[k];
+            if (p != k) {
+                const double t = x[k];
+                x[k] = x[p];
+                x[p] = t;
+            }
+        }
+    __syncwarp();
+    for (int m = 0; m < n; ++m) {  // forward: unit lower L
+        const double ym = x[m];
+        for (int i = m + 1 + lane; i < n; i += 32) x[i] -= F[i * n + m] * ym;
+        __syncwarp();
+    }
+    for (int m = n - 1; m >= 0; --m) {  // back: upper U
+        const double xm = x[m] / F[m * n + m];
+        __syncwarp();
+        if (lane == 0) x[m] = xm;
+        for (int i = lane; i < m; i += 32) x[i] -= F[i * n + m] * xm;
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) Ainv[(int64_t)i * n + j] = x[i];
 }
 
 inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -841,12 +882,9 @@ void run_compaction(Handle &H, std::vector<CompactItem> &items) {
 }
 
 struct LevelScratch {
-    uint8_t *wflags = nullptr, *fint = nullptr, *fbox = nullptr, *fghost = nullptr, *fact = nullptr, *fband = nullptr;
-    uint64_t *masks = nullptr;
-    uint32_t *wids = nullptr;
-    int64_t nwall = 0;
-    int wpr = 0;
-    int64_t nint = 0;
+    uint8_t *fred = nullptr, *fblack = nullptr, *fbox = nullptr, *fghost = nullptr, *fact = nullptr,
+            *fband = nullptr;
+    uint32_t *red = nullptr, *black = nullptr;
     unsigned long long *cnt = nullptr;  // clamp / fall-back counters
     int64_t *ecnt = nullptr;
 };
@@ -878,7 +916,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     }
     const int nc = (int)H.L.size();
     std::vector<LevelScratch> S(nc);
-    // phase A: phi by injection, classes, window masks and class flags
+    // phase A: phi by injection, classes and class flags
     for (int l = 0; l < nc; ++l) {
         Level &L = H.L[l];
         LevelScratch &s = S[l];
@@ -887,28 +925,23 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             L.phi = phi0;
         } else {
             double *phic = (double *)dalloc(H, sizeof(double) * L.nn, true);
-            k_inject<<<nblocks(L.nn, T), T, 0, H.st>>>(H.L[l - 1].phi, geo_of(H.L[l - 1]), G, phic);
+            const dim3 ig((unsigned)nblocks(L.n, 128), (unsigned)L.n, H.d == 3 ? (unsigned)L.n : 1u);
+            k_inject<<<ig, 128, 0, H.st>>>(H.L[l - 1].phi, geo_of(H.L[l - 1]), G, phic);
             count_launch(H);
             L.phi = phic;
         }
         L.cls = (uint8_t *)dalloc(H, L.nn);
-        k_classify<<<nblocks(L.nn, T), T, 0, H.st>>>(L.phi, G, L.nn, L.cls);
-        count_launch(H);
-        s.wpr = (L.n + kWin - 1) / kWin;
-        s.nwall = (L.nn / L.n) * s.wpr;
-        s.masks = (uint64_t *)dalloc(H, sizeof(uint64_t) * s.nwall, true);
-        s.wflags = (uint8_t *)dalloc(H, (size_t)s.nwall, true);
-        k_win_mask<<<nblocks(s.nwall, T), T, 0, H.st>>>(L.cls, G, s.nwall, s.wpr, s.masks, s.wflags);
-        count_launch(H);
-        s.fint = (uint8_t *)dalloc(H, (size_t)L.nn, true);
+        s.fred = (uint8_t *)dalloc(H, (size_t)L.nn, true);
+        s.fblack = (uint8_t *)dalloc(H, (size_t)L.nn, true);
         s.fbox = (uint8_t *)dalloc(H, (size_t)L.nn, true);
         s.fghost = (uint8_t *)dalloc(H, (size_t)L.nn, true);
         s.fact = (uint8_t *)dalloc(H, (size_t)L.nn, true);
-        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_INTERIOR, CL_INTERIOR, s.fint);
-        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_BOXDIR, CL_BOXDIR, s.fbox);
-        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_GHOST, CL_GHOST, s.fghost);
-        k_flag_class<<<nblocks(L.nn, T), T, 0, H.st>>>(L.cls, L.nn, CL_INTERIOR, CL_GHOST, s.fact);
-        for (int i = 0; i < 4; ++i) count_launch(H);
+        const dim3 cg((unsigned)nblocks(L.n, 128), (unsigned)L.n, H.d == 3 ? (unsigned)L.n : 1u);
+        if (H.d == 3)
+            k_classify<3><<<cg, 128, 0, H.st>>>(L.phi, G, L.cls, s.fred, s.fblack, s.fbox, s.fghost, s.fact);
+        else
+            k_classify<2><<<cg, 128, 0, H.st>>>(L.phi, G, L.cls, s.fred, s.fblack, s.fbox, s.fghost, s.fact);
+        count_launch(H);
         check_cuda(cudaGetLastError(), "classification");
     }
     // round 1: counts of every list on every candidate level (one sync)
@@ -917,16 +950,16 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         for (int l = 0; l < nc; ++l) {
             Level &L = H.L[l];
             LevelScratch &s = S[l];
-            items.push_back({s.wflags, s.nwall, 0, 0, &s.wids, true, 0});
-            items.push_back({s.fint, L.nn, 0, 0, nullptr, true, 0});
+            items.push_back({s.fred, L.nn, 0, 0, &s.red, true, 0});
+            items.push_back({s.fblack, L.nn, 0, 0, &s.black, true, 0});
             items.push_back({s.fbox, L.nn, 0, 0, l == 0 ? &L.boxidx : nullptr, false, 0});
             items.push_back({s.fghost, L.nn, 0, 0, &L.gidx, false, 0});
         }
         run_compaction(H, items);
         for (int l = 0; l < nc; ++l) {
             Level &L = H.L[l];
-            L.nwin = items[4 * l + 0].total;
-            L.nint = items[4 * l + 1].total;
+            L.nred = items[4 * l + 0].total;
+            L.nint = L.nred + items[4 * l + 1].total;
             L.nbox = items[4 * l + 2].total;
             L.ng = items[4 * l + 3].total;
         }
@@ -940,7 +973,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         }
     H.L.resize(keep);
     S.resize(keep);
-    // phase B: windows and ghost arrays per level, then the ghost geometry
+    // phase B: interior lists and ghost arrays per level, then the ghost geometry
     // and band marks of every level in one launch
     std::vector<LevelTab> tab(keep);
     int64_t gblocks = 0;
@@ -948,11 +981,14 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         Level &L = H.L[l];
         LevelScratch &s = S[l];
         Geo G = geo_of(L);
-        L.win = (Win *)dalloc(H, sizeof(Win) * (size_t)std::max<int64_t>(L.nwin, 1));
-        if (L.nwin > 0) {
-            k_make_win<<<nblocks(L.nwin, T), T, 0, H.st>>>(s.wids, L.nwin, s.masks, G, s.wpr, L.win);
-            count_launch(H);
-        }
+        L.ilist = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(L.nint, 1));
+        if (L.nred > 0)
+            check_cuda(cudaMemcpyAsync(L.ilist, s.red, sizeof(uint32_t) * L.nred, cudaMemcpyDeviceToDevice, H.st),
+                       "red list");
+        if (L.nint > L.nred)
+            check_cuda(cudaMemcpyAsync(L.ilist + L.nred, s.black, sizeof(uint32_t) * (L.nint - L.nred),
+                                       cudaMemcpyDeviceToDevice, H.st),
+                       "black list");
         int64_t ng1 = std::max<int64_t>(L.ng, 1);
         L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1);
         L.gxi = (double *)dalloc(H, sizeof(double) * 3 * ng1);
@@ -962,7 +998,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
         L.gtmp = (double *)dalloc(H, sizeof(double) * ng1);
         s.cnt = (unsigned long long *)dalloc(H, 2 * sizeof(unsigned long long), true);
-        s.fband = s.fint;  // reuse: cleared here
+        s.fband = s.fred;  // reuse: cleared here
         check_cuda(cudaMemsetAsync(s.fband, 0, (size_t)L.nn, H.st), "band memset");
         LevelTab &t = tab[l];
         t = LevelTab{};
@@ -1072,12 +1108,22 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     int *sing = (int *)dalloc(H, sizeof(int), true);
     k_assemble<<<nblocks(n, 128), 128, 0, H.st>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.ng, G, A);
     count_launch(H);
-    k_identity<<<nblocks(n * n, T), T, 0, H.st>>>(L.Ainv, n);
-    count_launch(H);
-    if (n <= kGjSmall) {
-        k_gj_small<<<1, 1024, 0, H.st>>>(A, L.Ainv, (int)n, sing);
+    if (n <= kLuSmall) {
+        double *LU = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
+        int *perm = (int *)dalloc(H, sizeof(int) * std::max<int64_t>(n, 1), true);
+        const size_t smem = sizeof(double) * (size_t)(n * n);
+        check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "LU shared memory");
+        k_lu_small<<<1, 1024, smem, H.st>>>(A, (int)n, LU, perm, sing);
+        count_launch(H);
+        const size_t smem2 = sizeof(double) * (size_t)(n * n + kLuColsPerBlock * n);
+        check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
+                   "LU inverse shared memory");
+        k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st>>>(LU, (int)n, perm, L.Ainv);
         count_launch(H);
     } else {
+        k_identity<<<nblocks(n * n, T), T, 0, H.st>>>(L.Ainv, n);
+        count_launch(H);
         for (int64_t k = 0; k < n; ++k) {
             k_gj_pivot<<<1, 1024, 0, H.st>>>(A, L.Ainv, n, k, col, sing);
             k_gj_elim<<<nblocks(n * n, T), T, 0, H.st>>>(A, L.Ainv, n, k, col);
