@@ -85,6 +85,15 @@ struct Level {
     const double *phi = nullptr;
 };
 
+// device-side state of a solve run as one graph (WHILE conditional node)
+struct SolveState {
+    double rtol;     // in: stop when ||r|| / ||r0|| <= rtol
+    int max_cycles;  // in
+    int cycles;      // out: cycles done
+    double r0, rel;  // out: initial residual norm, final relative residual
+    int status;      // out: BCMG_OK or BCMG_ENONFINITE
+};
+
 struct Handle {
     int d = 0;
     int64_t N = 0;
@@ -99,6 +108,11 @@ struct Handle {
     double *nhost = nullptr;     // pinned copy of the 4 norms
     cudaGraphExec_t vgraph = nullptr;
     cudaGraphExec_t ngraph = nullptr;  // V-cycle followed by norms
+    // whole solve on the device: norms, then WHILE (cycle, norms, check)
+    cudaGraphExec_t sgraph = nullptr;
+    bool sgraph_failed = false;  // graph with a conditional node unavailable
+    int64_t sgraph_prefix = 0, sgraph_body = 0;  // kernels before / per iteration
+    SolveState *sdev = nullptr, *shost = nullptr;
     int64_t vgraph_kernels = 0, ngraph_kernels = 0;
     // coarse end of the V-cycle on one thread-block cluster: first level (-1:
     // none), cluster size
@@ -152,6 +166,10 @@ void residual_norms(Handle &H, const double *u, double *out4);
 int64_t norm_parts(const Level &L);  // block partials residual_norms writes
 // ghost weights of every level; the levels of the cluster tail and their tables
 void setup_cycle(Handle &H);
+// device-side solve control: initial and per-cycle convergence checks that
+// set the WHILE condition of the solve graph
+void solve_init_enqueue(Handle &H, unsigned long long cond);
+void solve_check_enqueue(Handle &H, unsigned long long cond);
 void vcycle_enqueue(Handle &H, int l, double *u);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,
 // u += correction; r must hold the FP64 residual of u

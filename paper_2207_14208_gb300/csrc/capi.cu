@@ -86,6 +86,8 @@ void destroy(Handle *H) {
     if (H->st) cudaStreamSynchronize(H->st);
     if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
     if (H->ngraph) cudaGraphExecDestroy(H->ngraph);
+    if (H->sgraph) cudaGraphExecDestroy(H->sgraph);
+    if (H->shost) cudaFreeHost(H->shost);
     if (H->st) {
         free_temps(*H);
         for (void *p : H->allocs) cudaFreeAsync(p, H->st);
@@ -197,6 +199,72 @@ void run_vcycle_norms(Handle &H) {
     }
 }
 
+// The whole solve as one graph: residual norms of the start, k_solve_init,
+// then a WHILE conditional node whose body is one cycle, its residual norms
+// and k_solve_check (which sets the condition).  No host round trip per
+// cycle.  Built once per handle; on any failure the handle falls back to the
+// host-driven loop of cycle graphs.
+cudaGraphExec_t build_solve_graph(Handle &H) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool capturing = false;
+    try {
+        check_cuda(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+        cudaGraphConditionalHandle cond;
+        check_cuda(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault),
+                   "cudaGraphConditionalHandleCreate");
+        check_cuda(cudaStreamBeginCaptureToGraph(H.st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                   "capture solve prefix");
+        capturing = true;
+        H.capturing = true;
+        H.captured = 0;
+        enqueue_norms(H);
+        solve_init_enqueue(H, (unsigned long long)cond);
+        H.sgraph_prefix = H.captured;
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        check_cuda(cudaStreamGetCaptureInfo(H.st, &cs, nullptr, nullptr, &deps, nullptr, &nd), "capture info");
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = cond;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t cn;
+        check_cuda(cudaGraphAddNode(&cn, g, deps, nullptr, nd, &p), "add WHILE node");
+        check_cuda(cudaStreamUpdateCaptureDependencies(H.st, &cn, nullptr, 1, cudaStreamSetCaptureDependencies),
+                   "capture dependencies");
+        capturing = false;
+        check_cuda(cudaStreamEndCapture(H.st, &g), "end capture solve prefix");
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        check_cuda(cudaStreamBeginCaptureToGraph(H.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                   "capture solve body");
+        capturing = true;
+        H.captured = 0;
+        if (H.o.precision == BCMG_PREC_MIXED) mixed_step_enqueue(H, H.u0);
+        else vcycle_enqueue(H, 0, H.u0);
+        enqueue_norms(H);
+        solve_check_enqueue(H, (unsigned long long)cond);
+        H.sgraph_body = H.captured;
+        capturing = false;
+        check_cuda(cudaStreamEndCapture(H.st, &body), "end capture solve body");
+        H.capturing = false;
+        check_cuda(cudaGraphInstantiate(&ex, g, 0), "instantiate solve graph");
+        cudaGraphDestroy(g);
+        return ex;
+    } catch (const Error &) {
+        H.capturing = false;
+        if (capturing) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(H.st, &junk);
+        }
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        H.sgraph_failed = true;
+        return nullptr;
+    }
+}
+
 void fetch_norms(Handle &H, double out[4]) {
     check_cuda(cudaMemcpyAsync(H.nhost, H.nout, 4 * sizeof(double), cudaMemcpyDeviceToHost, H.st), "norms D2H");
     check_cuda(cudaStreamSynchronize(H.st), "norms sync");
@@ -288,6 +356,8 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         setup_cycle(*H);
         H->nout = (double *)dalloc(*H, sizeof(double) * 4);
         check_cuda(cudaMallocHost((void **)&H->nhost, 4 * sizeof(double)), "cudaMallocHost");
+        check_cuda(cudaMallocHost((void **)&H->shost, sizeof(SolveState)), "cudaMallocHost");
+        H->sdev = (SolveState *)dalloc(*H, sizeof(SolveState));
         set_interior_rhs(*H, L0, f_dev, L0.F);
         for (auto &L : H->L) L.phi = nullptr;
         check_cuda(cudaStreamSynchronize(H->st), "create sync");
@@ -369,22 +439,42 @@ int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *c
         if (!u_dev || max_cycles < 0 || !(rtol >= 0.0)) throw Error{BCMG_EINVAL, "bad u, rtol or max_cycles"};
         enter(H);
         copy_active(H, u_dev, H.u0, true);
-        enqueue_norms(H);
-        double nr[4];
-        fetch_norms(H, nr);
-        const double r0 = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
-        double rel = (r0 > 0.0) ? 1.0 : 0.0;
+        double rel = 0.0, r0 = 0.0;
         int c = 0;
-        if (!std::isfinite(r0)) status = BCMG_ENONFINITE;
-        while (status == BCMG_OK && r0 > 0.0 && c < max_cycles) {
-            run_vcycle_norms(H);
+        // device-driven loop (one graph launch) unless sweeps are profiled
+        // (event records cannot sit inside a conditional body) or graphs are off
+        if (H.o.use_graph && !H.o.profile && !H.sgraph && !H.sgraph_failed) H.sgraph = build_solve_graph(H);
+        if (H.o.use_graph && !H.o.profile && H.sgraph) {
+            H.shost->rtol = rtol;
+            H.shost->max_cycles = max_cycles;
+            check_cuda(cudaMemcpyAsync(H.sdev, H.shost, sizeof(SolveState), cudaMemcpyHostToDevice, H.st),
+                       "solve state H2D");
+            check_cuda(cudaGraphLaunch(H.sgraph, H.st), "cudaGraphLaunch(solve)");
+            check_cuda(cudaMemcpyAsync(H.shost, H.sdev, sizeof(SolveState), cudaMemcpyDeviceToHost, H.st),
+                       "solve state D2H");
+            check_cuda(cudaStreamSynchronize(H.st), "solve sync");
+            c = H.shost->cycles;
+            r0 = H.shost->r0;
+            rel = H.shost->rel;
+            status = H.shost->status;
+            add_launches(H.sgraph_prefix + H.sgraph_body * (int64_t)c);
+        } else {
+            enqueue_norms(H);
+            double nr[4];
             fetch_norms(H, nr);
-            profile_collect(H);
-            ++c;
-            const double rn = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
-            rel = rn / r0;
-            if (!std::isfinite(rn)) status = BCMG_ENONFINITE;
-            else if (rel <= rtol) break;
+            r0 = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
+            rel = (r0 > 0.0) ? 1.0 : 0.0;
+            if (!std::isfinite(r0)) status = BCMG_ENONFINITE;
+            while (status == BCMG_OK && r0 > 0.0 && c < max_cycles) {
+                run_vcycle_norms(H);
+                fetch_norms(H, nr);
+                profile_collect(H);
+                ++c;
+                const double rn = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
+                rel = rn / r0;
+                if (!std::isfinite(rn)) status = BCMG_ENONFINITE;
+                else if (rel <= rtol) break;
+            }
         }
         if (status == BCMG_OK && r0 > 0.0 && rel > rtol) status = BCMG_ENOCONV;
         copy_active(H, H.u0, u_dev, false);

@@ -676,6 +676,42 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
     }
 }
 
+// ------------------------------------------------------------ solve control
+// norms of the residual (interior, ghost) -> sqrt(a^2 + b^2), rounded step by step
+__device__ __forceinline__ double resid_norm(const double *nout) {
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(nout[0], nout[0]), __dmul_rn(nout[1], nout[1])));
+}
+
+__device__ __forceinline__ bool finite_d(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
+}
+
+// before the loop: r0 from the initial norms; run the body iff r0 > 0 is
+// finite and cycles are allowed
+__global__ void k_solve_init(SolveState *st, const double *__restrict__ nout, cudaGraphConditionalHandle cond) {
+    pdl_begin();
+    const double r0 = resid_norm(nout);
+    const bool fin = finite_d(r0);
+    st->r0 = r0;
+    st->cycles = 0;
+    st->rel = r0 > 0.0 ? 1.0 : 0.0;
+    st->status = fin ? BCMG_OK : BCMG_ENONFINITE;
+    cudaGraphSetConditional(cond, (fin && r0 > 0.0 && st->max_cycles > 0) ? 1u : 0u);
+}
+
+// after each cycle: count it, relative residual, continue while above rtol
+__global__ void k_solve_check(SolveState *st, const double *__restrict__ nout, cudaGraphConditionalHandle cond) {
+    pdl_begin();
+    const int c = st->cycles + 1;
+    st->cycles = c;
+    const double rn = resid_norm(nout);
+    const double rel = rn / st->r0;
+    st->rel = rel;
+    const bool fin = finite_d(rn);
+    if (!fin) st->status = BCMG_ENONFINITE;
+    cudaGraphSetConditional(cond, (fin && rel > st->rtol && c < st->max_cycles) ? 1u : 0u);
+}
+
 // ------------------------------------------------------------ mixed precision
 // Start of one refinement step on the finest level: the FP32 right-hand side
 // is the FP64 residual rounded to FP32, the FP32 correction starts at zero.
@@ -1063,6 +1099,15 @@ void setup_cycle(Handle &H) {
                                    H.st),
                    "tail table");
     }
+}
+
+void solve_init_enqueue(Handle &H, unsigned long long cond) {
+    launch(H, "k_solve_init", k_solve_init, 1u, 1u, H.sdev, (const double *)H.nout, (cudaGraphConditionalHandle)cond);
+}
+
+void solve_check_enqueue(Handle &H, unsigned long long cond) {
+    launch(H, "k_solve_check", k_solve_check, 1u, 1u, H.sdev, (const double *)H.nout,
+           (cudaGraphConditionalHandle)cond);
 }
 
 void copy_active(Handle &H, const double *src, double *dst, bool with_boxdir) {
