@@ -67,6 +67,7 @@ struct Level {
     // values to band values: per band node up to kExtCap (ghost node,
     // weight) terms, ELL layout (term-major); null ecnt = sweep by sweep
     uint8_t *ecnt = nullptr;  // nb
+    int ell_max = 0;          // longest row
     uint32_t *eg = nullptr;   // kExtCap * nb
     double *ew = nullptr;     // kExtCap * nb
     // boxdir list (finest level only)

@@ -556,10 +556,14 @@ __global__ void __launch_bounds__(kT) k_ghost_weights(const GwTab *__restrict__ 
 // ------------------------------------------------------------ coarse tail
 // Levels tail[0..nl-1] (the last one is the coarsest) of the V-cycle in one
 // launch on one thread-block cluster: the same per-node steps as the grid
-// kernels, every thread of the cluster striding over each phase's nodes, the
-// phases separated by the cluster barrier (release / acquire at cluster
-// scope, so global writes of one CTA are seen by the others).  Every thread
-// reaches every barrier.
+// kernels, separated by the cluster barrier (release / acquire at cluster
+// scope, so global writes of one CTA are seen by the others).  Every list of
+// a tail level has at most one entry per thread of the cluster, so thread t
+// owns entry t of each list; at the start each CTA stages its threads'
+// entries of every level in shared memory, which leaves one dependent global
+// access in most phases.  A ghost's relaxed value stays in a register across
+// the barrier that separates the Jacobi update from its write-back.  Every
+// thread reaches every barrier.
 template <typename T>
 struct TailLevel {
     G2 g;
@@ -575,8 +579,9 @@ struct TailLevel {
     const uint32_t *eg;
     const double *ew;
     int64_t nb;
+    int ell_rounds;  // ceil(longest expansion / 8)
     const uint8_t *cls;
-    T *u, *F, *r, *gtmp;
+    T *u, *F, *r;
     const uint32_t *act;
     int64_t nact;
     const double *Ainv;
@@ -585,96 +590,165 @@ struct TailLevel {
 
 namespace cg = cooperative_groups;
 
-struct TailCtx {
-    int64_t tid, nthr;
+constexpr uint32_t kNone = 0xffffffffu;
+
+// per-level staged entries of one CTA's threads (dynamic shared memory)
+struct TailSlots {
+    uint32_t *red, *black, *gh, *band, *act;  // [level * kTailThreads + thread]
+    uint16_t *gcode;
 };
 
 __device__ __forceinline__ void tail_sync() { cg::this_cluster().sync(); }
 
+// List entry owned by this thread: whole warps of entries are dealt out
+// round-robin over the CTAs (so over the SMs and their FP64 pipes), the
+// k-th warp of entries going to CTA k % cs, local warp k / cs.
+__device__ __forceinline__ int64_t tail_entry() {
+    const int64_t k = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    return k * 32 + (threadIdx.x & 31);
+}
+
+// band value of slot b with a fixed number of 8-term rounds: the term loads
+// do not wait for the row length
+template <typename T>
+__device__ __forceinline__ T extend_fixed(int64_t b, int rounds, const uint8_t *ecnt, const uint32_t *eg,
+                                          const double *ew, int64_t nb, const T *a) {
+    const int c = ecnt[b];
+    T v = T(0);
+    for (int r0 = 0; r0 < rounds; ++r0) {
+        uint32_t e[8];
+        double w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t q = (int64_t)(r0 * 8 + j) * nb + b;
+            e[j] = eg[q];
+            w[j] = ew[q];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool p = r0 * 8 + j < c;
+            const T x = p ? a[e[j]] : T(0);
+            if (p) v = fma((T)w[j], x, v);
+        }
+    }
+    return v;
+}
+
 template <int D, typename T>
-__device__ void tail_smooth(const TailCtx &c, const TailLevel<T> &A, int nsteps) {
+__device__ void tail_smooth(const TailLevel<T> &A, const TailSlots &S, int l, int nsteps) {
+    const int t = threadIdx.x;
+    const uint32_t xr = S.red[l * kTailThreads + t], xb = S.black[l * kTailThreads + t];
+    const uint32_t xg = S.gh[l * kTailThreads + t];
+    const uint16_t code = S.gcode[l * kTailThreads + t];
+    const int64_t g = tail_entry();
     for (int s = 0; s < nsteps; ++s) {
-        for (int64_t i = c.tid; i < A.nred; i += c.nthr) smooth_at<D, T>(A.ilist[i], A.u, A.F, A.g);
+        if (xr != kNone) smooth_at<D, T>(xr, A.u, A.F, A.g);
         tail_sync();
-        for (int64_t i = A.nred + c.tid; i < A.nint; i += c.nthr) smooth_at<D, T>(A.ilist[i], A.u, A.F, A.g);
+        if (xb != kNone) smooth_at<D, T>(xb, A.u, A.F, A.g);
         tail_sync();
-        for (int64_t g = c.tid; g < A.ng; g += c.nthr)
-            A.gtmp[g] = ghost_new<D, T>(g, A.gidx, A.gcode, A.gw, A.gdt, A.ng, A.u, A.F, A.g);
+        T gv = T(0);
+        if (xg != kNone) gv = fma((T)A.gdt[g], A.F[xg] - ghost_B<D, T>(xg, code, A.gw, A.ng, g, A.u, A.g), A.u[xg]);
         tail_sync();
-        for (int64_t g = c.tid; g < A.ng; g += c.nthr) A.u[A.gidx[g]] = A.gtmp[g];
+        if (xg != kNone) A.u[xg] = gv;
         tail_sync();
     }
 }
 
 template <int D, typename T>
-__device__ void tail_residual(const TailCtx &c, const TailLevel<T> &A) {
-    for (int64_t i = c.tid; i < A.nint; i += c.nthr) {
-        const int64_t X = A.ilist[i];
-        A.r[X] = residual_int<D, T>(X, A.u, A.F, A.g);
-    }
-    for (int64_t g = c.tid; g < A.ng; g += c.nthr) {
-        const int64_t X = A.gidx[g];
-        A.r[X] = A.F[X] - ghost_B<D, T>(X, A.gcode[g], A.gw, A.ng, g, A.u, A.g);
+__device__ void tail_residual(const TailLevel<T> &A, const TailSlots &S, int l) {
+    const int t = threadIdx.x;
+    const int64_t i = tail_entry();
+    const uint32_t xa = S.act[l * kTailThreads + t];
+    if (xa != kNone) {
+        if (i < A.nint) A.r[xa] = residual_int<D, T>(xa, A.u, A.F, A.g);
+        else {
+            const int64_t g = i - A.nint;
+            A.r[xa] = A.F[xa] - ghost_B<D, T>(xa, A.gcode[g], A.gw, A.ng, g, A.u, A.g);
+        }
     }
     tail_sync();
 }
 
 template <typename T>
-__device__ void tail_extend(const TailCtx &c, const TailLevel<T> &A, T *a) {
-    for (int64_t b = c.tid; b < A.nb; b += c.nthr) a[A.bidx[b]] = extend_at<T>(b, A.ecnt, A.eg, A.ew, A.nb, a);
+__device__ void tail_extend(const TailLevel<T> &A, const TailSlots &S, int l, T *a) {
+    const int t = threadIdx.x;
+    const uint32_t xb = S.band[l * kTailThreads + t];
+    if (xb != kNone)
+        a[xb] = extend_fixed<T>(tail_entry(), A.ell_rounds, A.ecnt, A.eg, A.ew, A.nb, a);
     tail_sync();
 }
 
 template <int D, typename T>
 __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ tl, int nl, int nu1,
-                                                       int nu2) {
+                                                          int nu2) {
     pdl_begin();
-    TailCtx c;
-    c.tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // the grid is one cluster
-    c.nthr = (int64_t)gridDim.x * blockDim.x;
+    extern __shared__ uint32_t tsm[];
+    TailSlots S;
+    const int n = nl * kTailThreads;
+    S.red = tsm;
+    S.black = tsm + n;
+    S.gh = tsm + 2 * n;
+    S.band = tsm + 3 * n;
+    S.act = tsm + 4 * n;
+    S.gcode = (uint16_t *)(tsm + 5 * n);
+    const int t = threadIdx.x;
+    const int64_t i = tail_entry();  // the grid is one cluster
+    for (int l = 0; l < nl; ++l) {
+        const TailLevel<T> &A = tl[l];
+        const int k = l * kTailThreads + t;
+        S.red[k] = i < A.nred ? A.ilist[i] : kNone;
+        S.black[k] = i < A.nint - A.nred ? A.ilist[A.nred + i] : kNone;
+        S.gh[k] = i < A.ng ? A.gidx[i] : kNone;
+        S.gcode[k] = i < A.ng ? A.gcode[i] : (uint16_t)0;
+        S.band[k] = i < A.nb ? A.bidx[i] : kNone;
+        S.act[k] = i < A.nint ? A.ilist[i] : (i < A.nint + A.ng ? A.gidx[i - A.nint] : kNone);
+    }
+    __syncthreads();
     for (int l = 0; l + 1 < nl; ++l) {
         const TailLevel<T> &A = tl[l], &B = tl[l + 1];
-        tail_smooth<D, T>(c, A, nu1);
-        tail_residual<D, T>(c, A);
-        tail_extend<T>(c, A, A.r);
-        for (int64_t i = c.tid; i < B.nint + B.ng; i += c.nthr) {
-            const bool interior = i < B.nint;
-            const uint32_t Xc = interior ? B.ilist[i] : B.gidx[i - B.nint];
+        tail_smooth<D, T>(A, S, l, nu1);
+        tail_residual<D, T>(A, S, l);
+        tail_extend<T>(A, S, l, A.r);
+        const uint32_t xc = S.act[(l + 1) * kTailThreads + t];
+        if (xc != kNone) {
             int ic[3];
-            coords(Xc, (uint32_t)B.g.n, D, ic);
-            B.F[Xc] = restrict_at<D, T>(ic, interior, A.cls, A.r, A.g);
-            B.u[Xc] = T(0);
+            coords(xc, (uint32_t)B.g.n, D, ic);
+            B.F[xc] = restrict_at<D, T>(ic, i < B.nint, A.cls, A.r, A.g);
+            B.u[xc] = T(0);
         }
         tail_sync();
     }
     {
         const TailLevel<T> &C = tl[nl - 1];
-        tail_residual<D, T>(c, C);
-        for (int64_t j = c.tid; j < C.nact; j += c.nthr) C.crhs[j] = (double)C.r[C.act[j]];
+        tail_residual<D, T>(C, S, nl - 1);
+        if (i < C.nact) C.crhs[i] = (double)C.r[C.act[i]];
         tail_sync();
-        const int lane = threadIdx.x & 31;
-        for (int64_t i = c.tid >> 5; i < C.nact; i += c.nthr >> 5) {
+        const int lane = t & 31;
+        const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t row = i >> 5; row < C.nact; row += nthr >> 5) {  // rows by warp, spread over the SMs
             double s = 0.0;
-            for (int64_t j = lane; j < C.nact; j += 32) s = fma(C.Ainv[i * C.nact + j], C.crhs[j], s);
+            for (int64_t j = lane; j < C.nact; j += 32) s = fma(C.Ainv[row * C.nact + j], C.crhs[j], s);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) C.u[C.act[i]] += (T)s;
+            if (lane == 0) C.u[C.act[row]] += (T)s;
         }
         tail_sync();
     }
     for (int l = nl - 2; l >= 0; --l) {
         const TailLevel<T> &A = tl[l], &B = tl[l + 1];
-        tail_extend<T>(c, B, B.u);
-        for (int64_t i = c.tid; i < A.nint + A.ng; i += c.nthr) {
-            const uint32_t X = (i < A.nint) ? A.ilist[i] : A.gidx[i - A.nint];
+        tail_extend<T>(B, S, l + 1, B.u);
+        const uint32_t xa = S.act[l * kTailThreads + t];
+        if (xa != kNone) {
             int iy[3];
-            coords(X, (uint32_t)A.g.n, D, iy);
-            A.u[X] += prolong_at<D, T>(iy, B.u, B.g);
+            coords(xa, (uint32_t)A.g.n, D, iy);
+            A.u[xa] += prolong_at<D, T>(iy, B.u, B.g);
         }
         tail_sync();
-        tail_smooth<D, T>(c, A, nu2);
+        tail_smooth<D, T>(A, S, l, nu2);
     }
 }
+
+size_t tail_smem(int nl) { return (size_t)nl * kTailThreads * (5 * sizeof(uint32_t) + sizeof(uint16_t)); }
 
 // ------------------------------------------------------------ solve control
 // norms of the residual (interior, ghost) -> sqrt(a^2 + b^2), rounded step by step
@@ -831,11 +905,11 @@ TailLevel<T> tail_level(Level &L) {
     t.eg = L.eg;
     t.ew = L.ew;
     t.nb = L.nb;
+    t.ell_rounds = (L.ell_max + 7) / 8;
     t.cls = L.cls;
     t.u = Arr<T>::u(L);
     t.F = Arr<T>::F(L);
     t.r = Arr<T>::r(L);
-    t.gtmp = Arr<T>::gtmp(L);
     t.act = L.act;
     t.nact = L.nact;
     t.Ainv = L.Ainv;
@@ -851,11 +925,11 @@ TailKernel<T> tail_kernel(int d) {
     return d == 3 ? k_tail<3, T> : k_tail<2, T>;
 }
 
-cudaLaunchConfig_t tail_config(Handle &H, int csize, cudaLaunchAttribute *at, bool pdl) {
+cudaLaunchConfig_t tail_config(Handle &H, int csize, int nl, cudaLaunchAttribute *at, bool pdl) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)csize, 1, 1);
     cfg.blockDim = dim3(kTailThreads, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = tail_smem(nl);
     cfg.stream = H.st;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)csize;
@@ -868,18 +942,22 @@ cudaLaunchConfig_t tail_config(Handle &H, int csize, cudaLaunchAttribute *at, bo
     return cfg;
 }
 
-// largest cluster (16, else 8) of kTailThreads-thread CTAs that the device
-// can place; 0 if none
+// largest cluster (16, else 8) of kTailThreads-thread CTAs with the shared
+// memory of nl staged levels that the device can place; 0 if none
 template <typename T>
-int tail_cluster_size(Handle &H) {
+int tail_cluster_size(Handle &H, int nl) {
     TailKernel<T> k = tail_kernel<T>(H.d);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem(nl)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
     for (int cs : {16, 8}) {
         if (cs > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
             (void)cudaGetLastError();
             continue;
         }
         cudaLaunchAttribute at[2];
-        cudaLaunchConfig_t cfg = tail_config(H, cs, at, false);
+        cudaLaunchConfig_t cfg = tail_config(H, cs, nl, at, false);
         int n = 0;
         if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n >= 1) return cs;
         (void)cudaGetLastError();
@@ -892,7 +970,7 @@ void run_tail(Handle &H) {
     const int nl = (int)H.L.size() - H.tail_start;
     const TailLevel<T> *tab = (const TailLevel<T> *)(sizeof(T) == 8 ? H.tail64 : H.tail32);
     cudaLaunchAttribute at[2];
-    cudaLaunchConfig_t cfg = tail_config(H, H.tail_cluster, at, true);
+    cudaLaunchConfig_t cfg = tail_config(H, H.tail_cluster, nl, at, true);
     check_cuda(cudaLaunchKernelEx(&cfg, tail_kernel<T>(H.d), tab, nl, H.o.nu1, H.o.nu2), "k_tail");
     count_launch(H);
 }
@@ -1071,18 +1149,26 @@ void setup_cycle(Handle &H) {
         launch(H, "k_ghost_weights", k_ghost_weights, (unsigned)blocks, kT, (const GwTab *)gt_d, L, H.d);
     }
 
+    // a level fits the tail if each of its lists has at most one entry per
+    // thread of the cluster (and at most kTailNodes) and its extension is
+    // expanded; the coarsest level also needs at most kTailCoarse unknowns
     H.tail_start = -1;
-    int lt = L - 1;
-    while (lt - 1 >= 1) {
-        const Level &A = H.L[lt - 1];
-        if (A.nint + A.ng + A.nb > kTailNodes || (A.nb > 0 && !A.ecnt)) break;
-        --lt;
-    }
-    if (lt >= L - 1 || lt < 1) return;
+    auto fits = [&](const Level &A, int64_t lim) {
+        return A.nint + A.ng <= lim && A.nb <= lim && (A.nb == 0 || A.ecnt != nullptr);
+    };
+    auto first_level = [&](int64_t lim) {
+        int lt = L - 1;
+        while (lt - 1 >= 1 && fits(H.L[lt - 1], lim)) --lt;
+        return lt;
+    };
     const Level &C = H.L[L - 1];
-    if (C.nint + C.ng + C.nb > kTailNodes || (C.nb > 0 && !C.ecnt) || C.nact > kTailCoarse) return;
-    const int cs = tail_cluster_size<double>(H);
-    if (cs == 0 || (mixed && tail_cluster_size<float>(H) < cs)) return;
+    int lt = first_level(kTailNodes);
+    if (lt >= L - 1 || !fits(C, kTailNodes) || C.nact > kTailCoarse) return;
+    const int cs = tail_cluster_size<double>(H, L - lt);
+    if (cs == 0 || (mixed && tail_cluster_size<float>(H, L - lt) < cs)) return;
+    const int64_t lim = std::min<int64_t>(kTailNodes, (int64_t)cs * kTailThreads);
+    lt = std::max(lt, first_level(lim));
+    if (lt >= L - 1 || !fits(C, lim) || C.nact > lim) return;
     H.tail_cluster = cs;
     H.tail_start = lt;
     const int nl = L - lt;

@@ -197,17 +197,23 @@ __device__ double interp_phi(const Geo &G, const double *phi, const double p[3],
         cc.c[1] = c[1];
         cc.c[2] = c[2];
     }
+    // corner weights prod_a (b_a ? t_a : 1 - t_a), multiplied in axis order
+    // (the leading 1.0 factor is exact and dropped), the x-y products shared
+    // by the corners that differ only in z; sum in corner order
+    double f[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        f[a][0] = (a < G.d) ? __dsub_rn(1.0, t[a]) : 1.0;
+        f[a][1] = t[a];
+    }
+    double p01[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p01[k] = (G.d >= 2) ? __dmul_rn(f[0][k & 1], f[1][k >> 1]) : f[0][k & 1];
     double val = 0.0;
 #pragma unroll
     for (int corner = 0; corner < 8; ++corner) {
         if (corner >= (1 << G.d)) break;
-        double w = 1.0;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a >= G.d) break;
-            int b = (corner >> a) & 1;
-            w = __dmul_rn(w, b ? t[a] : __dsub_rn(1.0, t[a]));
-        }
+        const double w = (G.d == 3) ? __dmul_rn(p01[corner & 3], f[2][corner >> 2]) : p01[corner & 3];
         val = __dadd_rn(val, __dmul_rn(w, cc.v[corner]));
     }
     return val;
@@ -306,9 +312,15 @@ __device__ void ghost_one(const uint32_t *__restrict__ gidx, int64_t ng, const d
             eta = 1.0;
             atomicAdd(out.nclamp, 1ull);
         } else {
+            // once the midpoint rounds onto an end of the interval, every
+            // remaining halving leaves eta = that midpoint: stop there
             double lo = 0.0, hi = 1.0;
             for (int it = 0; it < 64; ++it) {
                 double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+                if (mid == lo || mid == hi) {
+                    lo = hi = mid;
+                    break;
+                }
                 double pm[3];
                 for (int a = 0; a < 3; ++a)
                     pm[a] = (a < d) ? __dsub_rn((double)ix[a], __dmul_rn(mid, n[a])) : (double)ix[a];
@@ -538,6 +550,7 @@ __global__ void k_ext_all(const LevelTab *__restrict__ tab, int nl, int d, int K
         }
     }
     if (over) atomicOr(overflow + l, 1);
+    atomicMax(overflow + nl + l, cnt);  // longest row of the level
     T.ecnt[b] = (uint8_t)cnt;
     for (int k = 0; k < cnt; ++k) {
         T.eg[(int64_t)k * nb + b] = g[k];
@@ -683,6 +696,7 @@ __global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A,
     extern __shared__ double S[];  // n * n
     __shared__ long long bv[32];
     __shared__ int bi[32];
+    __shared__ double sinv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) S[t] = A[t];
     __syncthreads();
@@ -744,9 +758,9 @@ __global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A,
                 S[k * n + j] = S[p * n + j];
                 S[p * n + j] = t;
             }
+        if (threadIdx.x == 0) sinv = sing ? 0.0 : 1.0 / S[k * n + k];  // one division per step
         __syncthreads();
-        const double ukk = S[k * n + k];
-        const double inv = sing ? 0.0 : 1.0 / ukk;
+        const double inv = sinv;
         for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * n + k] *= inv;
         __syncthreads();
         // rank-1 update of the trailing block: rows by warp, columns by lane
@@ -761,39 +775,40 @@ __global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A,
 
 // column j of A^-1: solve L U x = P e_j, one warp per column; the block
 // first copies the factor into shared memory (every step of the sequential
-// substitutions then reads shared memory, not L2)
-constexpr int kLuColsPerBlock = 8;
+// substitutions then reads shared memory, not L2) together with the
+// reciprocals of U's diagonal (one FP64 division per diagonal entry, not per
+// step and lane).  P e_j is a unit vector e_q, so the forward substitution
+// starts at row q.
+constexpr int kLuColsPerBlock = 2;
 
 __global__ void __launch_bounds__(32 * kLuColsPerBlock) k_lu_inverse(const double *__restrict__ LU, int n,
                                                                      const int *__restrict__ perm,
                                                                      double *__restrict__ Ainv) {
-    extern __shared__ double sm[];  // n * n factor, then kLuColsPerBlock * n vectors
-    double *F = sm;
+    extern __shared__ double sm[];  // n * n factor, n reciprocals, kLuColsPerBlock * n vectors
+    double *F = sm, *rd = sm + n * n;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) F[t] = LU[t];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) rd[t] = 1.0 / LU[t * n + t];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j = blockIdx.x * kLuColsPerBlock + w;
     if (j >= n) return;  // whole warps leave together, after the block barrier
-    double *x = sm + n * n + w * n;
-    for (int i = lane; i < n; i += 32) x[i] = (i == j) ? 1.0 : 0.0;
+    double *x = sm + n * n + n + w * n;
+    // position of e_j after the row swaps of the factorisation
+    int q = j;
+    for (int k = 0; k < n; ++k) {
+        const int p = perm[k];
+        if (q == k) q = p;
+        else if (q == p) q = k;
+    }
+    for (int i = lane; i < n; i += 32) x[i] = (i == q) ? 1.0 : 0.0;
     __syncwarp();
-    if (lane == 0)
-        for (int k = 0; k < n; ++k) {
-            const int p = perm[k];
-            if (p != k) {
-                const double t = x[k];
-                x[k] = x[p];
-                x[p] = t;
-            }
-        }
-    __syncwarp();
-    for (int m = 0; m < n; ++m) {  // forward: unit lower L
+    for (int m = q; m < n; ++m) {  // forward: unit lower L (rows above q stay 0)
         const double ym = x[m];
         for (int i = m + 1 + lane; i < n; i += 32) x[i] -= F[i * n + m] * ym;
         __syncwarp();
     }
     for (int m = n - 1; m >= 0; --m) {  // back: upper U
-        const double xm = x[m] / F[m * n + m];
+        const double xm = x[m] * rd[m];
         __syncwarp();
         if (lane == 0) x[m] = xm;
         for (int i = lane; i < m; i += 32) x[i] -= F[i * n + m] * xm;
@@ -1034,7 +1049,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     // level in one launch each
     const bool ell = ext_ell_ok(H.d, H.o.ext_sweeps);
     int64_t bblocks = 0;
-    int *ovf = (int *)dalloc(H, sizeof(int) * keep, true);
+    int *ovf = (int *)dalloc(H, sizeof(int) * 2 * keep, true);  // overflow flags, longest rows
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
         int64_t nb1 = std::max<int64_t>(L.nb, 1);
@@ -1069,18 +1084,19 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     check_cuda(cudaGetLastError(), "band set-up");
     // round 3: clamp / fall-back counters and ELL overflows (one sync)
     {
-        int64_t *hc = pinned_scratch(3 * (size_t)keep + 1);
+        int64_t *hc = pinned_scratch(3 * (size_t)keep + 2);
         for (int l = 0; l < keep; ++l)
             check_cuda(cudaMemcpyAsync(hc + 2 * l, S[l].cnt, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, H.st),
                        "ghost counters");
         int *hov = (int *)(hc + 2 * keep);
-        check_cuda(cudaMemcpyAsync(hov, ovf, sizeof(int) * keep, cudaMemcpyDeviceToHost, H.st), "overflow");
+        check_cuda(cudaMemcpyAsync(hov, ovf, sizeof(int) * 2 * keep, cudaMemcpyDeviceToHost, H.st), "overflow");
         check_cuda(cudaStreamSynchronize(H.st), "set-up sync 3");
         for (int l = 0; l < keep; ++l) {
             Level &L = H.L[l];
             L.nclamp = hc[2 * l];
             L.nfall = hc[2 * l + 1];
             if (hov[l]) L.ecnt = nullptr;  // a row longer than kExtCap: sweep by sweep
+            L.ell_max = hov[keep + l];
         }
     }
     // level arrays
@@ -1116,7 +1132,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
                    "LU shared memory");
         k_lu_small<<<1, 1024, smem, H.st>>>(A, (int)n, LU, perm, sing);
         count_launch(H);
-        const size_t smem2 = sizeof(double) * (size_t)(n * n + kLuColsPerBlock * n);
+        const size_t smem2 = sizeof(double) * (size_t)(n * n + n + kLuColsPerBlock * n);
         check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
                    "LU inverse shared memory");
         k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st>>>(LU, (int)n, perm, L.Ainv);
