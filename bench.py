@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--arms", choices=["both", "fp64", "mixed"], default="both")
+    # the default workload is the 3D ellipsoid at 257^3; the other two are the
+    # batched and the served workloads (single GPU, extra lines, not defaults)
+    p.add_argument("--config", choices=["ellipsoid256", "stars_batched", "served"], default="ellipsoid256")
     return p.parse_args()
 
 
@@ -392,9 +395,188 @@ def run_reference(args, ws, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------ batched / served
+def _g2_torch(Q):
+    import torch
+    x, y = Q[:, 0], Q[:, 1]
+    return torch.sin(math.pi * x) * torch.cos(math.pi * y) * torch.exp(x)
+
+
+def _g3_torch(Q):
+    import torch
+    x, y, z = Q[:, 0], Q[:, 1], Q[:, 2]
+    return torch.exp(x + y + z) * torch.sin(math.pi * z)
+
+
+def run_stars_batched(args):
+    """256 seeded star domains (N log-uniform 64..1024), FP32 cycles inside
+    FP64 refinement: per step every hierarchy is built (16 host threads, one
+    library stream each), its g(Q) set, and all 256 solved by one
+    bcmg_solve_batch call (the solves run concurrently on the device).  The
+    same domains solved one after another give the single-solve rate."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2207_14208_gb300 import bcmg
+    from paper_2207_14208_gb300 import build as B
+    B.build()
+    params = W.star_params(256, 1)
+    data = []
+    for N, a, k, psi in params:
+        data.append((N, torch.from_numpy(W.phi_star(N, a, k, psi)).cuda(),
+                     torch.from_numpy(W.manufactured(2, N)[0]).cuda()))
+    stream = torch.cuda.current_stream()
+
+    def make(i):
+        # the hierarchy is ordered on the stream current at its creation, so
+        # that stream is kept with it
+        N, phi, f = data[i]
+        cs = torch.cuda.Stream()
+        with torch.cuda.stream(cs):
+            s = bcmg.Solver(2, N, phi, f, precision=bcmg.PREC_MIXED)
+            s.set_boundary_values(_g2_torch(s.ghost_points()).contiguous())
+            u = torch.zeros((N + 1) ** 2, dtype=torch.float64, device="cuda")
+            cs.synchronize()
+        return s, u, cs
+
+    def step(pool):
+        trip = list(pool.map(make, range(len(data))))
+        cyc, rel, st = bcmg.solve_batch([t[0] for t in trip], [t[1] for t in trip], args.rtol, 100)
+        torch.cuda.synchronize()
+        for t in trip:
+            t[0].close()
+        return cyc, st
+
+    steps = max(1, min(args.steps, 5))
+    with ThreadPoolExecutor(16) as pool:
+        for _ in range(max(1, args.warmup)):
+            step(pool)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        launches0 = bcmg.kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ok = 0
+        cycles = []
+        for _ in range(steps):
+            cyc, st = step(pool)
+            ok += st.count(bcmg.OK)
+            cycles += cyc
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = bcmg.kernel_launches() - launches0
+        clk = clocks.stop()
+    # single solves, one after another (same work)
+    t0 = time.perf_counter()
+    for i in range(len(data)):
+        s, u, cs = make(i)
+        with torch.cuda.stream(cs):
+            s.solve(u, args.rtol, 100, raise_noconv=False)
+        s.close()
+    torch.cuda.synchronize()
+    single = len(data) / (time.perf_counter() - t0)
+    value = ok / (ms / 1e3)
+    return {"metric": "solves/s, 256 batched 2D star domains (N 64..1024), FP32 cycles in FP64 refinement to 1e-10",
+            "value": value, "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": max(1, args.warmup),
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 cycles in f64 refinement", "data": "synthetic (seeded star level sets, manufactured solution)",
+            "config": {"workload": "256 star domains r = 0.5 + a sin(k theta + psi), PCG64 seed 1, N 64..1024",
+                       "solves_per_step": len(data), "converged_per_step": ok / steps,
+                       "mean_cycles": float(np.mean(cycles)), "single_solves_per_s": single,
+                       "batch_over_single": value / single,
+                       "step": "threaded create x256 + g(Q) + one bcmg_solve_batch + destroy",
+                       "parallelism": "single"},
+            "clocks": clk, "gpu_launches": launches}
+
+
+def served_requests(rate, count, seed=2):
+    """Poisson arrivals (rate per second, PCG64 seed): half 2D star domains
+    (N log-uniform 64..2048), half 3D ellipsoids with random semi-axes
+    (N log-uniform 64..256; stand-in for the sphere unions, whose coarse
+    levels do not converge with the paper's re-discretised hierarchy), half
+    FP64 and half mixed precision."""
+    from paper_2207_14208_gb300 import bcmg, serve
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cands = sorted({m << k for m in range(8, 16) for k in range(0, 12)})
+
+    def pick(lo, hi):
+        c = np.array([x for x in cands if lo // 2 <= x <= hi * 2])
+        return int(c[np.argmin(np.abs(c - math.exp(rng.uniform(math.log(lo), math.log(hi)))))])
+
+    reqs, t = [], 0.0
+    for i in range(count):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        prec = bcmg.PREC_FP64 if rng.uniform() < 0.5 else bcmg.PREC_MIXED
+        if rng.uniform() < 0.5:
+            N = pick(64, 2048)
+            a, k, psi = rng.uniform(0.05, 0.2), int(rng.integers(3, 9)), rng.uniform(0, 2 * math.pi)
+            reqs.append(serve.Request(i, 2, N, W.phi_star(N, a, k, psi), W.manufactured(2, N)[0], _g2_torch,
+                                      precision=prec, arrival=t))
+        else:
+            N = pick(64, 256)
+            ax = rng.uniform(0.35, 0.7, size=3)
+            X, Y, Z = W.coords(3, N)
+            phi = ((X / ax[0]) ** 2 + (Y / ax[1]) ** 2 + (Z / ax[2]) ** 2 - 1.0).reshape(-1)
+            reqs.append(serve.Request(i, 3, N, phi, W.manufactured(3, N)[0], _g3_torch, precision=prec, arrival=t))
+    return reqs
+
+
+def run_served(args):
+    """Saturation throughput (every request present at t = 0), then Poisson
+    arrivals at 50 % and 80 % of it: solves/s and p50 / p99 latency."""
+    import torch
+    from paper_2207_14208_gb300 import bcmg, serve
+    from paper_2207_14208_gb300 import build as B
+    B.build()
+    count = 64
+    budget = int(64e9)
+    server = serve.Server(budget, workers=16)
+    server.run(served_requests(0.0, 8, seed=7))  # warm-up
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = bcmg.kernel_launches()
+    reqs = served_requests(0.0, count)  # built on the host before the clock starts
+    t0 = time.perf_counter()
+    res = server.run(reqs)
+    sat_s = time.perf_counter() - t0
+    ok = [r for r in res if r.status == bcmg.OK]
+    sat = len(ok) / sat_s
+    lines = {"saturation": {"solves_per_s": sat, **{"p%d_ms" % p: v * 1e3 for p, v in
+                                                    serve.percentiles([r.latency for r in ok]).items()}}}
+    for frac in (0.5, 0.8):
+        reqs = served_requests(frac * sat, count)
+        t0 = time.perf_counter()
+        res = server.run(reqs)
+        el = time.perf_counter() - t0
+        okf = [r for r in res if r.status == bcmg.OK]
+        lines["%d%%" % int(frac * 100)] = {"offered_per_s": frac * sat, "solves_per_s": len(okf) / el,
+                                            **{"p%d_ms" % p: v * 1e3 for p, v in
+                                               serve.percentiles([r.latency for r in okf]).items()}}
+    launches = bcmg.kernel_launches() - launches0
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    return {"metric": "solves/s and p50/p99 latency, served stream (Poisson arrivals, 2D stars + 3D ellipsoids, "
+                      "FP64 and mixed, rtol 1e-10)",
+            "value": sat, "unit": "solves/s", "n_gpus": 1, "steps": count, "warmup": 8,
+            "ms_per_step": 1e3 / sat, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 and f32-in-f64 mix", "data": "synthetic (seeded level sets, manufactured solutions)",
+            "config": {"workload": "64 requests, PCG64 seed 2: 2D stars N 64..2048, 3D ellipsoids N 64..256",
+                       "admission": "estimated footprint within a %d GB budget, 16 workers" % (budget // 10 ** 9),
+                       "rates": lines, "converged_at_saturation": len(ok), "parallelism": "single"},
+            "clocks": clk, "gpu_launches": launches}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_info()
+    if args.impl == "ours" and args.config != "ellipsoid256":
+        if ws > 1 and rank != 0:
+            return
+        out = run_stars_batched(args) if args.config == "stars_batched" else run_served(args)
+        print(json.dumps(out))
+        return
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
         if out is not None:

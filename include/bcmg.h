@@ -127,6 +127,33 @@ int bcmg_vcycle(bcmg_handle h, double *u_dev, int ncycles);
 int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *cycles_done,
                double *final_rel_res);
 
+/* Many solves at once (uneven sizes and geometries welcome): every handle's
+ * solve is enqueued on that handle's own stream before any is waited for,
+ * so the GPU runs them concurrently; then each is finished in order.
+ *   handles[n], u_devs[n]  distinct handles and their u arrays (as for
+ *                          bcmg_solve); rtol, max_cycles shared by all
+ *   cycles_done[n], final_rel_res[n], statuses[n]   per-solve results
+ *                          (host arrays, each may be NULL)
+ * A solve whose handle was created with profile = 1 or use_graph = 0 runs
+ * its host-driven loop in the second pass.  Results are identical to
+ * bcmg_solve on each handle alone.  Returns BCMG_OK if every solve
+ * converged, else the first failing status (per-solve ones in statuses);
+ * EINVAL for null arrays or a handle that appears twice. */
+int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, int max_cycles,
+                     int *cycles_done, double *final_rel_res, int *statuses);
+
+/* Device memory (bytes) the handle holds: every level's arrays, lists and
+ * tables (not the caller's phi, f or u). */
+int bcmg_memory_footprint(bcmg_handle h, int64_t *bytes);
+
+/* A-priori estimate of the device memory a hierarchy of this size will hold
+ * (no phi needed), for admission control: the dense per-level arrays over
+ * the levels the coarsening rule allows, times 2 for the compacted lists,
+ * plus 1 MiB.  It exceeds bcmg_memory_footprint on the shapes the tests
+ * cover; geometries with far more boundary than the test domains can
+ * exceed it.  opts may be NULL (defaults). */
+int bcmg_footprint_estimate(int dim, int64_t N, const bcmg_opts *opts, int64_t *bytes);
+
 /* Residual norms of u_dev on the finest level into out_host[4]:
  * ||r_I||_2, ||r_G||_2, ||r_I||_inf, ||r_G||_inf (unscaled residuals). */
 int bcmg_residual_norm(bcmg_handle h, const double *u_dev, double *out_host);

@@ -68,6 +68,9 @@ def load():
             "bcmg_vcycle": (i32, [vp, vp, i32]),
             "bcmg_solve": (i32, [vp, vp, f64, i32, vp, vp]),
             "bcmg_residual_norm": (i32, [vp, vp, vp]),
+            "bcmg_solve_batch": (i32, [vp, vp, i32, f64, i32, vp, vp, vp]),
+            "bcmg_memory_footprint": (i32, [vp, vp]),
+            "bcmg_footprint_estimate": (i32, [i32, i64, vp, vp]),
             "bcmg_last_error": (C.c_char_p, []),
             "bcmg_kernel_launches": (i64, []),
             "bcmg_profile_read": (i32, [vp, vp]),
@@ -141,6 +144,32 @@ def default_opts(**kw) -> Opts:
     return o
 
 
+def footprint_estimate(dim: int, N: int, **opts) -> int:
+    """A-priori device-memory estimate (bytes) of a hierarchy (bcmg_footprint_estimate)."""
+    o = default_opts(**opts)
+    out = C.c_int64()
+    _check(load().bcmg_footprint_estimate(int(dim), int(N), C.byref(o), C.byref(out)))
+    return out.value
+
+
+def solve_batch(solvers, us, rtol: float = 1e-10, max_cycles: int = 100):
+    """Solve on many hierarchies at once (bcmg_solve_batch): the solves run
+    concurrently on the device.  Returns (cycles, rel, statuses) lists; does
+    not raise for a solve that stopped at max_cycles (its status says so)."""
+    n = len(solvers)
+    if len(us) != n:
+        raise ValueError("one u per solver")
+    hs = (C.c_void_p * n)(*[s.h.value for s in solvers])
+    ps = (C.c_void_p * n)(*[_dptr(u).value for u in us])
+    cyc = np.zeros(n, dtype=np.int32)
+    rel = np.zeros(n)
+    st = np.zeros(n, dtype=np.int32)
+    rc = load().bcmg_solve_batch(hs, ps, n, float(rtol), int(max_cycles), _hptr(cyc), _hptr(rel), _hptr(st))
+    if rc not in (OK, ENOCONV, ENONFINITE):
+        _check(rc)
+    return [int(c) for c in cyc], [float(r) for r in rel], [int(x) for x in st]
+
+
 class Solver:
     """A BCMG hierarchy on the current CUDA device.
 
@@ -209,6 +238,12 @@ class Solver:
         out = np.zeros(2)
         _check(self.lib.bcmg_profile_read(self.h, _hptr(out)))
         return {"smooth_ms": float(out[0]), "smooth_launches": int(out[1])}
+
+    def memory_footprint(self) -> int:
+        """Device memory (bytes) this hierarchy holds."""
+        out = C.c_int64()
+        _check(self.lib.bcmg_memory_footprint(self.h, C.byref(out)))
+        return out.value
 
     def residual_norm(self, u) -> np.ndarray:
         out = np.zeros(4)

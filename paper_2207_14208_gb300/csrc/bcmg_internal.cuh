@@ -95,7 +95,10 @@ struct SolveState {
     int status;      // out: BCMG_OK or BCMG_ENONFINITE
 };
 
+constexpr uint32_t kHandleMagic = 0x474d4342u;  // set while a handle is live
+
 struct Handle {
+    uint32_t magic = kHandleMagic;
     int d = 0;
     int64_t N = 0;
     bcmg_opts o{};
@@ -124,6 +127,7 @@ struct Handle {
     bool capturing = false;
     int64_t captured = 0;
     std::vector<void *> allocs;
+    int64_t dev_bytes = 0;      // device memory the handle holds
     std::vector<void *> temps;  // set-up scratch, freed when creation ends
     // profiling of the finest-level sweeps (opts.profile)
     std::vector<cudaEvent_t> pev;

@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "bcmg_internal.cuh"
 
@@ -38,6 +40,7 @@ void *dalloc(Handle &H, size_t bytes, bool temp) {
         throw Error{BCMG_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
     }
     (temp ? H.temps : H.allocs).push_back(p);
+    if (!temp) H.dev_bytes += (int64_t)bytes;
     check_cuda(cudaMemsetAsync(p, 0, bytes, H.st), "cudaMemsetAsync");
     return p;
 }
@@ -81,23 +84,52 @@ void keep_pool_memory() {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
 }
 
+// Small pinned host blocks (norms, solve state) come from a process-wide
+// pool that is never returned to the driver: cudaFreeHost waits for the
+// whole device, which would make every handle's destroy wait for the work
+// of all other handles in flight.
+constexpr size_t kPinBlock = 256;
+std::mutex g_pin_mu;
+std::vector<void *> g_pin_free;
+
+void *pinned_get() {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        if (!g_pin_free.empty()) {
+            void *p = g_pin_free.back();
+            g_pin_free.pop_back();
+            return p;
+        }
+    }
+    void *p = nullptr;
+    check_cuda(cudaMallocHost(&p, kPinBlock), "cudaMallocHost");
+    return p;
+}
+
+void pinned_put(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+}
+
 void destroy(Handle *H) {
     if (!H) return;
     if (H->st) cudaStreamSynchronize(H->st);
     if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
     if (H->ngraph) cudaGraphExecDestroy(H->ngraph);
     if (H->sgraph) cudaGraphExecDestroy(H->sgraph);
-    if (H->shost) cudaFreeHost(H->shost);
+    pinned_put(H->shost);
     if (H->st) {
         free_temps(*H);
         for (void *p : H->allocs) cudaFreeAsync(p, H->st);
         cudaStreamSynchronize(H->st);
     }
-    if (H->nhost) cudaFreeHost(H->nhost);
+    pinned_put(H->nhost);
     for (cudaEvent_t e : H->pev) cudaEventDestroy(e);
     if (H->ev_in) cudaEventDestroy(H->ev_in);
     if (H->ev_out) cudaEventDestroy(H->ev_out);
     if (H->st) cudaStreamDestroy(H->st);
+    H->magic = 0;
     delete H;
 }
 
@@ -273,7 +305,9 @@ void fetch_norms(Handle &H, double out[4]) {
 
 Handle *checked(bcmg_handle h) {
     if (!h) throw Error{BCMG_EINVAL, "null handle"};
-    return reinterpret_cast<Handle *>(h);
+    Handle *H = reinterpret_cast<Handle *>(h);
+    if (H->magic != kHandleMagic) throw Error{BCMG_EINVAL, "not a live handle"};
+    return H;
 }
 
 Level &level_of(Handle &H, int l) {
@@ -294,6 +328,75 @@ int guarded(Fn fn) {
     } catch (...) {
         return fail(BCMG_ECUDA, "unexpected exception");
     }
+}
+
+// Enqueue a whole device-driven solve on the handle's stream (no host wait):
+// copy u in, the solve graph, the state back, u out.  False if this handle
+// solves with the host loop instead (profiling, graphs off, or no graph).
+bool solve_enqueue(Handle &H, double *u_dev, double rtol, int max_cycles) {
+    if (!H.o.use_graph || H.o.profile) return false;
+    if (!H.sgraph && !H.sgraph_failed) H.sgraph = build_solve_graph(H);
+    if (!H.sgraph) return false;
+    enter(H);
+    copy_active(H, u_dev, H.u0, true);
+    H.shost->rtol = rtol;
+    H.shost->max_cycles = max_cycles;
+    check_cuda(cudaMemcpyAsync(H.sdev, H.shost, sizeof(SolveState), cudaMemcpyHostToDevice, H.st), "solve state H2D");
+    check_cuda(cudaGraphLaunch(H.sgraph, H.st), "cudaGraphLaunch(solve)");
+    check_cuda(cudaMemcpyAsync(H.shost, H.sdev, sizeof(SolveState), cudaMemcpyDeviceToHost, H.st), "solve state D2H");
+    copy_active(H, H.u0, u_dev, false);
+    leave(H);
+    return true;
+}
+
+// wait for an enqueued solve and read its state
+int solve_finish(Handle &H, double rtol, int *cycles, double *rel) {
+    check_cuda(cudaStreamSynchronize(H.st), "solve sync");
+    const SolveState &s = *H.shost;
+    *cycles = s.cycles;
+    *rel = s.rel;
+    add_launches(H.sgraph_prefix + H.sgraph_body * (int64_t)s.cycles);
+    int status = s.status;
+    if (status == BCMG_OK && s.r0 > 0.0 && s.rel > rtol) status = BCMG_ENOCONV;
+    return status;
+}
+
+// host-driven loop over captured cycle graphs (or plain launches), reading
+// the norms after every cycle
+int solve_host_loop(Handle &H, double *u_dev, double rtol, int max_cycles, int *cycles, double *rel_out) {
+    int status = BCMG_OK;
+    enter(H);
+    copy_active(H, u_dev, H.u0, true);
+    enqueue_norms(H);
+    double nr[4];
+    fetch_norms(H, nr);
+    const double r0 = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
+    double rel = (r0 > 0.0) ? 1.0 : 0.0;
+    int c = 0;
+    if (!std::isfinite(r0)) status = BCMG_ENONFINITE;
+    while (status == BCMG_OK && r0 > 0.0 && c < max_cycles) {
+        run_vcycle_norms(H);
+        fetch_norms(H, nr);
+        profile_collect(H);
+        ++c;
+        const double rn = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
+        rel = rn / r0;
+        if (!std::isfinite(rn)) status = BCMG_ENONFINITE;
+        else if (rel <= rtol) break;
+    }
+    if (status == BCMG_OK && r0 > 0.0 && rel > rtol) status = BCMG_ENOCONV;
+    copy_active(H, H.u0, u_dev, false);
+    leave(H);
+    *cycles = c;
+    *rel_out = rel;
+    return status;
+}
+
+int solve_status(int status) {
+    if (status == BCMG_ENOCONV) return fail(status, "max_cycles reached before rtol");
+    if (status == BCMG_ENONFINITE) return fail(status, "non-finite residual");
+    g_last_error.clear();
+    return BCMG_OK;
 }
 
 }  // namespace
@@ -355,8 +458,9 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         H->npart = (double *)dalloc(*H, sizeof(double) * 4 * (norm_parts(L0) + 1));
         setup_cycle(*H);
         H->nout = (double *)dalloc(*H, sizeof(double) * 4);
-        check_cuda(cudaMallocHost((void **)&H->nhost, 4 * sizeof(double)), "cudaMallocHost");
-        check_cuda(cudaMallocHost((void **)&H->shost, sizeof(SolveState)), "cudaMallocHost");
+        static_assert(sizeof(SolveState) <= kPinBlock && 4 * sizeof(double) <= kPinBlock, "pinned block");
+        H->nhost = (double *)pinned_get();
+        H->shost = (SolveState *)pinned_get();
         H->sdev = (SolveState *)dalloc(*H, sizeof(SolveState));
         set_interior_rhs(*H, L0, f_dev, L0.F);
         for (auto &L : H->L) L.phi = nullptr;
@@ -437,54 +541,82 @@ int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *c
     int rc = guarded([&] {
         Handle &H = *checked(h);
         if (!u_dev || max_cycles < 0 || !(rtol >= 0.0)) throw Error{BCMG_EINVAL, "bad u, rtol or max_cycles"};
-        enter(H);
-        copy_active(H, u_dev, H.u0, true);
-        double rel = 0.0, r0 = 0.0;
         int c = 0;
-        // device-driven loop (one graph launch) unless sweeps are profiled
-        // (event records cannot sit inside a conditional body) or graphs are off
-        if (H.o.use_graph && !H.o.profile && !H.sgraph && !H.sgraph_failed) H.sgraph = build_solve_graph(H);
-        if (H.o.use_graph && !H.o.profile && H.sgraph) {
-            H.shost->rtol = rtol;
-            H.shost->max_cycles = max_cycles;
-            check_cuda(cudaMemcpyAsync(H.sdev, H.shost, sizeof(SolveState), cudaMemcpyHostToDevice, H.st),
-                       "solve state H2D");
-            check_cuda(cudaGraphLaunch(H.sgraph, H.st), "cudaGraphLaunch(solve)");
-            check_cuda(cudaMemcpyAsync(H.shost, H.sdev, sizeof(SolveState), cudaMemcpyDeviceToHost, H.st),
-                       "solve state D2H");
-            check_cuda(cudaStreamSynchronize(H.st), "solve sync");
-            c = H.shost->cycles;
-            r0 = H.shost->r0;
-            rel = H.shost->rel;
-            status = H.shost->status;
-            add_launches(H.sgraph_prefix + H.sgraph_body * (int64_t)c);
-        } else {
-            enqueue_norms(H);
-            double nr[4];
-            fetch_norms(H, nr);
-            r0 = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
-            rel = (r0 > 0.0) ? 1.0 : 0.0;
-            if (!std::isfinite(r0)) status = BCMG_ENONFINITE;
-            while (status == BCMG_OK && r0 > 0.0 && c < max_cycles) {
-                run_vcycle_norms(H);
-                fetch_norms(H, nr);
-                profile_collect(H);
-                ++c;
-                const double rn = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
-                rel = rn / r0;
-                if (!std::isfinite(rn)) status = BCMG_ENONFINITE;
-                else if (rel <= rtol) break;
-            }
-        }
-        if (status == BCMG_OK && r0 > 0.0 && rel > rtol) status = BCMG_ENOCONV;
-        copy_active(H, H.u0, u_dev, false);
-        leave(H);
+        double rel = 0.0;
+        if (solve_enqueue(H, u_dev, rtol, max_cycles)) status = solve_finish(H, rtol, &c, &rel);
+        else status = solve_host_loop(H, u_dev, rtol, max_cycles, &c, &rel);
         if (cycles_done) *cycles_done = c;
         if (final_rel_res) *final_rel_res = rel;
     });
     if (rc != BCMG_OK) return rc;
-    if (status == BCMG_ENOCONV) return fail(status, "max_cycles reached before rtol");
-    if (status == BCMG_ENONFINITE) return fail(status, "non-finite residual");
+    return solve_status(status);
+}
+
+int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, int max_cycles,
+                     int *cycles_done, double *final_rel_res, int *statuses) {
+    if (n < 0 || (n > 0 && (!handles || !u_devs))) return fail(BCMG_EINVAL, "bad batch arrays");
+    int first = BCMG_OK;
+    int rc = guarded([&] {
+        if (max_cycles < 0 || !(rtol >= 0.0)) throw Error{BCMG_EINVAL, "bad rtol or max_cycles"};
+        std::vector<Handle *> hs(n);
+        for (int i = 0; i < n; ++i) {
+            hs[i] = checked(handles[i]);
+            if (!u_devs[i]) throw Error{BCMG_EINVAL, "null u in batch"};
+            for (int j = 0; j < i; ++j)
+                if (hs[j] == hs[i]) throw Error{BCMG_EINVAL, "a handle appears twice in the batch"};
+        }
+        // the solve graphs are built first (no capture while other solves
+        // run), then every device-driven solve is enqueued on its handle's
+        // own stream before any is waited for, so the solves run concurrently
+        for (int i = 0; i < n; ++i) {
+            Handle &H = *hs[i];
+            if (H.o.use_graph && !H.o.profile && !H.sgraph && !H.sgraph_failed) H.sgraph = build_solve_graph(H);
+        }
+        std::vector<char> queued(n, 0);
+        for (int i = 0; i < n; ++i) queued[i] = solve_enqueue(*hs[i], u_devs[i], rtol, max_cycles) ? 1 : 0;
+        for (int i = 0; i < n; ++i) {
+            int c = 0;
+            double rel = 0.0;
+            const int st = queued[i] ? solve_finish(*hs[i], rtol, &c, &rel)
+                                     : solve_host_loop(*hs[i], u_devs[i], rtol, max_cycles, &c, &rel);
+            if (cycles_done) cycles_done[i] = c;
+            if (final_rel_res) final_rel_res[i] = rel;
+            if (statuses) statuses[i] = st;
+            if (first == BCMG_OK && st != BCMG_OK) first = st;
+        }
+    });
+    if (rc != BCMG_OK) return rc;
+    return solve_status(first);
+}
+
+int bcmg_memory_footprint(bcmg_handle h, int64_t *bytes) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!bytes) throw Error{BCMG_EINVAL, "bytes is null"};
+        *bytes = H.dev_bytes;
+    });
+}
+
+int bcmg_footprint_estimate(int dim, int64_t N, const bcmg_opts *opts, int64_t *bytes) {
+    if (!bytes) return fail(BCMG_EINVAL, "bytes is null");
+    if ((dim != 2 && dim != 3) || N < 4 || N > 65534) return fail(BCMG_EINVAL, "bad dim or N");
+    bcmg_opts o;
+    if (opts) o = *opts;
+    else bcmg_default_opts(&o);
+    // dense per-level arrays (class byte, u, F, r; FP32 u, F, r for the mixed
+    // path) over the levels the coarsening rule allows, doubled to cover the
+    // compacted lists (ghost weights, expanded extension), which hold far
+    // fewer entries than the grid but more bytes per entry
+    const double per_node = 1.0 + 3.0 * 8.0 + (o.precision == BCMG_PREC_MIXED ? 3.0 * 4.0 : 0.0);
+    double total = 0.0;
+    int64_t Nl = N;
+    for (int l = 0; l < std::max(o.max_levels, 1); ++l) {
+        total += std::pow((double)(Nl + 1), dim) * per_node;
+        if (Nl % 2 != 0 || Nl / 2 < o.min_coarse) break;
+        Nl /= 2;
+    }
+    *bytes = (int64_t)(2.0 * total) + (int64_t)(1 << 20);
+    g_last_error.clear();
     return BCMG_OK;
 }
 

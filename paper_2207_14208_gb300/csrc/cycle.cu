@@ -15,6 +15,9 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "bcmg_internal.cuh"
 
@@ -750,6 +753,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
 
 size_t tail_smem(int nl) { return (size_t)nl * kTailThreads * (5 * sizeof(uint32_t) + sizeof(uint16_t)); }
 
+// The dynamic shared-memory limit is a property of the kernel for the whole
+// process, shared by every handle: it is always set to what the deepest
+// allowed tail needs (kTailMaxLevels levels, 176 KiB), never to one
+// handle's need, so no handle can lower it under another's launches.
+constexpr int kTailMaxLevels = 16;
+
 // ------------------------------------------------------------ solve control
 // norms of the residual (interior, ghost) -> sqrt(a^2 + b^2), rounded step by step
 __device__ __forceinline__ double resid_norm(const double *nout) {
@@ -943,11 +952,14 @@ cudaLaunchConfig_t tail_config(Handle &H, int csize, int nl, cudaLaunchAttribute
 }
 
 // largest cluster (16, else 8) of kTailThreads-thread CTAs with the shared
-// memory of nl staged levels that the device can place; 0 if none
+// memory of the deepest allowed tail that the device can place; 0 if none.
+// Queried once per device, dimension and precision (the answer does not
+// depend on the handle).
 template <typename T>
-int tail_cluster_size(Handle &H, int nl) {
+int tail_cluster_size_query(Handle &H) {
     TailKernel<T> k = tail_kernel<T>(H.d);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem(nl)) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem(kTailMaxLevels)) !=
+        cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
@@ -957,12 +969,29 @@ int tail_cluster_size(Handle &H, int nl) {
             continue;
         }
         cudaLaunchAttribute at[2];
-        cudaLaunchConfig_t cfg = tail_config(H, cs, nl, at, false);
+        cudaLaunchConfig_t cfg = tail_config(H, cs, kTailMaxLevels, at, false);
         int n = 0;
         if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n >= 1) return cs;
         (void)cudaGetLastError();
     }
     return 0;
+}
+
+std::mutex g_tail_mu;
+std::map<std::tuple<int, int, int>, int> g_tail_cs;
+
+template <typename T>
+int tail_cluster_size(Handle &H, int nl) {
+    if (nl > kTailMaxLevels) return 0;
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    const auto key = std::make_tuple(dev, H.d, (int)sizeof(T));
+    std::lock_guard<std::mutex> lk(g_tail_mu);
+    auto it = g_tail_cs.find(key);
+    if (it != g_tail_cs.end()) return it->second;
+    const int cs = tail_cluster_size_query<T>(H);
+    g_tail_cs[key] = cs;
+    return cs;
 }
 
 template <typename T>

@@ -1058,8 +1058,10 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         L.bbuf = (double *)dalloc(H, sizeof(double) * 2 * nb1);
         if (ell && L.nb > 0) {
             L.ecnt = (uint8_t *)dalloc(H, (size_t)nb1);
-            L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1);
-            L.ew = (double *)dalloc(H, sizeof(double) * kExtCap * nb1);
+            // expansion scratch with kExtCap slots; the resident copy keeps
+            // only the slots the level's longest row needs (see round 3)
+            L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1, true);
+            L.ew = (double *)dalloc(H, sizeof(double) * kExtCap * nb1, true);
         }
         LevelTab &t = tab[l];
         t.bidx = L.bidx;
@@ -1097,6 +1099,23 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             L.nfall = hc[2 * l + 1];
             if (hov[l]) L.ecnt = nullptr;  // a row longer than kExtCap: sweep by sweep
             L.ell_max = hov[keep + l];
+            if (L.ecnt) {
+                // term-major ELL: the first ell_max slabs are the whole map;
+                // keep a multiple of 8 slots (the tail reads 8-term rounds),
+                // the extra slots zero
+                const int64_t nb1 = std::max<int64_t>(L.nb, 1);
+                const int slots = std::min(kExtCap, ((std::max(L.ell_max, 1) + 7) / 8) * 8);
+                uint32_t *eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * slots * nb1);
+                double *ew = (double *)dalloc(H, sizeof(double) * slots * nb1);
+                check_cuda(cudaMemcpyAsync(eg, L.eg, sizeof(uint32_t) * (size_t)L.ell_max * nb1,
+                                           cudaMemcpyDeviceToDevice, H.st),
+                           "ELL copy");
+                check_cuda(cudaMemcpyAsync(ew, L.ew, sizeof(double) * (size_t)L.ell_max * nb1,
+                                           cudaMemcpyDeviceToDevice, H.st),
+                           "ELL copy");
+                L.eg = eg;
+                L.ew = ew;
+            }
         }
     }
     // level arrays
@@ -1127,13 +1146,18 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     if (n <= kLuSmall) {
         double *LU = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
         int *perm = (int *)dalloc(H, sizeof(int) * std::max<int64_t>(n, 1), true);
+        // shared-memory limits are per kernel for the whole process: always
+        // the largest size (n = kLuSmall), never one handle's n
         const size_t smem = sizeof(double) * (size_t)(n * n);
-        check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * kLuSmall * kLuSmall)),
                    "LU shared memory");
         k_lu_small<<<1, 1024, smem, H.st>>>(A, (int)n, LU, perm, sing);
         count_launch(H);
         const size_t smem2 = sizeof(double) * (size_t)(n * n + n + kLuColsPerBlock * n);
-        check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2),
+        check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + (2 + kLuColsPerBlock) *
+                                                                                        kLuSmall))),
                    "LU inverse shared memory");
         k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st>>>(LU, (int)n, perm, L.Ainv);
         count_launch(H);

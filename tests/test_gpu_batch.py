@@ -1,0 +1,89 @@
+"""Batched solves (bcmg_solve_batch) and device-memory footprints.
+
+Many hierarchies of uneven size and shape are solved in one call; their
+solves run concurrently on the device (each on its own stream).  Each result
+must be bit-identical to the same solve alone, in FP64 and in mixed
+precision, and the footprint estimate used for admission must cover what a
+hierarchy actually holds."""
+
+import numpy as np
+import pytest
+
+from paper_2207_14208_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bcmg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_14208_gb300 import bcmg as B
+    from paper_2207_14208_gb300 import build
+    build.build()
+    return B
+
+
+def _problems():
+    """Seeded star domains of the batched workload (sizes 64..1024 drawn
+    log-uniformly; the small ones kept so the test stays quick) plus a 3D
+    ellipsoid."""
+    out = []
+    for N, a, k, psi in W.star_params(256, 1):
+        if N <= 320 and len(out) < 6:
+            out.append((2, N, W.phi_star(N, a, k, psi)))
+    out.append((3, 40, W.phi_ellipsoid(40)))
+    return out
+
+
+def _make(B, d, N, phi, precision):
+    f, _ = W.manufactured(d, N)
+    s = B.Solver(d, N, torch.from_numpy(phi).cuda(), torch.from_numpy(f).cuda(), precision=precision)
+    g = W.g_at(d, s.ghost_points().cpu().numpy())
+    s.set_boundary_values(torch.from_numpy(g).cuda())
+    return s, torch.zeros((N + 1) ** d, dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_alone(bcmg, prec):
+    B = bcmg
+    p = B.PREC_FP64 if prec == "fp64" else B.PREC_MIXED
+    probs = _problems()
+    alone = []
+    for d, N, phi in probs:
+        s, u = _make(B, d, N, phi, p)
+        c, rel = s.solve(u, 1e-10, 100)
+        torch.cuda.synchronize()
+        alone.append((c, rel, u.cpu().numpy()))
+        s.close()
+    pairs = [_make(B, d, N, phi, p) for d, N, phi in probs]
+    cyc, rel, st = B.solve_batch([s for s, _ in pairs], [u for _, u in pairs], 1e-10, 100)
+    torch.cuda.synchronize()
+    assert st == [B.OK] * len(probs)
+    for i, (s, u) in enumerate(pairs):
+        assert cyc[i] == alone[i][0] and rel[i] == alone[i][1]
+        np.testing.assert_array_equal(u.cpu().numpy(), alone[i][2])
+        s.close()
+
+
+def test_batch_rejects_duplicates_and_reports_limits(bcmg):
+    B = bcmg
+    s, u = _make(B, 2, 64, W.phi_disk(64), B.PREC_FP64)
+    with pytest.raises(B.BcmgError):
+        B.solve_batch([s, s], [u, u.clone()])
+    cyc, rel, st = B.solve_batch([s], [u], 1e-14, 2)
+    assert cyc == [2] and st == [B.ENOCONV]
+    s.close()
+
+
+@pytest.mark.parametrize("d,N,mk,prec", [(2, 128, W.phi_disk, "fp64"), (2, 512, W.phi_disk, "mixed"),
+                                         (3, 96, W.phi_ellipsoid, "fp64"), (3, 256, W.phi_ellipsoid, "mixed")])
+def test_footprint_estimate_covers_actual(bcmg, d, N, mk, prec):
+    B = bcmg
+    p = B.PREC_FP64 if prec == "fp64" else B.PREC_MIXED
+    s, _ = _make(B, d, N, mk(N), p)
+    actual = s.memory_footprint()
+    est = B.footprint_estimate(d, N, precision=p)
+    assert 0 < actual <= est <= 4 * actual + (2 << 20)
+    s.close()
