@@ -62,7 +62,8 @@ typedef struct {
     int nu1;           /* pre-smoothing steps (Sec. 3.1: 2) */
     int nu2;           /* post-smoothing steps (Sec. 3.1: 1) */
     int dtau_mode;     /* BCMG_DTAU_* */
-    double dtau_const; /* Delta tau when dtau_mode == BCMG_DTAU_CONST */
+    double dtau_const; /* Delta tau (Neumann: Delta tau / h) when
+                          dtau_mode == BCMG_DTAU_CONST */
     int ext_sweeps;    /* pseudo-time sweeps of the normal extension (4) */
     int min_coarse;    /* coarsening stops before N_l / 2 < min_coarse (8) */
     int max_levels;    /* upper bound on the number of levels (24) */
@@ -70,7 +71,21 @@ typedef struct {
     int profile;       /* time every finest-level smoothing sweep with CUDA
                           events during bcmg_solve (0) */
     int precision;     /* BCMG_PREC_FP64 (default) or BCMG_PREC_MIXED */
+    int bc;            /* boundary condition on Gamma: BCMG_BC_DIRICHLET
+                          (default) or BCMG_BC_NEUMANN */
+    double reaction;   /* c >= 0 of the interior equation c u - Lap u = f
+                          (0: Poisson, the default; Sec. 4.2 Test2N: 1) */
 } bcmg_opts;
+
+/* Boundary conditions on Gamma (Sec. 3): Dirichlet u = g; Neumann
+ * grad u . n = g with n the ghost's outward unit normal (bcmg_ghost_normals),
+ * the ghost row being the normal derivative at Q of the same interpolant
+ * (Sec. 3.2.2, Sec. 4.1) relaxed with Delta tau = h (Delta tau / h)_OPT(theta)
+ * (eqs. dtauoptLFA_Neumann, dtauoptLFA3D_Neumann; with BCMG_DTAU_CONST,
+ * dtau_const is Delta tau / h).  Box-boundary nodes inside the domain stay
+ * eliminated Dirichlet nodes (Test1N of Sec. 4.2). */
+#define BCMG_BC_DIRICHLET 0
+#define BCMG_BC_NEUMANN 1
 
 #define BCMG_PREC_FP64 0  /* every cycle in FP64 */
 #define BCMG_PREC_MIXED 1 /* FP64 iterative refinement: FP64 residual and
@@ -109,8 +124,14 @@ int bcmg_ghost_count(bcmg_handle h, int64_t *n);
  * device buffer Q_dev.  The caller evaluates its boundary data there. */
 int bcmg_ghost_points(bcmg_handle h, double *Q_dev);
 
-/* Dirichlet values g(Q) for the finest-level ghosts (eq. BCh right-hand
- * side), count FP64 values in ghost-list order, device pointer. */
+/* Outward unit normals n (computed from phi at each ghost G, Sec. 3.3) of
+ * the finest-level ghosts, ghost-list order, count x dim FP64 to the device
+ * buffer n_dev: the direction of the Neumann data. */
+int bcmg_ghost_normals(bcmg_handle h, double *n_dev);
+
+/* Boundary data for the finest-level ghosts (eq. BCh right-hand side):
+ * Dirichlet values g(Q), or Neumann values grad u(Q) . n with n from
+ * bcmg_ghost_normals; count FP64 values in ghost-list order, device pointer. */
 int bcmg_set_boundary_values(bcmg_handle h, const double *g_dev);
 
 /* Replace the interior right-hand side f (n^dim, device; NULL = 0). */

@@ -21,6 +21,17 @@
  *   GHOST    : phi >= 0 with at least one of its 2d axis neighbours INTERIOR
  *   INACTIVE : everything else
  *
+ * Boundary condition on Gamma (Sec. 3, operator B of the problem statement):
+ *   Dirichlet (bc = 0): B u = u(Q), the tensor Lagrange interpolant of u on
+ *              the ghost stencil evaluated at Q (eq. BCh);
+ *   Neumann   (bc = 1): B u = grad u(Q) . n, the normal derivative of the same
+ *              interpolant at Q (Sec. 3.2.2 in 1D/2D, Sec. 4.1 in 3D), with n
+ *              the unit normal computed at G; its relaxation step is
+ *              Delta tau = h * (Delta tau / h)_OPT (eqs. dtauoptLFA_Neumann,
+ *              dtauoptLFA3D_Neumann).
+ * Interior equation: c u - Lap_h u = f with reaction coefficient c >= 0
+ * (c = 0: Poisson; c = 1: the reaction-diffusion problem of Test2N, Sec. 4.2).
+ *
  * Parity unpinned (no printed value in the paper fixes them; they are pinned
  * only by the convergence and accuracy tests): the band extension (number of
  * sweeps, upwind form), the coarse-level stencil fall-backs and the root
@@ -42,6 +53,8 @@ typedef struct {
     int d, N, n;
     long nn, st[3];
     double h;
+    int bc;       /* 0 Dirichlet, 1 Neumann on Gamma */
+    double react; /* reaction coefficient c of c u - Lap u = f */
     double *phi;
     unsigned char *cls;
     long nint, nbox;
@@ -70,6 +83,8 @@ typedef struct {
     int d, N, L;
     int nu1, nu2, ordering, dtau_mode, ext_sweeps, cycle, min_coarse, max_levels;
     int tgcs_maxit, rmode, ext_mode;
+    int bc;
+    double react;
     double ext_cfl;
     double dtau_const, tgcs_tol;
     long block_sweeps_last;
@@ -114,6 +129,20 @@ static void lagrange(int q, double xi, double w[3]) {
         w[1] = xi;
     } else {
         w[0] = 1.0;
+    }
+}
+
+/* derivatives d/dxi of the same basis (the Neumann rows of Sec. 3.2.2: at
+ * xi = theta they give -(c_0, c_-1, c_-2) of eq. coeffN) */
+static void lagrange_d(int q, double xi, double w[3]) {
+    w[0] = w[1] = w[2] = 0.0;
+    if (q == 2) {
+        w[0] = xi - 1.5;
+        w[1] = 2.0 - 2.0 * xi;
+        w[2] = xi - 0.5;
+    } else if (q == 1) {
+        w[0] = -1.0;
+        w[1] = 1.0;
     }
 }
 
@@ -394,7 +423,8 @@ static void setup_ghosts(oracle_t *O, olevel *L) {
         }
         /* Delta tau = Delta tau_OPT(theta~), theta~ = |G - Q| / h = eta
          * (eq. DtauOptTheta; exp form of G0 by Remark exptheta2D). */
-        L->gdt[g] = orc_dtau(d, 0, O->dtau_mode, O->dtau_const, eta);
+        L->gdt[g] = orc_dtau(d, O->bc, O->dtau_mode, O->dtau_const, eta);
+        if (O->bc == 1) L->gdt[g] *= L->h; /* Neumann: the formulas give Dtau / h */
         ++g;
     }
 }
@@ -461,25 +491,62 @@ static void setup_band(olevel *L) {
 /* operators                                                            */
 /* ------------------------------------------------------------------ */
 
-/* B u~ at ghost g: biquadratic (triquadratic) interpolant of u on ST_G
- * evaluated at Q (eq. BCh), i.e. sum_k w_k u_k with tensor Lagrange weights. */
-static double ghost_apply(const olevel *L, long g, const double *u) {
-    int d = L->d;
-    double w[3][3] = {{1, 0, 0}, {1, 0, 0}, {1, 0, 0}};
-    int q[3] = {0, 0, 0}, s[3] = {0, 0, 0};
-    for (int a = 0; a < d; ++a) {
-        q[a] = L->gq[3 * g + a];
-        s[a] = L->gs[3 * g + a];
-        lagrange(q[a], L->gxi[3 * g + a], w[a]);
+/* Per-ghost basis values w[a][o] = L_o(xi_a) and derivatives dw[a][o] =
+ * L_o'(xi_a) on the stencil ST_G = {X - sum_a s_a o_a e_a, 0 <= o_a <= q_a}. */
+typedef struct {
+    int q[3], s[3];
+    double w[3][3], dw[3][3], n[3];
+} gstencil;
+
+static void ghost_stencil(const olevel *L, long g, gstencil *S) {
+    for (int a = 0; a < 3; ++a) {
+        S->q[a] = 0;
+        S->s[a] = 0;
+        S->n[a] = 0.0;
+        S->w[a][0] = 1.0;
+        S->w[a][1] = S->w[a][2] = 0.0;
+        S->dw[a][0] = S->dw[a][1] = S->dw[a][2] = 0.0;
     }
+    for (int a = 0; a < L->d; ++a) {
+        S->q[a] = L->gq[3 * g + a];
+        S->s[a] = L->gs[3 * g + a];
+        S->n[a] = L->gn[3 * g + a];
+        lagrange(S->q[a], L->gxi[3 * g + a], S->w[a]);
+        lagrange_d(S->q[a], L->gxi[3 * g + a], S->dw[a]);
+    }
+}
+
+/* weight of stencil node (o0, o1, o2) in the ghost row.  Dirichlet: the
+ * tensor Lagrange weight.  Neumann: sum_a n_a d/dx_a of it; with the local
+ * coordinate t_a = -s_a (x_a - x_G,a) / h of the stencil axis, d/dx_a =
+ * (-s_a / h) d/dt_a, evaluated at t = xi (the position of Q). */
+static double ghost_weight(const olevel *L, const gstencil *S, int o0, int o1, int o2) {
+    const int o[3] = {o0, o1, o2};
+    if (L->bc == 0) return S->w[0][o0] * S->w[1][o1] * S->w[2][o2];
+    double v = 0.0;
+    for (int a = 0; a < L->d; ++a) {
+        double t = S->n[a] * (-(double)S->s[a] / L->h) * S->dw[a][o[a]];
+        for (int b = 0; b < L->d; ++b)
+            if (b != a) t *= S->w[b][o[b]];
+        v += t;
+    }
+    return v;
+}
+
+/* B u~ at ghost g: the boundary operator of the ghost row applied to the
+ * (tri/bi)quadratic interpolant of u on ST_G at Q (eq. BCh), i.e.
+ * sum_k w_k u_k with the row's weights. */
+static double ghost_apply(const olevel *L, long g, const double *u) {
+    gstencil S;
+    ghost_stencil(L, g, &S);
     long X = L->gidx[g];
     double B = 0.0;
-    for (int o2 = 0; o2 <= q[2]; ++o2)
-        for (int o1 = 0; o1 <= q[1]; ++o1)
-            for (int o0 = 0; o0 <= q[0]; ++o0) {
-                long Y = X - (long)s[0] * o0 * L->st[0] - (long)s[1] * o1 * L->st[1] -
-                         (long)s[2] * o2 * L->st[2];
-                B += w[0][o0] * w[1][o1] * w[2][o2] * u[Y];
+    for (int o2 = 0; o2 <= S.q[2]; ++o2)
+        for (int o1 = 0; o1 <= S.q[1]; ++o1)
+            for (int o0 = 0; o0 <= S.q[0]; ++o0) {
+                long Y = X - (long)S.s[0] * o0 * L->st[0] - (long)S.s[1] * o1 * L->st[1] -
+                         (long)S.s[2] * o2 * L->st[2];
+                B += ghost_weight(L, &S, o0, o1, o2) * u[Y];
             }
     return B;
 }
@@ -509,10 +576,11 @@ static int parity(const olevel *L, long lin) {
     return (ix[0] + ix[1] + ix[2]) & 1;
 }
 
-/* Gauss-Seidel on the 5/7-point equations (eq. GSLEX_2D, eq. Laph):
- * u_X = (sum nbrs + h^2 F_X) / (2d); ghost neighbours hold their old values. */
+/* Gauss-Seidel on the 5/7-point equations (eq. GSLEX_2D, eq. Laph) of
+ * c u - Lap_h u = f: u_X = (sum nbrs + h^2 F_X) / (2d + c h^2); ghost
+ * neighbours hold their old values. */
 static void interior_update(olevel *L, long lin, double *u, const double *F) {
-    u[lin] = (nbr_sum(L, lin, u) + L->h * L->h * F[lin]) / (2.0 * L->d);
+    u[lin] = (nbr_sum(L, lin, u) + L->h * L->h * F[lin]) / (2.0 * L->d + L->react * L->h * L->h);
 }
 
 static void interior_lex(olevel *L, double *u, const double *F) {
@@ -561,7 +629,7 @@ static void residual(const olevel *L, const double *u, const double *F, double *
     for (long lin = 0; lin < L->nn; ++lin) r[lin] = 0.0;
     for (long lin = 0; lin < L->nn; ++lin)
         if (L->cls[lin] == CL_INTERIOR)
-            r[lin] = F[lin] - (2.0 * L->d * u[lin] - nbr_sum(L, lin, u)) / h2;
+            r[lin] = F[lin] - ((2.0 * L->d + L->react * h2) * u[lin] - nbr_sum(L, lin, u)) / h2;
     for (long g = 0; g < L->ng; ++g) {
         long X = L->gidx[g];
         r[X] = F[X] - ghost_apply(L, g, u);
@@ -734,7 +802,7 @@ static void assemble(const olevel *L, const long *act, const int *apos, long nac
     for (long r = 0; r < nact; ++r) {
         long X = act[r];
         if (L->cls[X] == CL_INTERIOR) {
-            A[r * nact + r] += 2.0 * d * ih2;
+            A[r * nact + r] += 2.0 * d * ih2 + L->react;
             for (int a = 0; a < d; ++a)
                 for (int dir = -1; dir <= 1; dir += 2) {
                     long Y = X + dir * L->st[a];
@@ -745,19 +813,14 @@ static void assemble(const olevel *L, const long *act, const int *apos, long nac
     for (long g = 0; g < L->ng; ++g) {
         long X = L->gidx[g];
         long r = apos[X];
-        double w[3][3] = {{1, 0, 0}, {1, 0, 0}, {1, 0, 0}};
-        int q[3] = {0, 0, 0}, s[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a) {
-            q[a] = L->gq[3 * g + a];
-            s[a] = L->gs[3 * g + a];
-            lagrange(q[a], L->gxi[3 * g + a], w[a]);
-        }
-        for (int o2 = 0; o2 <= q[2]; ++o2)
-            for (int o1 = 0; o1 <= q[1]; ++o1)
-                for (int o0 = 0; o0 <= q[0]; ++o0) {
-                    long Y = X - (long)s[0] * o0 * L->st[0] - (long)s[1] * o1 * L->st[1] -
-                             (long)s[2] * o2 * L->st[2];
-                    if (apos[Y] >= 0) A[r * nact + apos[Y]] += w[0][o0] * w[1][o1] * w[2][o2];
+        gstencil S;
+        ghost_stencil(L, g, &S);
+        for (int o2 = 0; o2 <= S.q[2]; ++o2)
+            for (int o1 = 0; o1 <= S.q[1]; ++o1)
+                for (int o0 = 0; o0 <= S.q[0]; ++o0) {
+                    long Y = X - (long)S.s[0] * o0 * L->st[0] - (long)S.s[1] * o1 * L->st[1] -
+                             (long)S.s[2] * o2 * L->st[2];
+                    if (apos[Y] >= 0) A[r * nact + apos[Y]] += ghost_weight(L, &S, o0, o1, o2);
                 }
     }
 }
@@ -870,6 +933,8 @@ static void level_free(olevel *L) {
 }
 
 static void level_finish(oracle_t *O, olevel *L) {
+    L->bc = O->bc;
+    L->react = O->react;
     setup_ghosts(O, L);
     setup_band(L);
     L->u = (double *)calloc((size_t)L->nn, sizeof(double));
@@ -887,8 +952,10 @@ void orc_destroy(void *hp) {
 }
 
 /* iopts: nu1, nu2, ordering, dtau_mode, ext_sweeps, cycle, min_coarse,
- *        max_levels, tgcs_maxit
- * dopts: dtau_const, tgcs_tol
+ *        max_levels, tgcs_maxit, rmode, ext_mode, bc (0 Dirichlet,
+ *        1 Neumann on Gamma)
+ * dopts: dtau_const (Dtau, or Dtau / h for Neumann), tgcs_tol, ext_cfl,
+ *        reaction coefficient c
  * Coarsening (geometric re-discretisation, Sec. 2.1): N_{l+1} = N_l / 2
  * while N_l is even, N_l / 2 >= min_coarse and the coarse level still has
  * interior nodes.  Returns NULL if the finest level has no interior node or
@@ -909,6 +976,8 @@ void *orc_create(int d, int N, const double *phi, const int *iopts, const double
     O->tgcs_maxit = iopts[8];
     O->rmode = iopts[9];
     O->ext_mode = iopts[10];
+    O->bc = iopts[11];
+    O->react = dopts[3];
     O->ext_cfl = dopts[2];
     O->dtau_const = dopts[0];
     O->tgcs_tol = dopts[1];
@@ -1234,19 +1303,14 @@ void orc_assemble(void *hp, int l, const double *u, const double *F, long *act, 
     for (long g = 0; g < L->ng; ++g) {
         long X = L->gidx[g];
         long r = apos[X];
-        double w[3][3] = {{1, 0, 0}, {1, 0, 0}, {1, 0, 0}};
-        int q[3] = {0, 0, 0}, s[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a) {
-            q[a] = L->gq[3 * g + a];
-            s[a] = L->gs[3 * g + a];
-            lagrange(q[a], L->gxi[3 * g + a], w[a]);
-        }
-        for (int o2 = 0; o2 <= q[2]; ++o2)
-            for (int o1 = 0; o1 <= q[1]; ++o1)
-                for (int o0 = 0; o0 <= q[0]; ++o0) {
-                    long Y = X - (long)s[0] * o0 * L->st[0] - (long)s[1] * o1 * L->st[1] -
-                             (long)s[2] * o2 * L->st[2];
-                    if (L->cls[Y] == CL_BOXDIR) rhs[r] -= w[0][o0] * w[1][o1] * w[2][o2] * u[Y];
+        gstencil S;
+        ghost_stencil(L, g, &S);
+        for (int o2 = 0; o2 <= S.q[2]; ++o2)
+            for (int o1 = 0; o1 <= S.q[1]; ++o1)
+                for (int o0 = 0; o0 <= S.q[0]; ++o0) {
+                    long Y = X - (long)S.s[0] * o0 * L->st[0] - (long)S.s[1] * o1 * L->st[1] -
+                             (long)S.s[2] * o2 * L->st[2];
+                    if (L->cls[Y] == CL_BOXDIR) rhs[r] -= ghost_weight(L, &S, o0, o1, o2) * u[Y];
                 }
     }
     free(apos);

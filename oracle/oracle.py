@@ -29,6 +29,8 @@ RB, LEX, BLOCK = 0, 1, 2
 # Delta tau forms: exp form of G0 (Remark exptheta2D), polynomial form
 # (eqs. G / G3D), constant
 DT_EXP, DT_POLY, DT_CONST = 0, 1, 2
+# boundary condition on Gamma
+DIRICHLET, NEUMANN = 0, 1
 # cycles: V (gamma = 1), two-grid correction scheme, W (gamma = 2)
 CYC_V, CYC_TGCS, CYC_W = 0, 1, 2
 
@@ -128,7 +130,8 @@ class Oracle:
                  ordering: int = RB, dtau_mode: int = DT_EXP, dtau_const: float = 1.75,
                  ext_sweeps: int = 4, cycle: int = CYC_V, min_coarse: int = 8,
                  max_levels: int = 24, tgcs_tol: float = 1e-13, tgcs_maxit: int = 200,
-                 rmode: int = 3, ext_mode: int = 0, ext_cfl: float = 0.5):
+                 rmode: int = 3, ext_mode: int = 0, ext_cfl: float = 0.5, bc: int = 0,
+                 reaction: float = 0.0):
         self.lib = _load()
         self.d, self.N = d, N
         self.n = N + 1
@@ -136,8 +139,8 @@ class Oracle:
         phi = _f64(phi).reshape(-1)
         assert phi.size == self.n ** d
         iopts = np.array([nu1, nu2, ordering, dtau_mode, ext_sweeps, cycle, min_coarse,
-                          max_levels, tgcs_maxit, rmode, ext_mode], dtype=np.int32)
-        dopts = np.array([dtau_const, tgcs_tol, ext_cfl], dtype=np.float64)
+                          max_levels, tgcs_maxit, rmode, ext_mode, bc], dtype=np.int32)
+        dopts = np.array([dtau_const, tgcs_tol, ext_cfl, reaction], dtype=np.float64)
         self.h = self.lib.orc_create(d, N, _p(phi), _p(iopts), _p(dopts))
         if not self.h:
             raise ValueError("oracle: no interior node on the finest level")

@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, EGEOM, ENOCONV, ENONFINITE, ETIMEOUT = range(8)
 INACTIVE, INTERIOR, GHOST, BOXDIR = 0, 1, 2, 3
 DTAU_EXP, DTAU_POLY, DTAU_CONST = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
+BC_DIRICHLET, BC_NEUMANN = 0, 1
 
 _lib = None
 _lock = threading.Lock()
@@ -38,7 +39,7 @@ class Opts(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("dtau_mode", C.c_int),
                 ("dtau_const", C.c_double), ("ext_sweeps", C.c_int), ("min_coarse", C.c_int),
                 ("max_levels", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("bc", C.c_int), ("reaction", C.c_double)]
 
 
 def declared_functions():
@@ -69,6 +70,7 @@ def load():
             "bcmg_solve": (i32, [vp, vp, f64, i32, vp, vp]),
             "bcmg_residual_norm": (i32, [vp, vp, vp]),
             "bcmg_solve_batch": (i32, [vp, vp, i32, f64, i32, vp, vp, vp]),
+            "bcmg_ghost_normals": (i32, [vp, vp]),
             "bcmg_memory_footprint": (i32, [vp, vp]),
             "bcmg_footprint_estimate": (i32, [i32, i64, vp, vp]),
             "bcmg_last_error": (C.c_char_p, []),
@@ -213,6 +215,15 @@ class Solver:
         Q = torch.empty((max(ng, 1), self.dim), dtype=torch.float64, device="cuda")
         _check(self.lib.bcmg_ghost_points(self.h, _dptr(Q)))
         return Q[:ng]
+
+    def ghost_normals(self):
+        """Outward unit normals at the finest-level ghosts (count x dim CUDA
+        tensor): the direction of Neumann data."""
+        import torch
+        ng = self.ghost_count()
+        n = torch.empty((max(ng, 1), self.dim), dtype=torch.float64, device="cuda")
+        _check(self.lib.bcmg_ghost_normals(self.h, _dptr(n)))
+        return n[:ng]
 
     def set_boundary_values(self, g):
         _check(self.lib.bcmg_set_boundary_values(self.h, _dptr(g)))

@@ -42,6 +42,7 @@ struct Level {
     int64_t nn = 0;
     int64_t st[3] = {0, 0, 0};
     double h = 0.0;
+    double react = 0.0;  // reaction coefficient c of c u - Lap u = f
     uint8_t *cls = nullptr;
     int64_t nint = 0, nbox = 0, ng = 0, nb = 0, nclamp = 0, nfall = 0, nact = 0;
     int64_t nred = 0;            // red interior nodes (head of ilist)
@@ -153,7 +154,7 @@ int report(int code, const std::string &msg);  // sets the thread's last error
 
 // ---- set-up (setup.cu) -------------------------------------------------
 void setup_hierarchy(Handle &H, const double *phi0);
-double dtau_of(int d, int mode, double cst, double theta);
+double dtau_of(int d, int bc, int mode, double cst, double theta);
 bool ext_ell_ok(int d, int K);
 constexpr int kExtCap = 32;  // terms per band node of the expanded extension
 

@@ -418,6 +418,8 @@ void bcmg_default_opts(bcmg_opts *o) {
     o->use_graph = 1;
     o->profile = 0;
     o->precision = BCMG_PREC_FP64;
+    o->bc = BCMG_BC_DIRICHLET;
+    o->reaction = 0.0;
 }
 
 int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
@@ -438,7 +440,9 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         else bcmg_default_opts(&H->o);
         if (H->o.nu1 < 0 || H->o.nu2 < 0 || H->o.ext_sweeps < 1 || H->o.min_coarse < 2 ||
             H->o.max_levels < 1 || H->o.dtau_mode < 0 || H->o.dtau_mode > 2 ||
-            (H->o.precision != BCMG_PREC_FP64 && H->o.precision != BCMG_PREC_MIXED))
+            (H->o.precision != BCMG_PREC_FP64 && H->o.precision != BCMG_PREC_MIXED) ||
+            (H->o.bc != BCMG_BC_DIRICHLET && H->o.bc != BCMG_BC_NEUMANN) ||
+            !(H->o.reaction >= 0.0 && H->o.reaction < 1e300))
             throw Error{BCMG_EINVAL, "invalid options"};
         H->user = (cudaStream_t)stream;
         keep_pool_memory();
@@ -500,6 +504,21 @@ int bcmg_ghost_points(bcmg_handle h, double *Q_dev) {
         if (L.ng > 0)
             check_cuda(cudaMemcpyAsync(Q_dev, L.gQ, sizeof(double) * L.ng * H.d, cudaMemcpyDeviceToDevice, H.st),
                        "ghost points copy");
+        leave(H);
+    });
+}
+
+int bcmg_ghost_normals(bcmg_handle h, double *n_dev) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!n_dev) throw Error{BCMG_EINVAL, "n is null"};
+        enter(H);
+        Level &L = H.L[0];
+        // the list holds n axis-major (3 x count); the caller gets count x dim
+        for (int a = 0; a < H.d && L.ng > 0; ++a)
+            check_cuda(cudaMemcpy2DAsync(n_dev + a, sizeof(double) * H.d, L.gn + (int64_t)a * L.ng, sizeof(double),
+                                         sizeof(double), (size_t)L.ng, cudaMemcpyDeviceToDevice, H.st),
+                       "ghost normals copy");
         leave(H);
     });
 }

@@ -28,7 +28,8 @@ namespace {
 struct G2 {
     int d, N, n;
     int64_t sy, sz;
-    double h2, ih2, inv2d;
+    double h2, ih2;
+    double diag, inv_diag;  // 2d + c h^2 of c u - Lap_h u = f, and its inverse
 };
 
 G2 g2_of(const Level &L) {
@@ -40,7 +41,8 @@ G2 g2_of(const Level &L) {
     g.sz = L.st[2];
     g.h2 = L.h * L.h;
     g.ih2 = 1.0 / g.h2;
-    g.inv2d = 1.0 / (2.0 * L.d);
+    g.diag = 2.0 * L.d + L.react * g.h2;  // exactly 2d without reaction
+    g.inv_diag = 1.0 / g.diag;
     return g;
 }
 
@@ -152,11 +154,12 @@ __device__ __forceinline__ T nbr_sum(const T *u, int64_t X, const G2 &G) {
 
 // ------------------------------------------------------------ per-node steps
 // red-black Gauss-Seidel update of interior node X (eq. GSLEX_2D in
-// red-black order): u_X = (sum of 2d neighbours + h^2 F_X) / (2d)
+// red-black order) of c u - Lap_h u = f: u_X = (sum of 2d neighbours +
+// h^2 F_X) / (2d + c h^2)
 template <int D, typename T>
 __device__ __forceinline__ void smooth_at(int64_t X, T *u, const T *F, const G2 &G) {
     const T s = nbr_sum<D, T>(u, X, G);
-    u[X] = fma((T)G.h2, F[X], s) * (T)G.inv2d;
+    u[X] = fma((T)G.h2, F[X], s) * (T)G.inv_diag;
 }
 
 // fictitious-time relaxation of ghost g (eq. rel with eq. DtauOptTheta)
@@ -168,11 +171,11 @@ __device__ __forceinline__ T ghost_new(int64_t g, const uint32_t *gidx, const ui
     return fma((T)gdt[g], F[X] - B, u[X]);
 }
 
-// interior residual (eq. Laph)
+// interior residual (eq. Laph, with the reaction term c u)
 template <int D, typename T>
 __device__ __forceinline__ T residual_int(int64_t X, const T *u, const T *F, const G2 &G) {
     const T s = nbr_sum<D, T>(u, X, G);
-    return F[X] - (T(2 * D) * u[X] - s) * (T)G.ih2;
+    return F[X] - ((T)G.diag * u[X] - s) * (T)G.ih2;
 }
 
 // Restriction (Sec. 2.1 eq. coarseFW, Sec. 3.3.2): FW if all 3^d fine
@@ -516,18 +519,22 @@ __global__ void __launch_bounds__(1024) k_norm_final(const double *__restrict__ 
     }
 }
 
-// tensor-product Lagrange weights of every ghost's interpolation stencil
-// (eq. BCh), all levels in one launch; FP32 copies for the mixed cycle
+// Weights of every ghost row, all levels in one launch; FP32 copies for the
+// mixed cycle.  Dirichlet (eq. BCh): the tensor-product Lagrange weights of
+// the interpolant at Q.  Neumann (Sec. 3.2.2, 4.1): its normal derivative at
+// Q, sum_a n_a (-s_a / h) L'(xi_a) prod_{b != a} L(xi_b) (the stencil's local
+// coordinate along axis a runs against s_a in steps of h).
 struct GwTab {
     const uint16_t *gcode;
-    const double *gxi;
+    const double *gxi, *gn;
     int64_t ng;
+    double h;
     double *gw;
     float *gw32;
     int64_t blk;  // first block of this level
 };
 
-__global__ void __launch_bounds__(kT) k_ghost_weights(const GwTab *__restrict__ tab, int nl, int d) {
+__global__ void __launch_bounds__(kT) k_ghost_weights(const GwTab *__restrict__ tab, int nl, int d, int bc) {
     pdl_begin();
     int l = 0;
     for (int i = 1; i < nl; ++i)
@@ -536,10 +543,24 @@ __global__ void __launch_bounds__(kT) k_ghost_weights(const GwTab *__restrict__ 
     const int64_t g = ((int64_t)blockIdx.x - t.blk) * blockDim.x + threadIdx.x;
     if (g >= t.ng) return;
     const uint16_t code = t.gcode[g];
-    double w[3][3];
+    double w[3][3], dw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, c[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 3; ++a) {
-        if (a < d) lagrange<double>((code >> (3 + 2 * a)) & 3, t.gxi[(int64_t)a * t.ng + g], w[a]);
-        else {
+        if (a < d) {
+            const int q = (code >> (3 + 2 * a)) & 3;
+            const double xi = t.gxi[(int64_t)a * t.ng + g];
+            lagrange<double>(q, xi, w[a]);
+            if (q == 2) {
+                dw[a][0] = __dsub_rn(xi, 1.5);
+                dw[a][1] = __dsub_rn(2.0, __dmul_rn(2.0, xi));
+                dw[a][2] = __dsub_rn(xi, 0.5);
+            } else if (q == 1) {
+                dw[a][0] = -1.0;
+                dw[a][1] = 1.0;
+            }
+            // n_a (-s_a / h): s_a = -1 when bit a of the code is set
+            const double sa = ((code >> a) & 1) ? -1.0 : 1.0;
+            c[a] = __dmul_rn(t.gn[(int64_t)a * t.ng + g], __ddiv_rn(-sa, t.h));
+        } else {
             w[a][0] = 1.0;
             w[a][1] = 0.0;
             w[a][2] = 0.0;
@@ -549,7 +570,19 @@ __global__ void __launch_bounds__(kT) k_ghost_weights(const GwTab *__restrict__ 
     for (int o2 = 0; o2 < n2; ++o2)
         for (int o1 = 0; o1 < 3; ++o1)
             for (int o0 = 0; o0 < 3; ++o0) {
-                const double v = __dmul_rn(__dmul_rn(w[2][o2], w[1][o1]), w[0][o0]);
+                const int o[3] = {o0, o1, o2};
+                double v;
+                if (bc == BCMG_BC_NEUMANN) {
+                    v = 0.0;
+                    for (int a = 0; a < d; ++a) {
+                        double x = __dmul_rn(c[a], dw[a][o[a]]);
+                        for (int b = 0; b < d; ++b)
+                            if (b != a) x = __dmul_rn(x, w[b][o[b]]);
+                        v = __dadd_rn(v, x);
+                    }
+                } else {
+                    v = __dmul_rn(__dmul_rn(w[2][o2], w[1][o1]), w[0][o0]);
+                }
                 const int64_t k = (int64_t)((o2 * 3 + o1) * 3 + o0) * t.ng + g;
                 t.gw[k] = v;
                 if (t.gw32) t.gw32[k] = (float)v;
@@ -1169,13 +1202,13 @@ void setup_cycle(Handle &H) {
         const size_t n1 = (size_t)std::max<int64_t>(A.ng, 1) * nterm;
         A.gw = (double *)dalloc(H, sizeof(double) * n1);
         if (mixed) A.gw32 = (float *)dalloc(H, sizeof(float) * n1);
-        gt[l] = GwTab{A.gcode, A.gxi, A.ng, A.gw, A.gw32, blocks};
+        gt[l] = GwTab{A.gcode, A.gxi, A.gn, A.ng, A.h, A.gw, A.gw32, blocks};
         blocks += nblk(A.ng, kT);
     }
     if (blocks > 0) {
         GwTab *gt_d = (GwTab *)dalloc(H, sizeof(GwTab) * L, true);
         check_cuda(cudaMemcpyAsync(gt_d, gt.data(), sizeof(GwTab) * L, cudaMemcpyHostToDevice, H.st), "gw table");
-        launch(H, "k_ghost_weights", k_ghost_weights, (unsigned)blocks, kT, (const GwTab *)gt_d, L, H.d);
+        launch(H, "k_ghost_weights", k_ghost_weights, (unsigned)blocks, kT, (const GwTab *)gt_d, L, H.d, H.o.bc);
     }
 
     // a level fits the tail if each of its lists has at most one entry per

@@ -234,9 +234,12 @@ __device__ bool stencil_ok(const Geo &G, const uint8_t *cls, const int ix[3], co
 
 // Delta tau_OPT(theta): 2 / (G0min + G0max) over the corner frequencies
 // A_m (eq. G0minmax_dD); p(A_m) = acosh(1 + m) for m < d and acosh(2d - 1)
-// for A_d (eqs. alphaNalpha, alphaNalpha3D).  G0 of Remark exptheta2D (exp)
-// or of eqs. G / G3D with coefficients eq. coeff (poly).
-__host__ __device__ double dtau_formula(int d, int mode, double cst, double theta) {
+// for A_d (eqs. alphaNalpha, alphaNalpha3D).  Dirichlet: G0 of Remark
+// exptheta2D, exp(-p theta) (exp), or of eqs. G / G3D with coefficients
+// eq. coeff (poly).  Neumann: p exp(-p theta) (Remark exptheta2D) or eq. GN
+// with coefficients eq. coeffN; the result is Delta tau / h (eqs.
+// dtauoptLFA_Neumann, dtauoptLFA3D_Neumann).
+__host__ __device__ double dtau_formula(int d, int bc, int mode, double cst, double theta) {
     if (mode == BCMG_DTAU_CONST) return cst;
     double gmin = 1e300, gmax = 0.0;
     for (int m = 1; m <= d; ++m) {
@@ -244,12 +247,19 @@ __host__ __device__ double dtau_formula(int d, int mode, double cst, double thet
         double p = acosh(arg);
         double g;
         if (mode == BCMG_DTAU_EXP) {
-            g = exp(-p * theta);
+            g = (bc == BCMG_BC_NEUMANN) ? p * exp(-p * theta) : exp(-p * theta);
         } else {
             double e1 = exp(-p), e2 = exp(-2.0 * p);
-            double cm2 = theta * (theta - 1.0) / 2.0;
-            double cm1 = theta * (2.0 - theta);
-            double c0 = (1.0 - theta) * (2.0 - theta) / 2.0;
+            double cm2, cm1, c0;
+            if (bc == BCMG_BC_NEUMANN) {
+                cm2 = 0.5 - theta;
+                cm1 = 2.0 * (theta - 1.0);
+                c0 = 1.5 - theta;
+            } else {
+                cm2 = theta * (theta - 1.0) / 2.0;
+                cm1 = theta * (2.0 - theta);
+                c0 = (1.0 - theta) * (2.0 - theta) / 2.0;
+            }
             g = cm2 * e2 + cm1 * e1 + c0;
         }
         g = fabs(g);
@@ -266,7 +276,7 @@ struct GhostOut {
 };
 
 // geometry of ghost g of one level (normal, eta, stencil, xi, Q, Delta tau)
-__device__ void ghost_one(const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
+__device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
                           const uint8_t *__restrict__ cls, const Geo &G, int dmode, double dconst,
                           const GhostOut &out, int64_t g) {
     const int d = G.d;
@@ -381,7 +391,8 @@ __device__ void ghost_one(const uint32_t *__restrict__ gidx, int64_t ng, const d
     }
     out.code[g] = code;
     out.eta[g] = eta;
-    out.dt[g] = dtau_formula(d, dmode, dconst, eta);
+    // Neumann: the formula gives Delta tau / h
+    out.dt[g] = dtau_formula(d, bc, dmode, dconst, eta) * (bc == BCMG_BC_NEUMANN ? G.h : 1.0);
 }
 
 // ---------------------------------------------------------------- band
@@ -440,12 +451,12 @@ __device__ __forceinline__ int level_of_block(const LevelTab *tab, int nl, bool 
 }
 
 // ghost geometry and band marks of every level
-__global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int dmode, double dconst) {
+__global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int bc, int dmode, double dconst) {
     const int l = level_of_block(tab, nl, false);
     const LevelTab &T = tab[l];
     const int64_t g = ((int64_t)blockIdx.x - T.blk_g) * blockDim.x + threadIdx.x;
     if (g >= T.ng) return;
-    ghost_one(T.gidx, T.ng, T.phi, T.cls, T.G, dmode, dconst, T.gout, g);
+    ghost_one(bc, T.gidx, T.ng, T.phi, T.cls, T.G, dmode, dconst, T.gout, g);
     band_mark_one(T.gidx, T.cls, T.G, T.mark, g);
 }
 
@@ -573,16 +584,33 @@ __device__ __forceinline__ void lagrange_w(int q, double xi, double w[3]) {
     }
 }
 
+// derivatives of the Lagrange basis (Neumann rows, Sec. 3.2.2)
+__device__ __forceinline__ void lagrange_dw(int q, double xi, double w[3]) {
+    w[0] = w[1] = w[2] = 0.0;
+    if (q == 2) {
+        w[0] = __dsub_rn(xi, 1.5);
+        w[1] = __dsub_rn(2.0, __dmul_rn(2.0, xi));
+        w[2] = __dsub_rn(xi, 0.5);
+    } else if (q == 1) {
+        w[0] = -1.0;
+        w[1] = 1.0;
+    }
+}
+
+// Coarsest system: interior rows c u - Lap_h u (eq. Laph), ghost rows the
+// boundary operator on the ghost stencil (Dirichlet: tensor Lagrange weights;
+// Neumann: sum_a n_a (-s_a / h) L'(xi_a) prod_{b != a} L(xi_b))
 __global__ void k_assemble(const uint32_t *__restrict__ act, int64_t nact, const uint8_t *__restrict__ cls,
                            const uint32_t *__restrict__ gidx, const uint16_t *__restrict__ gcode,
-                           const double *__restrict__ gxi, int64_t ng, Geo G, double *__restrict__ A) {
+                           const double *__restrict__ gxi, const double *__restrict__ gn, int64_t ng, Geo G,
+                           int bc, double react, double *__restrict__ A) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nact) return;
     int64_t X = act[r];
     double *row = A + r * nact;
     if (cls[X] == CL_INTERIOR) {
         double ih2 = 1.0 / (G.h * G.h);
-        row[r] += 2.0 * G.d * ih2;
+        row[r] += 2.0 * G.d * ih2 + react;
         for (int a = 0; a < G.d; ++a)
             for (int dir = -1; dir <= 1; dir += 2) {
                 int64_t c = find_sorted(act, nact, (uint32_t)(X + dir * G.st[a]));
@@ -593,11 +621,14 @@ __global__ void k_assemble(const uint32_t *__restrict__ act, int64_t nact, const
     int64_t g = find_sorted(gidx, ng, (uint32_t)X);
     uint16_t code = gcode[g];
     int s[3] = {0, 0, 0}, q[3] = {0, 0, 0};
-    double w[3][3] = {{1, 0, 0}, {1, 0, 0}, {1, 0, 0}};
+    double w[3][3] = {{1, 0, 0}, {1, 0, 0}, {1, 0, 0}}, dw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double nv[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < G.d; ++a) {
         s[a] = ((code >> a) & 1) ? -1 : 1;
         q[a] = (code >> (3 + 2 * a)) & 3;
         lagrange_w(q[a], gxi[(int64_t)a * ng + g], w[a]);
+        lagrange_dw(q[a], gxi[(int64_t)a * ng + g], dw[a]);
+        nv[a] = gn[(int64_t)a * ng + g];
     }
     for (int o2 = 0; o2 <= q[2]; ++o2)
         for (int o1 = 0; o1 <= q[1]; ++o1)
@@ -605,7 +636,21 @@ __global__ void k_assemble(const uint32_t *__restrict__ act, int64_t nact, const
                 int64_t Y = X - (int64_t)s[0] * o0 * G.st[0] - (int64_t)s[1] * o1 * G.st[1] -
                             (int64_t)s[2] * o2 * G.st[2];
                 int64_t c = find_sorted(act, nact, (uint32_t)Y);
-                if (c >= 0) row[c] += w[0][o0] * w[1][o1] * w[2][o2];
+                if (c < 0) continue;
+                const int o[3] = {o0, o1, o2};
+                double v;
+                if (bc == BCMG_BC_NEUMANN) {
+                    v = 0.0;
+                    for (int a = 0; a < G.d; ++a) {
+                        double t = __dmul_rn(__dmul_rn(nv[a], __ddiv_rn(-(double)s[a], G.h)), dw[a][o[a]]);
+                        for (int b = 0; b < G.d; ++b)
+                            if (b != a) t = __dmul_rn(t, w[b][o[b]]);
+                        v = __dadd_rn(v, t);
+                    }
+                } else {
+                    v = __dmul_rn(__dmul_rn(w[0][o0], w[1][o1]), w[2][o2]);
+                }
+                row[c] += v;
             }
 }
 
@@ -821,7 +866,7 @@ inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-double dtau_of(int d, int mode, double cst, double theta) { return dtau_formula(d, mode, cst, theta); }
+double dtau_of(int d, int bc, int mode, double cst, double theta) { return dtau_formula(d, bc, mode, cst, theta); }
 
 // the path expansion fits the per-thread buffers: at most d (d^K - 1)/(d - 1)
 // ghost terms and a depth-first stack of (d - 1)(K - 1) + d entries
@@ -919,6 +964,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             L.N = (int)Nl;
             L.n = (int)Nl + 1;
             L.h = 2.0 / (double)Nl;
+            L.react = H.o.reaction;
             L.nn = 1;
             for (int a = 0; a < H.d; ++a) {
                 L.st[a] = L.nn;
@@ -1030,7 +1076,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     LevelTab *tab_d = (LevelTab *)dalloc(H, sizeof(LevelTab) * keep, true);
     check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(LevelTab) * keep, cudaMemcpyHostToDevice, H.st), "tab");
     if (gblocks > 0) {
-        k_ghost_all<<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.dtau_mode, H.o.dtau_const);
+        k_ghost_all<<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.bc, H.o.dtau_mode, H.o.dtau_const);
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "ghost set-up");
@@ -1141,7 +1187,8 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     L.crhs = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1));
     double *col = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1), true);
     int *sing = (int *)dalloc(H, sizeof(int), true);
-    k_assemble<<<nblocks(n, 128), 128, 0, H.st>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.ng, G, A);
+    k_assemble<<<nblocks(n, 128), 128, 0, H.st>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.gn, L.ng, G, H.o.bc,
+                                                  H.o.reaction, A);
     count_launch(H);
     if (n <= kLuSmall) {
         double *LU = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);

@@ -1,0 +1,149 @@
+"""GPU parity for Neumann boundary rows and the reaction term against the
+FP64 oracle (the same bar as the Dirichlet path: set-up data exact or to
+1e-14 / 1e-13, stage operators and V-cycles to 1e-12 relative)."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2207_14208_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def bcmg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_14208_gb300 import bcmg as B
+    from paper_2207_14208_gb300 import build
+    build.build()
+    O.build()
+    return B
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _phi_line(N, beta=0.35, c=0.1):
+    X, Y = W.coords(2, N)
+    return (X * math.cos(beta) + Y * math.sin(beta) - c).reshape(-1)
+
+
+def _grad_u(d, P):
+    if d == 2:
+        x, y = P[:, 0], P[:, 1]
+        return np.stack([(np.pi * np.cos(np.pi * x) + np.sin(np.pi * x)) * np.cos(np.pi * y) * np.exp(x),
+                         -np.pi * np.sin(np.pi * x) * np.sin(np.pi * y) * np.exp(x)], 1)
+    x, y, z = P[:, 0], P[:, 1], P[:, 2]
+    e = np.exp(x + y + z)
+    return np.stack([e * np.sin(np.pi * z), e * np.sin(np.pi * z),
+                     e * (np.sin(np.pi * z) + np.pi * np.cos(np.pi * z))], 1)
+
+
+# (name, d, N, phi maker, reaction): Test2N-type (reaction 1) on curved
+# domains, Test1N-type (Poisson, Dirichlet box sides) on an oblique line
+CASES = [("disk96_r1", 2, 96, W.phi_disk, 1.0), ("flower64_r1", 2, 64, W.phi_flower_paper, 1.0),
+         ("line64_r0", 2, 64, _phi_line, 0.0), ("ellipsoid40_r1", 3, 40, W.phi_ellipsoid, 1.0)]
+
+
+def _pair(B, d, N, phi, f, react, **kw):
+    s = B.Solver(d, N, dev(phi), dev(f), bc=B.BC_NEUMANN, reaction=react, **kw)
+    o = O.Oracle(d, N, phi, bc=O.NEUMANN, reaction=react)
+    return s, o
+
+
+def _problem(d, N, react):
+    f, us = W.manufactured(d, N)  # f = -Lap u*
+    return f + react * us, us
+
+
+@pytest.mark.parametrize("name,d,N,mk,react", CASES, ids=[c[0] for c in CASES])
+def test_neumann_setup_and_vcycle_match_oracle(bcmg, name, d, N, mk, react):
+    B = bcmg
+    phi = mk(N)
+    f, us = _problem(d, N, react)
+    s, o = _pair(B, d, N, phi, f, react)
+    assert s.levels == o.L
+    for l in range(o.L):
+        gg, og = s.ghosts(l), o.ghosts(l)
+        np.testing.assert_array_equal(gg["idx"], og["idx"])
+        np.testing.assert_allclose(gg["dtau"], og["dtau"], rtol=1e-13)
+    og = o.ghosts(0)
+    np.testing.assert_allclose(host(s.ghost_normals()), og["n"][:, :d], rtol=0, atol=1e-15)
+    g = (_grad_u(d, og["Q"]) * og["n"][:, :d]).sum(1)
+    o.set_rhs(f, g)
+    s.set_boundary_values(dev(g))
+    cls = o.cls(0)
+    act = (cls == O.INTERIOR) | (cls == O.GHOST)
+    u0 = np.where(cls == O.BOXDIR, us, 0.0)
+    uo, ug = u0.copy(), dev(u0)
+    for cyc in range(3):
+        uo = o.vcycle(uo, 1)
+        s.vcycle(ug, 1)
+        got = host(ug)
+        assert np.abs(got[act] - uo[act]).max() <= REL * np.abs(uo[act]).max(), cyc
+        np.testing.assert_array_equal(got[~act], u0[~act])
+
+
+@pytest.mark.parametrize("name,d,N,mk,react", CASES[:2], ids=[c[0] for c in CASES[:2]])
+def test_neumann_stage_operators_match_oracle(bcmg, name, d, N, mk, react):
+    B = bcmg
+    phi = mk(N)
+    f, _ = _problem(d, N, react)
+    s, o = _pair(B, d, N, phi, f, react)
+    rng = np.random.default_rng(5)
+    for l in range(o.L):
+        cls = o.cls(l)
+        nn = o.info(l)["nn"]
+        act = (cls == O.INTERIOR) | (cls == O.GHOST)
+        u = np.where(cls != O.INACTIVE, rng.uniform(-1, 1, nn), 0.0)
+        F = np.where(act, rng.uniform(-1, 1, nn), 0.0)
+        ug = dev(u)
+        s.smooth(l, ug, dev(F), 1)
+        uo = o.smooth(l, u, F, 1)
+        assert np.abs(host(ug) - uo).max() <= REL * np.abs(uo).max()
+        rg = torch.zeros(nn, dtype=torch.float64, device="cuda")
+        s.residual(l, dev(uo), dev(F), rg)
+        ro = o.residual(l, uo, F)
+        h = 2.0 / o.info(l)["N"]
+        rscale = np.abs(F).max() + (2 * d / (h * h) + react + 8 / h) * np.abs(uo).max()
+        np.testing.assert_allclose(host(rg)[act], ro[act], rtol=0, atol=REL * rscale)
+        if l == o.L - 1:
+            ug3 = dev(u)
+            s.coarsest_solve(ug3, dev(F))
+            co = o.coarsest_solve(u, F)
+            np.testing.assert_allclose(host(ug3)[act], co[act], rtol=0, atol=1e-11 * np.abs(co).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_neumann_solve_matches_oracle(bcmg, prec):
+    # Test2N on the disk: both solves reach 1e-10 and agree; mixed precision
+    # lands on the FP64 solution
+    B = bcmg
+    d, N, react = 2, 128, 1.0
+    phi = W.phi_disk(N)
+    f, us = _problem(d, N, react)
+    p = B.PREC_FP64 if prec == "fp64" else B.PREC_MIXED
+    s, o = _pair(B, d, N, phi, f, react, precision=p)
+    og = o.ghosts(0)
+    g = (_grad_u(d, og["Q"]) * og["n"][:, :d]).sum(1)
+    o.set_rhs(f, g)
+    s.set_boundary_values(dev(g))
+    ug = dev(np.zeros(o.nn(0)))
+    c, rel = s.solve(ug, 1e-12, 100)
+    uo, co, _ = o.solve(np.zeros(o.nn(0)), 1e-12, 100)
+    assert rel <= 1e-12 and abs(c - co) <= (1 if prec == "fp64" else 4)
+    act = np.isin(o.cls(0), [O.INTERIOR, O.GHOST])
+    assert np.abs(host(ug)[act] - uo[act]).max() <= 1e-9 * np.abs(uo[act]).max()
