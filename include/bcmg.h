@@ -75,7 +75,12 @@ typedef struct {
                           (default) or BCMG_BC_NEUMANN */
     double reaction;   /* c >= 0 of the interior equation c u - Lap u = f
                           (0: Poisson, the default; Sec. 4.2 Test2N: 1) */
+    int cycle;         /* BCMG_CYCLE_V (gamma = 1, default) or BCMG_CYCLE_W
+                          (gamma = 2), Sec. 2.1 */
 } bcmg_opts;
+
+#define BCMG_CYCLE_V 0
+#define BCMG_CYCLE_W 1
 
 /* Boundary conditions on Gamma (Sec. 3): Dirichlet u = g; Neumann
  * grad u . n = g with n the ghost's outward unit normal (bcmg_ghost_normals),

@@ -124,6 +124,8 @@ struct Handle {
     // and the per-level tables of the FP64 and FP32 cycles
     int tail_start = -1, tail_cluster = 0;
     void *tail64 = nullptr, *tail32 = nullptr;
+    void *tail_ops = nullptr;  // (kind, level) schedule of the tail
+    int tail_nops = 0;
     int nsm = 152;  // SMs of the device (block sizes of the FP64 kernels)
     bool capturing = false;
     int64_t captured = 0;

@@ -714,8 +714,17 @@ __device__ void tail_extend(const TailLevel<T> &A, const TailSlots &S, int l, T 
     tail_sync();
 }
 
+// Schedule of the tail (built on the host): a cycle visit of tail level l
+// is DOWN(l) (pre-smoothing, residual, extension, restriction to l + 1 with
+// the coarse correction zeroed), gamma visits of level l + 1, then UP(l)
+// (extension of the coarse correction, prolongation, post-smoothing); a visit
+// of the coarsest level is COARSE (its exact correction).  gamma = 1 gives
+// the V-cycle, gamma = 2 the W-cycle (Sec. 2.1).
+enum : uint8_t { kOpDown = 0, kOpCoarse = 1, kOpUp = 2 };
+
 template <int D, typename T>
-__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ tl, int nl, int nu1,
+__global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ tl, int nl,
+                                                          const uint8_t *__restrict__ ops, int nops, int nu1,
                                                           int nu2) {
     pdl_begin();
     extern __shared__ uint32_t tsm[];
@@ -740,48 +749,64 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
         S.act[k] = i < A.nint ? A.ilist[i] : (i < A.nint + A.ng ? A.gidx[i - A.nint] : kNone);
     }
     __syncthreads();
-    for (int l = 0; l + 1 < nl; ++l) {
-        const TailLevel<T> &A = tl[l], &B = tl[l + 1];
-        tail_smooth<D, T>(A, S, l, nu1);
-        tail_residual<D, T>(A, S, l);
-        tail_extend<T>(A, S, l, A.r);
-        const uint32_t xc = S.act[(l + 1) * kTailThreads + t];
-        if (xc != kNone) {
-            int ic[3];
-            coords(xc, (uint32_t)B.g.n, D, ic);
-            B.F[xc] = restrict_at<D, T>(ic, i < B.nint, A.cls, A.r, A.g);
-            B.u[xc] = T(0);
-        }
-        tail_sync();
-    }
-    {
-        const TailLevel<T> &C = tl[nl - 1];
-        tail_residual<D, T>(C, S, nl - 1);
-        if (i < C.nact) C.crhs[i] = (double)C.r[C.act[i]];
-        tail_sync();
-        const int lane = t & 31;
-        const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t row = i >> 5; row < C.nact; row += nthr >> 5) {  // rows by warp, spread over the SMs
-            double s = 0.0;
-            for (int64_t j = lane; j < C.nact; j += 32) s = fma(C.Ainv[row * C.nact + j], C.crhs[j], s);
+    for (int op = 0; op < nops; ++op) {
+        const int kind = ops[2 * op], l = ops[2 * op + 1];
+        if (kind == kOpDown) {
+            const TailLevel<T> &A = tl[l], &B = tl[l + 1];
+            tail_smooth<D, T>(A, S, l, nu1);
+            tail_residual<D, T>(A, S, l);
+            tail_extend<T>(A, S, l, A.r);
+            const uint32_t xc = S.act[(l + 1) * kTailThreads + t];
+            if (xc != kNone) {
+                int ic[3];
+                coords(xc, (uint32_t)B.g.n, D, ic);
+                B.F[xc] = restrict_at<D, T>(ic, i < B.nint, A.cls, A.r, A.g);
+                B.u[xc] = T(0);
+            }
+            tail_sync();
+        } else if (kind == kOpCoarse) {
+            const TailLevel<T> &C = tl[l];
+            tail_residual<D, T>(C, S, l);
+            if (i < C.nact) C.crhs[i] = (double)C.r[C.act[i]];
+            tail_sync();
+            const int lane = t & 31;
+            const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+            for (int64_t row = i >> 5; row < C.nact; row += nthr >> 5) {  // rows by warp, spread over the SMs
+                double sum = 0.0;
+                for (int64_t j = lane; j < C.nact; j += 32) sum = fma(C.Ainv[row * C.nact + j], C.crhs[j], sum);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) C.u[C.act[row]] += (T)s;
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+                if (lane == 0) C.u[C.act[row]] += (T)sum;
+            }
+            tail_sync();
+        } else {
+            const TailLevel<T> &A = tl[l], &B = tl[l + 1];
+            tail_extend<T>(B, S, l + 1, B.u);
+            const uint32_t xa = S.act[l * kTailThreads + t];
+            if (xa != kNone) {
+                int iy[3];
+                coords(xa, (uint32_t)A.g.n, D, iy);
+                A.u[xa] += prolong_at<D, T>(iy, B.u, B.g);
+            }
+            tail_sync();
+            tail_smooth<D, T>(A, S, l, nu2);
         }
-        tail_sync();
     }
-    for (int l = nl - 2; l >= 0; --l) {
-        const TailLevel<T> &A = tl[l], &B = tl[l + 1];
-        tail_extend<T>(B, S, l + 1, B.u);
-        const uint32_t xa = S.act[l * kTailThreads + t];
-        if (xa != kNone) {
-            int iy[3];
-            coords(xa, (uint32_t)A.g.n, D, iy);
-            A.u[xa] += prolong_at<D, T>(iy, B.u, B.g);
-        }
-        tail_sync();
-        tail_smooth<D, T>(A, S, l, nu2);
+}
+
+// the schedule of one visit of tail level l (levels 0..nl-1, the last the
+// coarsest), appended as (kind, level) pairs
+void tail_schedule(int l, int nl, int gamma, std::vector<uint8_t> &ops) {
+    if (l == nl - 1) {
+        ops.push_back(kOpCoarse);
+        ops.push_back((uint8_t)l);
+        return;
     }
+    ops.push_back(kOpDown);
+    ops.push_back((uint8_t)l);
+    for (int g = 0; g < gamma; ++g) tail_schedule(l + 1, nl, gamma, ops);
+    ops.push_back(kOpUp);
+    ops.push_back((uint8_t)l);
 }
 
 size_t tail_smem(int nl) { return (size_t)nl * kTailThreads * (5 * sizeof(uint32_t) + sizeof(uint16_t)); }
@@ -924,7 +949,8 @@ void vcycle_t(Handle &H, int l, T *u) {
     residual<T>(H, A, u, Arr<T>::F(A), Arr<T>::r(A));
     extend<T>(H, A, Arr<T>::r(A));
     restrict_to<T>(H, A, B, Arr<T>::r(A), Arr<T>::F(B), Arr<T>::u(B));
-    vcycle_t<T>(H, l + 1, Arr<T>::u(B));
+    const int gamma = H.o.cycle == BCMG_CYCLE_W ? 2 : 1;
+    for (int g = 0; g < gamma; ++g) vcycle_t<T>(H, l + 1, Arr<T>::u(B));
     extend<T>(H, B, Arr<T>::u(B));
     prolong<T>(H, A, B, Arr<T>::u(B), u);
     smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu2);
@@ -960,7 +986,7 @@ TailLevel<T> tail_level(Level &L) {
 }
 
 template <typename T>
-using TailKernel = void (*)(const TailLevel<T> *, int, int, int);
+using TailKernel = void (*)(const TailLevel<T> *, int, const uint8_t *, int, int, int);
 
 template <typename T>
 TailKernel<T> tail_kernel(int d) {
@@ -1033,7 +1059,9 @@ void run_tail(Handle &H) {
     const TailLevel<T> *tab = (const TailLevel<T> *)(sizeof(T) == 8 ? H.tail64 : H.tail32);
     cudaLaunchAttribute at[2];
     cudaLaunchConfig_t cfg = tail_config(H, H.tail_cluster, nl, at, true);
-    check_cuda(cudaLaunchKernelEx(&cfg, tail_kernel<T>(H.d), tab, nl, H.o.nu1, H.o.nu2), "k_tail");
+    check_cuda(cudaLaunchKernelEx(&cfg, tail_kernel<T>(H.d), tab, nl, (const uint8_t *)H.tail_ops, H.tail_nops,
+                                  H.o.nu1, H.o.nu2),
+               "k_tail");
     count_launch(H);
 }
 
@@ -1234,6 +1262,11 @@ void setup_cycle(Handle &H) {
     H.tail_cluster = cs;
     H.tail_start = lt;
     const int nl = L - lt;
+    std::vector<uint8_t> ops;
+    tail_schedule(0, nl, H.o.cycle == BCMG_CYCLE_W ? 2 : 1, ops);
+    H.tail_nops = (int)(ops.size() / 2);
+    H.tail_ops = dalloc(H, ops.size());
+    check_cuda(cudaMemcpyAsync(H.tail_ops, ops.data(), ops.size(), cudaMemcpyHostToDevice, H.st), "tail schedule");
     std::vector<TailLevel<double>> t64;
     for (int l = lt; l < L; ++l) t64.push_back(tail_level<double>(H.L[l]));
     H.tail64 = dalloc(H, sizeof(TailLevel<double>) * nl);

@@ -272,3 +272,38 @@ def test_full_size_ellipsoid_256(bcmg):
     interior = o.cls(0) == O.INTERIOR
     err = np.abs(host(ug) - us)[interior].max()
     assert err < 5e-5
+
+
+@pytest.mark.parametrize("name,d,N,mk", [("disk128", 2, 128, W.phi_disk), ("ellipsoid48", 3, 48, W.phi_ellipsoid),
+                                         ("flower96", 2, 96, W.phi_flower_paper)],
+                         ids=["disk128", "ellipsoid48", "flower96"])
+def test_wcycle_matches_oracle(bcmg, name, d, N, mk):
+    # W-cycle (gamma = 2, Sec. 2.1): every coarse level visited twice per
+    # visit of the level above (the grid path and the cluster tail alike)
+    B = bcmg
+    phi = mk(N)
+    f, us = W.manufactured(d, N)
+    s = B.Solver(d, N, dev(phi), dev(f), cycle=B.CYCLE_W)
+    o = O.Oracle(d, N, phi, cycle=O.CYC_W)
+    g = W.g_at(d, o.ghosts(0)["Q"])
+    o.set_rhs(f, g)
+    s.set_boundary_values(dev(g))
+    act = np.isin(o.cls(0), [O.INTERIOR, O.GHOST])
+    uo = np.zeros(o.nn(0))
+    ug = dev(uo)
+    for cyc in range(3):
+        uo = o.vcycle(uo, 1)
+        s.vcycle(ug, 1)
+        assert np.abs(host(ug)[act] - uo[act]).max() <= REL * np.abs(uo[act]).max(), cyc
+    c, rel = s.solve(dev(np.zeros(o.nn(0))), 1e-10, 60)
+    assert rel <= 1e-10
+
+
+def test_rho_harness_matches_oracle(bcmg):
+    # the reproduction harness's rho (Sec. 2.2 protocol) against the oracle's
+    from paper_2207_14208_gb300 import repro
+    N = 64
+    phi = W.phi_circle_paper(N)
+    r_gpu = repro.rho(2, N, phi)
+    r_orc, _ = O.Oracle(2, N, phi).rho(np.random.Generator(np.random.PCG64(3)).uniform(-1.0, 1.0, (N + 1) ** 2))
+    assert r_gpu == pytest.approx(r_orc, rel=1e-6)
