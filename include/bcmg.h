@@ -99,6 +99,14 @@ typedef struct {
 /* Fill *opts with the defaults above. */
 void bcmg_default_opts(bcmg_opts *opts);
 
+/* The relaxation parameter the library gives a ghost at distance theta
+ * (= |G - Q| / h, in [0, 1]): Delta tau_OPT(theta) of eqs. DtauOptTheta,
+ * dtauoptLFA / dtauoptLFA3D (Dirichlet) or Delta tau_OPT / h of eqs.
+ * dtauoptLFA_Neumann / dtauoptLFA3D_Neumann (Neumann), with the G0 form of
+ * dtau_mode (BCMG_DTAU_EXP, BCMG_DTAU_POLY) or dtau_const for
+ * BCMG_DTAU_CONST.  Host function; *out receives the value. */
+int bcmg_dtau_opt(int dim, int bc, int dtau_mode, double dtau_const, double theta, double *out);
+
 /* Build the level hierarchy (Sec. 2.1 re-discretisation, Sec. 3.3 geometry):
  * per level the node classes from phi injected to the level, the ghost list
  * with projection points Q = G - eta h n (phi(Q) = 0), upwind 3^d stencils,

@@ -72,6 +72,7 @@ def load():
             "bcmg_residual_norm": (i32, [vp, vp, vp]),
             "bcmg_solve_batch": (i32, [vp, vp, i32, f64, i32, vp, vp, vp]),
             "bcmg_ghost_normals": (i32, [vp, vp]),
+            "bcmg_dtau_opt": (i32, [i32, i32, i32, f64, f64, vp]),
             "bcmg_memory_footprint": (i32, [vp, vp]),
             "bcmg_footprint_estimate": (i32, [i32, i64, vp, vp]),
             "bcmg_last_error": (C.c_char_p, []),
@@ -145,6 +146,13 @@ def default_opts(**kw) -> Opts:
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def dtau_opt(dim: int, theta: float, mode: int = DTAU_EXP, bc: int = BC_DIRICHLET, const: float = 1.75) -> float:
+    """The library's Delta tau_OPT(theta) (Neumann: Delta tau_OPT / h)."""
+    out = C.c_double()
+    _check(load().bcmg_dtau_opt(int(dim), int(bc), int(mode), float(const), float(theta), C.byref(out)))
+    return out.value
 
 
 def footprint_estimate(dim: int, N: int, **opts) -> int:

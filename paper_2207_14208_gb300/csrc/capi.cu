@@ -610,6 +610,16 @@ int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, 
     return solve_status(first);
 }
 
+int bcmg_dtau_opt(int dim, int bc, int dtau_mode, double dtau_const, double theta, double *out) {
+    if (!out) return fail(BCMG_EINVAL, "out is null");
+    if ((dim != 2 && dim != 3) || (bc != BCMG_BC_DIRICHLET && bc != BCMG_BC_NEUMANN) || dtau_mode < 0 ||
+        dtau_mode > 2 || !(theta >= 0.0 && theta <= 1.0))
+        return fail(BCMG_EINVAL, "bad dim, bc, dtau_mode or theta");
+    *out = dtau_of(dim, bc, dtau_mode, dtau_const, theta);
+    g_last_error.clear();
+    return BCMG_OK;
+}
+
 int bcmg_memory_footprint(bcmg_handle h, int64_t *bytes) {
     return guarded([&] {
         Handle &H = *checked(h);

@@ -57,6 +57,55 @@ def theta_histogram(d: int, N: int, phi: np.ndarray, bins: int = 10):
     return h / max(1, eta.size), edges
 
 
+def rectangle_phi(N: int, theta: float):
+    """The rectangle set-up of Sec. 3.2 in [-1, 1]^2: the domain x < xV with
+    one column of ghosts at node column 3N/4 + 1 (not a coarse-grid column),
+    all at distance theta h from the boundary; box sides inside the domain
+    are eliminated Dirichlet nodes."""
+    h = 2.0 / N
+    xV = (-1.0 + (3 * N // 4 + 1) * h) - theta * h
+    return (W.coords(2, N)[0] - xV).reshape(-1)
+
+
+def ghost_residual_spectrum(N: int, theta: float, dtau: float, nsmooth: int = 10, seed: int = 4):
+    """Sec. 3.2.1 smoothing check: from u ~ U(-1, 1) (PCG64 seed), nsmooth
+    relaxations of the homogeneous problem on the finest level with a
+    constant Delta tau, then the DFT of the ghost residual along the ghost
+    column, R_k = mean_j r_j exp(-i alpha_k j), alpha_k = -pi + 2 pi k / M.
+    Returns (alpha_k in (0, pi), amplitudes 2 |R_k|)."""
+    import torch
+    s = bcmg.Solver(2, N, torch.from_numpy(rectangle_phi(N, theta)).cuda(), None,
+                    dtau_mode=bcmg.DTAU_CONST, dtau_const=float(dtau))
+    try:
+        cls = s.cls(0)
+        rng = np.random.Generator(np.random.PCG64(seed))
+        u0 = rng.uniform(-1.0, 1.0, s.nn)
+        u0[cls == bcmg.BOXDIR] = 0.0
+        u = torch.from_numpy(u0).cuda()
+        F = torch.zeros_like(u)
+        s.smooth(0, u, F, nsmooth)
+        r = torch.zeros_like(u)
+        s.residual(0, u, F, r)
+        torch.cuda.synchronize()
+        idx = s.ghosts(0)["idx"]
+        rr = r.cpu().numpy()
+    finally:
+        s.close()
+    j = idx // (N + 1)
+    order = np.argsort(j)
+    rb, jj = rr[idx[order]], j[order]
+    M = rb.size
+    ak = -np.pi + np.arange(1, M + 1) * 2.0 * np.pi / M
+    R = np.exp(-1j * np.outer(ak, jj)) @ rb / M
+    pos = ak > 0
+    return ak[pos], 2.0 * np.abs(R[pos])
+
+
+def high_low_ratio(alpha, amp):
+    """Summed high-frequency (alpha > pi/2) over low-frequency amplitude."""
+    return float(amp[alpha > np.pi / 2].sum() / amp[alpha < np.pi / 2].sum())
+
+
 def _table(rows, cols, cell):
     out = ["| | " + " | ".join(str(c) for c in cols) + " |", "|---" * (len(cols) + 1) + "|"]
     for r in rows:
@@ -88,6 +137,12 @@ def main():
     print(_table(["circle V", "circle W"], Ns2[:4],
                  lambda r, N: "%.3f" % rho(2, N, W.phi_circle_paper(N),
                                           cycle=bcmg.CYCLE_W if r.endswith("W") else bcmg.CYCLE_V)))
+    print("\nRectangle (Sec. 3.2.1), N = 128, 10 relaxations from U(-1, 1): high/low ratio of the "
+          "ghost-residual spectrum at (0.5, 1, 1.5) x Delta tau_OPT(theta)")
+    for theta in (0.2, 0.5, 0.8):
+        opt = bcmg.dtau_opt(2, theta, bcmg.DTAU_POLY)
+        ratios = [high_low_ratio(*ghost_residual_spectrum(128, theta, f * opt)) for f in (0.5, 1.0, 1.5)]
+        print("theta %.1f: " % theta + " ".join("%.3g" % x for x in ratios))
     for dname, mk in doms2.items():
         h, edges = theta_histogram(2, 2048, mk(2048))
         print("\ntheta~ histogram, %s N = 2048 (fraction of ghosts per bin of width 0.1):" % dname)

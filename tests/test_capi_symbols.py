@@ -33,3 +33,22 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(bcmg, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="library missing"):
         bcmg.load()
+
+
+def test_dtau_opt_host_matches_oracle():
+    # the library's Delta tau_OPT (a host function: no GPU needed) against
+    # the oracle's, for both boundary conditions, both G0 forms, 2D and 3D
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2207_14208_gb300 import bcmg, build
+    build.build()
+    for d in (2, 3):
+        for bc in (0, 1):
+            for mode in (bcmg.DTAU_EXP, bcmg.DTAU_POLY):
+                for th in np.linspace(0.0, 1.0, 11):
+                    a = bcmg.dtau_opt(d, th, mode, bc=bc)
+                    b = O.dtau(d, th, mode, bc=bc)
+                    assert abs(a - b) <= 1e-14 * abs(b), (d, bc, mode, th, a, b)
+    # the Neumann 2D values of eq. dtauoptLFA_Neumann at theta = 0, 1/2, 1
+    for th, want in [(0.0, 0.92099), (0.5, 1.28166), (1.0, 2.10663)]:
+        assert abs(bcmg.dtau_opt(2, th, bcmg.DTAU_POLY, bc=1) - want) < 1e-5
