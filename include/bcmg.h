@@ -77,7 +77,15 @@ typedef struct {
                           (0: Poisson, the default; Sec. 4.2 Test2N: 1) */
     int cycle;         /* BCMG_CYCLE_V (gamma = 1, default) or BCMG_CYCLE_W
                           (gamma = 2), Sec. 2.1 */
+    int ordering;      /* interior Gauss-Seidel order: BCMG_ORDER_RB
+                          (red-black, default) or BCMG_ORDER_LEX
+                          (lexicographic, the paper's GS-LEX, eq. GSLEX_2D,
+                          run as a sweep over the hyperplanes i+j(+k) = p;
+                          one launch per hyperplane, for comparisons) */
 } bcmg_opts;
+
+#define BCMG_ORDER_RB 0
+#define BCMG_ORDER_LEX 1
 
 #define BCMG_CYCLE_V 0
 #define BCMG_CYCLE_W 1

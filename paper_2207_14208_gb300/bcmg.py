@@ -25,6 +25,7 @@ DTAU_EXP, DTAU_POLY, DTAU_CONST = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
 CYCLE_V, CYCLE_W = 0, 1
+ORDER_RB, ORDER_LEX = 0, 1
 
 _lib = None
 _lock = threading.Lock()
@@ -40,7 +41,8 @@ class Opts(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("dtau_mode", C.c_int),
                 ("dtau_const", C.c_double), ("ext_sweeps", C.c_int), ("min_coarse", C.c_int),
                 ("max_levels", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
-                ("precision", C.c_int), ("bc", C.c_int), ("reaction", C.c_double), ("cycle", C.c_int)]
+                ("precision", C.c_int), ("bc", C.c_int), ("reaction", C.c_double), ("cycle", C.c_int),
+                ("ordering", C.c_int)]
 
 
 def declared_functions():

@@ -47,6 +47,10 @@ struct Level {
     int64_t nint = 0, nbox = 0, ng = 0, nb = 0, nclamp = 0, nfall = 0, nact = 0;
     int64_t nred = 0;            // red interior nodes (head of ilist)
     uint32_t *ilist = nullptr;  // nint interior node indices, red then black
+    // GS-LEX order only: interior nodes grouped by hyperplane p = i + j (+ k),
+    // hyperplane p at hlist[hoff[p] .. hoff[p + 1])
+    uint32_t *hlist = nullptr;
+    std::vector<int64_t> hoff;
     // ghosts (SoA)
     uint32_t *gidx = nullptr;
     uint16_t *gcode = nullptr;  // bit a: s_a = -1; bits 3+2a..4+2a: degree q_a

@@ -421,6 +421,7 @@ void bcmg_default_opts(bcmg_opts *o) {
     o->bc = BCMG_BC_DIRICHLET;
     o->reaction = 0.0;
     o->cycle = BCMG_CYCLE_V;
+    o->ordering = BCMG_ORDER_RB;
 }
 
 int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
@@ -444,7 +445,8 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
             (H->o.precision != BCMG_PREC_FP64 && H->o.precision != BCMG_PREC_MIXED) ||
             (H->o.bc != BCMG_BC_DIRICHLET && H->o.bc != BCMG_BC_NEUMANN) ||
             !(H->o.reaction >= 0.0 && H->o.reaction < 1e300) ||
-            (H->o.cycle != BCMG_CYCLE_V && H->o.cycle != BCMG_CYCLE_W))
+            (H->o.cycle != BCMG_CYCLE_V && H->o.cycle != BCMG_CYCLE_W) ||
+            (H->o.ordering != BCMG_ORDER_RB && H->o.ordering != BCMG_ORDER_LEX))
             throw Error{BCMG_EINVAL, "invalid options"};
         H->user = (cudaStream_t)stream;
         keep_pool_memory();

@@ -1079,7 +1079,20 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps) {
     const int64_t nblack = L.nint - L.nred;
     const int bg = bs_for(H, L.ng);
     for (int s = 0; s < nsteps; ++s) {
-        for (int c = 0; c < 2; ++c) {
+        if (H.o.ordering == BCMG_ORDER_LEX) {
+            // GS-LEX (eq. GSLEX_2D): hyperplanes in increasing p; each node
+            // sees new values below it and old values above, as in the
+            // lexicographic loop
+            for (size_t q = 0; q + 1 < L.hoff.size(); ++q) {
+                const int64_t n = L.hoff[q + 1] - L.hoff[q];
+                if (n == 0) continue;
+                const int bs = bs_for(H, n);
+                const uint32_t *list = L.hlist + L.hoff[q];
+                if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, G);
+                else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, G);
+            }
+        }
+        for (int c = 0; c < 2 && H.o.ordering == BCMG_ORDER_RB; ++c) {
             const uint32_t *list = L.ilist + (c ? L.nred : 0);
             const int64_t n = c ? nblack : L.nred;
             const int bs = bs_for(H, n);
@@ -1243,6 +1256,7 @@ void setup_cycle(Handle &H) {
     // thread of the cluster (and at most kTailNodes) and its extension is
     // expanded; the coarsest level also needs at most kTailCoarse unknowns
     H.tail_start = -1;
+    if (H.o.ordering != BCMG_ORDER_RB) return;  // the tail runs red-black sweeps
     auto fits = [&](const Level &A, int64_t lim) {
         return A.nint + A.ng <= lim && A.nb <= lim && (A.nb == 0 || A.ecnt != nullptr);
     };

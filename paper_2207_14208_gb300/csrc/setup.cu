@@ -941,6 +941,27 @@ void run_compaction(Handle &H, std::vector<CompactItem> &items) {
     check_cuda(cudaStreamSynchronize(H.st), "compaction sync 2");
 }
 
+// hyperplane (p = i + j + k) of each interior node: counts, then positions
+__global__ void k_hp_count(const uint32_t *__restrict__ ilist, int64_t nint, Geo G, int *__restrict__ counts) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nint) return;
+    int ix[3];
+    decode(G, ilist[t], ix);
+    atomicAdd(counts + ix[0] + ix[1] + ix[2], 1);
+}
+
+// within a hyperplane the order does not matter: its nodes are not
+// neighbours of one another
+__global__ void k_hp_scatter(const uint32_t *__restrict__ ilist, int64_t nint, Geo G, int *__restrict__ cursor,
+                             uint32_t *__restrict__ hlist) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nint) return;
+    const uint32_t X = ilist[t];
+    int ix[3];
+    decode(G, X, ix);
+    hlist[atomicAdd(cursor + ix[0] + ix[1] + ix[2], 1)] = X;
+}
+
 struct LevelScratch {
     uint8_t *fred = nullptr, *fblack = nullptr, *fbox = nullptr, *fghost = nullptr, *fact = nullptr,
             *fband = nullptr;
@@ -1163,6 +1184,48 @@ void setup_hierarchy(Handle &H, const double *phi0) {
                 L.ew = ew;
             }
         }
+    }
+    // GS-LEX: interior nodes grouped by hyperplane on every level (one sync)
+    if (H.o.ordering == BCMG_ORDER_LEX) {
+        std::vector<int *> cnt(keep);
+        std::vector<int64_t> base(keep + 1, 0);
+        for (int l = 0; l < keep; ++l) base[l + 1] = base[l] + (int64_t)H.d * H.L[l].N + 1;
+        int *counts = (int *)dalloc(H, sizeof(int) * base[keep], true);
+        for (int l = 0; l < keep; ++l) {
+            Level &L = H.L[l];
+            if (L.nint > 0) {
+                k_hp_count<<<nblocks(L.nint, T), T, 0, H.st>>>(L.ilist, L.nint, geo_of(L), counts + base[l]);
+                count_launch(H);
+            }
+        }
+        int64_t *hc = pinned_scratch((size_t)base[keep]);
+        int *hci = (int *)hc;
+        check_cuda(cudaMemcpyAsync(hci, counts, sizeof(int) * base[keep], cudaMemcpyDeviceToHost, H.st), "hp counts");
+        check_cuda(cudaStreamSynchronize(H.st), "hp sync");
+        std::vector<int> cursor((size_t)base[keep]);
+        for (int l = 0; l < keep; ++l) {
+            Level &L = H.L[l];
+            const int64_t np = base[l + 1] - base[l];
+            L.hoff.assign((size_t)np + 1, 0);
+            for (int64_t q = 0; q < np; ++q) {
+                cursor[base[l] + q] = (int)L.hoff[q];
+                L.hoff[q + 1] = L.hoff[q] + hci[base[l] + q];
+            }
+        }
+        check_cuda(cudaMemcpyAsync(counts, cursor.data(), sizeof(int) * base[keep], cudaMemcpyHostToDevice, H.st),
+                   "hp cursor");
+        for (int l = 0; l < keep; ++l) {
+            Level &L = H.L[l];
+            L.hlist = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(L.nint, 1));
+            if (L.nint > 0) {
+                k_hp_scatter<<<nblocks(L.nint, T), T, 0, H.st>>>(L.ilist, L.nint, geo_of(L), counts + base[l],
+                                                                 L.hlist);
+                count_launch(H);
+            }
+        }
+        check_cuda(cudaGetLastError(), "hyperplanes");
+        // the pageable cursor copy must be done before the vector goes
+        check_cuda(cudaStreamSynchronize(H.st), "hp sync 2");
     }
     // level arrays
     for (int l = 0; l < keep; ++l) {

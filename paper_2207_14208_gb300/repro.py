@@ -133,6 +133,11 @@ def main():
     Ns3 = [32, 64, 128, 256]
     print(_table([v[0] for v in variants], Ns3,
                  lambda r, N: "%.3f" % rho(3, N, W.phi_ellipsoid(N), **dict(variants)[r])))
+    print("\nGS-LEX (the paper's order) against red-black, V(2,1), Dtau_OPT exp: rho")
+    print(_table(["circle RB", "circle LEX", "flower RB", "flower LEX"], [64, 128, 256],
+                 lambda r, N: "%.3f" % rho(2, N, (W.phi_circle_paper if r.startswith("circle") else
+                                                  W.phi_flower_paper)(N),
+                                          ordering=bcmg.ORDER_LEX if r.endswith("LEX") else bcmg.ORDER_RB)))
     print("\nW(2,1) against V(2,1), Dtau_OPT exp: rho")
     print(_table(["circle V", "circle W"], Ns2[:4],
                  lambda r, N: "%.3f" % rho(2, N, W.phi_circle_paper(N),

@@ -307,3 +307,27 @@ def test_rho_harness_matches_oracle(bcmg):
     r_gpu = repro.rho(2, N, phi)
     r_orc, _ = O.Oracle(2, N, phi).rho(np.random.Generator(np.random.PCG64(3)).uniform(-1.0, 1.0, (N + 1) ** 2))
     assert r_gpu == pytest.approx(r_orc, rel=1e-6)
+
+
+@pytest.mark.parametrize("name,d,N,mk", [("disk64", 2, 64, W.phi_disk), ("flower48", 2, 48, W.phi_flower_paper),
+                                         ("ellipsoid24", 3, 24, W.phi_ellipsoid)],
+                         ids=["disk64", "flower48", "ellipsoid24"])
+def test_gslex_matches_oracle(bcmg, name, d, N, mk):
+    # the paper's GS-LEX interior order (eq. GSLEX_2D), run on the GPU as a
+    # sweep over the hyperplanes i + j (+ k) = p, against the oracle's
+    # lexicographic loop
+    B = bcmg
+    phi = mk(N)
+    f, us = W.manufactured(d, N)
+    s = B.Solver(d, N, dev(phi), dev(f), ordering=B.ORDER_LEX)
+    o = O.Oracle(d, N, phi, ordering=O.LEX)
+    g = W.g_at(d, o.ghosts(0)["Q"])
+    o.set_rhs(f, g)
+    s.set_boundary_values(dev(g))
+    act = np.isin(o.cls(0), [O.INTERIOR, O.GHOST])
+    uo = np.where(o.cls(0) == O.BOXDIR, us, 0.0)
+    ug = dev(uo)
+    for cyc in range(3):
+        uo = o.vcycle(uo, 1)
+        s.vcycle(ug, 1)
+        assert np.abs(host(ug)[act] - uo[act]).max() <= REL * np.abs(uo[act]).max(), cyc
