@@ -191,7 +191,7 @@ int bcmg_memory_footprint(bcmg_handle h, int64_t *bytes);
 /* A-priori estimate of the device memory a hierarchy of this size will hold
  * (no phi needed), for admission control: the dense per-level arrays over
  * the levels the coarsening rule allows, times 2 for the compacted lists,
- * plus 1 MiB.  It exceeds bcmg_memory_footprint on the shapes the tests
+ * plus 12 MiB for the chunks small arrays are carved from.  It exceeds bcmg_memory_footprint on the shapes the tests
  * cover; geometries with far more boundary than the test domains can
  * exceed it.  opts may be NULL (defaults). */
 int bcmg_footprint_estimate(int dim, int64_t N, const bcmg_opts *opts, int64_t *bytes);

@@ -102,6 +102,11 @@ struct SolveState {
 
 constexpr uint32_t kHandleMagic = 0x474d4342u;  // set while a handle is live
 
+struct Arena {  // bump allocation inside one zero-filled device chunk
+    char *base = nullptr;
+    size_t used = 0, cap = 0;
+};
+
 struct Handle {
     uint32_t magic = kHandleMagic;
     int d = 0;
@@ -135,6 +140,7 @@ struct Handle {
     int64_t captured = 0;
     std::vector<void *> allocs;
     int64_t dev_bytes = 0;      // device memory the handle holds
+    Arena arena_perm, arena_temp;
     std::vector<void *> temps;  // set-up scratch, freed when creation ends
     // profiling of the finest-level sweeps (opts.profile)
     std::vector<cudaEvent_t> pev;
@@ -152,7 +158,9 @@ struct Error {
     std::string msg;
 };
 void check_cuda(cudaError_t e, const char *what);
-void *dalloc(Handle &H, size_t bytes, bool temp = false);  // zero-filled; temp: freed after set-up
+// device array of the handle; temp: freed when creation ends; zero: the
+// array must start zero-filled (small arrays always are)
+void *dalloc(Handle &H, size_t bytes, bool temp = false, bool zero = true);
 void count_launch(Handle &H);
 int64_t launches_total();
 void add_launches(int64_t n);

@@ -29,11 +29,17 @@ void check_cuda(cudaError_t e, const char *what) {
     }
 }
 
-void *dalloc(Handle &H, size_t bytes, bool temp) {
+// Device memory of a handle.  Arrays up to kSmallAlloc bytes are carved from
+// kChunk-byte chunks that are zero-filled once when taken, so a hierarchy
+// needs a few dozen driver calls rather than two per array; larger arrays
+// get their own stream-ordered allocation from the device's default pool
+// (which keeps freed memory for reuse, so repeated create/destroy stays
+// cheap), zero-filled only when the caller needs zeros.
+constexpr size_t kChunk = 4u << 20;
+constexpr size_t kSmallAlloc = 256u << 10;
+
+void *raw_alloc(Handle &H, size_t bytes, bool temp) {
     void *p = nullptr;
-    if (bytes == 0) bytes = 8;
-    // stream-ordered allocation from the device's default pool (which keeps
-    // freed memory for reuse, so repeated create/destroy stays cheap)
     cudaError_t e = cudaMallocAsync(&p, bytes, H.st);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -41,7 +47,25 @@ void *dalloc(Handle &H, size_t bytes, bool temp) {
     }
     (temp ? H.temps : H.allocs).push_back(p);
     if (!temp) H.dev_bytes += (int64_t)bytes;
-    check_cuda(cudaMemsetAsync(p, 0, bytes, H.st), "cudaMemsetAsync");
+    return p;
+}
+
+void *dalloc(Handle &H, size_t bytes, bool temp, bool zero) {
+    bytes = (std::max<size_t>(bytes, 8) + 255) & ~(size_t)255;
+    if (bytes <= kSmallAlloc) {
+        Arena &A = temp ? H.arena_temp : H.arena_perm;
+        if (!A.base || A.used + bytes > A.cap) {
+            A.base = (char *)raw_alloc(H, kChunk, temp);
+            A.used = 0;
+            A.cap = kChunk;
+            check_cuda(cudaMemsetAsync(A.base, 0, kChunk, H.st), "cudaMemsetAsync");
+        }
+        void *p = A.base + A.used;
+        A.used += bytes;
+        return p;
+    }
+    void *p = raw_alloc(H, bytes, temp);
+    if (zero) check_cuda(cudaMemsetAsync(p, 0, bytes, H.st), "cudaMemsetAsync");
     return p;
 }
 
@@ -73,6 +97,7 @@ namespace {
 void free_temps(Handle &H) {
     for (void *p : H.temps) cudaFreeAsync(p, H.st);
     H.temps.clear();
+    H.arena_temp = Arena{};
 }
 
 void keep_pool_memory() {
@@ -462,7 +487,7 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         // the coarser level still has interior nodes (Sec. 2.1)
         setup_hierarchy(*H, phi_dev);
         Level &L0 = H->L[0];
-        H->u0 = (double *)dalloc(*H, sizeof(double) * L0.nn);
+        H->u0 = (double *)dalloc(*H, sizeof(double) * L0.nn, false, false);
         H->npart = (double *)dalloc(*H, sizeof(double) * 4 * (norm_parts(L0) + 1));
         setup_cycle(*H);
         H->nout = (double *)dalloc(*H, sizeof(double) * 4);
@@ -648,7 +673,8 @@ int bcmg_footprint_estimate(int dim, int64_t N, const bcmg_opts *opts, int64_t *
         if (Nl % 2 != 0 || Nl / 2 < o.min_coarse) break;
         Nl /= 2;
     }
-    *bytes = (int64_t)(2.0 * total) + (int64_t)(1 << 20);
+    // plus the chunks small arrays are carved from (a few per hierarchy)
+    *bytes = (int64_t)(2.0 * total) + 3 * (int64_t)(4 << 20);
     g_last_error.clear();
     return BCMG_OK;
 }

@@ -60,40 +60,71 @@ constexpr int kCompactThreads = 256;
 constexpr int kCompactPerThread = 16;
 constexpr int kCompactTile = kCompactThreads * kCompactPerThread;
 
-__global__ void k_count(const uint8_t *__restrict__ flags, int64_t n, int64_t *__restrict__ counts) {
-    __shared__ int64_t red[kCompactThreads];
-    int64_t base = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
-    int64_t c = 0;
+// Compaction of up to four lists from one byte array in one pass each: list
+// b holds, in increasing order, the indices i with flags[i] & mask_b != 0
+// (masks packed one per byte in `masks`).  Per block: the count of each
+// list (counts[block * nl + b]); then the scatter, whose per-thread counts
+// (at most kCompactPerThread each) are scanned as four 16-bit fields of one
+// 64-bit word (a block holds at most 4096 items, so no field overflows).
+__device__ __forceinline__ int bucket_hits(uint8_t f, uint32_t masks, int b) {
+    return (f & ((masks >> (8 * b)) & 0xffu)) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_count(const uint8_t *__restrict__ flags, int64_t n, int nl,
+                                                           uint32_t masks, int64_t *__restrict__ counts) {
+    __shared__ uint64_t red[kCompactThreads];
+    const int64_t base = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
+    uint64_t c = 0;
     for (int i = 0; i < kCompactPerThread; ++i)
-        if (base + i < n) c += flags[base + i] ? 1 : 0;
+        if (base + i < n) {
+            const uint8_t f = flags[base + i];
+            for (int b = 0; b < nl; ++b) c += (uint64_t)bucket_hits(f, masks, b) << (16 * b);
+        }
     red[threadIdx.x] = c;
     __syncthreads();
     for (int s = kCompactThreads / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) counts[blockIdx.x] = red[0];
+    if (threadIdx.x < nl) counts[(int64_t)blockIdx.x * nl + threadIdx.x] = (int64_t)((red[0] >> (16 * threadIdx.x)) & 0xffffu);
 }
 
-__global__ void k_scatter(const uint8_t *__restrict__ flags, int64_t n, const int64_t *__restrict__ offs,
-                          uint32_t *__restrict__ out) {
-    __shared__ int64_t sc[kCompactThreads];
-    int64_t base = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
-    int64_t c = 0;
+struct ScatterOut {
+    uint32_t *out[4];  // nullptr: list counted only
+};
+
+__global__ void __launch_bounds__(kCompactThreads) k_scatter(const uint8_t *__restrict__ flags, int64_t n, int nl,
+                                                             uint32_t masks, const int64_t *__restrict__ offs,
+                                                             ScatterOut so) {
+    __shared__ uint64_t sc[kCompactThreads];
+    const int64_t base = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
+    uint64_t c = 0;
     for (int i = 0; i < kCompactPerThread; ++i)
-        if (base + i < n) c += flags[base + i] ? 1 : 0;
+        if (base + i < n) {
+            const uint8_t f = flags[base + i];
+            for (int b = 0; b < nl; ++b) c += (uint64_t)bucket_hits(f, masks, b) << (16 * b);
+        }
     sc[threadIdx.x] = c;
     __syncthreads();
     // inclusive Hillis-Steele scan over the block (deterministic)
     for (int s = 1; s < kCompactThreads; s <<= 1) {
-        int64_t v = (threadIdx.x >= s) ? sc[threadIdx.x - s] : 0;
+        const uint64_t v = (threadIdx.x >= s) ? sc[threadIdx.x - s] : 0;
         __syncthreads();
         sc[threadIdx.x] += v;
         __syncthreads();
     }
-    int64_t pos = offs[blockIdx.x] + sc[threadIdx.x] - c;
+    const uint64_t excl = sc[threadIdx.x] - c;
+    int64_t pos[4];
+    for (int b = 0; b < nl; ++b) pos[b] = offs[(int64_t)blockIdx.x * nl + b] + (int64_t)((excl >> (16 * b)) & 0xffffu);
     for (int i = 0; i < kCompactPerThread; ++i)
-        if (base + i < n && flags[base + i]) out[pos++] = (uint32_t)(base + i);
+        if (base + i < n) {
+            const uint8_t f = flags[base + i];
+            for (int b = 0; b < nl; ++b)
+                if (bucket_hits(f, masks, b)) {
+                    if (so.out[b]) so.out[b][pos[b]] = (uint32_t)(base + i);
+                    ++pos[b];
+                }
+        }
 }
 
 // ---------------------------------------------------------------- classes
@@ -114,16 +145,19 @@ __device__ __forceinline__ bool neg_d(double x) {
     return b < 0 && m != 0 && m <= 0x7ff0000000000000LL;
 }
 
-// Node classes of one level (Sec. 3.3) and the flags of every list the
-// set-up compacts, one thread per node on a (x-blocks, j, k) grid (no index
-// division): red / black interior, box-edge Dirichlet, ghost, active.
+// Node classes of one level (Sec. 3.3) and, packed in one byte per node, the
+// flags of every list the set-up compacts (red / black interior, box-edge
+// Dirichlet, ghost, active), one thread per node on a (x-blocks, j, k) grid
+// (no index division).
+enum : uint8_t { kFlRed = 1, kFlBlack = 2, kFlBox = 4, kFlGhost = 8, kFlAct = 16 };
+
 template <int D>
 __global__ void __launch_bounds__(128) k_classify(const double *__restrict__ phi, Geo G, uint8_t *__restrict__ cls,
-                                                  uint8_t *__restrict__ fred, uint8_t *__restrict__ fblack,
-                                                  uint8_t *__restrict__ fbox, uint8_t *__restrict__ fghost,
-                                                  uint8_t *__restrict__ fact) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = (D == 3) ? blockIdx.z : 0;
-    if (i > G.N) return;
+                                                  uint8_t *__restrict__ flags) {
+    // 32 x 4 thread blocks over (i, j) rows: little idle work when N + 1 is
+    // not a multiple of the block width
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y, k = (D == 3) ? blockIdx.z : 0;
+    if (i > G.N || j > G.N) return;
     const int64_t sy = G.st[1], sz = (D == 3) ? G.st[2] : 0;
     const int64_t lin = (int64_t)i + (int64_t)j * sy + (int64_t)k * sz;
     const bool edge = i == 0 || i == G.N || j == 0 || j == G.N || (D == 3 && (k == 0 || k == G.N));
@@ -146,11 +180,11 @@ __global__ void __launch_bounds__(128) k_classify(const double *__restrict__ phi
     }
     cls[lin] = c;
     const int par = (i + j + k) & 1;
-    fred[lin] = (c == CL_INTERIOR && par == 0) ? 1 : 0;
-    fblack[lin] = (c == CL_INTERIOR && par == 1) ? 1 : 0;
-    fbox[lin] = (c == CL_BOXDIR) ? 1 : 0;
-    fghost[lin] = (c == CL_GHOST) ? 1 : 0;
-    fact[lin] = (c == CL_INTERIOR || c == CL_GHOST) ? 1 : 0;
+    uint8_t fl = 0;
+    if (c == CL_INTERIOR) fl = (par == 0 ? kFlRed : kFlBlack) | kFlAct;
+    else if (c == CL_GHOST) fl = kFlGhost | kFlAct;
+    else if (c == CL_BOXDIR) fl = kFlBox;
+    flags[lin] = fl;
 }
 
 // ---------------------------------------------------------------- ghosts
@@ -322,6 +356,59 @@ __device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng,
             eta = 1.0;
             atomicAdd(out.nclamp, 1ull);
         } else {
+            // For eta in (0, 1) the point G - eta h n stays in one grid cell
+            // (|n_a| <= 1), the one holding G - h n / 2, where the
+            // multilinear interpolant is a polynomial of degree d in eta:
+            // t_a(eta) = (i_a - c_a) - n_a eta.  Its coefficients are built
+            // once (x, then y, then z) and the halving runs on them (Horner);
+            // eta then differs from a pointwise evaluation only in rounding.
+            int c[3] = {0, 0, 0};
+            double al[3] = {0.0, 0.0, 0.0}, be[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < d; ++a) {
+                const double pmid = __dsub_rn((double)ix[a], __dmul_rn(0.5, n[a]));
+                int ci = (int)floor(pmid);
+                ci = max(0, min(G.N - 1, ci));
+                c[a] = ci;
+                al[a] = (double)(ix[a] - ci);
+                be[a] = -n[a];
+            }
+            double v[8];
+            for (int k = 0; k < (1 << d); ++k) {
+                int64_t idx = 0;
+                for (int a = 0; a < d; ++a) idx += (int64_t)(c[a] + ((k >> a) & 1)) * G.st[a];
+                v[k] = phi[idx];
+            }
+            // factors (1 - t_a) and t_a as (constant, slope) pairs
+            double f0[3][2], f1[3][2];
+            for (int a = 0; a < d; ++a) {
+                f1[a][0] = al[a];
+                f1[a][1] = be[a];
+                f0[a][0] = 1.0 - al[a];
+                f0[a][1] = -be[a];
+            }
+            // along x: 2^(d-1) linear polynomials
+            double gx[4][2];
+            for (int k = 0; k < (1 << (d - 1)); ++k) {
+                const double v0 = v[2 * k], v1 = v[2 * k + 1];
+                gx[k][0] = v0 * f0[0][0] + v1 * f1[0][0];
+                gx[k][1] = v0 * f0[0][1] + v1 * f1[0][1];
+            }
+            // along y: 2^(d-2) quadratics
+            double gy[2][3];
+            for (int k = 0; k < (1 << (d - 2)); ++k) {
+                const double *a0 = gx[2 * k], *a1 = gx[2 * k + 1];
+                gy[k][0] = a0[0] * f0[1][0] + a1[0] * f1[1][0];
+                gy[k][1] = a0[0] * f0[1][1] + a0[1] * f0[1][0] + a1[0] * f1[1][1] + a1[1] * f1[1][0];
+                gy[k][2] = a0[1] * f0[1][1] + a1[1] * f1[1][1];
+            }
+            double cf[4] = {gy[0][0], gy[0][1], gy[0][2], 0.0};
+            if (d == 3) {  // along z: the cubic
+                const double *a0 = gy[0], *a1 = gy[1];
+                cf[0] = a0[0] * f0[2][0] + a1[0] * f1[2][0];
+                cf[1] = a0[0] * f0[2][1] + a0[1] * f0[2][0] + a1[0] * f1[2][1] + a1[1] * f1[2][0];
+                cf[2] = a0[1] * f0[2][1] + a0[2] * f0[2][0] + a1[1] * f1[2][1] + a1[2] * f1[2][0];
+                cf[3] = a0[2] * f0[2][1] + a1[2] * f1[2][1];
+            }
             // once the midpoint rounds onto an end of the interval, every
             // remaining halving leaves eta = that midpoint: stop there
             double lo = 0.0, hi = 1.0;
@@ -331,10 +418,8 @@ __device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng,
                     lo = hi = mid;
                     break;
                 }
-                double pm[3];
-                for (int a = 0; a < 3; ++a)
-                    pm[a] = (a < d) ? __dsub_rn((double)ix[a], __dmul_rn(mid, n[a])) : (double)ix[a];
-                if (interp_phi(G, phi, pm, cc) >= 0.0) lo = mid;
+                const double val = fma(fma(fma(cf[3], mid, cf[2]), mid, cf[1]), mid, cf[0]);
+                if (val >= 0.0) lo = mid;
                 else hi = mid;
             }
             eta = __dmul_rn(0.5, __dadd_rn(lo, hi));
@@ -808,10 +893,12 @@ __global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A,
         const double inv = sinv;
         for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * n + k] *= inv;
         __syncthreads();
-        // rank-1 update of the trailing block: rows by warp, columns by lane
-        for (int i = k + 1 + warp; i < n; i += nw) {
-            const double l = S[i * n + k];
-            for (int j = k + 1 + lane; j < n; j += 32) S[i * n + j] -= l * S[k * n + j];
+        // rank-1 update of the trailing m x m block, its entries dealt out
+        // over all threads (every lane of every warp busy until the end)
+        const int m = n - k - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int i = k + 1 + t / m, j = k + 1 + t % m;
+            S[i * n + j] -= S[i * n + k] * S[k * n + j];
         }
         __syncthreads();
     }
@@ -824,14 +911,21 @@ __global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A,
 // reciprocals of U's diagonal (one FP64 division per diagonal entry, not per
 // step and lane).  P e_j is a unit vector e_q, so the forward substitution
 // starts at row q.
-constexpr int kLuColsPerBlock = 2;
+constexpr int kLuColsPerBlock = 4;
 
 __global__ void __launch_bounds__(32 * kLuColsPerBlock) k_lu_inverse(const double *__restrict__ LU, int n,
                                                                      const int *__restrict__ perm,
                                                                      double *__restrict__ Ainv) {
     extern __shared__ double sm[];  // n * n factor, n reciprocals, kLuColsPerBlock * n vectors
     double *F = sm, *rd = sm + n * n;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) F[t] = LU[t];
+    // 16-byte copies, several in flight per thread (both buffers are
+    // 16-byte aligned: a stream-ordered allocation and dynamic shared memory)
+    const int nn = n * n;
+    const double2 *src2 = reinterpret_cast<const double2 *>(LU);
+    double2 *dst2 = reinterpret_cast<double2 *>(F);
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nn / 2; t += blockDim.x) dst2[t] = src2[t];
+    if ((nn & 1) && threadIdx.x == 0) F[nn - 1] = LU[nn - 1];
     for (int t = threadIdx.x; t < n; t += blockDim.x) rd[t] = 1.0 / LU[t * n + t];
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -882,11 +976,28 @@ namespace {
 
 struct CompactItem {
     const uint8_t *flags;
-    int64_t n, nblk, base;
-    uint32_t **out;  // nullptr: count only
-    bool temp;
-    int64_t total;
+    int64_t n;
+    int nl;                // lists taken from this flag array (1..4)
+    uint8_t mask[4];       // list b: the indices with flags & mask[b] != 0
+    uint32_t **out[4];     // nullptr: counted only
+    bool temp[4];          // list freed when creation ends
+    int64_t total[4];
+    int64_t nblk = 0, base = 0;
 };
+
+CompactItem compact_item(const uint8_t *flags, int64_t n) {
+    CompactItem it{};
+    it.flags = flags;
+    it.n = n;
+    return it;
+}
+
+void add_list(CompactItem &it, uint8_t mask, uint32_t **out, bool temp) {
+    it.mask[it.nl] = mask;
+    it.out[it.nl] = out;
+    it.temp[it.nl] = temp;
+    it.nl++;
+}
 
 thread_local int64_t *t_pinned = nullptr;
 thread_local size_t t_pinned_n = 0;
@@ -908,32 +1019,49 @@ void run_compaction(Handle &H, std::vector<CompactItem> &items) {
     for (auto &it : items) {
         it.nblk = std::max<int64_t>((it.n + kCompactTile - 1) / kCompactTile, 1);
         it.base = B;
-        B += it.nblk;
+        B += it.nblk * it.nl;
     }
     if (B == 0) return;
+    auto masks_of = [](const CompactItem &it) {
+        uint32_t m = 0;
+        for (int b = 0; b < it.nl; ++b) m |= (uint32_t)it.mask[b] << (8 * b);
+        return m;
+    };
     int64_t *counts = (int64_t *)dalloc(H, sizeof(int64_t) * B, true);
     for (auto &it : items) {
-        k_count<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, counts + it.base);
+        k_count<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, it.nl, masks_of(it),
+                                                                  counts + it.base);
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "k_count");
     int64_t *hc = pinned_scratch((size_t)B);
     check_cuda(cudaMemcpyAsync(hc, counts, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, H.st), "counts D2H");
     check_cuda(cudaStreamSynchronize(H.st), "compaction sync");
-    for (auto &it : items) {
-        int64_t tot = 0;
-        for (int64_t b = 0; b < it.nblk; ++b) {
-            int64_t c = hc[it.base + b];
-            hc[it.base + b] = tot;
-            tot += c;
+    for (auto &it : items)
+        for (int b = 0; b < it.nl; ++b) {
+            int64_t tot = 0;
+            for (int64_t k = 0; k < it.nblk; ++k) {
+                int64_t &slot = hc[it.base + k * it.nl + b];
+                const int64_t c = slot;
+                slot = tot;
+                tot += c;
+            }
+            it.total[b] = tot;
         }
-        it.total = tot;
-    }
     check_cuda(cudaMemcpyAsync(counts, hc, sizeof(int64_t) * B, cudaMemcpyHostToDevice, H.st), "offsets H2D");
     for (auto &it : items) {
-        if (!it.out) continue;
-        *it.out = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(it.total, 1), it.temp);
-        k_scatter<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, counts + it.base, *it.out);
+        ScatterOut so{};
+        bool any = false;
+        for (int b = 0; b < it.nl; ++b) {
+            if (!it.out[b]) continue;
+            *it.out[b] = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(it.total[b], 1),
+                                            it.temp[b], false);
+            so.out[b] = *it.out[b];
+            any = true;
+        }
+        if (!any) continue;
+        k_scatter<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, it.nl, masks_of(it),
+                                                                    counts + it.base, so);
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "k_scatter");
@@ -963,8 +1091,7 @@ __global__ void k_hp_scatter(const uint32_t *__restrict__ ilist, int64_t nint, G
 }
 
 struct LevelScratch {
-    uint8_t *fred = nullptr, *fblack = nullptr, *fbox = nullptr, *fghost = nullptr, *fact = nullptr,
-            *fband = nullptr;
+    uint8_t *flags = nullptr, *fband = nullptr;
     uint32_t *red = nullptr, *black = nullptr;
     unsigned long long *cnt = nullptr;  // clamp / fall-back counters
     int64_t *ecnt = nullptr;
@@ -1006,23 +1133,19 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         if (l == 0) {
             L.phi = phi0;
         } else {
-            double *phic = (double *)dalloc(H, sizeof(double) * L.nn, true);
+            double *phic = (double *)dalloc(H, sizeof(double) * L.nn, true, false);
             const dim3 ig((unsigned)nblocks(L.n, 128), (unsigned)L.n, H.d == 3 ? (unsigned)L.n : 1u);
             k_inject<<<ig, 128, 0, H.st>>>(H.L[l - 1].phi, geo_of(H.L[l - 1]), G, phic);
             count_launch(H);
             L.phi = phic;
         }
-        L.cls = (uint8_t *)dalloc(H, L.nn);
-        s.fred = (uint8_t *)dalloc(H, (size_t)L.nn, true);
-        s.fblack = (uint8_t *)dalloc(H, (size_t)L.nn, true);
-        s.fbox = (uint8_t *)dalloc(H, (size_t)L.nn, true);
-        s.fghost = (uint8_t *)dalloc(H, (size_t)L.nn, true);
-        s.fact = (uint8_t *)dalloc(H, (size_t)L.nn, true);
-        const dim3 cg((unsigned)nblocks(L.n, 128), (unsigned)L.n, H.d == 3 ? (unsigned)L.n : 1u);
+        L.cls = (uint8_t *)dalloc(H, L.nn, false, false);  // k_classify writes every entry
+        s.flags = (uint8_t *)dalloc(H, (size_t)L.nn, true, false);
+        const dim3 cg((unsigned)nblocks(L.n, 32), (unsigned)nblocks(L.n, 4), H.d == 3 ? (unsigned)L.n : 1u);
         if (H.d == 3)
-            k_classify<3><<<cg, 128, 0, H.st>>>(L.phi, G, L.cls, s.fred, s.fblack, s.fbox, s.fghost, s.fact);
+            k_classify<3><<<cg, dim3(32, 4), 0, H.st>>>(L.phi, G, L.cls, s.flags);
         else
-            k_classify<2><<<cg, 128, 0, H.st>>>(L.phi, G, L.cls, s.fred, s.fblack, s.fbox, s.fghost, s.fact);
+            k_classify<2><<<cg, dim3(32, 4), 0, H.st>>>(L.phi, G, L.cls, s.flags);
         count_launch(H);
         check_cuda(cudaGetLastError(), "classification");
     }
@@ -1032,18 +1155,20 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         for (int l = 0; l < nc; ++l) {
             Level &L = H.L[l];
             LevelScratch &s = S[l];
-            items.push_back({s.fred, L.nn, 0, 0, &s.red, true, 0});
-            items.push_back({s.fblack, L.nn, 0, 0, &s.black, true, 0});
-            items.push_back({s.fbox, L.nn, 0, 0, l == 0 ? &L.boxidx : nullptr, false, 0});
-            items.push_back({s.fghost, L.nn, 0, 0, &L.gidx, false, 0});
+            CompactItem it = compact_item(s.flags, L.nn);
+            add_list(it, kFlRed, &s.red, true);
+            add_list(it, kFlBlack, &s.black, true);
+            add_list(it, kFlBox, l == 0 ? &L.boxidx : nullptr, false);
+            add_list(it, kFlGhost, &L.gidx, false);
+            items.push_back(it);
         }
         run_compaction(H, items);
         for (int l = 0; l < nc; ++l) {
             Level &L = H.L[l];
-            L.nred = items[4 * l + 0].total;
-            L.nint = L.nred + items[4 * l + 1].total;
-            L.nbox = items[4 * l + 2].total;
-            L.ng = items[4 * l + 3].total;
+            L.nred = items[l].total[0];
+            L.nint = L.nred + items[l].total[1];
+            L.nbox = items[l].total[2];
+            L.ng = items[l].total[3];
         }
     }
     if (H.L[0].nint == 0) throw Error{BCMG_EGEOM, "no interior node on the finest grid"};
@@ -1080,8 +1205,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
         L.gtmp = (double *)dalloc(H, sizeof(double) * ng1);
         s.cnt = (unsigned long long *)dalloc(H, 2 * sizeof(unsigned long long), true);
-        s.fband = s.fred;  // reuse: cleared here
-        check_cuda(cudaMemsetAsync(s.fband, 0, (size_t)L.nn, H.st), "band memset");
+        s.fband = (uint8_t *)dalloc(H, (size_t)L.nn, true);  // zero-filled
         LevelTab &t = tab[l];
         t = LevelTab{};
         t.G = G;
@@ -1104,12 +1228,18 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     // round 2: band lists on every level and the coarsest active list (one sync)
     {
         std::vector<CompactItem> items;
-        for (int l = 0; l < keep; ++l) items.push_back({S[l].fband, H.L[l].nn, 0, 0, &H.L[l].bidx, false, 0});
+        for (int l = 0; l < keep; ++l) {
+            CompactItem it = compact_item(S[l].fband, H.L[l].nn);
+            add_list(it, 0xff, &H.L[l].bidx, false);
+            items.push_back(it);
+        }
         Level &Lc = H.L[keep - 1];
-        items.push_back({S[keep - 1].fact, Lc.nn, 0, 0, &Lc.act, false, 0});
+        CompactItem ia = compact_item(S[keep - 1].flags, Lc.nn);
+        add_list(ia, kFlAct, &Lc.act, false);
+        items.push_back(ia);
         run_compaction(H, items);
-        for (int l = 0; l < keep; ++l) H.L[l].nb = items[l].total;
-        Lc.nact = items[keep].total;
+        for (int l = 0; l < keep; ++l) H.L[l].nb = items[l].total[0];
+        Lc.nact = items[keep].total[0];
     }
     if (H.L[keep - 1].nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
     // phase C: band sources and the ELL expansion of the extension, every
@@ -1231,11 +1361,14 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
         if (l > 0) L.u = (double *)dalloc(H, sizeof(double) * L.nn);
-        L.F = (double *)dalloc(H, sizeof(double) * L.nn);
+        // F is read on interior and ghost rows only; coarse levels get every
+        // such row from the restriction, the finest keeps zeros until the
+        // caller sets its data
+        L.F = (double *)dalloc(H, sizeof(double) * L.nn, false, l == 0);
         L.r = (double *)dalloc(H, sizeof(double) * L.nn);
         if (H.o.precision == BCMG_PREC_MIXED) {
             L.u32 = (float *)dalloc(H, sizeof(float) * L.nn);
-            L.F32 = (float *)dalloc(H, sizeof(float) * L.nn);
+            L.F32 = (float *)dalloc(H, sizeof(float) * L.nn, false, false);
             L.r32 = (float *)dalloc(H, sizeof(float) * L.nn);
             L.gtmp32 = (float *)dalloc(H, sizeof(float) * std::max<int64_t>(L.ng, 1));
             L.bbuf32 = (float *)dalloc(H, sizeof(float) * 2 * std::max<int64_t>(L.nb, 1));

@@ -85,5 +85,5 @@ def test_footprint_estimate_covers_actual(bcmg, d, N, mk, prec):
     s, _ = _make(B, d, N, mk(N), p)
     actual = s.memory_footprint()
     est = B.footprint_estimate(d, N, precision=p)
-    assert 0 < actual <= est <= 4 * actual + (2 << 20)
+    assert 0 < actual <= est <= 4 * actual + (16 << 20)
     s.close()
