@@ -525,6 +525,9 @@ struct LevelTab {
     uint32_t *eg;
     double *ew;
     uint8_t *ecnt;
+    uint32_t *eg2;  // second buffer of the expansion passes
+    double *ew2;
+    uint8_t *ecnt2;
     int64_t blk_g, blk_b;  // first block of this level in the ghost / band launches
 };
 
@@ -586,71 +589,61 @@ __global__ void k_band_all(const LevelTab *__restrict__ tab, int nl) {
     band_one(T.bidx, T.nb, T.phi, T.cls, T.G, T.bref, T.bw, b);
 }
 
-// The K Jacobi sweeps of the extension, started from zero, expand into a sum
-// over upwind paths of length <= K that end at a ghost: value(b) =
-// sum_paths (product of the normalised weights) * a[ghost].  The paths are
-// walked depth-first in a fixed order and equal ghosts merged as they come,
-// into at most kExtCap terms per band node (ELL layout, term-major); a level
-// with a longer row keeps the sweep-by-sweep extension instead.
-
-__global__ void k_ext_all(const LevelTab *__restrict__ tab, int nl, int d, int K, int *__restrict__ overflow) {
+// The K Jacobi sweeps of the extension, started from zero, are a fixed
+// linear map from ghost values to band values.  It is expanded pass by pass,
+// as the sweeps run: after pass k the term list of band node b is, over the
+// axis sources of b in axis order, the source ghost with its weight w_a, or
+// the source band node's list after pass k - 1 scaled by w_a, equal ghosts
+// merged (weights summed) in order of first appearance.  At most kExtCap
+// terms per band node (ELL layout, term-major); a level with a longer row
+// keeps the sweep-by-sweep extension instead.
+__global__ void k_ext_pass(const LevelTab *__restrict__ tab, int nl, int d, int first, int last, int to_final,
+                           int *__restrict__ overflow) {
     const int l = level_of_block(tab, nl, true);
     const LevelTab &T = tab[l];
     const int64_t b = ((int64_t)blockIdx.x - T.blk_b) * blockDim.x + threadIdx.x;
     if (b >= T.nb) return;
     const int64_t nb = T.nb;
+    // the previous pass wrote the other buffer
+    const uint8_t *cp = to_final ? T.ecnt2 : T.ecnt;
+    const uint32_t *gp = to_final ? T.eg2 : T.eg;
+    const double *wp = to_final ? T.ew2 : T.ew;
+    uint8_t *co = to_final ? T.ecnt : T.ecnt2;
+    uint32_t *go = to_final ? T.eg : T.eg2;
+    double *wo = to_final ? T.ew : T.ew2;
     uint32_t g[kExtCap];
     double w[kExtCap];
     int cnt = 0;
     bool over = false;
-    int64_t st_node[16];
-    int st_depth[16];
-    double st_w[16];
-    int sp = 1;
-    st_node[0] = b;
-    st_depth[0] = 1;
-    st_w[0] = 1.0;
-    while (sp > 0) {
-        --sp;
-        const int64_t x = st_node[sp];
-        const int j = st_depth[sp];
-        const double W = st_w[sp];
-        for (int ax = d - 1; ax >= 0; --ax) {
-            const int32_t ref = T.bref[(int64_t)ax * nb + x];
-            if (ref == kNoRef || ref < 0 || j >= K) continue;
-            if (sp < 16) {
-                st_node[sp] = ref;
-                st_depth[sp] = j + 1;
-                st_w[sp] = W * T.bw[(int64_t)ax * nb + x];
-                ++sp;
-            } else {
-                over = true;
-            }
+    auto add = [&](uint32_t gg, double ww) {
+        int k = 0;
+        while (k < cnt && g[k] != gg) ++k;
+        if (k < cnt) w[k] += ww;
+        else if (cnt < kExtCap) {
+            g[cnt] = gg;
+            w[cnt] = ww;
+            ++cnt;
+        } else {
+            over = true;
         }
-        for (int ax = 0; ax < d; ++ax) {
-            const int32_t ref = T.bref[(int64_t)ax * nb + x];
-            if (ref == kNoRef || ref >= 0) continue;
-            const uint32_t gg = (uint32_t)(-(int64_t)ref - 1);
-            const double ww = W * T.bw[(int64_t)ax * nb + x];
-            int k = 0;
-            while (k < cnt && g[k] != gg) ++k;
-            if (k < cnt) {
-                w[k] += ww;
-            } else if (cnt < kExtCap) {
-                g[cnt] = gg;
-                w[cnt] = ww;
-                ++cnt;
-            } else {
-                over = true;
-            }
+    };
+    for (int ax = 0; ax < d; ++ax) {
+        const int32_t ref = T.bref[(int64_t)ax * nb + b];
+        if (ref == kNoRef) continue;
+        const double wa = T.bw[(int64_t)ax * nb + b];
+        if (ref < 0) {
+            add((uint32_t)(-(int64_t)ref - 1), wa);
+        } else if (!first) {
+            const int c = cp[ref];
+            for (int k = 0; k < c; ++k) add(gp[(int64_t)k * nb + ref], wa * wp[(int64_t)k * nb + ref]);
         }
     }
     if (over) atomicOr(overflow + l, 1);
-    atomicMax(overflow + nl + l, cnt);  // longest row of the level
-    T.ecnt[b] = (uint8_t)cnt;
+    if (last) atomicMax(overflow + nl + l, cnt);  // longest row of the level
+    co[b] = (uint8_t)cnt;
     for (int k = 0; k < cnt; ++k) {
-        T.eg[(int64_t)k * nb + b] = g[k];
-        T.ew[(int64_t)k * nb + b] = w[k];
+        go[(int64_t)k * nb + b] = g[k];
+        wo[(int64_t)k * nb + b] = w[k];
     }
 }
 
@@ -823,43 +816,28 @@ constexpr int kLuSmall = 144;
 
 __global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A, int n, double *__restrict__ LU,
                                                    int *__restrict__ perm, int *__restrict__ singular) {
-    extern __shared__ double S[];  // n * n
-    __shared__ long long bv[32];
-    __shared__ int bi[32];
+    extern __shared__ double S[];      // n * n, then the n multipliers of the current column
+    double *Lc = S + n * n;
+    __shared__ int piv;
     __shared__ double sinv;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) S[t] = A[t];
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        // pivot search on the bit patterns of |a_ik| (for non-negative
-        // doubles integer order is numeric order; no FP64 compares): per
-        // thread, per warp, then across warps, lowest row on ties
-        long long best = -1;
-        int bidx = n;
-        for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-            const long long v = __double_as_longlong(S[i * n + k]) & 0x7fffffffffffffffLL;
-            if (v > best) {
-                best = v;
-                bidx = i;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long v = __shfl_down_sync(0xffffffffu, best, o);
-            const int ii = __shfl_down_sync(0xffffffffu, bidx, o);
-            if (v > best || (v == best && ii < bidx)) {
-                best = v;
-                bidx = ii;
-            }
-        }
-        if (lane == 0) {
-            bv[warp] = best;
-            bi[warp] = bidx;
-        }
-        __syncthreads();
+        // 1. pivot (warp 0): largest |a_ik| for i >= k, lowest row on ties,
+        //    compared on the bit patterns (integer order is numeric order
+        //    for non-negative doubles; no FP64 compares); the reciprocal of
+        //    the pivot (one FP64 division per step)
         if (warp == 0) {
-            best = lane < nw ? bv[lane] : -1;
-            bidx = lane < nw ? bi[lane] : n;
+            long long best = -1;
+            int bidx = n;
+            for (int i = k + lane; i < n; i += 32) {
+                const long long v = __double_as_longlong(S[i * n + k]) & 0x7fffffffffffffffLL;
+                if (v > best) {
+                    best = v;
+                    bidx = i;
+                }
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const long long v = __shfl_down_sync(0xffffffffu, best, o);
@@ -870,35 +848,36 @@ __global__ void __launch_bounds__(1024) k_lu_small(const double *__restrict__ A,
                 }
             }
             if (lane == 0) {
-                bv[0] = best;
-                bi[0] = bidx;
+                const bool sing = best <= 0;  // zero column (or nothing left)
+                const int pr = sing ? k : bidx;
+                piv = pr;
+                perm[k] = pr;
+                if (sing) *singular = 1;
+                sinv = sing ? 0.0 : 1.0 / S[pr * n + k];
             }
         }
         __syncthreads();
-        int p = bi[0];
-        const bool sing = bv[0] <= 0;  // zero column (or nothing left)
-        if (sing) p = k;
-        if (threadIdx.x == 0) {
-            perm[k] = p;
-            if (sing) *singular = 1;
-        }
+        // 2. swap rows k and p; the multipliers l_ik = a_ik / u_kk of the rows
+        //    below (row p's old entry is the old a_kk, read by its swapper)
+        const int p = piv;
+        const double inv = sinv;
         if (p != k)
             for (int j = threadIdx.x; j < n; j += blockDim.x) {
                 const double t = S[k * n + j];
                 S[k * n + j] = S[p * n + j];
                 S[p * n + j] = t;
+                if (j == k) Lc[p] = t * inv;
             }
-        if (threadIdx.x == 0) sinv = sing ? 0.0 : 1.0 / S[k * n + k];  // one division per step
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+            if (i != p) Lc[i] = S[i * n + k] * inv;
         __syncthreads();
-        const double inv = sinv;
-        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) S[i * n + k] *= inv;
-        __syncthreads();
-        // rank-1 update of the trailing m x m block, its entries dealt out
-        // over all threads (every lane of every warp busy until the end)
-        const int m = n - k - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int i = k + 1 + t / m, j = k + 1 + t % m;
-            S[i * n + j] -= S[i * n + k] * S[k * n + j];
+        // 3. multipliers into column k and the rank-1 update of the trailing
+        //    block, its m x (m + 1) entries dealt out over all threads
+        const int m = n - k - 1, w = m + 1;
+        for (int t = threadIdx.x; t < m * w; t += blockDim.x) {
+            const int i = k + 1 + t / w, jj = t % w;
+            if (jj == 0) S[i * n + k] = Lc[i];
+            else S[i * n + k + jj] -= Lc[i] * S[k * n + k + jj];
         }
         __syncthreads();
     }
@@ -963,10 +942,9 @@ inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 double dtau_of(int d, int bc, int mode, double cst, double theta) { return dtau_formula(d, bc, mode, cst, theta); }
 
 // the path expansion fits the per-thread buffers: at most d (d^K - 1)/(d - 1)
-// ghost terms and a depth-first stack of (d - 1)(K - 1) + d entries
-// the depth-first walk of the expansion keeps at most (d - 1)(K - 1) + d
-// pending nodes on its 16-entry stack
-bool ext_ell_ok(int d, int K) { return K >= 1 && (d - 1) * (K - 1) + d <= 16; }
+// the expansion passes work for any number of sweeps (rows longer than
+// kExtCap terms fall back per level)
+bool ext_ell_ok(int d, int K) { return d >= 1 && K >= 1; }
 
 // ------------------------------------------------------------ batched compaction
 // Many flag arrays are compacted with one device->host round trip: block
@@ -1257,8 +1235,8 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             L.ecnt = (uint8_t *)dalloc(H, (size_t)nb1);
             // expansion scratch with kExtCap slots; the resident copy keeps
             // only the slots the level's longest row needs (see round 3)
-            L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1, true);
-            L.ew = (double *)dalloc(H, sizeof(double) * kExtCap * nb1, true);
+            L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1, true, false);
+            L.ew = (double *)dalloc(H, sizeof(double) * kExtCap * nb1, true, false);
         }
         LevelTab &t = tab[l];
         t.bidx = L.bidx;
@@ -1268,6 +1246,11 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         t.eg = L.eg;
         t.ew = L.ew;
         t.ecnt = L.ecnt;
+        if (ell && L.nb > 0) {
+            t.ecnt2 = (uint8_t *)dalloc(H, (size_t)nb1, true, false);
+            t.eg2 = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1, true, false);
+            t.ew2 = (double *)dalloc(H, sizeof(double) * kExtCap * nb1, true, false);
+        }
         t.blk_b = bblocks;
         bblocks += nblocks(L.nb, 128);
     }
@@ -1276,8 +1259,14 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         k_band_all<<<(unsigned)bblocks, 128, 0, H.st>>>(tab_d, keep);
         count_launch(H);
         if (ell) {
-            k_ext_all<<<(unsigned)bblocks, 128, 0, H.st>>>(tab_d, keep, H.d, H.o.ext_sweeps, ovf);
-            count_launch(H);
+            // pass k writes the final buffer when K - k is even, so the last
+            // pass (k = K) lands in it
+            const int K = H.o.ext_sweeps;
+            for (int k = 1; k <= K; ++k) {
+                k_ext_pass<<<(unsigned)bblocks, 128, 0, H.st>>>(tab_d, keep, H.d, k == 1, k == K, (K - k) % 2 == 0,
+                                                                 ovf);
+                count_launch(H);
+            }
         }
     }
     check_cuda(cudaGetLastError(), "band set-up");
@@ -1391,9 +1380,9 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         int *perm = (int *)dalloc(H, sizeof(int) * std::max<int64_t>(n, 1), true);
         // shared-memory limits are per kernel for the whole process: always
         // the largest size (n = kLuSmall), never one handle's n
-        const size_t smem = sizeof(double) * (size_t)(n * n);
+        const size_t smem = sizeof(double) * (size_t)(n * n + n);
         check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(double) * kLuSmall * kLuSmall)),
+                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + kLuSmall))),
                    "LU shared memory");
         k_lu_small<<<1, 1024, smem, H.st>>>(A, (int)n, LU, perm, sing);
         count_launch(H);
