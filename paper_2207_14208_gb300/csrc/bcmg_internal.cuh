@@ -118,6 +118,7 @@ struct Handle {
     std::vector<Level> L;
     double *u0 = nullptr;        // finest-level working copy of u
     double *npart = nullptr;     // norm partials
+    unsigned *ncount = nullptr;  // blocks of the ghost residual done (zero between launches)
     double *nout = nullptr;      // 4 norms (device)
     double *nhost = nullptr;     // pinned copy of the 4 norms
     cudaGraphExec_t vgraph = nullptr;
@@ -181,8 +182,9 @@ template <typename T>
 void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero);
 template <typename T> void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf);
 template <typename T> void coarsest_correct(Handle &H, Level &L, T *u, const T *F);
-// finest-level residual r = F - A u and its four norms (out4, device)
-void residual_norms(Handle &H, const double *u, double *out4);
+// finest-level residual r = F - A u and its four norms (out4, device);
+// ctl 1 / 2 also enqueue the solve's start / per-cycle check on cond
+void residual_norms(Handle &H, const double *u, double *out4, int ctl = 0, unsigned long long cond = 0);
 int64_t norm_parts(const Level &L);  // block partials residual_norms writes
 // ghost weights of every level; the levels of the cluster tail and their tables
 void setup_cycle(Handle &H);

@@ -256,9 +256,10 @@ void run_vcycle_norms(Handle &H) {
     }
 }
 
-// The whole solve as one graph: residual norms of the start, k_solve_init,
-// then a WHILE conditional node whose body is one cycle, its residual norms
-// and k_solve_check (which sets the condition).  No host round trip per
+// The whole solve as one graph: residual norms of the start and the solve's
+// start (r0, first condition), then a WHILE conditional node whose body is
+// one cycle, its residual norms and the convergence check (which sets the
+// condition).  No host round trip per
 // cycle.  Built once per handle; on any failure the handle falls back to the
 // host-driven loop of cycle graphs.
 cudaGraphExec_t build_solve_graph(Handle &H) {
@@ -275,8 +276,7 @@ cudaGraphExec_t build_solve_graph(Handle &H) {
         capturing = true;
         H.capturing = true;
         H.captured = 0;
-        enqueue_norms(H);
-        solve_init_enqueue(H, (unsigned long long)cond);
+        residual_norms(H, H.u0, H.nout, 1, (unsigned long long)cond);
         H.sgraph_prefix = H.captured;
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t *deps = nullptr;
@@ -300,8 +300,7 @@ cudaGraphExec_t build_solve_graph(Handle &H) {
         H.captured = 0;
         if (H.o.precision == BCMG_PREC_MIXED) mixed_step_enqueue(H, H.u0);
         else vcycle_enqueue(H, 0, H.u0);
-        enqueue_norms(H);
-        solve_check_enqueue(H, (unsigned long long)cond);
+        residual_norms(H, H.u0, H.nout, 2, (unsigned long long)cond);
         H.sgraph_body = H.captured;
         capturing = false;
         check_cuda(cudaStreamEndCapture(H.st, &body), "end capture solve body");
@@ -489,6 +488,7 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         Level &L0 = H->L[0];
         H->u0 = (double *)dalloc(*H, sizeof(double) * L0.nn, false, false);
         H->npart = (double *)dalloc(*H, sizeof(double) * 4 * (norm_parts(L0) + 1));
+        H->ncount = (unsigned *)dalloc(*H, sizeof(unsigned));
         setup_cycle(*H);
         H->nout = (double *)dalloc(*H, sizeof(double) * 4);
         static_assert(sizeof(SolveState) <= kPinBlock && 4 * sizeof(double) <= kPinBlock, "pinned block");

@@ -316,21 +316,118 @@ __device__ __forceinline__ void block_partials(double s2, double mx, double *par
         sh[1][warp] = mx;
     }
     __syncthreads();
-    if (warp != 0) return;
-    const int nw = blockDim.x >> 5;
-    s2 = lane < nw ? sh[0][lane] : 0.0;
-    mx = lane < nw ? sh[1][lane] : 0.0;
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        s2 = lane < nw ? sh[0][lane] : 0.0;
+        mx = lane < nw ? sh[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s2 += __shfl_down_sync(0xffffffffu, s2, o);
+            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            double *p = part + slot * 4;
+            p[0] = interior ? s2 : 0.0;
+            p[1] = interior ? 0.0 : s2;
+            p[2] = interior ? mx : 0.0;
+            p[3] = interior ? 0.0 : mx;
+        }
+    }
+}
+
+// ------------------------------------------------------------ solve control
+// norms of the residual (interior, ghost) -> sqrt(a^2 + b^2), rounded step by step
+__device__ __forceinline__ double resid_norm(const double *nout) {
+    return __dsqrt_rn(__dadd_rn(__dmul_rn(nout[0], nout[0]), __dmul_rn(nout[1], nout[1])));
+}
+
+__device__ __forceinline__ bool finite_d(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
+}
+
+// before the loop: r0 from the initial norms; run the body iff r0 > 0 is
+// finite and cycles are allowed
+__device__ void solve_init_dev(SolveState *st, const double *nout, cudaGraphConditionalHandle cond) {
+    const double r0 = resid_norm(nout);
+    const bool fin = finite_d(r0);
+    st->r0 = r0;
+    st->cycles = 0;
+    st->rel = r0 > 0.0 ? 1.0 : 0.0;
+    st->status = fin ? BCMG_OK : BCMG_ENONFINITE;
+    cudaGraphSetConditional(cond, (fin && r0 > 0.0 && st->max_cycles > 0) ? 1u : 0u);
+}
+
+// after each cycle: count it, relative residual, continue while above rtol
+__device__ void solve_check_dev(SolveState *st, const double *nout, cudaGraphConditionalHandle cond) {
+    const int c = st->cycles + 1;
+    st->cycles = c;
+    const double rn = resid_norm(nout);
+    const double rel = rn / st->r0;
+    st->rel = rel;
+    const bool fin = finite_d(rn);
+    if (!fin) st->status = BCMG_ENONFINITE;
+    cudaGraphSetConditional(cond, (fin && rel > st->rtol && c < st->max_cycles) ? 1u : 0u);
+}
+
+// What the last block of the ghost residual kernel does once every partial
+// is written: mode 1 the four norms into nout, mode 2 also the solve's start
+// (solve_init_dev), mode 3 also the per-cycle check (solve_check_dev).
+struct NormTail {
+    int mode;
+    int64_t nparts;     // partials of the interior and the ghost kernels
+    unsigned *counter;  // ghost blocks done (zero between uses)
+    double *nout;
+    SolveState *st;
+    cudaGraphConditionalHandle cond;
+};
+
+// the last-arriving block (fence, then a counter) reduces all partials in
+// block order, like k_norm_final, and resets the counter
+__device__ void norm_tail(const NormTail &nt, const double *part) {
+    __shared__ int last;
+    __shared__ double sh[4][kT / 32];
+    __syncthreads();  // this block's partial is written
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(nt.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;  // uniform over the block
+    __threadfence();
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = threadIdx.x; i < nt.nparts; i += blockDim.x) {
+        a[0] += __ldcg(part + i * 4 + 0);
+        a[1] += __ldcg(part + i * 4 + 1);
+        a[2] = fmax(a[2], __ldcg(part + i * 4 + 2));
+        a[3] = fmax(a[3], __ldcg(part + i * 4 + 3));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        s2 += __shfl_down_sync(0xffffffffu, s2, o);
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        a[0] += __shfl_down_sync(0xffffffffu, a[0], o);
+        a[1] += __shfl_down_sync(0xffffffffu, a[1], o);
+        a[2] = fmax(a[2], __shfl_down_sync(0xffffffffu, a[2], o));
+        a[3] = fmax(a[3], __shfl_down_sync(0xffffffffu, a[3], o));
     }
-    if (lane == 0) {
-        double *p = part + slot * 4;
-        p[0] = interior ? s2 : 0.0;
-        p[1] = interior ? 0.0 : s2;
-        p[2] = interior ? mx : 0.0;
-        p[3] = interior ? 0.0 : mx;
+    if (lane == 0)
+        for (int q = 0; q < 4; ++q) sh[q][warp] = a[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        double b[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < nw; ++w) {
+            b[0] += sh[0][w];
+            b[1] += sh[1][w];
+            b[2] = fmax(b[2], sh[2][w]);
+            b[3] = fmax(b[3], sh[3][w]);
+        }
+        nt.nout[0] = sqrt(b[0]);
+        nt.nout[1] = sqrt(b[1]);
+        nt.nout[2] = b[2];
+        nt.nout[3] = b[3];
+        *nt.counter = 0u;
+        if (nt.mode == 2) solve_init_dev(nt.st, nt.nout, nt.cond);
+        else if (nt.mode == 3) solve_check_dev(nt.st, nt.nout, nt.cond);
     }
 }
 
@@ -359,7 +456,7 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
                                                     const uint16_t *__restrict__ gcode, const T *__restrict__ gw,
                                                     int64_t ng, const T *__restrict__ u, const T *__restrict__ F,
                                                     T *__restrict__ r, G2 G, double *__restrict__ part,
-                                                    int64_t slot0) {
+                                                    int64_t slot0, NormTail nt) {
     pdl_begin();
     double s2 = 0.0, mx = 0.0;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,6 +468,7 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
         mx = fabs((double)v);
     }
     if (part) block_partials(s2, mx, part, slot0 + blockIdx.x, false);
+    if (nt.mode) norm_tail(nt, part);
 }
 
 template <typename T>
@@ -818,39 +916,15 @@ size_t tail_smem(int nl) { return (size_t)nl * kTailThreads * (5 * sizeof(uint32
 constexpr int kTailMaxLevels = 16;
 
 // ------------------------------------------------------------ solve control
-// norms of the residual (interior, ghost) -> sqrt(a^2 + b^2), rounded step by step
-__device__ __forceinline__ double resid_norm(const double *nout) {
-    return __dsqrt_rn(__dadd_rn(__dmul_rn(nout[0], nout[0]), __dmul_rn(nout[1], nout[1])));
-}
-
-__device__ __forceinline__ bool finite_d(double x) {
-    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
-}
-
-// before the loop: r0 from the initial norms; run the body iff r0 > 0 is
-// finite and cycles are allowed
+// separate launches of the start and the check, for levels without ghosts
 __global__ void k_solve_init(SolveState *st, const double *__restrict__ nout, cudaGraphConditionalHandle cond) {
     pdl_begin();
-    const double r0 = resid_norm(nout);
-    const bool fin = finite_d(r0);
-    st->r0 = r0;
-    st->cycles = 0;
-    st->rel = r0 > 0.0 ? 1.0 : 0.0;
-    st->status = fin ? BCMG_OK : BCMG_ENONFINITE;
-    cudaGraphSetConditional(cond, (fin && r0 > 0.0 && st->max_cycles > 0) ? 1u : 0u);
+    solve_init_dev(st, nout, cond);
 }
 
-// after each cycle: count it, relative residual, continue while above rtol
 __global__ void k_solve_check(SolveState *st, const double *__restrict__ nout, cudaGraphConditionalHandle cond) {
     pdl_begin();
-    const int c = st->cycles + 1;
-    st->cycles = c;
-    const double rn = resid_norm(nout);
-    const double rel = rn / st->r0;
-    st->rel = rel;
-    const bool fin = finite_d(rn);
-    if (!fin) st->status = BCMG_ENONFINITE;
-    cudaGraphSetConditional(cond, (fin && rel > st->rtol && c < st->max_cycles) ? 1u : 0u);
+    solve_check_dev(st, nout, cond);
 }
 
 // ------------------------------------------------------------ mixed precision
@@ -1116,21 +1190,25 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps) {
 // registers would otherwise limit the occupancy of the interior rows);
 // returns the number of norm partials written
 template <typename T>
-static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, double *part) {
+static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, double *part,
+                             NormTail nt = NormTail{}) {
     const G2 G = g2_of(L);
     const int bi = bs_for(H, L.nint), bg = bs_for(H, L.ng);
     const int64_t ni = nblk(L.nint, bi);
     const T *gw = Arr<T>::gw(L);
+    nt.nparts = ni + nblk(L.ng, bg);
     if (L.d == 3) {
         launch(H, "k_residual_int", k_residual_int<3, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
                r, G, part);
+        if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", k_residual_gh<3, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
-               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni);
+               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni, nt);
     } else {
         launch(H, "k_residual_int", k_residual_int<2, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
                r, G, part);
+        if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", k_residual_gh<2, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
-               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni);
+               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni, nt);
     }
     return ni + nblk(L.ng, bg);
 }
@@ -1198,12 +1276,27 @@ void coarsest_correct(Handle &H, Level &L, T *u, const T *F) {
            (const double *)L.Ainv, (const double *)L.crhs, u);
 }
 
-// residual of the finest level and its four norms (one fused pass + a
-// single-block reduction of the block partials)
-void residual_norms(Handle &H, const double *u, double *out4) {
+// residual of the finest level and its four norms, optionally followed by
+// the solve's start (ctl 1) or per-cycle check (ctl 2).  With ghosts, the
+// last block of the ghost residual kernel reduces the block partials and
+// runs the control; without, a single-block reduction and a separate
+// control launch follow.
+void residual_norms(Handle &H, const double *u, double *out4, int ctl, unsigned long long cond) {
     Level &L = H.L[0];
+    if (L.ng > 0) {
+        NormTail nt{};
+        nt.mode = 1 + ctl;
+        nt.counter = H.ncount;
+        nt.nout = out4;
+        nt.st = H.sdev;
+        nt.cond = (cudaGraphConditionalHandle)cond;
+        residual_impl<double>(H, L, u, L.F, L.r, H.npart, nt);
+        return;
+    }
     const int64_t parts = residual_impl<double>(H, L, u, L.F, L.r, H.npart);
     launch(H, "k_norm_final", k_norm_final, 1u, 1024u, (const double *)H.npart, parts, out4);
+    if (ctl == 1) solve_init_enqueue(H, cond);
+    else if (ctl == 2) solve_check_enqueue(H, cond);
 }
 
 // an upper bound of the block partials residual_norms writes (64-thread blocks)
