@@ -60,10 +60,15 @@ int bs_for(const Handle &H, int64_t n) {
 
 // Programmatic dependent launch: every cycle kernel is launched with
 // programmatic stream serialisation, so its CTAs may be scheduled while its
-// predecessor drains; each kernel first waits (griddepcontrol.wait, a
-// hardware dependency wait that returns once the preceding grid has completed
-// and its writes are visible) and then allows its own successor to be
-// scheduled.  Nothing is read or written before the wait.
+// predecessor drains; each kernel waits (griddepcontrol.wait, a hardware
+// dependency wait that returns once the preceding grid has completed and its
+// writes are visible) and then allows its own successor to be scheduled.
+// Since every kernel waits before it triggers, a kernel that has started
+// knows that all grids before its predecessor are complete.  Before the wait
+// a kernel therefore reads only the level tables that are fixed once the
+// hierarchy exists (node lists, ghost codes, weights and steps, class bytes,
+// extension maps; creation ends with a stream synchronisation), never u, F,
+// r or other data a cycle writes, and writes nothing.
 __device__ __forceinline__ void pdl_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -123,26 +128,44 @@ __device__ __forceinline__ void coords(uint32_t X, uint32_t n, int D, int ic[3])
 // (o2 * 3 + o1) * 3 + o0, term-major).  Branch-free: every term's loads are
 // predicated on the term lying within the stencil's degrees, so all of them
 // are in flight together; one partial sum per stencil row.
-template <int D, typename T>
-__device__ __forceinline__ T ghost_B(int64_t X, uint16_t code, const T *gw, int64_t ng, int64_t g, const T *u,
-                                     const G2 &G) {
+template <int D>
+__device__ __forceinline__ bool ghost_term(uint16_t code, int k) {
     const int qx = (code >> 3) & 3, qy = (code >> 5) & 3, qz = (D == 3) ? ((code >> 7) & 3) : 0;
+    return k % 3 <= qx && (k / 3) % 3 <= qy && k / 9 <= qz;
+}
+
+// the ghost's tabulated weights (zero outside the stencil's degrees)
+template <int D, typename T>
+__device__ __forceinline__ void ghost_weights(uint16_t code, const T *gw, int64_t ng, int64_t g,
+                                              T w[(D == 3) ? 27 : 9]) {
+#pragma unroll
+    for (int k = 0; k < ((D == 3) ? 27 : 9); ++k) w[k] = ghost_term<D>(code, k) ? gw[(int64_t)k * ng + g] : T(0);
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T ghost_Bw(int64_t X, uint16_t code, const T *w, const T *u, const G2 &G) {
     const int64_t ox = (code & 1) ? 1 : -1;
     const int64_t oy = (code & 2) ? G.sy : -G.sy;
     const int64_t oz = (D == 3) ? ((code & 4) ? G.sz : -G.sz) : 0;
     constexpr int NT = (D == 3) ? 27 : 9;
-    T w[NT], v[NT];
+    T v[NT];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
         const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
-        const bool p = o0 <= qx && o1 <= qy && o2 <= qz;
-        w[k] = p ? gw[(int64_t)k * ng + g] : T(0);
-        v[k] = p ? u[X + o2 * oz + o1 * oy + o0 * ox] : T(0);
+        v[k] = ghost_term<D>(code, k) ? u[X + o2 * oz + o1 * oy + o0 * ox] : T(0);
     }
     T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int k = 0; k < NT; ++k) acc[(k / 3) % 3] = fma(w[k], v[k], acc[(k / 3) % 3]);
     return (acc[0] + acc[1]) + acc[2];
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T ghost_B(int64_t X, uint16_t code, const T *gw, int64_t ng, int64_t g, const T *u,
+                                     const G2 &G) {
+    T w[(D == 3) ? 27 : 9];
+    ghost_weights<D, T>(code, gw, ng, g, w);
+    return ghost_Bw<D, T>(X, code, w, u, G);
 }
 
 template <int D, typename T>
@@ -183,20 +206,35 @@ __device__ __forceinline__ T residual_int(int64_t X, const T *u, const T *F, con
 // average over the family members.  FW weights are the integers 1, 2, 4
 // (, 8) over 4^d; scaling by a power of two is exact.  All 3^d class and
 // residual loads are issued before any of them is used.
+template <int D>
+__device__ __forceinline__ bool restrict_nbr(const int ic[3], int k, const G2 &Gf, int64_t &Y) {
+    const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
+    const int y0 = 2 * ic[0] + ox, y1 = 2 * ic[1] + oy, y2 = 2 * ic[2] + oz;
+    Y = (int64_t)y0 + (int64_t)y1 * Gf.sy + (int64_t)y2 * Gf.sz;
+    return y0 >= 0 && y0 <= Gf.N && y1 >= 0 && y1 <= Gf.N && (D == 2 || (y2 >= 0 && y2 <= Gf.N));
+}
+
+// the fine class bytes around coarse node ic (outside the grid: never in a
+// family)
+template <int D>
+__device__ __forceinline__ void restrict_classes(const int ic[3], const uint8_t *clsf, const G2 &Gf,
+                                                 uint8_t c[(D == 3) ? 27 : 9]) {
+#pragma unroll
+    for (int k = 0; k < ((D == 3) ? 27 : 9); ++k) {
+        int64_t Y;
+        c[k] = restrict_nbr<D>(ic, k, Gf, Y) ? clsf[Y] : (uint8_t)CL_BOXDIR;
+    }
+}
+
 template <int D, typename T>
-__device__ __forceinline__ T restrict_at(const int ic[3], bool interior, const uint8_t *clsf, const T *rf,
-                                         const G2 &Gf) {
+__device__ __forceinline__ T restrict_with(const int ic[3], bool interior, const uint8_t *c, const T *rf,
+                                           const G2 &Gf) {
     constexpr int NT = (D == 3) ? 27 : 9;
-    uint8_t c[NT];
     T v[NT];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
-        const int y0 = 2 * ic[0] + ox, y1 = 2 * ic[1] + oy, y2 = 2 * ic[2] + oz;
-        const bool in = y0 >= 0 && y0 <= Gf.N && y1 >= 0 && y1 <= Gf.N && (D == 2 || (y2 >= 0 && y2 <= Gf.N));
-        const int64_t Y = (int64_t)y0 + (int64_t)y1 * Gf.sy + (int64_t)y2 * Gf.sz;
-        c[k] = in ? clsf[Y] : (uint8_t)CL_BOXDIR;  // outside the grid: never in a family
-        v[k] = in ? rf[Y] : T(0);
+        int64_t Y;
+        v[k] = restrict_nbr<D>(ic, k, Gf, Y) ? rf[Y] : T(0);
     }
     T fw = T(0);
     int wsum = 0;
@@ -214,6 +252,14 @@ __device__ __forceinline__ T restrict_at(const int ic[3], bool interior, const u
     }
     if (all) return fw * (D == 3 ? T(1.0 / 64.0) : T(1.0 / 16.0));
     return wsum > 0 ? fw / (T)wsum : T(0);
+}
+
+template <int D, typename T>
+__device__ __forceinline__ T restrict_at(const int ic[3], bool interior, const uint8_t *clsf, const T *rf,
+                                         const G2 &Gf) {
+    uint8_t c[(D == 3) ? 27 : 9];
+    restrict_classes<D>(ic, clsf, Gf, c);
+    return restrict_with<D, T>(ic, interior, c, rf, Gf);
 }
 
 // multilinear prolongation at fine node iy (Sec. 2.1, 3.2, 3.3.2): the 2^k
@@ -274,13 +320,64 @@ __device__ __forceinline__ T extend_at(int64_t b, const uint8_t *ecnt, const uin
     return v;
 }
 
+// the first round's map of band node b (read before the dependency wait)
+template <typename T>
+struct EllRound {
+    int c;
+    uint32_t g[8];
+    T w[8];
+};
+
+template <typename T>
+__device__ __forceinline__ void ell_first(int64_t b, const uint8_t *ecnt, const uint32_t *eg, const double *ew,
+                                          int64_t nb, EllRound<T> &R) {
+    R.c = ecnt[b];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const bool p = j < R.c;
+        R.g[j] = p ? eg[(int64_t)j * nb + b] : 0u;
+        R.w[j] = p ? (T)ew[(int64_t)j * nb + b] : T(0);
+    }
+}
+
+// extend_at with the first round's map already loaded; the same terms in
+// the same order
+template <typename T>
+__device__ __forceinline__ T extend_from(int64_t b, const EllRound<T> &R, const uint32_t *eg, const double *ew,
+                                         int64_t nb, const T *a) {
+    T v = T(0);
+    {
+        T x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = j < R.c ? a[R.g[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < R.c) v = fma(R.w[j], x[j], v);
+    }
+    for (int k0 = 8; k0 < R.c; k0 += 8) {
+        T w[8], x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool p = k0 + j < R.c;
+            const int64_t e = (int64_t)(k0 + j) * nb + b;
+            w[j] = p ? (T)ew[e] : T(0);
+            x[j] = p ? a[eg[e]] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (k0 + j < R.c) v = fma(w[j], x[j], v);
+    }
+    return v;
+}
+
 // ------------------------------------------------------------ grid kernels
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_smooth(const uint32_t *__restrict__ list, int64_t n, T *u,
                                                const T *__restrict__ F, G2 G) {
-    pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) smooth_at<D, T>(list[i], u, F, G);
+    const uint32_t X = i < n ? list[i] : 0u;
+    pdl_begin();
+    if (i < n) smooth_at<D, T>(X, u, F, G);
 }
 
 template <int D, typename T>
@@ -288,17 +385,24 @@ __global__ void __launch_bounds__(kT) k_ghost_relax(const uint32_t *__restrict__
                                                     const uint16_t *__restrict__ gcode, const T *__restrict__ gw,
                                                     const double *__restrict__ gdt, int64_t ng, const T *u,
                                                     const T *__restrict__ F, T *__restrict__ tmp, G2 G) {
-    pdl_begin();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < ng) tmp[g] = ghost_new<D, T>(g, gidx, gcode, gw, gdt, ng, u, F, G);
+    const bool on = g < ng;
+    const int64_t X = on ? gidx[g] : 0;
+    const uint16_t code = on ? gcode[g] : 0;
+    const T dt = on ? (T)gdt[g] : T(0);
+    T w[(D == 3) ? 27 : 9];
+    ghost_weights<D, T>(code, gw, ng, on ? g : 0, w);
+    pdl_begin();
+    if (on) tmp[g] = fma(dt, F[X] - ghost_Bw<D, T>(X, code, w, u, G), u[X]);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kT) k_ghost_scatter(const uint32_t *__restrict__ gidx, int64_t ng,
                                                       const T *__restrict__ tmp, T *__restrict__ u) {
-    pdl_begin();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < ng) u[gidx[g]] = tmp[g];
+    const uint32_t X = g < ng ? gidx[g] : 0u;
+    pdl_begin();
+    if (g < ng) u[X] = tmp[g];
 }
 
 // the block's norm partials (sum r^2, max|r|) of one row class, reduced in
@@ -437,11 +541,11 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict__ ilist, int64_t nint,
                                                      const T *__restrict__ u, const T *__restrict__ F,
                                                      T *__restrict__ r, G2 G, double *__restrict__ part) {
-    pdl_begin();
     double s2 = 0.0, mx = 0.0;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t X = i < nint ? ilist[i] : 0;
+    pdl_begin();
     if (i < nint) {
-        const int64_t X = ilist[i];
         const T v = residual_int<D, T>(X, u, F, G);
         r[X] = v;
         s2 = (double)v * (double)v;
@@ -457,12 +561,16 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
                                                     int64_t ng, const T *__restrict__ u, const T *__restrict__ F,
                                                     T *__restrict__ r, G2 G, double *__restrict__ part,
                                                     int64_t slot0, NormTail nt) {
-    pdl_begin();
     double s2 = 0.0, mx = 0.0;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < ng) {
-        const int64_t X = gidx[g];
-        const T v = F[X] - ghost_B<D, T>(X, gcode[g], gw, ng, g, u, G);
+    const bool on = g < ng;
+    const int64_t X = on ? gidx[g] : 0;
+    const uint16_t code = on ? gcode[g] : 0;
+    T w[(D == 3) ? 27 : 9];
+    ghost_weights<D, T>(code, gw, ng, on ? g : 0, w);
+    pdl_begin();
+    if (on) {
+        const T v = F[X] - ghost_Bw<D, T>(X, code, w, u, G);
         r[X] = v;
         s2 = (double)v * (double)v;
         mx = fabs((double)v);
@@ -476,9 +584,14 @@ __global__ void __launch_bounds__(kT) k_extend_ell(const uint32_t *__restrict__ 
                                                    const uint8_t *__restrict__ ecnt,
                                                    const uint32_t *__restrict__ eg, const double *__restrict__ ew,
                                                    int64_t nb, T *a) {
-    pdl_begin();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) a[bidx[b]] = extend_at<T>(b, ecnt, eg, ew, nb, a);
+    const bool on = b < nb;
+    const uint32_t X = on ? bidx[b] : 0u;
+    EllRound<T> R;
+    R.c = 0;
+    if (on) ell_first<T>(b, ecnt, eg, ew, nb, R);
+    pdl_begin();
+    if (on) a[X] = extend_from<T>(b, R, eg, ew, nb, a);
 }
 
 // One explicit pseudo-time sweep of dr/dsigma + dr/dn = 0 with upwind
@@ -512,23 +625,18 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
                                                  int64_t ng_c, const uint8_t *__restrict__ clsf,
                                                  const T *__restrict__ rf, T *__restrict__ Fc, T *__restrict__ uc,
                                                  G2 Gf, G2 Gc) {
-    pdl_begin();
-    uint32_t Xc;
-    bool interior;
-    if (blockIdx.x < iblocks) {
-        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= nint_c) return;
-        Xc = ilist_c[i];
-        interior = true;
-    } else {
-        const int64_t g = (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
-        if (g >= ng_c) return;
-        Xc = gidx_c[g];
-        interior = false;
-    }
+    const bool interior = blockIdx.x < iblocks;
+    const int64_t i = interior ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
+                               : (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
+    const bool on = i < (interior ? nint_c : ng_c);
+    const uint32_t Xc = on ? (interior ? ilist_c[i] : gidx_c[i]) : 0u;
     int ic[3];
     coords(Xc, (uint32_t)Gc.n, D, ic);
-    Fc[Xc] = restrict_at<D, T>(ic, interior, clsf, rf, Gf);
+    uint8_t c[(D == 3) ? 27 : 9];
+    restrict_classes<D>(ic, clsf, Gf, c);
+    pdl_begin();
+    if (!on) return;
+    Fc[Xc] = restrict_with<D, T>(ic, interior, c, rf, Gf);
     if (uc) uc[Xc] = T(0);
 }
 
@@ -536,17 +644,13 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_prolong(const uint32_t *__restrict__ ilist, int64_t nint, unsigned iblocks,
                                                 const uint32_t *__restrict__ gidx, int64_t ng,
                                                 const T *__restrict__ ec, T *__restrict__ uf, G2 Gf, G2 Gc) {
+    const bool inner = blockIdx.x < iblocks;
+    const int64_t i = inner ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
+                            : (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
+    const bool on = i < (inner ? nint : ng);
+    const uint32_t X = on ? (inner ? ilist[i] : gidx[i]) : 0u;
     pdl_begin();
-    uint32_t X;
-    if (blockIdx.x < iblocks) {
-        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= nint) return;
-        X = ilist[i];
-    } else {
-        const int64_t g = (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
-        if (g >= ng) return;
-        X = gidx[g];
-    }
+    if (!on) return;
     int iy[3];
     coords(X, (uint32_t)Gf.n, D, iy);
     uf[X] += prolong_at<D, T>(iy, ec, Gc);
@@ -555,9 +659,10 @@ __global__ void __launch_bounds__(kT) k_prolong(const uint32_t *__restrict__ ili
 template <typename T>
 __global__ void k_coarse_gather(const uint32_t *__restrict__ act, int64_t nact, const T *__restrict__ r,
                                 double *__restrict__ rhs) {
-    pdl_begin();
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < nact) rhs[j] = (double)r[act[j]];
+    const uint32_t X = j < nact ? act[j] : 0u;
+    pdl_begin();
+    if (j < nact) rhs[j] = (double)r[X];
 }
 
 // u[act[i]] += (A^-1 rhs)_i, one warp per row (FP64 accumulation)
@@ -824,7 +929,6 @@ template <int D, typename T>
 __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__restrict__ tl, int nl,
                                                           const uint8_t *__restrict__ ops, int nops, int nu1,
                                                           int nu2) {
-    pdl_begin();
     extern __shared__ uint32_t tsm[];
     TailSlots S;
     const int n = nl * kTailThreads;
@@ -847,6 +951,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
         S.act[k] = i < A.nint ? A.ilist[i] : (i < A.nint + A.ng ? A.gidx[i - A.nint] : kNone);
     }
     __syncthreads();
+    pdl_begin();  // the slots above come from fixed tables only
     for (int op = 0; op < nops; ++op) {
         const int kind = ops[2 * op], l = ops[2 * op + 1];
         if (kind == kOpDown) {
