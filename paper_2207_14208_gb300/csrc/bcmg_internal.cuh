@@ -114,11 +114,14 @@ struct Handle {
     bcmg_opts o{};
     cudaStream_t user = nullptr;  // caller's stream
     cudaStream_t st = nullptr;    // library stream (graph capture, all work)
+    cudaStream_t st2 = nullptr;   // side stream of creation (coarsest inverse)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<Level> L;
     double *u0 = nullptr;        // finest-level working copy of u
     double *npart = nullptr;     // norm partials
     unsigned *ncount = nullptr;  // blocks of the ghost residual done (zero between launches)
+    int *sing_host = nullptr;    // coarsest-system singular flag (pinned block; read after creation's sync)
     double *nout = nullptr;      // 4 norms (device)
     double *nhost = nullptr;     // pinned copy of the 4 norms
     cudaGraphExec_t vgraph = nullptr;

@@ -139,6 +139,7 @@ void pinned_put(void *p) {
 
 void destroy(Handle *H) {
     if (!H) return;
+    if (H->st2) cudaStreamSynchronize(H->st2);
     if (H->st) cudaStreamSynchronize(H->st);
     if (H->vgraph) cudaGraphExecDestroy(H->vgraph);
     if (H->ngraph) cudaGraphExecDestroy(H->ngraph);
@@ -150,7 +151,11 @@ void destroy(Handle *H) {
         cudaStreamSynchronize(H->st);
     }
     pinned_put(H->nhost);
+    pinned_put(H->sing_host);
     for (cudaEvent_t e : H->pev) cudaEventDestroy(e);
+    if (H->ev_fork) cudaEventDestroy(H->ev_fork);
+    if (H->ev_join) cudaEventDestroy(H->ev_join);
+    if (H->st2) cudaStreamDestroy(H->st2);
     if (H->ev_in) cudaEventDestroy(H->ev_in);
     if (H->ev_out) cudaEventDestroy(H->ev_out);
     if (H->st) cudaStreamDestroy(H->st);
@@ -481,6 +486,11 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
             H->pev.resize(4 * (size_t)(H->o.nu1 + H->o.nu2), nullptr);
             for (auto &e : H->pev) check_cuda(cudaEventCreate(&e), "cudaEventCreate(profile)");
         }
+        check_cuda(cudaStreamCreateWithFlags(&H->st2, cudaStreamNonBlocking), "cudaStreamCreate");
+        check_cuda(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+        check_cuda(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+        H->sing_host = (int *)pinned_get();
+        *H->sing_host = 0;
         enter(*H);
         // levels: N_l = N / 2^l while N_l is even, N_l / 2 >= min_coarse and
         // the coarser level still has interior nodes (Sec. 2.1)
@@ -497,7 +507,9 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         H->sdev = (SolveState *)dalloc(*H, sizeof(SolveState));
         set_interior_rhs(*H, L0, f_dev, L0.F);
         for (auto &L : H->L) L.phi = nullptr;
+        check_cuda(cudaStreamWaitEvent(H->st, H->ev_join, 0), "join wait");  // the coarsest inverse
         check_cuda(cudaStreamSynchronize(H->st), "create sync");
+        if (*H->sing_host) throw Error{BCMG_EGEOM, "coarsest system is singular"};
         free_temps(*H);
         leave(*H);
     });

@@ -487,6 +487,7 @@ struct NormTail {
 
 // the last-arriving block (fence, then a counter) reduces all partials in
 // block order, like k_norm_final, and resets the counter
+template <bool Ctl>
 __device__ void norm_tail(const NormTail &nt, const double *part) {
     __shared__ int last;
     __shared__ double sh[4][kT / 32];
@@ -530,8 +531,10 @@ __device__ void norm_tail(const NormTail &nt, const double *part) {
         nt.nout[2] = b[2];
         nt.nout[3] = b[3];
         *nt.counter = 0u;
-        if (nt.mode == 2) solve_init_dev(nt.st, nt.nout, nt.cond);
-        else if (nt.mode == 3) solve_check_dev(nt.st, nt.nout, nt.cond);
+        if constexpr (Ctl) {
+            if (nt.mode == 2) solve_init_dev(nt.st, nt.nout, nt.cond);
+            else if (nt.mode == 3) solve_check_dev(nt.st, nt.nout, nt.cond);
+        }
     }
 }
 
@@ -554,8 +557,10 @@ __global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict_
     if (part) block_partials(s2, mx, part, blockIdx.x, true);
 }
 
-// r = g - B u on the ghost rows (eq. BCh); norm partials at slot0 + block
-template <int D, typename T>
+// r = g - B u on the ghost rows (eq. BCh); norm partials at slot0 + block.
+// Ctl: the instance that may run the solve control (it holds the device
+// graph call; the other instance does not, so profilers list it)
+template <int D, typename T, bool Ctl>
 __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__ gidx,
                                                     const uint16_t *__restrict__ gcode, const T *__restrict__ gw,
                                                     int64_t ng, const T *__restrict__ u, const T *__restrict__ F,
@@ -576,7 +581,7 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
         mx = fabs((double)v);
     }
     if (part) block_partials(s2, mx, part, slot0 + blockIdx.x, false);
-    if (nt.mode) norm_tail(nt, part);
+    if (nt.mode) norm_tail<Ctl>(nt, part);
 }
 
 template <typename T>
@@ -1306,14 +1311,16 @@ static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, 
         launch(H, "k_residual_int", k_residual_int<3, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
                r, G, part);
         if (L.ng == 0) return ni;
-        launch(H, "k_residual_gh", k_residual_gh<3, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
-               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni, nt);
+        launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<3, T, true> : k_residual_gh<3, T, false>,
+               nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
+               ni, nt);
     } else {
         launch(H, "k_residual_int", k_residual_int<2, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
                r, G, part);
         if (L.ng == 0) return ni;
-        launch(H, "k_residual_gh", k_residual_gh<2, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
-               (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part, ni, nt);
+        launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<2, T, true> : k_residual_gh<2, T, false>,
+               nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
+               ni, nt);
     }
     return ni + nblk(L.ng, bg);
 }

@@ -980,8 +980,13 @@ void add_list(CompactItem &it, uint8_t mask, uint32_t **out, bool temp) {
 thread_local int64_t *t_pinned = nullptr;
 thread_local size_t t_pinned_n = 0;
 
-int64_t *pinned_scratch(size_t n) {
+// The host scratch of this thread.  Every host write to it follows a stream
+// synchronisation, so a copy from it that is still in flight when a set-up
+// step returns belongs to the handle being created; before the buffer grows,
+// that handle's stream is drained.
+int64_t *pinned_scratch(Handle &H, size_t n) {
     if (n > t_pinned_n) {
+        check_cuda(cudaStreamSynchronize(H.st), "scratch sync");
         if (t_pinned) cudaFreeHost(t_pinned);
         t_pinned = nullptr;
         t_pinned_n = 0;
@@ -1012,7 +1017,7 @@ void run_compaction(Handle &H, std::vector<CompactItem> &items) {
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "k_count");
-    int64_t *hc = pinned_scratch((size_t)B);
+    int64_t *hc = pinned_scratch(H, (size_t)B);
     check_cuda(cudaMemcpyAsync(hc, counts, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, H.st), "counts D2H");
     check_cuda(cudaStreamSynchronize(H.st), "compaction sync");
     for (auto &it : items)
@@ -1043,8 +1048,6 @@ void run_compaction(Handle &H, std::vector<CompactItem> &items) {
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "k_scatter");
-    // the pinned offsets are read by the H2D copy: keep them until it is done
-    check_cuda(cudaStreamSynchronize(H.st), "compaction sync 2");
 }
 
 // hyperplane (p = i + j + k) of each interior node: counts, then positions
@@ -1220,6 +1223,63 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         Lc.nact = items[keep].total[0];
     }
     if (H.L[keep - 1].nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
+    // coarsest: dense system and its inverse, on the side stream (one SM's
+    // work for small systems) while the main stream builds the band and its
+    // extension; joined before creation's closing synchronisation
+    {
+        Level &L = H.L[keep - 1];
+        Geo G = geo_of(L);
+        int64_t n = L.nact;
+        double *A = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
+        L.Ainv = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1));
+        L.crhs = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1));
+        double *col = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1), true);
+        int *sing = (int *)dalloc(H, sizeof(int), true);
+        double *LU = nullptr;
+        int *perm = nullptr;
+        if (n <= kLuSmall) {
+            LU = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
+            perm = (int *)dalloc(H, sizeof(int) * std::max<int64_t>(n, 1), true);
+    }
+    // every buffer above (and the level data it reads) is in place on the
+    // main stream before the side stream starts
+    check_cuda(cudaEventRecord(H.ev_fork, H.st), "fork record");
+    check_cuda(cudaStreamWaitEvent(H.st2, H.ev_fork, 0), "fork wait");
+    k_assemble<<<nblocks(n, 128), 128, 0, H.st2>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.gn, L.ng, G, H.o.bc,
+                                                  H.o.reaction, A);
+    count_launch(H);
+    if (n <= kLuSmall) {
+        // shared-memory limits are per kernel for the whole process: always
+        // the largest size (n = kLuSmall), never one handle's n
+        const size_t smem = sizeof(double) * (size_t)(n * n + n);
+        check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + kLuSmall))),
+                   "LU shared memory");
+        k_lu_small<<<1, 1024, smem, H.st2>>>(A, (int)n, LU, perm, sing);
+        count_launch(H);
+        const size_t smem2 = sizeof(double) * (size_t)(n * n + n + kLuColsPerBlock * n);
+        check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + (2 + kLuColsPerBlock) *
+                                                                                        kLuSmall))),
+                   "LU inverse shared memory");
+        k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st2>>>(LU, (int)n, perm, L.Ainv);
+        count_launch(H);
+    } else {
+        k_identity<<<nblocks(n * n, T), T, 0, H.st2>>>(L.Ainv, n);
+        count_launch(H);
+        for (int64_t k = 0; k < n; ++k) {
+            k_gj_pivot<<<1, 1024, 0, H.st2>>>(A, L.Ainv, n, k, col, sing);
+            k_gj_elim<<<nblocks(n * n, T), T, 0, H.st2>>>(A, L.Ainv, n, k, col);
+            count_launch(H);
+            count_launch(H);
+        }
+    }
+    check_cuda(cudaGetLastError(), "gauss-jordan");
+    // read by the caller after its closing synchronisation
+    H.sing_host = (int *)pinned_scratch(H, 1);
+    check_cuda(cudaMemcpyAsync(H.sing_host, sing, sizeof(int), cudaMemcpyDeviceToHost, H.st2), "singular flag");
+    check_cuda(cudaEventRecord(H.ev_join, H.st2), "join record");
+    }
     // phase C: band sources and the ELL expansion of the extension, every
     // level in one launch each
     const bool ell = ext_ell_ok(H.d, H.o.ext_sweeps);
@@ -1272,7 +1332,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     check_cuda(cudaGetLastError(), "band set-up");
     // round 3: clamp / fall-back counters and ELL overflows (one sync)
     {
-        int64_t *hc = pinned_scratch(3 * (size_t)keep + 2);
+        int64_t *hc = pinned_scratch(H, 3 * (size_t)keep + 2);
         for (int l = 0; l < keep; ++l)
             check_cuda(cudaMemcpyAsync(hc + 2 * l, S[l].cnt, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, H.st),
                        "ghost counters");
@@ -1317,7 +1377,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
                 count_launch(H);
             }
         }
-        int64_t *hc = pinned_scratch((size_t)base[keep]);
+        int64_t *hc = pinned_scratch(H, (size_t)base[keep]);
         int *hci = (int *)hc;
         check_cuda(cudaMemcpyAsync(hci, counts, sizeof(int) * base[keep], cudaMemcpyDeviceToHost, H.st), "hp counts");
         check_cuda(cudaStreamSynchronize(H.st), "hp sync");
@@ -1363,52 +1423,6 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             L.bbuf32 = (float *)dalloc(H, sizeof(float) * 2 * std::max<int64_t>(L.nb, 1));
         }
     }
-    // coarsest: dense system and its Gauss-Jordan inverse
-    Level &L = H.L[keep - 1];
-    Geo G = geo_of(L);
-    int64_t n = L.nact;
-    double *A = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
-    L.Ainv = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1));
-    L.crhs = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1));
-    double *col = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1), true);
-    int *sing = (int *)dalloc(H, sizeof(int), true);
-    k_assemble<<<nblocks(n, 128), 128, 0, H.st>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.gn, L.ng, G, H.o.bc,
-                                                  H.o.reaction, A);
-    count_launch(H);
-    if (n <= kLuSmall) {
-        double *LU = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
-        int *perm = (int *)dalloc(H, sizeof(int) * std::max<int64_t>(n, 1), true);
-        // shared-memory limits are per kernel for the whole process: always
-        // the largest size (n = kLuSmall), never one handle's n
-        const size_t smem = sizeof(double) * (size_t)(n * n + n);
-        check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + kLuSmall))),
-                   "LU shared memory");
-        k_lu_small<<<1, 1024, smem, H.st>>>(A, (int)n, LU, perm, sing);
-        count_launch(H);
-        const size_t smem2 = sizeof(double) * (size_t)(n * n + n + kLuColsPerBlock * n);
-        check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + (2 + kLuColsPerBlock) *
-                                                                                        kLuSmall))),
-                   "LU inverse shared memory");
-        k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st>>>(LU, (int)n, perm, L.Ainv);
-        count_launch(H);
-    } else {
-        k_identity<<<nblocks(n * n, T), T, 0, H.st>>>(L.Ainv, n);
-        count_launch(H);
-        for (int64_t k = 0; k < n; ++k) {
-            k_gj_pivot<<<1, 1024, 0, H.st>>>(A, L.Ainv, n, k, col, sing);
-            k_gj_elim<<<nblocks(n * n, T), T, 0, H.st>>>(A, L.Ainv, n, k, col);
-            count_launch(H);
-            count_launch(H);
-        }
-    }
-    check_cuda(cudaGetLastError(), "gauss-jordan");
-    int *hs = (int *)pinned_scratch(1);
-    check_cuda(cudaMemcpyAsync(hs, sing, sizeof(int), cudaMemcpyDeviceToHost, H.st), "singular flag");
-    check_cuda(cudaStreamSynchronize(H.st), "set-up sync 4");
-    if (*hs) throw Error{BCMG_EGEOM, "coarsest system is singular"};
-    for (auto &Lv : H.L) Lv.phi = nullptr;
 }
 
 }  // namespace bcmg
