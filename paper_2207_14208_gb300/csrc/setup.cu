@@ -63,47 +63,88 @@ constexpr int kCompactTile = kCompactThreads * kCompactPerThread;
 // Compaction of up to four lists from one byte array in one pass each: list
 // b holds, in increasing order, the indices i with flags[i] & mask_b != 0
 // (masks packed one per byte in `masks`).  Per block: the count of each
-// list (counts[block * nl + b]); then the scatter, whose per-thread counts
-// (at most kCompactPerThread each) are scanned as four 16-bit fields of one
-// 64-bit word (a block holds at most 4096 items, so no field overflows).
+// list (counts[base + block * nl + b]); then the scatter, whose per-thread
+// counts (at most kCompactPerThread each) are scanned as four 16-bit fields
+// of one 64-bit word (a block holds at most 4096 items, so no field
+// overflows).  Every flag array of a set-up round goes in one launch: the
+// blocks of array k start at blk0[k].
+constexpr int kCompactMax = 24;  // flag arrays per launch
+
+struct CompactArr {
+    const uint8_t *flags;
+    int64_t n;
+    int64_t blk0;   // first block of this array
+    int64_t base;   // its first count slot
+    uint32_t masks;
+    int nl;
+    uint32_t *out[4];  // nullptr: list counted only
+};
+
+struct CompactBatch {
+    int narr;
+    CompactArr a[kCompactMax];
+};
+
 __device__ __forceinline__ int bucket_hits(uint8_t f, uint32_t masks, int b) {
     return (f & ((masks >> (8 * b)) & 0xffu)) ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(kCompactThreads) k_count(const uint8_t *__restrict__ flags, int64_t n, int nl,
-                                                           uint32_t masks, int64_t *__restrict__ counts) {
-    __shared__ uint64_t red[kCompactThreads];
-    const int64_t base = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
+__device__ __forceinline__ int compact_arr_of(const CompactBatch &B) {
+    int k = 0;
+    for (int i = 1; i < B.narr; ++i)
+        if ((int64_t)blockIdx.x >= B.a[i].blk0) k = i;
+    return k;
+}
+
+// this thread's kCompactPerThread flag bytes (one 16-byte load when the
+// whole run is in range and aligned; zero past the end)
+__device__ __forceinline__ void compact_load(const CompactArr &A, int64_t base, uint8_t f[kCompactPerThread]) {
+    const bool vec = base + kCompactPerThread <= A.n && ((reinterpret_cast<uintptr_t>(A.flags + base) & 15) == 0);
+    if (vec) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(A.flags + base);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < kCompactPerThread; ++i) f[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+    } else {
+#pragma unroll
+        for (int i = 0; i < kCompactPerThread; ++i) f[i] = base + i < A.n ? A.flags[base + i] : (uint8_t)0;
+    }
+}
+
+__device__ __forceinline__ uint64_t compact_hits(const uint8_t f[kCompactPerThread], uint32_t masks, int nl) {
     uint64_t c = 0;
+#pragma unroll
     for (int i = 0; i < kCompactPerThread; ++i)
-        if (base + i < n) {
-            const uint8_t f = flags[base + i];
-            for (int b = 0; b < nl; ++b) c += (uint64_t)bucket_hits(f, masks, b) << (16 * b);
-        }
-    red[threadIdx.x] = c;
+        for (int b = 0; b < nl; ++b) c += (uint64_t)bucket_hits(f[i], masks, b) << (16 * b);
+    return c;
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_count(CompactBatch B, int64_t *__restrict__ counts) {
+    __shared__ uint64_t red[kCompactThreads];
+    const CompactArr &A = B.a[compact_arr_of(B)];
+    const int64_t blk = (int64_t)blockIdx.x - A.blk0;
+    const int64_t base = blk * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
+    uint8_t f[kCompactPerThread];
+    compact_load(A, base, f);
+    red[threadIdx.x] = compact_hits(f, A.masks, A.nl);
     __syncthreads();
     for (int s = kCompactThreads / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x < nl) counts[(int64_t)blockIdx.x * nl + threadIdx.x] = (int64_t)((red[0] >> (16 * threadIdx.x)) & 0xffffu);
+    if (threadIdx.x < A.nl)
+        counts[A.base + blk * A.nl + threadIdx.x] = (int64_t)((red[0] >> (16 * threadIdx.x)) & 0xffffu);
 }
 
-struct ScatterOut {
-    uint32_t *out[4];  // nullptr: list counted only
-};
-
-__global__ void __launch_bounds__(kCompactThreads) k_scatter(const uint8_t *__restrict__ flags, int64_t n, int nl,
-                                                             uint32_t masks, const int64_t *__restrict__ offs,
-                                                             ScatterOut so) {
+__global__ void __launch_bounds__(kCompactThreads) k_scatter(CompactBatch B, const int64_t *__restrict__ offs) {
     __shared__ uint64_t sc[kCompactThreads];
-    const int64_t base = (int64_t)blockIdx.x * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
-    uint64_t c = 0;
-    for (int i = 0; i < kCompactPerThread; ++i)
-        if (base + i < n) {
-            const uint8_t f = flags[base + i];
-            for (int b = 0; b < nl; ++b) c += (uint64_t)bucket_hits(f, masks, b) << (16 * b);
-        }
+    const CompactArr &A = B.a[compact_arr_of(B)];
+    if (!A.out[0] && !A.out[1] && !A.out[2] && !A.out[3]) return;  // counted only (uniform per block)
+    const int64_t blk = (int64_t)blockIdx.x - A.blk0;
+    const int64_t base = blk * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
+    uint8_t f[kCompactPerThread];
+    compact_load(A, base, f);
+    const uint64_t c = compact_hits(f, A.masks, A.nl);
     sc[threadIdx.x] = c;
     __syncthreads();
     // inclusive Hillis-Steele scan over the block (deterministic)
@@ -115,16 +156,14 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter(const uint8_t *__re
     }
     const uint64_t excl = sc[threadIdx.x] - c;
     int64_t pos[4];
-    for (int b = 0; b < nl; ++b) pos[b] = offs[(int64_t)blockIdx.x * nl + b] + (int64_t)((excl >> (16 * b)) & 0xffffu);
+    for (int b = 0; b < A.nl; ++b) pos[b] = offs[A.base + blk * A.nl + b] + (int64_t)((excl >> (16 * b)) & 0xffffu);
+#pragma unroll
     for (int i = 0; i < kCompactPerThread; ++i)
-        if (base + i < n) {
-            const uint8_t f = flags[base + i];
-            for (int b = 0; b < nl; ++b)
-                if (bucket_hits(f, masks, b)) {
-                    if (so.out[b]) so.out[b][pos[b]] = (uint32_t)(base + i);
-                    ++pos[b];
-                }
-        }
+        for (int b = 0; b < A.nl; ++b)
+            if (bucket_hits(f[i], A.masks, b)) {
+                if (A.out[b]) A.out[b][pos[b]] = (uint32_t)(base + i);
+                ++pos[b];
+            }
 }
 
 // ---------------------------------------------------------------- classes
@@ -273,12 +312,23 @@ __device__ bool stencil_ok(const Geo &G, const uint8_t *cls, const int ix[3], co
 // eq. coeff (poly).  Neumann: p exp(-p theta) (Remark exptheta2D) or eq. GN
 // with coefficients eq. coeffN; the result is Delta tau / h (eqs.
 // dtauoptLFA_Neumann, dtauoptLFA3D_Neumann).
-__host__ __device__ double dtau_formula(int d, int bc, int mode, double cst, double theta) {
+// The corner exponents p(A_m), m = 1..d, depend on d only: computed once on
+// the host and passed to every ghost.
+struct DtauP {
+    double p[3];
+};
+
+DtauP dtau_p(int d) {
+    DtauP r{};
+    for (int m = 1; m <= d && m <= 3; ++m) r.p[m - 1] = acosh((m < d) ? (1.0 + m) : (2.0 * d - 1.0));
+    return r;
+}
+
+__host__ __device__ double dtau_formula(int d, int bc, int mode, double cst, double theta, const DtauP &P) {
     if (mode == BCMG_DTAU_CONST) return cst;
     double gmin = 1e300, gmax = 0.0;
     for (int m = 1; m <= d; ++m) {
-        double arg = (m < d) ? (1.0 + m) : (2.0 * d - 1.0);
-        double p = acosh(arg);
+        const double p = P.p[m - 1];
         double g;
         if (mode == BCMG_DTAU_EXP) {
             g = (bc == BCMG_BC_NEUMANN) ? p * exp(-p * theta) : exp(-p * theta);
@@ -311,7 +361,7 @@ struct GhostOut {
 
 // geometry of ghost g of one level (normal, eta, stencil, xi, Q, Delta tau)
 __device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
-                          const uint8_t *__restrict__ cls, const Geo &G, int dmode, double dconst,
+                          const uint8_t *__restrict__ cls, const Geo &G, int dmode, double dconst, const DtauP &P,
                           const GhostOut &out, int64_t g) {
     const int d = G.d;
     int64_t lin = gidx[g];
@@ -410,19 +460,25 @@ __device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng,
                 cf[3] = a0[2] * f0[2][1] + a1[2] * f1[2][1];
             }
             // once the midpoint rounds onto an end of the interval, every
-            // remaining halving leaves eta = that midpoint: stop there
+            // remaining halving leaves eta = that midpoint: stop there.
+            // lo, hi and mid lie in [0, 1] with lo + hi >= 2^-64, so the
+            // halving is an exponent decrement and the comparisons are on
+            // bit patterns (equal doubles have equal bits here; val >= 0
+            // is "sign bit clear, or -0"), keeping them off the FP64 pipe
+            const long long kHalf = 1LL << 52, kSign = (long long)0x8000000000000000ULL;
             double lo = 0.0, hi = 1.0;
             for (int it = 0; it < 64; ++it) {
-                double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
-                if (mid == lo || mid == hi) {
+                const double mid = __longlong_as_double(__double_as_longlong(__dadd_rn(lo, hi)) - kHalf);
+                const long long bm = __double_as_longlong(mid);
+                if (bm == __double_as_longlong(lo) || bm == __double_as_longlong(hi)) {
                     lo = hi = mid;
                     break;
                 }
-                const double val = fma(fma(fma(cf[3], mid, cf[2]), mid, cf[1]), mid, cf[0]);
-                if (val >= 0.0) lo = mid;
+                const long long bv = __double_as_longlong(fma(fma(fma(cf[3], mid, cf[2]), mid, cf[1]), mid, cf[0]));
+                if (bv >= 0 || bv == kSign) lo = mid;
                 else hi = mid;
             }
-            eta = __dmul_rn(0.5, __dadd_rn(lo, hi));
+            eta = __longlong_as_double(__double_as_longlong(__dadd_rn(lo, hi)) - kHalf);
         }
     }
     // upwind 3^d stencil with G at a corner
@@ -477,7 +533,7 @@ __device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng,
     out.code[g] = code;
     out.eta[g] = eta;
     // Neumann: the formula gives Delta tau / h
-    out.dt[g] = dtau_formula(d, bc, dmode, dconst, eta) * (bc == BCMG_BC_NEUMANN ? G.h : 1.0);
+    out.dt[g] = dtau_formula(d, bc, dmode, dconst, eta, P) * (bc == BCMG_BC_NEUMANN ? G.h : 1.0);
 }
 
 // ---------------------------------------------------------------- band
@@ -539,12 +595,12 @@ __device__ __forceinline__ int level_of_block(const LevelTab *tab, int nl, bool 
 }
 
 // ghost geometry and band marks of every level
-__global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int bc, int dmode, double dconst) {
+__global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int bc, int dmode, double dconst, DtauP P) {
     const int l = level_of_block(tab, nl, false);
     const LevelTab &T = tab[l];
     const int64_t g = ((int64_t)blockIdx.x - T.blk_g) * blockDim.x + threadIdx.x;
     if (g >= T.ng) return;
-    ghost_one(bc, T.gidx, T.ng, T.phi, T.cls, T.G, dmode, dconst, T.gout, g);
+    ghost_one(bc, T.gidx, T.ng, T.phi, T.cls, T.G, dmode, dconst, P, T.gout, g);
     band_mark_one(T.gidx, T.cls, T.G, T.mark, g);
 }
 
@@ -939,7 +995,9 @@ inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
-double dtau_of(int d, int bc, int mode, double cst, double theta) { return dtau_formula(d, bc, mode, cst, theta); }
+double dtau_of(int d, int bc, int mode, double cst, double theta) {
+    return dtau_formula(d, bc, mode, cst, theta, dtau_p(d));
+}
 
 // the path expansion fits the per-thread buffers: at most d (d^K - 1)/(d - 1)
 // the expansion passes work for any number of sweeps (rows longer than
@@ -1010,12 +1068,31 @@ void run_compaction(Handle &H, std::vector<CompactItem> &items) {
         for (int b = 0; b < it.nl; ++b) m |= (uint32_t)it.mask[b] << (8 * b);
         return m;
     };
+    // the arrays in launches of at most kCompactMax
+    auto batches = [&](bool with_out, auto &&run) {
+        for (size_t i0 = 0; i0 < items.size(); i0 += kCompactMax) {
+            CompactBatch cb{};
+            int64_t nblk = 0;
+            for (size_t i = i0; i < items.size() && i < i0 + kCompactMax; ++i) {
+                const CompactItem &it = items[i];
+                CompactArr &a = cb.a[cb.narr++];
+                a.flags = it.flags;
+                a.n = it.n;
+                a.blk0 = nblk;
+                a.base = it.base;
+                a.masks = masks_of(it);
+                a.nl = it.nl;
+                for (int b = 0; b < it.nl; ++b) a.out[b] = (with_out && it.out[b]) ? *it.out[b] : nullptr;
+                nblk += it.nblk;
+            }
+            run(cb, nblk);
+        }
+    };
     int64_t *counts = (int64_t *)dalloc(H, sizeof(int64_t) * B, true);
-    for (auto &it : items) {
-        k_count<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, it.nl, masks_of(it),
-                                                                  counts + it.base);
+    batches(false, [&](const CompactBatch &cb, int64_t nblk) {
+        k_count<<<(unsigned)nblk, kCompactThreads, 0, H.st>>>(cb, counts);
         count_launch(H);
-    }
+    });
     check_cuda(cudaGetLastError(), "k_count");
     int64_t *hc = pinned_scratch(H, (size_t)B);
     check_cuda(cudaMemcpyAsync(hc, counts, sizeof(int64_t) * B, cudaMemcpyDeviceToHost, H.st), "counts D2H");
@@ -1032,21 +1109,15 @@ void run_compaction(Handle &H, std::vector<CompactItem> &items) {
             it.total[b] = tot;
         }
     check_cuda(cudaMemcpyAsync(counts, hc, sizeof(int64_t) * B, cudaMemcpyHostToDevice, H.st), "offsets H2D");
-    for (auto &it : items) {
-        ScatterOut so{};
-        bool any = false;
-        for (int b = 0; b < it.nl; ++b) {
-            if (!it.out[b]) continue;
-            *it.out[b] = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(it.total[b], 1),
-                                            it.temp[b], false);
-            so.out[b] = *it.out[b];
-            any = true;
-        }
-        if (!any) continue;
-        k_scatter<<<(unsigned)it.nblk, kCompactThreads, 0, H.st>>>(it.flags, it.n, it.nl, masks_of(it),
-                                                                    counts + it.base, so);
+    for (auto &it : items)
+        for (int b = 0; b < it.nl; ++b)
+            if (it.out[b])
+                *it.out[b] = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(it.total[b], 1),
+                                                it.temp[b], false);
+    batches(true, [&](const CompactBatch &cb, int64_t nblk) {
+        k_scatter<<<(unsigned)nblk, kCompactThreads, 0, H.st>>>(cb, counts);
         count_launch(H);
-    }
+    });
     check_cuda(cudaGetLastError(), "k_scatter");
 }
 
@@ -1202,7 +1273,8 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     LevelTab *tab_d = (LevelTab *)dalloc(H, sizeof(LevelTab) * keep, true);
     check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(LevelTab) * keep, cudaMemcpyHostToDevice, H.st), "tab");
     if (gblocks > 0) {
-        k_ghost_all<<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.bc, H.o.dtau_mode, H.o.dtau_const);
+        k_ghost_all<<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.bc, H.o.dtau_mode, H.o.dtau_const,
+                                                          dtau_p(H.d));
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "ghost set-up");
