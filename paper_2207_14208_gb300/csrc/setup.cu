@@ -120,24 +120,27 @@ __device__ __forceinline__ uint64_t compact_hits(const uint8_t f[kCompactPerThre
 }
 
 __global__ void __launch_bounds__(kCompactThreads) k_count(CompactBatch B, int64_t *__restrict__ counts) {
-    __shared__ uint64_t red[kCompactThreads];
+    __shared__ uint64_t red[kCompactThreads / 32];
     const CompactArr &A = B.a[compact_arr_of(B)];
     const int64_t blk = (int64_t)blockIdx.x - A.blk0;
     const int64_t base = blk * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
     uint8_t f[kCompactPerThread];
     compact_load(A, base, f);
-    red[threadIdx.x] = compact_hits(f, A.masks, A.nl);
+    uint64_t c = compact_hits(f, A.masks, A.nl);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) red[warp] = c;
     __syncthreads();
-    for (int s = kCompactThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
+    if (threadIdx.x < A.nl) {
+        uint64_t t = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w) t += red[w];
+        counts[A.base + blk * A.nl + threadIdx.x] = (int64_t)((t >> (16 * threadIdx.x)) & 0xffffu);
     }
-    if (threadIdx.x < A.nl)
-        counts[A.base + blk * A.nl + threadIdx.x] = (int64_t)((red[0] >> (16 * threadIdx.x)) & 0xffffu);
 }
 
 __global__ void __launch_bounds__(kCompactThreads) k_scatter(CompactBatch B, const int64_t *__restrict__ offs) {
-    __shared__ uint64_t sc[kCompactThreads];
+    __shared__ uint64_t sc[kCompactThreads / 32];
     const CompactArr &A = B.a[compact_arr_of(B)];
     if (!A.out[0] && !A.out[1] && !A.out[2] && !A.out[3]) return;  // counted only (uniform per block)
     const int64_t blk = (int64_t)blockIdx.x - A.blk0;
@@ -145,37 +148,44 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter(CompactBatch B, con
     uint8_t f[kCompactPerThread];
     compact_load(A, base, f);
     const uint64_t c = compact_hits(f, A.masks, A.nl);
-    sc[threadIdx.x] = c;
-    __syncthreads();
-    // inclusive Hillis-Steele scan over the block (deterministic)
-    for (int s = 1; s < kCompactThreads; s <<= 1) {
-        const uint64_t v = (threadIdx.x >= s) ? sc[threadIdx.x - s] : 0;
-        __syncthreads();
-        sc[threadIdx.x] += v;
-        __syncthreads();
+    // exclusive scan over the block: warp scans, then a scan of the warp
+    // totals by warp 0 (integer, deterministic)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    const uint64_t excl = sc[threadIdx.x] - c;
+    if (lane == 31) sc[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < kCompactThreads / 32 ? sc[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kCompactThreads / 32) sc[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t excl = x - c + (warp > 0 ? sc[warp - 1] : 0);
+    // the four lists unrolled (registers); lists past nl have mask 0
     int64_t pos[4];
-    for (int b = 0; b < A.nl; ++b) pos[b] = offs[A.base + blk * A.nl + b] + (int64_t)((excl >> (16 * b)) & 0xffffu);
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        pos[b] = b < A.nl ? offs[A.base + blk * A.nl + b] + (int64_t)((excl >> (16 * b)) & 0xffffu) : 0;
 #pragma unroll
     for (int i = 0; i < kCompactPerThread; ++i)
-        for (int b = 0; b < A.nl; ++b)
-            if (bucket_hits(f[i], A.masks, b)) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (b < A.nl && bucket_hits(f[i], A.masks, b)) {
                 if (A.out[b]) A.out[b][pos[b]] = (uint32_t)(base + i);
                 ++pos[b];
             }
 }
 
 // ---------------------------------------------------------------- classes
-// coarse phi by injection: one thread per coarse node on a (x-blocks, j, k) grid
-__global__ void __launch_bounds__(128) k_inject(const double *__restrict__ phif, Geo Gf, Geo Gc,
-                                                double *__restrict__ phic) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i > Gc.N) return;
-    phic[(int64_t)i + (int64_t)j * Gc.st[1] + (int64_t)k * Gc.st[2]] =
-        phif[2 * (int64_t)i + 2 * (int64_t)j * Gf.st[1] + 2 * (int64_t)k * Gf.st[2]];
-}
-
 // x < 0.0 decided on the IEEE bit pattern (sign set, not -0, not NaN), so
 // the test runs on the integer pipe instead of the FP64 pipe
 __device__ __forceinline__ bool neg_d(double x) {
@@ -190,40 +200,84 @@ __device__ __forceinline__ bool neg_d(double x) {
 // (no index division).
 enum : uint8_t { kFlRed = 1, kFlBlack = 2, kFlBox = 4, kFlGhost = 8, kFlAct = 16 };
 
+// One launch classifies every candidate level.  Level l reads the finest
+// phi at stride 2^l (the injection, Sec. 2.1) and, for l > 0, stores its
+// phi.  Threads of a 32 x 4 block own (i, j) columns and march a chunk of
+// kClassPlanes planes in k, keeping phi of planes k - 1, k, k + 1 in
+// registers, so each phi value is read from memory about once per column
+// step besides the four in-plane neighbours (which the block's other threads
+// read too: cache hits).
+constexpr int kClassPlanes = 16;
+constexpr int kClassMax = 24;
+
+struct ClassLevel {
+    Geo G;
+    int s;                 // stride in the finest grid (2^l)
+    double *phic;          // this level's phi (nullptr on the finest)
+    uint8_t *cls, *flags;
+    int64_t blk0;          // first block
+    int bx, by;            // blocks along i and j (chunks along k follow)
+};
+
+struct ClassBatch {
+    int nl;
+    const double *phi0;
+    int64_t st0[3];        // strides of the finest grid
+    ClassLevel lv[kClassMax];
+};
+
 template <int D>
-__global__ void __launch_bounds__(128) k_classify(const double *__restrict__ phi, Geo G, uint8_t *__restrict__ cls,
-                                                  uint8_t *__restrict__ flags) {
-    // 32 x 4 thread blocks over (i, j) rows: little idle work when N + 1 is
-    // not a multiple of the block width
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 4 + threadIdx.y, k = (D == 3) ? blockIdx.z : 0;
+__global__ void __launch_bounds__(128) k_classify(ClassBatch B) {
+    int l = 0;
+    for (int q = 1; q < B.nl; ++q)
+        if ((int64_t)blockIdx.x >= B.lv[q].blk0) l = q;
+    const ClassLevel &C = B.lv[l];
+    const Geo &G = C.G;
+    const int64_t bl = (int64_t)blockIdx.x - C.blk0;
+    const int bxi = (int)(bl % C.bx), byi = (int)((bl / C.bx) % C.by), ch = (int)(bl / ((int64_t)C.bx * C.by));
+    const int i = bxi * 32 + threadIdx.x, j = byi * 4 + threadIdx.y;
     if (i > G.N || j > G.N) return;
-    const int64_t sy = G.st[1], sz = (D == 3) ? G.st[2] : 0;
-    const int64_t lin = (int64_t)i + (int64_t)j * sy + (int64_t)k * sz;
-    const bool edge = i == 0 || i == G.N || j == 0 || j == G.N || (D == 3 && (k == 0 || k == G.N));
-    uint8_t c = CL_INACTIVE;
-    if (neg_d(phi[lin])) {
-        c = edge ? CL_BOXDIR : CL_INTERIOR;
-    } else {
-        // a neighbour is interior if it is off the box edge with phi < 0
-        const int ix[3] = {i, j, k};
-        const int64_t st[3] = {1, sy, sz};
-        for (int a = 0; a < D; ++a)
-            for (int dir = -1; dir <= 1; dir += 2) {
-                int ok = 1;
-                for (int b2 = 0; b2 < D; ++b2) {
-                    const int v = ix[b2] + (b2 == a ? dir : 0);
-                    ok &= (v > 0 && v < G.N) ? 1 : 0;
-                }
-                if (ok && neg_d(phi[lin + dir * st[a]])) c = CL_GHOST;
+    const int k0 = (D == 3) ? ch * kClassPlanes : 0;
+    const int k1 = (D == 3) ? min(k0 + kClassPlanes, G.N + 1) : 1;
+    const int64_t s0 = (int64_t)C.s * B.st0[0], s1 = (int64_t)C.s * B.st0[1], s2 = (D == 3) ? (int64_t)C.s * B.st0[2] : 0;
+    const double *col = B.phi0 + (int64_t)i * s0 + (int64_t)j * s1;  // phi at (i, j, 0)
+    // a neighbour counts when it is off the box edge (all coordinates
+    // strictly inside) and has phi < 0; the in-plane part of that test is
+    // fixed per column
+    const bool inx = j > 0 && j < G.N, iny = i > 0 && i < G.N;
+    const bool xm = (i - 1 > 0) && inx, xp = (i + 1 < G.N) && inx;
+    const bool ym = (j - 1 > 0) && iny, yp = (j + 1 < G.N) && iny;
+    double pm = (D == 3 && k0 > 0) ? col[(int64_t)(k0 - 1) * s2] : 0.0;
+    double pc = col[(int64_t)k0 * s2];
+    for (int k = k0; k < k1; ++k) {
+        const double pn = (D == 3 && k < G.N) ? col[(int64_t)(k + 1) * s2] : 0.0;
+        const int64_t lin = (int64_t)i + (int64_t)j * G.st[1] + (D == 3 ? (int64_t)k * G.st[2] : 0);
+        if (C.phic) C.phic[lin] = pc;
+        const bool inz = (D == 2) || (k > 0 && k < G.N);
+        const bool edge = i == 0 || i == G.N || j == 0 || j == G.N || (D == 3 && (k == 0 || k == G.N));
+        uint8_t c = CL_INACTIVE;
+        if (neg_d(pc)) {
+            c = edge ? CL_BOXDIR : CL_INTERIOR;
+        } else {
+            const double *p = col + (D == 3 ? (int64_t)k * s2 : 0);
+            bool gh = false;
+            if (inz) {
+                gh = (xm && neg_d(p[-s0])) || (xp && neg_d(p[s0])) || (ym && neg_d(p[-s1])) || (yp && neg_d(p[s1]));
             }
+            if (D == 3 && inx && iny)
+                gh = gh || (k - 1 > 0 && neg_d(pm)) || (k + 1 < G.N && neg_d(pn));
+            if (gh) c = CL_GHOST;
+        }
+        C.cls[lin] = c;
+        const int par = (i + j + k) & 1;
+        uint8_t fl = 0;
+        if (c == CL_INTERIOR) fl = (par == 0 ? kFlRed : kFlBlack) | kFlAct;
+        else if (c == CL_GHOST) fl = kFlGhost | kFlAct;
+        else if (c == CL_BOXDIR) fl = kFlBox;
+        C.flags[lin] = fl;
+        pm = pc;
+        pc = pn;
     }
-    cls[lin] = c;
-    const int par = (i + j + k) & 1;
-    uint8_t fl = 0;
-    if (c == CL_INTERIOR) fl = (par == 0 ? kFlRed : kFlBlack) | kFlAct;
-    else if (c == CL_GHOST) fl = kFlGhost | kFlAct;
-    else if (c == CL_BOXDIR) fl = kFlBox;
-    flags[lin] = fl;
 }
 
 // ---------------------------------------------------------------- ghosts
@@ -243,7 +297,7 @@ struct CellCache {
     double v[8];
 };
 
-__device__ double interp_phi(const Geo &G, const double *phi, const double p[3], CellCache &cc) {
+__device__ __forceinline__ double interp_phi(const Geo &G, const double *phi, const double p[3], CellCache &cc) {
     int64_t c[3] = {0, 0, 0};
     double t[3] = {0.0, 0.0, 0.0};
 #pragma unroll
@@ -292,7 +346,7 @@ __device__ double interp_phi(const Geo &G, const double *phi, const double p[3],
     return val;
 }
 
-__device__ bool stencil_ok(const Geo &G, const uint8_t *cls, const int ix[3], const int s[3], const int q[3]) {
+__device__ __forceinline__ bool stencil_ok(const Geo &G, const uint8_t *cls, const int ix[3], const int s[3], const int q[3]) {
     int o[3];
     for (o[2] = 0; o[2] <= (G.d > 2 ? q[2] : 0); ++o[2])
         for (o[1] = 0; o[1] <= (G.d > 1 ? q[1] : 0); ++o[1])
@@ -360,7 +414,7 @@ struct GhostOut {
 };
 
 // geometry of ghost g of one level (normal, eta, stencil, xi, Q, Delta tau)
-__device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
+__device__ __forceinline__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
                           const uint8_t *__restrict__ cls, const Geo &G, int dmode, double dconst, const DtauP &P,
                           const GhostOut &out, int64_t g) {
     const int d = G.d;
@@ -538,7 +592,7 @@ __device__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng,
 
 // ---------------------------------------------------------------- band
 // mark the inactive nodes within Chebyshev distance 2 of ghost g
-__device__ void band_mark_one(const uint32_t *__restrict__ gidx, const uint8_t *__restrict__ cls, const Geo &G,
+__device__ __forceinline__ void band_mark_one(const uint32_t *__restrict__ gidx, const uint8_t *__restrict__ cls, const Geo &G,
                               uint8_t *__restrict__ mark, int64_t g) {
     int ix[3];
     decode(G, gidx[g], ix);
@@ -594,14 +648,18 @@ __device__ __forceinline__ int level_of_block(const LevelTab *tab, int nl, bool 
     return l;
 }
 
-// ghost geometry and band marks of every level
+// ghost geometry and band marks of every level; the dimension is a template
+// argument so that every per-axis array of the geometry stays in registers
+template <int D>
 __global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int bc, int dmode, double dconst, DtauP P) {
     const int l = level_of_block(tab, nl, false);
     const LevelTab &T = tab[l];
     const int64_t g = ((int64_t)blockIdx.x - T.blk_g) * blockDim.x + threadIdx.x;
     if (g >= T.ng) return;
-    ghost_one(bc, T.gidx, T.ng, T.phi, T.cls, T.G, dmode, dconst, P, T.gout, g);
-    band_mark_one(T.gidx, T.cls, T.G, T.mark, g);
+    Geo G = T.G;
+    G.d = D;
+    ghost_one(bc, T.gidx, T.ng, T.phi, T.cls, G, dmode, dconst, P, T.gout, g);
+    band_mark_one(T.gidx, T.cls, G, T.mark, g);
 }
 
 __device__ void band_one(const uint32_t *__restrict__ bidx, int64_t nb, const double *__restrict__ phi,
@@ -1145,6 +1203,8 @@ __global__ void k_hp_scatter(const uint32_t *__restrict__ ilist, int64_t nint, G
 struct LevelScratch {
     uint8_t *flags = nullptr, *fband = nullptr;
     uint32_t *red = nullptr, *black = nullptr;
+    uint32_t *act = nullptr;  // active list of a coarse level (round 1)
+    int64_t nact = 0;
     unsigned long long *cnt = nullptr;  // clamp / fall-back counters
     int64_t *ecnt = nullptr;
 };
@@ -1177,29 +1237,44 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     }
     const int nc = (int)H.L.size();
     std::vector<LevelScratch> S(nc);
-    // phase A: phi by injection, classes and class flags
-    for (int l = 0; l < nc; ++l) {
-        Level &L = H.L[l];
-        LevelScratch &s = S[l];
-        Geo G = geo_of(L);
-        if (l == 0) {
-            L.phi = phi0;
-        } else {
-            double *phic = (double *)dalloc(H, sizeof(double) * L.nn, true, false);
-            const dim3 ig((unsigned)nblocks(L.n, 128), (unsigned)L.n, H.d == 3 ? (unsigned)L.n : 1u);
-            k_inject<<<ig, 128, 0, H.st>>>(H.L[l - 1].phi, geo_of(H.L[l - 1]), G, phic);
+    // phase A: phi by injection, classes and class flags (one launch per
+    // kClassMax levels)
+    {
+        ClassBatch cb{};
+        int64_t nblk = 0;
+        auto flush = [&]() {
+            if (cb.nl == 0) return;
+            if (H.d == 3) k_classify<3><<<(unsigned)nblk, dim3(32, 4), 0, H.st>>>(cb);
+            else k_classify<2><<<(unsigned)nblk, dim3(32, 4), 0, H.st>>>(cb);
             count_launch(H);
-            L.phi = phic;
+            check_cuda(cudaGetLastError(), "classification");
+            cb.nl = 0;
+            nblk = 0;
+        };
+        const Geo G0 = geo_of(H.L[0]);
+        for (int l = 0; l < nc; ++l) {
+            Level &L = H.L[l];
+            LevelScratch &s = S[l];
+            Geo G = geo_of(L);
+            double *phic = l == 0 ? nullptr : (double *)dalloc(H, sizeof(double) * L.nn, true, false);
+            L.phi = l == 0 ? phi0 : phic;
+            L.cls = (uint8_t *)dalloc(H, L.nn, false, false);  // k_classify writes every entry
+            s.flags = (uint8_t *)dalloc(H, (size_t)L.nn, true, false);
+            if (cb.nl == kClassMax) flush();
+            cb.phi0 = phi0;
+            for (int a = 0; a < 3; ++a) cb.st0[a] = G0.st[a];
+            ClassLevel &c = cb.lv[cb.nl++];
+            c.G = G;
+            c.s = 1 << l;
+            c.phic = phic;
+            c.cls = L.cls;
+            c.flags = s.flags;
+            c.blk0 = nblk;
+            c.bx = nblocks(L.n, 32);
+            c.by = nblocks(L.n, 4);
+            nblk += (int64_t)c.bx * c.by * (H.d == 3 ? nblocks(L.n, kClassPlanes) : 1);
         }
-        L.cls = (uint8_t *)dalloc(H, L.nn, false, false);  // k_classify writes every entry
-        s.flags = (uint8_t *)dalloc(H, (size_t)L.nn, true, false);
-        const dim3 cg((unsigned)nblocks(L.n, 32), (unsigned)nblocks(L.n, 4), H.d == 3 ? (unsigned)L.n : 1u);
-        if (H.d == 3)
-            k_classify<3><<<cg, dim3(32, 4), 0, H.st>>>(L.phi, G, L.cls, s.flags);
-        else
-            k_classify<2><<<cg, dim3(32, 4), 0, H.st>>>(L.phi, G, L.cls, s.flags);
-        count_launch(H);
-        check_cuda(cudaGetLastError(), "classification");
+        flush();
     }
     // round 1: counts of every list on every candidate level (one sync)
     {
@@ -1214,6 +1289,13 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             add_list(it, kFlGhost, &L.gidx, false);
             items.push_back(it);
         }
+        // the active list of every coarse level (small), so that the
+        // coarsest system can be set up as soon as its ghosts are
+        for (int l = 1; l < nc; ++l) {
+            CompactItem it = compact_item(S[l].flags, H.L[l].nn);
+            add_list(it, kFlAct, &S[l].act, true);
+            items.push_back(it);
+        }
         run_compaction(H, items);
         for (int l = 0; l < nc; ++l) {
             Level &L = H.L[l];
@@ -1221,6 +1303,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             L.nint = L.nred + items[l].total[1];
             L.nbox = items[l].total[2];
             L.ng = items[l].total[3];
+            if (l > 0) S[l].nact = items[nc + l - 1].total[0];
         }
     }
     if (H.L[0].nint == 0) throw Error{BCMG_EGEOM, "no interior node on the finest grid"};
@@ -1232,6 +1315,64 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         }
     H.L.resize(keep);
     S.resize(keep);
+    // coarsest: dense system and its inverse, on the side stream (one SM's
+    // work for small systems) while the main stream goes on with the set-up;
+    // needs the coarsest active list and ghost geometry; joined before
+    // creation's closing synchronisation
+    auto coarsest_on_side = [&]() {
+        Level &L = H.L[keep - 1];
+        Geo G = geo_of(L);
+        int64_t n = L.nact;
+        double *A = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
+        L.Ainv = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1));
+        L.crhs = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1));
+        double *col = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1), true);
+        int *sing = (int *)dalloc(H, sizeof(int), true);
+        double *LU = nullptr;
+        int *perm = nullptr;
+        if (n <= kLuSmall) {
+            LU = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
+            perm = (int *)dalloc(H, sizeof(int) * std::max<int64_t>(n, 1), true);
+        }
+        // every buffer above (and the level data it reads) is in place on the
+        // main stream before the side stream starts
+        check_cuda(cudaEventRecord(H.ev_fork, H.st), "fork record");
+        check_cuda(cudaStreamWaitEvent(H.st2, H.ev_fork, 0), "fork wait");
+        k_assemble<<<nblocks(n, 128), 128, 0, H.st2>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.gn, L.ng, G, H.o.bc,
+                                                      H.o.reaction, A);
+        count_launch(H);
+        if (n <= kLuSmall) {
+            // shared-memory limits are per kernel for the whole process: always
+            // the largest size (n = kLuSmall), never one handle's n
+            const size_t smem = sizeof(double) * (size_t)(n * n + n);
+            check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(double) * (kLuSmall * kLuSmall + kLuSmall))),
+                       "LU shared memory");
+            k_lu_small<<<1, 1024, smem, H.st2>>>(A, (int)n, LU, perm, sing);
+            count_launch(H);
+            const size_t smem2 = sizeof(double) * (size_t)(n * n + n + kLuColsPerBlock * n);
+            check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(double) * (kLuSmall * kLuSmall + (2 + kLuColsPerBlock) *
+                                                                                            kLuSmall))),
+                       "LU inverse shared memory");
+            k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st2>>>(LU, (int)n, perm, L.Ainv);
+            count_launch(H);
+        } else {
+            k_identity<<<nblocks(n * n, T), T, 0, H.st2>>>(L.Ainv, n);
+            count_launch(H);
+            for (int64_t k = 0; k < n; ++k) {
+                k_gj_pivot<<<1, 1024, 0, H.st2>>>(A, L.Ainv, n, k, col, sing);
+                k_gj_elim<<<nblocks(n * n, T), T, 0, H.st2>>>(A, L.Ainv, n, k, col);
+                count_launch(H);
+                count_launch(H);
+            }
+        }
+        check_cuda(cudaGetLastError(), "gauss-jordan");
+        // into the handle's own pinned block, read after creation's closing
+        // synchronisation
+        check_cuda(cudaMemcpyAsync(H.sing_host, sing, sizeof(int), cudaMemcpyDeviceToHost, H.st2), "singular flag");
+        check_cuda(cudaEventRecord(H.ev_join, H.st2), "join record");
+    };
     // phase B: interior lists and ghost arrays per level, then the ghost geometry
     // and band marks of every level in one launch
     std::vector<LevelTab> tab(keep);
@@ -1273,12 +1414,29 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     LevelTab *tab_d = (LevelTab *)dalloc(H, sizeof(LevelTab) * keep, true);
     check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(LevelTab) * keep, cudaMemcpyHostToDevice, H.st), "tab");
     if (gblocks > 0) {
-        k_ghost_all<<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.bc, H.o.dtau_mode, H.o.dtau_const,
-                                                          dtau_p(H.d));
+        if (H.d == 3)
+            k_ghost_all<3><<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.bc, H.o.dtau_mode, H.o.dtau_const,
+                                                                 dtau_p(H.d));
+        else
+            k_ghost_all<2><<<(unsigned)gblocks, 128, 0, H.st>>>(tab_d, keep, H.o.bc, H.o.dtau_mode, H.o.dtau_const,
+                                                                 dtau_p(H.d));
         count_launch(H);
     }
     check_cuda(cudaGetLastError(), "ghost set-up");
-    // round 2: band lists on every level and the coarsest active list (one sync)
+    Level &Lc = H.L[keep - 1];
+    if (keep > 1) {
+        // a coarse level is the coarsest: its active list is there
+        Lc.nact = S[keep - 1].nact;
+        if (Lc.nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
+        Lc.act = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(Lc.nact, 1), false, false);
+        if (Lc.nact > 0)
+            check_cuda(cudaMemcpyAsync(Lc.act, S[keep - 1].act, sizeof(uint32_t) * Lc.nact, cudaMemcpyDeviceToDevice,
+                                       H.st),
+                       "active list");
+        coarsest_on_side();
+    }
+    // round 2: band lists on every level (and the active list of a finest
+    // level that is also the coarsest) (one sync)
     {
         std::vector<CompactItem> items;
         for (int l = 0; l < keep; ++l) {
@@ -1286,71 +1444,18 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             add_list(it, 0xff, &H.L[l].bidx, false);
             items.push_back(it);
         }
-        Level &Lc = H.L[keep - 1];
-        CompactItem ia = compact_item(S[keep - 1].flags, Lc.nn);
-        add_list(ia, kFlAct, &Lc.act, false);
-        items.push_back(ia);
+        if (keep == 1) {
+            CompactItem ia = compact_item(S[0].flags, Lc.nn);
+            add_list(ia, kFlAct, &Lc.act, false);
+            items.push_back(ia);
+        }
         run_compaction(H, items);
         for (int l = 0; l < keep; ++l) H.L[l].nb = items[l].total[0];
-        Lc.nact = items[keep].total[0];
+        if (keep == 1) Lc.nact = items[keep].total[0];
     }
-    if (H.L[keep - 1].nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
-    // coarsest: dense system and its inverse, on the side stream (one SM's
-    // work for small systems) while the main stream builds the band and its
-    // extension; joined before creation's closing synchronisation
-    {
-        Level &L = H.L[keep - 1];
-        Geo G = geo_of(L);
-        int64_t n = L.nact;
-        double *A = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
-        L.Ainv = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1));
-        L.crhs = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1));
-        double *col = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n, 1), true);
-        int *sing = (int *)dalloc(H, sizeof(int), true);
-        double *LU = nullptr;
-        int *perm = nullptr;
-        if (n <= kLuSmall) {
-            LU = (double *)dalloc(H, sizeof(double) * std::max<int64_t>(n * n, 1), true);
-            perm = (int *)dalloc(H, sizeof(int) * std::max<int64_t>(n, 1), true);
-    }
-    // every buffer above (and the level data it reads) is in place on the
-    // main stream before the side stream starts
-    check_cuda(cudaEventRecord(H.ev_fork, H.st), "fork record");
-    check_cuda(cudaStreamWaitEvent(H.st2, H.ev_fork, 0), "fork wait");
-    k_assemble<<<nblocks(n, 128), 128, 0, H.st2>>>(L.act, n, L.cls, L.gidx, L.gcode, L.gxi, L.gn, L.ng, G, H.o.bc,
-                                                  H.o.reaction, A);
-    count_launch(H);
-    if (n <= kLuSmall) {
-        // shared-memory limits are per kernel for the whole process: always
-        // the largest size (n = kLuSmall), never one handle's n
-        const size_t smem = sizeof(double) * (size_t)(n * n + n);
-        check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + kLuSmall))),
-                   "LU shared memory");
-        k_lu_small<<<1, 1024, smem, H.st2>>>(A, (int)n, LU, perm, sing);
-        count_launch(H);
-        const size_t smem2 = sizeof(double) * (size_t)(n * n + n + kLuColsPerBlock * n);
-        check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(double) * (kLuSmall * kLuSmall + (2 + kLuColsPerBlock) *
-                                                                                        kLuSmall))),
-                   "LU inverse shared memory");
-        k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st2>>>(LU, (int)n, perm, L.Ainv);
-        count_launch(H);
-    } else {
-        k_identity<<<nblocks(n * n, T), T, 0, H.st2>>>(L.Ainv, n);
-        count_launch(H);
-        for (int64_t k = 0; k < n; ++k) {
-            k_gj_pivot<<<1, 1024, 0, H.st2>>>(A, L.Ainv, n, k, col, sing);
-            k_gj_elim<<<nblocks(n * n, T), T, 0, H.st2>>>(A, L.Ainv, n, k, col);
-            count_launch(H);
-            count_launch(H);
-        }
-    }
-    check_cuda(cudaGetLastError(), "gauss-jordan");
-    // read by the caller after its closing synchronisation
-    H.sing_host = (int *)pinned_scratch(H, 1);
-    check_cuda(cudaMemcpyAsync(H.sing_host, sing, sizeof(int), cudaMemcpyDeviceToHost, H.st2), "singular flag");
-    check_cuda(cudaEventRecord(H.ev_join, H.st2), "join record");
+    if (keep == 1) {
+        if (Lc.nact > kMaxCoarse) throw Error{BCMG_EGEOM, "coarsest system has more than 4096 unknowns"};
+        coarsest_on_side();
     }
     // phase C: band sources and the ELL expansion of the extension, every
     // level in one launch each
