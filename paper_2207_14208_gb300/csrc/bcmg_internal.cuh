@@ -140,12 +140,13 @@ struct Handle {
     void *tail_ops = nullptr;  // (kind, level) schedule of the tail
     int tail_nops = 0;
     int nsm = 152;  // SMs of the device (block sizes of the FP64 kernels)
+    int dev = 0;    // the device the handle was created on
     bool capturing = false;
     int64_t captured = 0;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;
     int64_t dev_bytes = 0;      // device memory the handle holds
     Arena arena_perm, arena_temp;
-    std::vector<void *> temps;  // set-up scratch, freed when creation ends
+    std::vector<std::pair<void *, size_t>> temps;  // set-up scratch, freed when creation ends
     // profiling of the finest-level sweeps (opts.profile)
     std::vector<cudaEvent_t> pev;
     int pev_next = 0, pev_pairs = 0;

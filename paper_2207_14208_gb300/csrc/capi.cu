@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -30,22 +31,78 @@ void check_cuda(cudaError_t e, const char *what) {
 }
 
 // Device memory of a handle.  Arrays up to kSmallAlloc bytes are carved from
-// kChunk-byte chunks that are zero-filled once when taken, so a hierarchy
-// needs a few dozen driver calls rather than two per array; larger arrays
-// get their own stream-ordered allocation from the device's default pool
-// (which keeps freed memory for reuse, so repeated create/destroy stays
-// cheap), zero-filled only when the caller needs zeros.
+// kChunk-byte chunks that are zero-filled once when taken; larger arrays get
+// their own block, zero-filled only when the caller needs zeros.  Blocks
+// come from a process-wide cache keyed by (device, size) before the
+// device's stream-ordered pool: the blocks of a destroyed handle, or of a
+// finished set-up's scratch, enter the cache only after every stream that
+// used them has been synchronised, so any stream may take them, and
+// repeated creations of the same hierarchy (a solve service, a benchmark
+// loop) need no driver call at all.  At most kCacheMax bytes are cached;
+// when the pool cannot allocate, the cache goes back to the driver and the
+// allocation is retried once.
 constexpr size_t kChunk = 4u << 20;
 constexpr size_t kSmallAlloc = 256u << 10;
+constexpr size_t kCacheMax = 16ull << 30;
+
+std::mutex g_cache_mu;
+std::multimap<std::pair<int, size_t>, void *> g_cache;
+size_t g_cache_bytes = 0;
+
+void *cache_take(int dev, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find({dev, bytes});
+    if (it == g_cache.end()) return nullptr;
+    void *p = it->second;
+    g_cache.erase(it);
+    g_cache_bytes -= bytes;
+    return p;
+}
+
+// p is idle on every stream; past the cap it is freed on st instead
+void cache_put(int dev, size_t bytes, void *p, cudaStream_t st) {
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        if (g_cache_bytes + bytes <= kCacheMax) {
+            g_cache.emplace(std::make_pair(dev, bytes), p);
+            g_cache_bytes += bytes;
+            return;
+        }
+    }
+    cudaFreeAsync(p, st);
+}
+
+void cache_drain() {
+    std::multimap<std::pair<int, size_t>, void *> all;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        all.swap(g_cache);
+        g_cache_bytes = 0;
+    }
+    int cur = 0;
+    (void)cudaGetDevice(&cur);
+    for (auto &kv : all) {
+        (void)cudaSetDevice(kv.first.first);
+        (void)cudaFree(kv.second);
+    }
+    (void)cudaSetDevice(cur);
+}
 
 void *raw_alloc(Handle &H, size_t bytes, bool temp) {
-    void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, bytes, H.st);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        throw Error{BCMG_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+    void *p = cache_take(H.dev, bytes);
+    if (!p) {
+        cudaError_t e = cudaMallocAsync(&p, bytes, H.st);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            cache_drain();
+            e = cudaMallocAsync(&p, bytes, H.st);
+        }
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            throw Error{BCMG_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+        }
     }
-    (temp ? H.temps : H.allocs).push_back(p);
+    (temp ? H.temps : H.allocs).push_back({p, bytes});
     if (!temp) H.dev_bytes += (int64_t)bytes;
     return p;
 }
@@ -94,8 +151,9 @@ void profile_mark(Handle &H, const Level &L) {
 
 namespace {
 
+// H's streams are synchronised (creation's closing sync, or destroy)
 void free_temps(Handle &H) {
-    for (void *p : H.temps) cudaFreeAsync(p, H.st);
+    for (auto &pb : H.temps) cache_put(H.dev, pb.second, pb.first, H.st);
     H.temps.clear();
     H.arena_temp = Arena{};
 }
@@ -147,7 +205,8 @@ void destroy(Handle *H) {
     pinned_put(H->shost);
     if (H->st) {
         free_temps(*H);
-        for (void *p : H->allocs) cudaFreeAsync(p, H->st);
+        for (auto &pb : H->allocs) cache_put(H->dev, pb.second, pb.first, H->st);
+        H->allocs.clear();
         cudaStreamSynchronize(H->st);
     }
     pinned_put(H->nhost);
@@ -478,6 +537,7 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
             (H->o.ordering != BCMG_ORDER_RB && H->o.ordering != BCMG_ORDER_LEX))
             throw Error{BCMG_EINVAL, "invalid options"};
         H->user = (cudaStream_t)stream;
+        check_cuda(cudaGetDevice(&H->dev), "cudaGetDevice");
         keep_pool_memory();
         check_cuda(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking), "cudaStreamCreate");
         check_cuda(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming), "cudaEventCreate");

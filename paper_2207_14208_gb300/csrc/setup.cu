@@ -85,10 +85,6 @@ struct CompactBatch {
     CompactArr a[kCompactMax];
 };
 
-__device__ __forceinline__ int bucket_hits(uint8_t f, uint32_t masks, int b) {
-    return (f & ((masks >> (8 * b)) & 0xffu)) ? 1 : 0;
-}
-
 __device__ __forceinline__ int compact_arr_of(const CompactBatch &B) {
     int k = 0;
     for (int i = 1; i < B.narr; ++i)
@@ -96,26 +92,52 @@ __device__ __forceinline__ int compact_arr_of(const CompactBatch &B) {
     return k;
 }
 
-// this thread's kCompactPerThread flag bytes (one 16-byte load when the
-// whole run is in range and aligned; zero past the end)
-__device__ __forceinline__ void compact_load(const CompactArr &A, int64_t base, uint8_t f[kCompactPerThread]) {
+// this thread's kCompactPerThread flag bytes as four little-endian words
+// (one 16-byte load when the whole run is in range and aligned; zero past
+// the end)
+__device__ __forceinline__ void compact_load(const CompactArr &A, int64_t base, uint32_t w[4]) {
     const bool vec = base + kCompactPerThread <= A.n && ((reinterpret_cast<uintptr_t>(A.flags + base) & 15) == 0);
     if (vec) {
         const uint4 v = *reinterpret_cast<const uint4 *>(A.flags + base);
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int i = 0; i < kCompactPerThread; ++i) f[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
     } else {
 #pragma unroll
-        for (int i = 0; i < kCompactPerThread; ++i) f[i] = base + i < A.n ? A.flags[base + i] : (uint8_t)0;
+        for (int q = 0; q < 4; ++q) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int64_t i = base + 4 * q + r;
+                x |= (uint32_t)(i < A.n ? A.flags[i] : (uint8_t)0) << (8 * r);
+            }
+            w[q] = x;
+        }
     }
 }
 
-__device__ __forceinline__ uint64_t compact_hits(const uint8_t f[kCompactPerThread], uint32_t masks, int nl) {
+// bit i of the result: byte i of the 16 has a bit of mask m (byte-parallel:
+// the high bit of each byte of ((t & 0x7f..) + 0x7f..) | t is set iff the
+// byte of t is non-zero)
+__device__ __forceinline__ uint32_t compact_hitmask(const uint32_t w[4], uint32_t m) {
+    const uint32_t mm = m * 0x01010101u;
+    uint32_t hm = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t t = w[q] & mm;
+        const uint32_t nz = (((t & 0x7f7f7f7fu) + 0x7f7f7f7fu) | t) & 0x80808080u;
+        hm |= (((nz >> 7) & 1u) | ((nz >> 14) & 2u) | ((nz >> 21) & 4u) | ((nz >> 28) & 8u)) << (4 * q);
+    }
+    return hm;
+}
+
+// the counts of the (up to four) lists as 16-bit fields
+__device__ __forceinline__ uint64_t compact_hits(const uint32_t w[4], uint32_t masks, int nl) {
     uint64_t c = 0;
 #pragma unroll
-    for (int i = 0; i < kCompactPerThread; ++i)
-        for (int b = 0; b < nl; ++b) c += (uint64_t)bucket_hits(f[i], masks, b) << (16 * b);
+    for (int b = 0; b < 4; ++b)
+        if (b < nl) c += (uint64_t)__popc(compact_hitmask(w, (masks >> (8 * b)) & 0xffu)) << (16 * b);
     return c;
 }
 
@@ -124,9 +146,9 @@ __global__ void __launch_bounds__(kCompactThreads) k_count(CompactBatch B, int64
     const CompactArr &A = B.a[compact_arr_of(B)];
     const int64_t blk = (int64_t)blockIdx.x - A.blk0;
     const int64_t base = blk * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
-    uint8_t f[kCompactPerThread];
-    compact_load(A, base, f);
-    uint64_t c = compact_hits(f, A.masks, A.nl);
+    uint32_t w[4];
+    compact_load(A, base, w);
+    uint64_t c = compact_hits(w, A.masks, A.nl);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
@@ -145,9 +167,9 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter(CompactBatch B, con
     if (!A.out[0] && !A.out[1] && !A.out[2] && !A.out[3]) return;  // counted only (uniform per block)
     const int64_t blk = (int64_t)blockIdx.x - A.blk0;
     const int64_t base = blk * kCompactTile + (int64_t)threadIdx.x * kCompactPerThread;
-    uint8_t f[kCompactPerThread];
-    compact_load(A, base, f);
-    const uint64_t c = compact_hits(f, A.masks, A.nl);
+    uint32_t w[4];
+    compact_load(A, base, w);
+    const uint64_t c = compact_hits(w, A.masks, A.nl);
     // exclusive scan over the block: warp scans, then a scan of the warp
     // totals by warp 0 (integer, deterministic)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -170,19 +192,17 @@ __global__ void __launch_bounds__(kCompactThreads) k_scatter(CompactBatch B, con
     }
     __syncthreads();
     const uint64_t excl = x - c + (warp > 0 ? sc[warp - 1] : 0);
-    // the four lists unrolled (registers); lists past nl have mask 0
-    int64_t pos[4];
+    // each list's hits in increasing index order from the thread's offset
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
-        pos[b] = b < A.nl ? offs[A.base + blk * A.nl + b] + (int64_t)((excl >> (16 * b)) & 0xffffu) : 0;
-#pragma unroll
-    for (int i = 0; i < kCompactPerThread; ++i)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if (b < A.nl && bucket_hits(f[i], A.masks, b)) {
-                if (A.out[b]) A.out[b][pos[b]] = (uint32_t)(base + i);
-                ++pos[b];
-            }
+    for (int b = 0; b < 4; ++b) {
+        if (b >= A.nl || !A.out[b]) continue;
+        int64_t pos = offs[A.base + blk * A.nl + b] + (int64_t)((excl >> (16 * b)) & 0xffffu);
+        uint32_t hm = compact_hitmask(w, (A.masks >> (8 * b)) & 0xffu);
+        while (hm) {
+            A.out[b][pos++] = (uint32_t)(base + __ffs(hm) - 1);
+            hm &= hm - 1;
+        }
+    }
 }
 
 // ---------------------------------------------------------------- classes
@@ -207,7 +227,7 @@ enum : uint8_t { kFlRed = 1, kFlBlack = 2, kFlBox = 4, kFlGhost = 8, kFlAct = 16
 // registers, so each phi value is read from memory about once per column
 // step besides the four in-plane neighbours (which the block's other threads
 // read too: cache hits).
-constexpr int kClassPlanes = 16;
+constexpr int kClassPlanes = 8;
 constexpr int kClassMax = 24;
 
 struct ClassLevel {
@@ -232,51 +252,61 @@ __global__ void __launch_bounds__(128) k_classify(ClassBatch B) {
     for (int q = 1; q < B.nl; ++q)
         if ((int64_t)blockIdx.x >= B.lv[q].blk0) l = q;
     const ClassLevel &C = B.lv[l];
-    const Geo &G = C.G;
-    const int64_t bl = (int64_t)blockIdx.x - C.blk0;
-    const int bxi = (int)(bl % C.bx), byi = (int)((bl / C.bx) % C.by), ch = (int)(bl / ((int64_t)C.bx * C.by));
-    const int i = bxi * 32 + threadIdx.x, j = byi * 4 + threadIdx.y;
-    if (i > G.N || j > G.N) return;
-    const int k0 = (D == 3) ? ch * kClassPlanes : 0;
-    const int k1 = (D == 3) ? min(k0 + kClassPlanes, G.N + 1) : 1;
-    const int64_t s0 = (int64_t)C.s * B.st0[0], s1 = (int64_t)C.s * B.st0[1], s2 = (D == 3) ? (int64_t)C.s * B.st0[2] : 0;
-    const double *col = B.phi0 + (int64_t)i * s0 + (int64_t)j * s1;  // phi at (i, j, 0)
+    const int N = C.G.N;
+    // node indices fit 32 bits (checked at creation), so does the block count
+    const uint32_t bl = (uint32_t)((int64_t)blockIdx.x - C.blk0);
+    const uint32_t bxy = (uint32_t)C.bx * (uint32_t)C.by;
+    const uint32_t ch = bl / bxy, r = bl - ch * bxy, byi = r / (uint32_t)C.bx, bxi = r - byi * (uint32_t)C.bx;
+    const int i = (int)bxi * 32 + threadIdx.x, j = (int)byi * 4 + threadIdx.y;
+    if (i > N || j > N) return;
+    const int k0 = (D == 3) ? (int)ch * kClassPlanes : 0;
+    const int nk = (D == 3) ? min(kClassPlanes, N + 1 - k0) : 1;
+    const uint32_t s0 = (uint32_t)C.s, s1 = (uint32_t)C.s * (uint32_t)B.st0[1];
+    const uint32_t s2 = (D == 3) ? (uint32_t)C.s * (uint32_t)B.st0[2] : 0u;
+    const uint32_t sy = (uint32_t)C.G.st[1], sz = (D == 3) ? (uint32_t)C.G.st[2] : 0u;
     // a neighbour counts when it is off the box edge (all coordinates
     // strictly inside) and has phi < 0; the in-plane part of that test is
     // fixed per column
-    const bool inx = j > 0 && j < G.N, iny = i > 0 && i < G.N;
-    const bool xm = (i - 1 > 0) && inx, xp = (i + 1 < G.N) && inx;
-    const bool ym = (j - 1 > 0) && iny, yp = (j + 1 < G.N) && iny;
-    double pm = (D == 3 && k0 > 0) ? col[(int64_t)(k0 - 1) * s2] : 0.0;
-    double pc = col[(int64_t)k0 * s2];
-    for (int k = k0; k < k1; ++k) {
-        const double pn = (D == 3 && k < G.N) ? col[(int64_t)(k + 1) * s2] : 0.0;
-        const int64_t lin = (int64_t)i + (int64_t)j * G.st[1] + (D == 3 ? (int64_t)k * G.st[2] : 0);
+    const bool inx = j > 0 && j < N, iny = i > 0 && i < N;
+    const bool xm = (i - 1 > 0) && inx, xp = (i + 1 < N) && inx;
+    const bool ym = (j - 1 > 0) && iny, yp = (j + 1 < N) && iny;
+    const bool zin = inx && iny;
+    const bool edge_ij = i == 0 || i == N || j == 0 || j == N;
+    const uint8_t par0 = (uint8_t)((i + j + k0) & 1);
+    const double *p = B.phi0 + ((uint32_t)i * s0 + (uint32_t)j * s1 + (uint32_t)k0 * s2);
+    uint32_t lin = (uint32_t)i + (uint32_t)j * sy + (uint32_t)k0 * sz;
+    // the column's phi on planes k0 - 1 .. k0 + kClassPlanes, all loads in
+    // flight together
+    constexpr int NP = (D == 3) ? kClassPlanes + 2 : 3;
+    double pz[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int kk = k0 - 1 + q;
+        pz[q] = (D == 3) ? ((kk >= 0 && kk <= N) ? p[(int)(q - 1) * (int64_t)s2] : 0.0) : (q == 1 ? p[0] : 0.0);
+    }
+#pragma unroll
+    for (int q = 0; q < NP - 2; ++q) {
+        if (q >= nk) break;
+        const int k = k0 + q;
+        const double pc = pz[q + 1];
         if (C.phic) C.phic[lin] = pc;
-        const bool inz = (D == 2) || (k > 0 && k < G.N);
-        const bool edge = i == 0 || i == G.N || j == 0 || j == G.N || (D == 3 && (k == 0 || k == G.N));
-        uint8_t c = CL_INACTIVE;
-        if (neg_d(pc)) {
-            c = edge ? CL_BOXDIR : CL_INTERIOR;
-        } else {
-            const double *p = col + (D == 3 ? (int64_t)k * s2 : 0);
-            bool gh = false;
-            if (inz) {
-                gh = (xm && neg_d(p[-s0])) || (xp && neg_d(p[s0])) || (ym && neg_d(p[-s1])) || (yp && neg_d(p[s1]));
-            }
-            if (D == 3 && inx && iny)
-                gh = gh || (k - 1 > 0 && neg_d(pm)) || (k + 1 < G.N && neg_d(pn));
-            if (gh) c = CL_GHOST;
-        }
+        // the four in-plane neighbours are loaded together (predicated on
+        // the box, not branched on one another)
+        const bool inz = (D == 2) || (k > 0 && k < N);
+        const double ax = (inz && xm) ? p[-(int64_t)s0] : 1.0, bx = (inz && xp) ? p[s0] : 1.0;
+        const double ay = (inz && ym) ? p[-(int64_t)s1] : 1.0, by = (inz && yp) ? p[s1] : 1.0;
+        bool gh = neg_d(ax) | neg_d(bx) | neg_d(ay) | neg_d(by);
+        if (D == 3) gh = gh | (zin & (k - 1 > 0) & neg_d(pz[q])) | (zin & (k + 1 < N) & neg_d(pz[q + 2]));
+        const bool edge = edge_ij || (D == 3 && (k == 0 || k == N));
+        const uint8_t c = neg_d(pc) ? (edge ? CL_BOXDIR : CL_INTERIOR) : (gh ? CL_GHOST : CL_INACTIVE);
         C.cls[lin] = c;
-        const int par = (i + j + k) & 1;
         uint8_t fl = 0;
-        if (c == CL_INTERIOR) fl = (par == 0 ? kFlRed : kFlBlack) | kFlAct;
+        if (c == CL_INTERIOR) fl = ((par0 ^ (uint8_t)(q & 1)) == 0 ? kFlRed : kFlBlack) | kFlAct;
         else if (c == CL_GHOST) fl = kFlGhost | kFlAct;
         else if (c == CL_BOXDIR) fl = kFlBox;
         C.flags[lin] = fl;
-        pm = pc;
-        pc = pn;
+        p += s2;
+        lin += sz;
     }
 }
 
@@ -413,11 +443,14 @@ struct GhostOut {
     unsigned long long *nclamp, *nfall;
 };
 
-// geometry of ghost g of one level (normal, eta, stencil, xi, Q, Delta tau)
+// geometry of ghost g of one level (normal, eta, stencil, xi, Q, Delta tau);
+// the dimension is a template argument so that the per-axis arrays stay in
+// registers
+template <int D>
 __device__ __forceinline__ void ghost_one(int bc, const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ phi,
                           const uint8_t *__restrict__ cls, const Geo &G, int dmode, double dconst, const DtauP &P,
                           const GhostOut &out, int64_t g) {
-    const int d = G.d;
+    constexpr int d = D;
     int64_t lin = gidx[g];
     int ix[3];
     decode(G, lin, ix);
@@ -648,8 +681,7 @@ __device__ __forceinline__ int level_of_block(const LevelTab *tab, int nl, bool 
     return l;
 }
 
-// ghost geometry and band marks of every level; the dimension is a template
-// argument so that every per-axis array of the geometry stays in registers
+// ghost geometry and band marks of every level
 template <int D>
 __global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int bc, int dmode, double dconst, DtauP P) {
     const int l = level_of_block(tab, nl, false);
@@ -658,7 +690,7 @@ __global__ void k_ghost_all(const LevelTab *__restrict__ tab, int nl, int bc, in
     if (g >= T.ng) return;
     Geo G = T.G;
     G.d = D;
-    ghost_one(bc, T.gidx, T.ng, T.phi, T.cls, G, dmode, dconst, P, T.gout, g);
+    ghost_one<D>(bc, T.gidx, T.ng, T.phi, T.cls, G, dmode, dconst, P, T.gout, g);
     band_mark_one(T.gidx, T.cls, G, T.mark, g);
 }
 
@@ -1381,7 +1413,9 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         Level &L = H.L[l];
         LevelScratch &s = S[l];
         Geo G = geo_of(L);
-        L.ilist = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(L.nint, 1));
+        // arrays every entry of which a set-up kernel or copy writes take
+        // no zero-fill
+        L.ilist = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(L.nint, 1), false, false);
         if (L.nred > 0)
             check_cuda(cudaMemcpyAsync(L.ilist, s.red, sizeof(uint32_t) * L.nred, cudaMemcpyDeviceToDevice, H.st),
                        "red list");
@@ -1390,13 +1424,13 @@ void setup_hierarchy(Handle &H, const double *phi0) {
                                        cudaMemcpyDeviceToDevice, H.st),
                        "black list");
         int64_t ng1 = std::max<int64_t>(L.ng, 1);
-        L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1);
+        L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1, false, false);
         L.gxi = (double *)dalloc(H, sizeof(double) * 3 * ng1);
         L.gn = (double *)dalloc(H, sizeof(double) * 3 * ng1);
-        L.gdt = (double *)dalloc(H, sizeof(double) * ng1);
-        L.geta = (double *)dalloc(H, sizeof(double) * ng1);
+        L.gdt = (double *)dalloc(H, sizeof(double) * ng1, false, false);
+        L.geta = (double *)dalloc(H, sizeof(double) * ng1, false, false);
         L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
-        L.gtmp = (double *)dalloc(H, sizeof(double) * ng1);
+        L.gtmp = (double *)dalloc(H, sizeof(double) * ng1, false, false);
         s.cnt = (unsigned long long *)dalloc(H, 2 * sizeof(unsigned long long), true);
         s.fband = (uint8_t *)dalloc(H, (size_t)L.nn, true);  // zero-filled
         LevelTab &t = tab[l];
@@ -1465,11 +1499,11 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
         int64_t nb1 = std::max<int64_t>(L.nb, 1);
-        L.bref = (int32_t *)dalloc(H, sizeof(int32_t) * 3 * nb1);
-        L.bw = (double *)dalloc(H, sizeof(double) * 3 * nb1);
-        L.bbuf = (double *)dalloc(H, sizeof(double) * 2 * nb1);
+        L.bref = (int32_t *)dalloc(H, sizeof(int32_t) * 3 * nb1, false, false);
+        L.bw = (double *)dalloc(H, sizeof(double) * 3 * nb1, false, false);
+        L.bbuf = (double *)dalloc(H, sizeof(double) * 2 * nb1, false, false);
         if (ell && L.nb > 0) {
-            L.ecnt = (uint8_t *)dalloc(H, (size_t)nb1);
+            L.ecnt = (uint8_t *)dalloc(H, (size_t)nb1, false, false);
             // expansion scratch with kExtCap slots; the resident copy keeps
             // only the slots the level's longest row needs (see round 3)
             L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1, true, false);
