@@ -407,29 +407,36 @@ __global__ void __launch_bounds__(kT) k_ghost_scatter(const uint32_t *__restrict
 
 // the block's norm partials (sum r^2, max|r|) of one row class, reduced in
 // a fixed order (warp shuffles, then the block's warps); every thread calls it
-__device__ __forceinline__ void block_partials(double s2, double mx, double *part, int64_t slot, bool interior) {
-    __shared__ double sh[2][kT / 32];
+// max |r| is carried as the bit pattern of a non-negative double: integer
+// order is numeric order there, so the maxima run on the integer pipe
+// (FP64 issue slots are the scarce resource)
+__device__ __forceinline__ long long abs_bits(double v) { return __double_as_longlong(v) & 0x7fffffffffffffffLL; }
+
+__device__ __forceinline__ void block_partials(double s2, long long mxb, double *part, int64_t slot, bool interior) {
+    __shared__ double sh[kT / 32];
+    __shared__ long long shm[kT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s2 += __shfl_down_sync(0xffffffffu, s2, o);
-        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        mxb = max(mxb, __shfl_down_sync(0xffffffffu, mxb, o));
     }
     if (lane == 0) {
-        sh[0][warp] = s2;
-        sh[1][warp] = mx;
+        sh[warp] = s2;
+        shm[warp] = mxb;
     }
     __syncthreads();
     if (warp == 0) {
         const int nw = blockDim.x >> 5;
-        s2 = lane < nw ? sh[0][lane] : 0.0;
-        mx = lane < nw ? sh[1][lane] : 0.0;
+        s2 = lane < nw ? sh[lane] : 0.0;
+        mxb = lane < nw ? shm[lane] : 0LL;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             s2 += __shfl_down_sync(0xffffffffu, s2, o);
-            mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+            mxb = max(mxb, __shfl_down_sync(0xffffffffu, mxb, o));
         }
         if (lane == 0) {
+            const double mx = __longlong_as_double(mxb);
             double *p = part + slot * 4;
             p[0] = interior ? s2 : 0.0;
             p[1] = interior ? 0.0 : s2;
@@ -499,12 +506,27 @@ __device__ void norm_tail(const NormTail &nt, const double *part) {
     __syncthreads();
     if (!last) return;  // uniform over the block
     __threadfence();
+    // eight partials per thread in flight at once (16-byte loads), then
+    // folded in slot order
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t i = threadIdx.x; i < nt.nparts; i += blockDim.x) {
-        a[0] += __ldcg(part + i * 4 + 0);
-        a[1] += __ldcg(part + i * 4 + 1);
-        a[2] = fmax(a[2], __ldcg(part + i * 4 + 2));
-        a[3] = fmax(a[3], __ldcg(part + i * 4 + 3));
+    const double2 *p2 = reinterpret_cast<const double2 *>(part);
+    constexpr int U = 8;
+    for (int64_t i0 = threadIdx.x; i0 < nt.nparts; i0 += (int64_t)U * blockDim.x) {
+        double2 lo[U], hi[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            const bool ok = i < nt.nparts;
+            lo[u] = ok ? __ldcg(p2 + 2 * i) : make_double2(0.0, 0.0);
+            hi[u] = ok ? __ldcg(p2 + 2 * i + 1) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[0] += lo[u].x;
+            a[1] += lo[u].y;
+            a[2] = fmax(a[2], hi[u].x);
+            a[3] = fmax(a[3], hi[u].y);
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -539,22 +561,33 @@ __device__ void norm_tail(const NormTail &nt, const double *part) {
 }
 
 // r = F - A u on the interior rows (eq. Laph); with part != null also the
-// block's norm partials (slot = block)
-template <int D, typename T>
+// block's norm partials (slot = block).  NPT rows per thread (strided by the
+// block size): with norm partials the squares are summed in the thread first
+// (one FMA per row), so the warp reduction's FP64 adds are shared by NPT rows
+template <int D, typename T, int NPT>
 __global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict__ ilist, int64_t nint,
                                                      const T *__restrict__ u, const T *__restrict__ F,
                                                      T *__restrict__ r, G2 G, double *__restrict__ part) {
-    double s2 = 0.0, mx = 0.0;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t X = i < nint ? ilist[i] : 0;
-    pdl_begin();
-    if (i < nint) {
-        const T v = residual_int<D, T>(X, u, F, G);
-        r[X] = v;
-        s2 = (double)v * (double)v;
-        mx = fabs((double)v);
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * NPT + threadIdx.x;
+    int64_t X[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = i0 + (int64_t)j * blockDim.x;
+        X[j] = i < nint ? ilist[i] : 0;
     }
-    if (part) block_partials(s2, mx, part, blockIdx.x, true);
+    pdl_begin();
+    double s2 = 0.0;
+    long long mxb = 0;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        if (i0 + (int64_t)j * blockDim.x < nint) {
+            const T v = residual_int<D, T>(X[j], u, F, G);
+            r[X[j]] = v;
+            s2 = fma((double)v, (double)v, s2);
+            mxb = max(mxb, abs_bits((double)v));
+        }
+    }
+    if (part) block_partials(s2, mxb, part, blockIdx.x, true);
 }
 
 // r = g - B u on the ghost rows (eq. BCh); norm partials at slot0 + block.
@@ -566,7 +599,8 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
                                                     int64_t ng, const T *__restrict__ u, const T *__restrict__ F,
                                                     T *__restrict__ r, G2 G, double *__restrict__ part,
                                                     int64_t slot0, NormTail nt) {
-    double s2 = 0.0, mx = 0.0;
+    double s2 = 0.0;
+    long long mxb = 0;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool on = g < ng;
     const int64_t X = on ? gidx[g] : 0;
@@ -578,9 +612,9 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
         const T v = F[X] - ghost_Bw<D, T>(X, code, w, u, G);
         r[X] = v;
         s2 = (double)v * (double)v;
-        mx = fabs((double)v);
+        mxb = abs_bits((double)v);
     }
-    if (part) block_partials(s2, mx, part, slot0 + blockIdx.x, false);
+    if (part) block_partials(s2, mxb, part, slot0 + blockIdx.x, false);
     if (nt.mode) norm_tail<Ctl>(nt, part);
 }
 
@@ -1303,20 +1337,24 @@ template <typename T>
 static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, double *part,
                              NormTail nt = NormTail{}) {
     const G2 G = g2_of(L);
-    const int bi = bs_for(H, L.nint), bg = bs_for(H, L.ng);
-    const int64_t ni = nblk(L.nint, bi);
+    // with norm partials, kNormRows interior rows per thread; with the norm
+    // tail, full-size ghost blocks (the last one reduces every partial)
+    constexpr int kNormRows = 4;
+    const int npt = part ? kNormRows : 1;
+    const int bi = bs_for(H, (L.nint + npt - 1) / npt), bg = nt.mode ? kT : bs_for(H, L.ng);
+    const int64_t ni = nblk(L.nint, bi * npt);
     const T *gw = Arr<T>::gw(L);
     nt.nparts = ni + nblk(L.ng, bg);
     if (L.d == 3) {
-        launch(H, "k_residual_int", k_residual_int<3, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
-               r, G, part);
+        launch(H, "k_residual_int", part ? k_residual_int<3, T, kNormRows> : k_residual_int<3, T, 1>, (unsigned)ni,
+               bi, (const uint32_t *)L.ilist, L.nint, u, F, r, G, part);
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<3, T, true> : k_residual_gh<3, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
                ni, nt);
     } else {
-        launch(H, "k_residual_int", k_residual_int<2, T>, (unsigned)ni, bi, (const uint32_t *)L.ilist, L.nint, u, F,
-               r, G, part);
+        launch(H, "k_residual_int", part ? k_residual_int<2, T, kNormRows> : k_residual_int<2, T, 1>, (unsigned)ni,
+               bi, (const uint32_t *)L.ilist, L.nint, u, F, r, G, part);
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<2, T, true> : k_residual_gh<2, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
