@@ -63,6 +63,9 @@ struct Level {
     // + o0, term-major (gw[term * ng + g]); FP32 copy for the mixed cycle
     double *gw = nullptr;
     float *gw32 = nullptr;
+    // restriction family of each coarse row (interior rows, then ghosts):
+    // bit k for fine neighbour k (levels >= 1)
+    uint32_t *fmask = nullptr;
     // band (SoA)
     uint32_t *bidx = nullptr;
     int32_t *bref = nullptr;  // 3 * nb, axis-major: >= 0 band position,

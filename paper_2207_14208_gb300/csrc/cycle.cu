@@ -204,8 +204,10 @@ __device__ __forceinline__ T residual_int(int64_t X, const T *u, const T *F, con
 // Restriction (Sec. 2.1 eq. coarseFW, Sec. 3.3.2): FW if all 3^d fine
 // neighbours belong to the coarse node's class family, else the FW-weight
 // average over the family members.  FW weights are the integers 1, 2, 4
-// (, 8) over 4^d; scaling by a power of two is exact.  All 3^d class and
-// residual loads are issued before any of them is used.
+// (, 8) over 4^d; scaling by a power of two is exact.  The family of each
+// coarse row is fixed by the classes, so it is computed once at set-up as a
+// bit mask (family_mask); the cycle loads the mask and the members'
+// residuals only (restrict_masked), all loads issued before any is used.
 template <int D>
 __device__ __forceinline__ bool restrict_nbr(const int ic[3], int k, const G2 &Gf, int64_t &Y) {
     const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
@@ -226,40 +228,86 @@ __device__ __forceinline__ void restrict_classes(const int ic[3], const uint8_t 
     }
 }
 
+// reciprocals 1/w (correctly rounded) of the family weight sums 1..64
+__device__ const double c_rcp64[65] = {
+    0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11,
+    1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21,
+    1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31,
+    1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40, 1.0 / 41,
+    1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51,
+    1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55, 1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61,
+    1.0 / 62, 1.0 / 63, 1.0 / 64};
+__device__ const float c_rcp32[65] = {
+    0.0f, 1.0f / 1, 1.0f / 2, 1.0f / 3, 1.0f / 4, 1.0f / 5, 1.0f / 6, 1.0f / 7, 1.0f / 8, 1.0f / 9, 1.0f / 10,
+    1.0f / 11, 1.0f / 12, 1.0f / 13, 1.0f / 14, 1.0f / 15, 1.0f / 16, 1.0f / 17, 1.0f / 18, 1.0f / 19,
+    1.0f / 20, 1.0f / 21, 1.0f / 22, 1.0f / 23, 1.0f / 24, 1.0f / 25, 1.0f / 26, 1.0f / 27, 1.0f / 28,
+    1.0f / 29, 1.0f / 30, 1.0f / 31, 1.0f / 32, 1.0f / 33, 1.0f / 34, 1.0f / 35, 1.0f / 36, 1.0f / 37,
+    1.0f / 38, 1.0f / 39, 1.0f / 40, 1.0f / 41, 1.0f / 42, 1.0f / 43, 1.0f / 44, 1.0f / 45, 1.0f / 46,
+    1.0f / 47, 1.0f / 48, 1.0f / 49, 1.0f / 50, 1.0f / 51, 1.0f / 52, 1.0f / 53, 1.0f / 54, 1.0f / 55,
+    1.0f / 56, 1.0f / 57, 1.0f / 58, 1.0f / 59, 1.0f / 60, 1.0f / 61, 1.0f / 62, 1.0f / 63, 1.0f / 64};
+
+// a / w for an integer weight sum 1 <= w <= 64: q = a y with y = 1/w from
+// the table, then one FMA correction with the exact remainder a - q w (a
+// divide subroutine costs tens of FP64 instructions)
+template <typename T>
+__device__ __forceinline__ T div_wsum(T a, int w) {
+    const T y = sizeof(T) == 8 ? (T)c_rcp64[w] : (T)c_rcp32[w];
+    const T q = a * y;
+    const T r = fma(-q, (T)w, a);
+    return fma(r, y, q);
+}
+
+// FW weight (1, 2, 4, 8) of fine neighbour k, and the bits of the
+// neighbours with weight w
+template <int D>
+__host__ __device__ constexpr int fw_weight(int k) {
+    return (k % 3 == 1 ? 2 : 1) * ((k / 3) % 3 == 1 ? 2 : 1) * ((D == 3 && k / 9 == 1) ? 2 : 1);
+}
+
+template <int D>
+__host__ __device__ constexpr uint32_t fw_bits(int w) {
+    uint32_t m = 0;
+    for (int k = 0; k < ((D == 3) ? 27 : 9); ++k)
+        if (fw_weight<D>(k) == w) m |= 1u << k;
+    return m;
+}
+
+// The restriction's class family of a coarse node as a bit mask, fixed once
+// the classes exist: bit k is set when fine neighbour k lies in the grid and
+// in the family (interior node: interior; ghost: ghost or inactive)
+template <int D>
+__device__ __forceinline__ uint32_t family_mask(const int ic[3], bool interior, const uint8_t *clsf, const G2 &Gf) {
+    uint8_t c[(D == 3) ? 27 : 9];
+    restrict_classes<D>(ic, clsf, Gf, c);
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < ((D == 3) ? 27 : 9); ++k) {
+        const bool fam = interior ? (c[k] == CL_INTERIOR) : (c[k] == CL_GHOST || c[k] == CL_INACTIVE);
+        m |= fam ? (1u << k) : 0u;
+    }
+    return m;
+}
+
+// restrict_with from the family mask: the same terms in the same order (a
+// non-member adds an exact zero), the weight sum from population counts
 template <int D, typename T>
-__device__ __forceinline__ T restrict_with(const int ic[3], bool interior, const uint8_t *c, const T *rf,
-                                           const G2 &Gf) {
+__device__ __forceinline__ T restrict_masked(const int ic[3], uint32_t mask, const T *rf, const G2 &Gf) {
     constexpr int NT = (D == 3) ? 27 : 9;
     T v[NT];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-        int64_t Y;
-        v[k] = restrict_nbr<D>(ic, k, Gf, Y) ? rf[Y] : T(0);
+        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
+        const int64_t Y = (int64_t)(2 * ic[0] + ox) + (int64_t)(2 * ic[1] + oy) * Gf.sy +
+                          (int64_t)(2 * ic[2] + oz) * Gf.sz;
+        v[k] = ((mask >> k) & 1u) ? rf[Y] : T(0);
     }
     T fw = T(0);
-    int wsum = 0;
-    bool all = true;
 #pragma unroll
-    for (int k = 0; k < NT; ++k) {
-        const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
-        const bool fam = interior ? (c[k] == CL_INTERIOR) : (c[k] == CL_GHOST || c[k] == CL_INACTIVE);
-        const int wi = (ox == 0 ? 2 : 1) * (oy == 0 ? 2 : 1) * ((D == 3 && oz == 0) ? 2 : 1);
-        all = all && fam;
-        if (fam) {
-            fw = fma((T)wi, v[k], fw);
-            wsum += wi;
-        }
-    }
-    if (all) return fw * (D == 3 ? T(1.0 / 64.0) : T(1.0 / 16.0));
-    return wsum > 0 ? fw / (T)wsum : T(0);
-}
-
-template <int D, typename T>
-__device__ __forceinline__ T restrict_at(const int ic[3], bool interior, const uint8_t *clsf, const T *rf,
-                                         const G2 &Gf) {
-    uint8_t c[(D == 3) ? 27 : 9];
-    restrict_classes<D>(ic, clsf, Gf, c);
-    return restrict_with<D, T>(ic, interior, c, rf, Gf);
+    for (int k = 0; k < NT; ++k) fw = fma((T)fw_weight<D>(k), v[k], fw);
+    if (mask == (1u << NT) - 1u) return fw * (D == 3 ? T(1.0 / 64.0) : T(1.0 / 16.0));
+    const int wsum = __popc(mask & fw_bits<D>(1)) + 2 * __popc(mask & fw_bits<D>(2)) +
+                     4 * __popc(mask & fw_bits<D>(4)) + 8 * __popc(mask & fw_bits<D>(8));
+    return wsum > 0 ? div_wsum<T>(fw, wsum) : T(0);
 }
 
 // multilinear prolongation at fine node iy (Sec. 2.1, 3.2, 3.3.2): the 2^k
@@ -657,11 +705,12 @@ __global__ void __launch_bounds__(kT) k_extend(const uint32_t *__restrict__ bidx
 }
 
 // F_c from the fine residual on coarse interior nodes (first iblocks) and
-// coarse ghosts; uc (the coarse correction) is zeroed on the same nodes
+// coarse ghosts; uc (the coarse correction) is zeroed on the same nodes.
+// fmask_c: the family masks of the coarse rows (interior rows, then ghosts)
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ ilist_c, int64_t nint_c,
                                                  unsigned iblocks, const uint32_t *__restrict__ gidx_c,
-                                                 int64_t ng_c, const uint8_t *__restrict__ clsf,
+                                                 int64_t ng_c, const uint32_t *__restrict__ fmask_c,
                                                  const T *__restrict__ rf, T *__restrict__ Fc, T *__restrict__ uc,
                                                  G2 Gf, G2 Gc) {
     const bool interior = blockIdx.x < iblocks;
@@ -669,14 +718,40 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
                                : (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
     const bool on = i < (interior ? nint_c : ng_c);
     const uint32_t Xc = on ? (interior ? ilist_c[i] : gidx_c[i]) : 0u;
+    const uint32_t mask = on ? fmask_c[interior ? i : nint_c + i] : 0u;
     int ic[3];
     coords(Xc, (uint32_t)Gc.n, D, ic);
-    uint8_t c[(D == 3) ? 27 : 9];
-    restrict_classes<D>(ic, clsf, Gf, c);
     pdl_begin();
     if (!on) return;
-    Fc[Xc] = restrict_with<D, T>(ic, interior, c, rf, Gf);
+    Fc[Xc] = restrict_masked<D, T>(ic, mask, rf, Gf);
     if (uc) uc[Xc] = T(0);
+}
+
+// family masks of every coarse level (one launch); level l of the table
+// holds the coarse rows of level l, its fine classes those of level l - 1
+struct FamTab {
+    const uint32_t *ilist, *gidx;
+    int64_t nint, ng;
+    const uint8_t *clsf;
+    G2 Gf, Gc;
+    uint32_t *mask;
+    int64_t blk;  // first block
+};
+
+template <int D>
+__global__ void __launch_bounds__(kT) k_family_masks(const FamTab *__restrict__ tab, int nl) {
+    pdl_begin();
+    int l = 0;
+    for (int q = 1; q < nl; ++q)
+        if ((int64_t)blockIdx.x >= tab[q].blk) l = q;
+    const FamTab &t = tab[l];
+    const int64_t i = ((int64_t)blockIdx.x - t.blk) * blockDim.x + threadIdx.x;
+    if (i >= t.nint + t.ng) return;
+    const bool interior = i < t.nint;
+    const uint32_t Xc = interior ? t.ilist[i] : t.gidx[i - t.nint];
+    int ic[3];
+    coords(Xc, (uint32_t)t.Gc.n, D, ic);
+    t.mask[i] = family_mask<D>(ic, interior, t.clsf, t.Gf);
 }
 
 template <int D, typename T>
@@ -859,6 +934,7 @@ struct TailLevel {
     int64_t nb;
     int ell_rounds;  // ceil(longest expansion / 8)
     const uint8_t *cls;
+    const uint32_t *fmask;  // restriction families of this level's rows
     T *u, *F, *r;
     const uint32_t *act;
     int64_t nact;
@@ -872,7 +948,7 @@ constexpr uint32_t kNone = 0xffffffffu;
 
 // per-level staged entries of one CTA's threads (dynamic shared memory)
 struct TailSlots {
-    uint32_t *red, *black, *gh, *band, *act;  // [level * kTailThreads + thread]
+    uint32_t *red, *black, *gh, *band, *act, *fmask;  // [level * kTailThreads + thread]
     uint16_t *gcode;
 };
 
@@ -976,7 +1052,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
     S.gh = tsm + 2 * n;
     S.band = tsm + 3 * n;
     S.act = tsm + 4 * n;
-    S.gcode = (uint16_t *)(tsm + 5 * n);
+    S.fmask = tsm + 5 * n;
+    S.gcode = (uint16_t *)(tsm + 6 * n);
     const int t = threadIdx.x;
     const int64_t i = tail_entry();  // the grid is one cluster
     for (int l = 0; l < nl; ++l) {
@@ -988,6 +1065,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
         S.gcode[k] = i < A.ng ? A.gcode[i] : (uint16_t)0;
         S.band[k] = i < A.nb ? A.bidx[i] : kNone;
         S.act[k] = i < A.nint ? A.ilist[i] : (i < A.nint + A.ng ? A.gidx[i - A.nint] : kNone);
+        S.fmask[k] = (A.fmask && i < A.nint + A.ng) ? A.fmask[i] : 0u;
     }
     __syncthreads();
     pdl_begin();  // the slots above come from fixed tables only
@@ -1002,7 +1080,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
             if (xc != kNone) {
                 int ic[3];
                 coords(xc, (uint32_t)B.g.n, D, ic);
-                B.F[xc] = restrict_at<D, T>(ic, i < B.nint, A.cls, A.r, A.g);
+                B.F[xc] = restrict_masked<D, T>(ic, S.fmask[(l + 1) * kTailThreads + t], A.r, A.g);
                 B.u[xc] = T(0);
             }
             tail_sync();
@@ -1051,7 +1129,7 @@ void tail_schedule(int l, int nl, int gamma, std::vector<uint8_t> &ops) {
     ops.push_back((uint8_t)l);
 }
 
-size_t tail_smem(int nl) { return (size_t)nl * kTailThreads * (5 * sizeof(uint32_t) + sizeof(uint16_t)); }
+size_t tail_smem(int nl) { return (size_t)nl * kTailThreads * (6 * sizeof(uint32_t) + sizeof(uint16_t)); }
 
 // The dynamic shared-memory limit is a property of the kernel for the whole
 // process, shared by every handle: it is always set to what the deepest
@@ -1193,6 +1271,7 @@ TailLevel<T> tail_level(Level &L) {
     t.nb = L.nb;
     t.ell_rounds = (L.ell_max + 7) / 8;
     t.cls = L.cls;
+    t.fmask = L.fmask;
     t.u = Arr<T>::u(L);
     t.F = Arr<T>::F(L);
     t.r = Arr<T>::r(L);
@@ -1397,10 +1476,10 @@ void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero
     const unsigned grid = ib + nblk(Lc.ng, bs);
     if (Lf.d == 3)
         launch(H, "k_restrict", k_restrict<3, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
-               (const uint32_t *)Lc.gidx, Lc.ng, (const uint8_t *)Lf.cls, rf, Fc, uc_zero, Gf, Gc);
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc);
     else
         launch(H, "k_restrict", k_restrict<2, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
-               (const uint32_t *)Lc.gidx, Lc.ng, (const uint8_t *)Lf.cls, rf, Fc, uc_zero, Gf, Gc);
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc);
 }
 
 template <typename T>
@@ -1493,6 +1572,27 @@ void setup_cycle(Handle &H) {
         GwTab *gt_d = (GwTab *)dalloc(H, sizeof(GwTab) * L, true);
         check_cuda(cudaMemcpyAsync(gt_d, gt.data(), sizeof(GwTab) * L, cudaMemcpyHostToDevice, H.st), "gw table");
         launch(H, "k_ghost_weights", k_ghost_weights, (unsigned)blocks, kT, (const GwTab *)gt_d, L, H.d, H.o.bc);
+    }
+    // restriction families of the coarse rows, every coarse level in one launch
+    if (L > 1) {
+        std::vector<FamTab> ft(L - 1);
+        int64_t fblocks = 0;
+        for (int l = 1; l < L; ++l) {
+            Level &C = H.L[l], &F = H.L[l - 1];
+            C.fmask = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(C.nint + C.ng, 1), false,
+                                         false);
+            ft[l - 1] = FamTab{C.ilist, C.gidx, C.nint, C.ng, F.cls, g2_of(F), g2_of(C), C.fmask, fblocks};
+            fblocks += nblk(C.nint + C.ng, kT);
+        }
+        if (fblocks > 0) {
+            FamTab *ft_d = (FamTab *)dalloc(H, sizeof(FamTab) * (L - 1), true);
+            check_cuda(cudaMemcpyAsync(ft_d, ft.data(), sizeof(FamTab) * (L - 1), cudaMemcpyHostToDevice, H.st),
+                       "family table");
+            if (H.d == 3)
+                launch(H, "k_family_masks", k_family_masks<3>, (unsigned)fblocks, kT, (const FamTab *)ft_d, L - 1);
+            else
+                launch(H, "k_family_masks", k_family_masks<2>, (unsigned)fblocks, kT, (const FamTab *)ft_d, L - 1);
+        }
     }
 
     // a level fits the tail if each of its lists has at most one entry per
