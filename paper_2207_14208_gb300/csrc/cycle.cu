@@ -1069,12 +1069,28 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
     }
     __syncthreads();
     pdl_begin();  // the slots above come from fixed tables only
+    // each phase helper appears once in the loop (one copy of its code: the
+    // tail runs every phase of a cycle once per launch, so its instruction
+    // fetches are mostly cold)
     for (int op = 0; op < nops; ++op) {
         const int kind = ops[2 * op], l = ops[2 * op + 1];
-        if (kind == kOpDown) {
-            const TailLevel<T> &A = tl[l], &B = tl[l + 1];
-            tail_smooth<D, T>(A, S, l, nu1);
-            tail_residual<D, T>(A, S, l);
+        const TailLevel<T> &A = tl[l];
+        if (kind == kOpUp) {  // the coarse correction into level l
+            const TailLevel<T> &B = tl[l + 1];
+            tail_extend<T>(B, S, l + 1, B.u);
+            const uint32_t xa = S.act[l * kTailThreads + t];
+            if (xa != kNone) {
+                int iy[3];
+                coords(xa, (uint32_t)A.g.n, D, iy);
+                A.u[xa] += prolong_at<D, T>(iy, B.u, B.g);
+            }
+            tail_sync();
+        }
+        if (kind != kOpCoarse) tail_smooth<D, T>(A, S, l, kind == kOpDown ? nu1 : nu2);
+        if (kind == kOpUp) continue;
+        tail_residual<D, T>(A, S, l);
+        if (kind == kOpDown) {  // extension, restriction to level l + 1
+            const TailLevel<T> &B = tl[l + 1];
             tail_extend<T>(A, S, l, A.r);
             const uint32_t xc = S.act[(l + 1) * kTailThreads + t];
             if (xc != kNone) {
@@ -1084,32 +1100,19 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
                 B.u[xc] = T(0);
             }
             tail_sync();
-        } else if (kind == kOpCoarse) {
-            const TailLevel<T> &C = tl[l];
-            tail_residual<D, T>(C, S, l);
-            if (i < C.nact) C.crhs[i] = (double)C.r[C.act[i]];
+        } else {  // coarsest: u += A^-1 r on the active rows
+            if (i < A.nact) A.crhs[i] = (double)A.r[A.act[i]];
             tail_sync();
             const int lane = t & 31;
             const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-            for (int64_t row = i >> 5; row < C.nact; row += nthr >> 5) {  // rows by warp, spread over the SMs
+            for (int64_t row = i >> 5; row < A.nact; row += nthr >> 5) {  // rows by warp, spread over the SMs
                 double sum = 0.0;
-                for (int64_t j = lane; j < C.nact; j += 32) sum = fma(C.Ainv[row * C.nact + j], C.crhs[j], sum);
+                for (int64_t j = lane; j < A.nact; j += 32) sum = fma(A.Ainv[row * A.nact + j], A.crhs[j], sum);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-                if (lane == 0) C.u[C.act[row]] += (T)sum;
+                if (lane == 0) A.u[A.act[row]] += (T)sum;
             }
             tail_sync();
-        } else {
-            const TailLevel<T> &A = tl[l], &B = tl[l + 1];
-            tail_extend<T>(B, S, l + 1, B.u);
-            const uint32_t xa = S.act[l * kTailThreads + t];
-            if (xa != kNone) {
-                int iy[3];
-                coords(xa, (uint32_t)A.g.n, D, iy);
-                A.u[xa] += prolong_at<D, T>(iy, B.u, B.g);
-            }
-            tail_sync();
-            tail_smooth<D, T>(A, S, l, nu2);
         }
     }
 }
