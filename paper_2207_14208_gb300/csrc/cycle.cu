@@ -963,27 +963,30 @@ __device__ __forceinline__ int64_t tail_entry() {
 }
 
 // band value of slot b with a fixed number of 8-term rounds: the term loads
-// do not wait for the row length
+// do not wait for the row length, and two rounds go together (their 16
+// indices and weights, then their 16 values), so a row of up to 16 terms
+// costs two dependent round trips
 template <typename T>
 __device__ __forceinline__ T extend_fixed(int64_t b, int rounds, const uint8_t *ecnt, const uint32_t *eg,
                                           const double *ew, int64_t nb, const T *a) {
     const int c = ecnt[b];
     T v = T(0);
-    for (int r0 = 0; r0 < rounds; ++r0) {
-        uint32_t e[8];
-        double w[8];
+    for (int r0 = 0; r0 < rounds; r0 += 2) {
+        uint32_t e[16];
+        double w[16];
+        const int nt = (rounds - r0 >= 2) ? 16 : 8;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 16; ++j) {
             const int64_t q = (int64_t)(r0 * 8 + j) * nb + b;
-            e[j] = eg[q];
-            w[j] = ew[q];
+            e[j] = j < nt ? eg[q] : 0u;
+            w[j] = j < nt ? ew[q] : 0.0;
         }
+        T x[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const bool p = r0 * 8 + j < c;
-            const T x = p ? a[e[j]] : T(0);
-            if (p) v = fma((T)w[j], x, v);
-        }
+        for (int j = 0; j < 16; ++j) x[j] = (r0 * 8 + j < c) ? a[e[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (r0 * 8 + j < c) v = fma((T)w[j], x[j], v);
     }
     return v;
 }
