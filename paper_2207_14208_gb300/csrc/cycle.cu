@@ -368,12 +368,15 @@ __device__ __forceinline__ T extend_at(int64_t b, const uint8_t *ecnt, const uin
     return v;
 }
 
-// the first round's map of band node b (read before the dependency wait)
+// the map of the first kEllFirst terms of band node b (read before the
+// dependency wait)
+constexpr int kEllFirst = 16;
+
 template <typename T>
 struct EllRound {
     int c;
-    uint32_t g[8];
-    T w[8];
+    uint32_t g[kEllFirst];
+    T w[kEllFirst];
 };
 
 template <typename T>
@@ -381,28 +384,28 @@ __device__ __forceinline__ void ell_first(int64_t b, const uint8_t *ecnt, const 
                                           int64_t nb, EllRound<T> &R) {
     R.c = ecnt[b];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < kEllFirst; ++j) {
         const bool p = j < R.c;
         R.g[j] = p ? eg[(int64_t)j * nb + b] : 0u;
         R.w[j] = p ? (T)ew[(int64_t)j * nb + b] : T(0);
     }
 }
 
-// extend_at with the first round's map already loaded; the same terms in
+// extend_at with the first terms' map already loaded; the same terms in
 // the same order
 template <typename T>
 __device__ __forceinline__ T extend_from(int64_t b, const EllRound<T> &R, const uint32_t *eg, const double *ew,
                                          int64_t nb, const T *a) {
     T v = T(0);
     {
-        T x[8];
+        T x[kEllFirst];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) x[j] = j < R.c ? a[R.g[j]] : T(0);
+        for (int j = 0; j < kEllFirst; ++j) x[j] = j < R.c ? a[R.g[j]] : T(0);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < kEllFirst; ++j)
             if (j < R.c) v = fma(R.w[j], x[j], v);
     }
-    for (int k0 = 8; k0 < R.c; k0 += 8) {
+    for (int k0 = kEllFirst; k0 < R.c; k0 += 8) {
         T w[8], x[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
