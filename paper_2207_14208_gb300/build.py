@@ -48,7 +48,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB_PATH
     os.makedirs(OUT_DIR, exist_ok=True)
     nv = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    # host code is not contracted into FMAs (gcc does so by default on
+    # aarch64): the host's stopping rule must round like the device's
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                      "-I", os.path.join(ROOT, "include")]
     if verbose:
         common += ["-Xptxas", "-v"]

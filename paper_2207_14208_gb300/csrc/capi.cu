@@ -458,6 +458,8 @@ int solve_host_loop(Handle &H, double *u_dev, double rtol, int max_cycles, int *
     enqueue_norms(H);
     double nr[4];
     fetch_norms(H, nr);
+    // sqrt(a^2 + b^2) rounded step by step, as the device's solve control
+    // does (the library's host code is built without FMA contraction)
     const double r0 = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1]);
     double rel = (r0 > 0.0) ? 1.0 : 0.0;
     int c = 0;

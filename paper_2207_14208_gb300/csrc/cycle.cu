@@ -168,6 +168,43 @@ __device__ __forceinline__ T ghost_B(int64_t X, uint16_t code, const T *gw, int6
     return ghost_Bw<D, T>(X, code, w, u, G);
 }
 
+// One stencil row of B u~ (the terms with outermost offset `row`: o2 in 3D,
+// o1 in 2D), for lanes that share a ghost; B u~ is the sum of the rows
+template <int D, typename T>
+__device__ __forceinline__ T ghost_row(int64_t X, uint16_t code, const T *gw, int64_t ng, int64_t g, const T *u,
+                                       const G2 &G, int row) {
+    const int64_t ox = (code & 1) ? 1 : -1;
+    const int64_t oy = (code & 2) ? G.sy : -G.sy;
+    const int64_t oz = (D == 3) ? ((code & 4) ? G.sz : -G.sz) : 0;
+    constexpr int NR = (D == 3) ? 9 : 3;
+    const int64_t base = X + (D == 3 ? row * oz : row * oy);
+    T w[NR], v[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int k = row * NR + j;
+        const int o0 = j % 3, o1 = (D == 3) ? j / 3 : 0;
+        const bool p = ghost_term<D>(code, k);
+        w[j] = p ? gw[(int64_t)k * ng + g] : T(0);
+        v[j] = p ? u[base + o1 * oy + o0 * ox] : T(0);
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc = fma(w[j], v[j], acc);
+    return acc;
+}
+
+// B u~ of the ghost shared by the four lanes of a group (lane sub < 3 takes
+// row sub, lane 3 none); every lane of the warp must call it; all four get
+// the sum
+template <int D, typename T>
+__device__ __forceinline__ T ghost_B4(bool on, int sub, int64_t X, uint16_t code, const T *gw, int64_t ng,
+                                      int64_t g, const T *u, const G2 &G) {
+    T part = (on && sub < 3) ? ghost_row<D, T>(X, code, gw, ng, g, u, G, sub) : T(0);
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    return part;
+}
+
 template <int D, typename T>
 __device__ __forceinline__ T nbr_sum(const T *u, int64_t X, const G2 &G) {
     T s = (u[X - 1] + u[X + 1]) + (u[X - G.sy] + u[X + G.sy]);
@@ -998,18 +1035,22 @@ template <int D, typename T>
 __device__ void tail_smooth(const TailLevel<T> &A, const TailSlots &S, int l, int nsteps) {
     const int t = threadIdx.x;
     const uint32_t xr = S.red[l * kTailThreads + t], xb = S.black[l * kTailThreads + t];
+    // ghosts four lanes each (group g = entry / 4, row = entry % 4)
     const uint32_t xg = S.gh[l * kTailThreads + t];
     const uint16_t code = S.gcode[l * kTailThreads + t];
-    const int64_t g = tail_entry();
+    const int64_t e = tail_entry(), g = e >> 2;
+    const int sub = (int)(e & 3);
+    const bool on = xg != kNone;
     for (int s = 0; s < nsteps; ++s) {
         if (xr != kNone) smooth_at<D, T>(xr, A.u, A.F, A.g);
         tail_sync();
         if (xb != kNone) smooth_at<D, T>(xb, A.u, A.F, A.g);
         tail_sync();
+        const T B = ghost_B4<D, T>(on, sub, xg, code, A.gw, A.ng, g, A.u, A.g);
         T gv = T(0);
-        if (xg != kNone) gv = fma((T)A.gdt[g], A.F[xg] - ghost_B<D, T>(xg, code, A.gw, A.ng, g, A.u, A.g), A.u[xg]);
+        if (on && sub == 0) gv = fma((T)A.gdt[g], A.F[xg] - B, A.u[xg]);
         tail_sync();
-        if (xg != kNone) A.u[xg] = gv;
+        if (on && sub == 0) A.u[xg] = gv;
         tail_sync();
     }
 }
@@ -1019,13 +1060,13 @@ __device__ void tail_residual(const TailLevel<T> &A, const TailSlots &S, int l) 
     const int t = threadIdx.x;
     const int64_t i = tail_entry();
     const uint32_t xa = S.act[l * kTailThreads + t];
-    if (xa != kNone) {
-        if (i < A.nint) A.r[xa] = residual_int<D, T>(xa, A.u, A.F, A.g);
-        else {
-            const int64_t g = i - A.nint;
-            A.r[xa] = A.F[xa] - ghost_B<D, T>(xa, A.gcode[g], A.gw, A.ng, g, A.u, A.g);
-        }
-    }
+    if (xa != kNone && i < A.nint) A.r[xa] = residual_int<D, T>(xa, A.u, A.F, A.g);
+    // ghost rows four lanes each, as in the relaxation
+    const uint32_t xg = S.gh[l * kTailThreads + t];
+    const int64_t g = i >> 2;
+    const int sub = (int)(i & 3);
+    const T B = ghost_B4<D, T>(xg != kNone, sub, xg, S.gcode[l * kTailThreads + t], A.gw, A.ng, g, A.u, A.g);
+    if (xg != kNone && sub == 0) A.r[xg] = A.F[xg] - B;
     tail_sync();
 }
 
@@ -1067,8 +1108,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
         const int k = l * kTailThreads + t;
         S.red[k] = i < A.nred ? A.ilist[i] : kNone;
         S.black[k] = i < A.nint - A.nred ? A.ilist[A.nred + i] : kNone;
-        S.gh[k] = i < A.ng ? A.gidx[i] : kNone;
-        S.gcode[k] = i < A.ng ? A.gcode[i] : (uint16_t)0;
+        S.gh[k] = (i >> 2) < A.ng ? A.gidx[i >> 2] : kNone;  // four lanes per ghost
+        S.gcode[k] = (i >> 2) < A.ng ? A.gcode[i >> 2] : (uint16_t)0;
         S.band[k] = i < A.nb ? A.bidx[i] : kNone;
         S.act[k] = i < A.nint ? A.ilist[i] : (i < A.nint + A.ng ? A.gidx[i - A.nint] : kNone);
         S.fmask[k] = (A.fmask && i < A.nint + A.ng) ? A.fmask[i] : 0u;
@@ -1605,12 +1646,13 @@ void setup_cycle(Handle &H) {
     }
 
     // a level fits the tail if each of its lists has at most one entry per
-    // thread of the cluster (and at most kTailNodes) and its extension is
-    // expanded; the coarsest level also needs at most kTailCoarse unknowns
+    // thread of the cluster (four threads per ghost; at most kTailNodes) and
+    // its extension is expanded; the coarsest level also needs at most
+    // kTailCoarse unknowns
     H.tail_start = -1;
     if (H.o.ordering != BCMG_ORDER_RB) return;  // the tail runs red-black sweeps
     auto fits = [&](const Level &A, int64_t lim) {
-        return A.nint + A.ng <= lim && A.nb <= lim && (A.nb == 0 || A.ecnt != nullptr);
+        return A.nint + A.ng <= lim && 4 * A.ng <= lim && A.nb <= lim && (A.nb == 0 || A.ecnt != nullptr);
     };
     auto first_level = [&](int64_t lim) {
         int lt = L - 1;
