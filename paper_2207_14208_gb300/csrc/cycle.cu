@@ -68,7 +68,9 @@ int bs_for(const Handle &H, int64_t n) {
 // a kernel therefore reads only the level tables that are fixed once the
 // hierarchy exists (node lists, ghost codes, weights and steps, class bytes,
 // extension maps; creation ends with a stream synchronisation), never u, F,
-// r or other data a cycle writes, and writes nothing.
+// r or other data a cycle writes, and writes nothing -- except the ghost
+// rows of a residual, whose predecessor is the interior rows of the same
+// residual (k_residual_gh).
 __device__ __forceinline__ void pdl_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -686,7 +688,7 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
                                                     const uint16_t *__restrict__ gcode, const T *__restrict__ gw,
                                                     int64_t ng, const T *__restrict__ u, const T *__restrict__ F,
                                                     T *__restrict__ r, G2 G, double *__restrict__ part,
-                                                    int64_t slot0, NormTail nt) {
+                                                    int64_t slot0, NormTail nt, int early) {
     double s2 = 0.0;
     long long mxb = 0;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -695,7 +697,12 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
     const uint16_t code = on ? gcode[g] : 0;
     T w[(D == 3) ? 27 : 9];
     ghost_weights<D, T>(code, gw, ng, on ? g : 0, w);
-    pdl_begin();
+    // early: the predecessor is the interior-row kernel of the same
+    // residual, which neither reads nor writes what the ghost rows touch; u
+    // and F were written by grids before it, which are complete once this
+    // grid runs.  So the ghost rows (and their partials) are computed while
+    // the interior rows still run; only the final reduction waits for them.
+    if (!early) pdl_begin();
     if (on) {
         const T v = F[X] - ghost_Bw<D, T>(X, code, w, u, G);
         r[X] = v;
@@ -703,6 +710,7 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
         mxb = abs_bits((double)v);
     }
     if (part) block_partials(s2, mxb, part, slot0 + blockIdx.x, false);
+    if (early) pdl_begin();
     if (nt.mode) norm_tail<Ctl>(nt, part);
 }
 
@@ -1480,14 +1488,14 @@ static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, 
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<3, T, true> : k_residual_gh<3, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
-               ni, nt);
+               ni, nt, (int)(ni > 0));
     } else {
         launch(H, "k_residual_int", part ? k_residual_int<2, T, kNormRows> : k_residual_int<2, T, 1>, (unsigned)ni,
                bi, (const uint32_t *)L.ilist, L.nint, u, F, r, G, part);
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<2, T, true> : k_residual_gh<2, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
-               ni, nt);
+               ni, nt, (int)(ni > 0));
     }
     return ni + nblk(L.ng, bg);
 }
