@@ -185,9 +185,12 @@ constexpr int kExtCap = 32;  // terms per band node of the expanded extension
 template <typename T> void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps);
 template <typename T> void residual(Handle &H, Level &L, const T *u, const T *F, T *r);
 template <typename T> void extend(Handle &H, Level &L, T *a);
+// early_ok: the fine level's residual (and band extension) are the launches
+// right before
 template <typename T>
-void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero);
-template <typename T> void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf);
+void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero, bool early_ok = false);
+// early_ok: the coarse correction's extension is the launch right before
+template <typename T> void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf, bool early_ok = false);
 template <typename T> void coarsest_correct(Handle &H, Level &L, T *u, const T *F);
 // finest-level residual r = F - A u and its four norms (out4, device);
 // ctl 1 / 2 also enqueue the solve's start / per-cycle check on cond

@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
                                                  unsigned iblocks, const uint32_t *__restrict__ gidx_c,
                                                  int64_t ng_c, const uint32_t *__restrict__ fmask_c,
                                                  const T *__restrict__ rf, T *__restrict__ Fc, T *__restrict__ uc,
-                                                 G2 Gf, G2 Gc) {
+                                                 G2 Gf, G2 Gc, int early) {
     const bool interior = blockIdx.x < iblocks;
     const int64_t i = interior ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
                                : (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
@@ -769,10 +769,16 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
     const uint32_t mask = on ? fmask_c[interior ? i : nint_c + i] : 0u;
     int ic[3];
     coords(Xc, (uint32_t)Gc.n, D, ic);
-    pdl_begin();
-    if (!on) return;
-    Fc[Xc] = restrict_masked<D, T>(ic, mask, rf, Gf);
-    if (uc) uc[Xc] = T(0);
+    // early (the predecessor is the fine level's ghost residual or band
+    // extension): coarse interior rows read fine interior residuals only,
+    // which complete grids wrote, and are restricted before the wait
+    const bool now = early && interior;
+    if (!now) pdl_begin();
+    if (on) {
+        Fc[Xc] = restrict_masked<D, T>(ic, mask, rf, Gf);
+        if (uc) uc[Xc] = T(0);
+    }
+    if (now) pdl_begin();
 }
 
 // family masks of every coarse level (one launch); level l of the table
@@ -802,20 +808,38 @@ __global__ void __launch_bounds__(kT) k_family_masks(const FamTab *__restrict__ 
     t.mask[i] = family_mask<D>(ic, interior, t.clsf, t.Gf);
 }
 
+// early (the predecessor is the coarse correction's extension, which writes
+// coarse band values only): a fine row none of whose coarse corners is
+// inactive (so none is a band node) reads only values of complete grids, and
+// is prolonged before the dependency wait; the others after it
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_prolong(const uint32_t *__restrict__ ilist, int64_t nint, unsigned iblocks,
                                                 const uint32_t *__restrict__ gidx, int64_t ng,
-                                                const T *__restrict__ ec, T *__restrict__ uf, G2 Gf, G2 Gc) {
+                                                const T *__restrict__ ec, T *__restrict__ uf, G2 Gf, G2 Gc,
+                                                const uint8_t *__restrict__ clsc, int early) {
     const bool inner = blockIdx.x < iblocks;
     const int64_t i = inner ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
                             : (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
     const bool on = i < (inner ? nint : ng);
     const uint32_t X = on ? (inner ? ilist[i] : gidx[i]) : 0u;
-    pdl_begin();
-    if (!on) return;
     int iy[3];
     coords(X, (uint32_t)Gf.n, D, iy);
-    uf[X] += prolong_at<D, T>(iy, ec, Gc);
+    bool now = false;
+    if (early && on) {
+        const int t0 = iy[0] & 1, t1 = iy[1] & 1, t2 = (D == 3) ? (iy[2] & 1) : 0;
+        const int64_t C0 = (int64_t)(iy[0] >> 1) + (int64_t)(iy[1] >> 1) * Gc.sy +
+                           (D == 3 ? (int64_t)(iy[2] >> 1) * Gc.sz : 0);
+        bool band = false;
+#pragma unroll
+        for (int k = 0; k < ((D == 3) ? 8 : 4); ++k) {
+            const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
+            if (b0 <= t0 && b1 <= t1 && b2 <= t2) band |= clsc[C0 + b0 + b1 * Gc.sy + b2 * Gc.sz] == CL_INACTIVE;
+        }
+        now = !band;
+    }
+    if (now) uf[X] += prolong_at<D, T>(iy, ec, Gc);
+    pdl_begin();
+    if (on && !now) uf[X] += prolong_at<D, T>(iy, ec, Gc);
 }
 
 template <typename T>
@@ -1302,11 +1326,11 @@ void vcycle_t(Handle &H, int l, T *u) {
     smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu1);
     residual<T>(H, A, u, Arr<T>::F(A), Arr<T>::r(A));
     extend<T>(H, A, Arr<T>::r(A));
-    restrict_to<T>(H, A, B, Arr<T>::r(A), Arr<T>::F(B), Arr<T>::u(B));
+    restrict_to<T>(H, A, B, Arr<T>::r(A), Arr<T>::F(B), Arr<T>::u(B), true);
     const int gamma = H.o.cycle == BCMG_CYCLE_W ? 2 : 1;
     for (int g = 0; g < gamma; ++g) vcycle_t<T>(H, l + 1, Arr<T>::u(B));
     extend<T>(H, B, Arr<T>::u(B));
-    prolong<T>(H, A, B, Arr<T>::u(B), u);
+    prolong<T>(H, A, B, Arr<T>::u(B), u, true);
     smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu2);
 }
 
@@ -1527,31 +1551,38 @@ void extend(Handle &H, Level &L, T *a) {
 }
 
 template <typename T>
-void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero) {
+void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero, bool early_ok) {
     const G2 Gf = g2_of(Lf), Gc = g2_of(Lc);
     const int bs = bs_for(H, Lc.nint + Lc.ng);
     const unsigned ib = nblk(Lc.nint, bs);
     const unsigned grid = ib + nblk(Lc.ng, bs);
+    // in the cycle the fine residual's interior rows are at least two
+    // launches back when the level has ghost rows or a band
+    const int early = (int)(early_ok && (Lf.ng > 0 || Lf.nb > 0));
     if (Lf.d == 3)
         launch(H, "k_restrict", k_restrict<3, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
-               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc);
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc, early);
     else
         launch(H, "k_restrict", k_restrict<2, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
-               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc);
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc, early);
 }
 
 template <typename T>
-void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf) {
+void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf, bool early_ok) {
     const G2 Gf = g2_of(Lf), Gc = g2_of(Lc);
     const int bs = bs_for(H, Lf.nint + Lf.ng);
     const unsigned ib = nblk(Lf.nint, bs);
     const unsigned grid = ib + nblk(Lf.ng, bs);
+    // the cycle extends the coarse correction right before (when the
+    // coarse level has a band); a caller's own prolongation has no
+    // predecessor on the library stream
+    const int early = (int)(early_ok && Lc.nb > 0);
     if (Lf.d == 3)
         launch(H, "k_prolong", k_prolong<3, T>, grid, bs, (const uint32_t *)Lf.ilist, Lf.nint, ib,
-               (const uint32_t *)Lf.gidx, Lf.ng, ec, uf, Gf, Gc);
+               (const uint32_t *)Lf.gidx, Lf.ng, ec, uf, Gf, Gc, (const uint8_t *)Lc.cls, early);
     else
         launch(H, "k_prolong", k_prolong<2, T>, grid, bs, (const uint32_t *)Lf.ilist, Lf.nint, ib,
-               (const uint32_t *)Lf.gidx, Lf.ng, ec, uf, Gf, Gc);
+               (const uint32_t *)Lf.gidx, Lf.ng, ec, uf, Gf, Gc, (const uint8_t *)Lc.cls, early);
 }
 
 template <typename T>
@@ -1725,14 +1756,14 @@ void set_interior_rhs(Handle &H, Level &L, const double *f, double *F) {
 template void smooth<double>(Handle &, Level &, double *, const double *, int);
 template void residual<double>(Handle &, Level &, const double *, const double *, double *);
 template void extend<double>(Handle &, Level &, double *);
-template void restrict_to<double>(Handle &, Level &, Level &, const double *, double *, double *);
-template void prolong<double>(Handle &, Level &, Level &, const double *, double *);
+template void restrict_to<double>(Handle &, Level &, Level &, const double *, double *, double *, bool);
+template void prolong<double>(Handle &, Level &, Level &, const double *, double *, bool);
 template void coarsest_correct<double>(Handle &, Level &, double *, const double *);
 template void smooth<float>(Handle &, Level &, float *, const float *, int);
 template void residual<float>(Handle &, Level &, const float *, const float *, float *);
 template void extend<float>(Handle &, Level &, float *);
-template void restrict_to<float>(Handle &, Level &, Level &, const float *, float *, float *);
-template void prolong<float>(Handle &, Level &, Level &, const float *, float *);
+template void restrict_to<float>(Handle &, Level &, Level &, const float *, float *, float *, bool);
+template void prolong<float>(Handle &, Level &, Level &, const float *, float *, bool);
 template void coarsest_correct<float>(Handle &, Level &, float *, const float *);
 
 }  // namespace bcmg
