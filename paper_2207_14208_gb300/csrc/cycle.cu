@@ -837,7 +837,10 @@ __global__ void __launch_bounds__(kT) k_prolong(const uint32_t *__restrict__ ili
         }
         now = !band;
     }
-    if (now) uf[X] += prolong_at<D, T>(iy, ec, Gc);
+    // warp-uniform (no lane does its FP64 work twice): early only when the
+    // whole warp can go
+    now = __all_sync(0xffffffffu, now || !on) && early;
+    if (now && on) uf[X] += prolong_at<D, T>(iy, ec, Gc);
     pdl_begin();
     if (on && !now) uf[X] += prolong_at<D, T>(iy, ec, Gc);
 }
