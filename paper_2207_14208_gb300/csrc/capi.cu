@@ -37,26 +37,42 @@ void check_cuda(cudaError_t e, const char *what) {
 // device's stream-ordered pool: the blocks of a destroyed handle, or of a
 // finished set-up's scratch, enter the cache only after every stream that
 // used them has been synchronised, so any stream may take them, and
-// repeated creations of the same hierarchy (a solve service, a benchmark
-// loop) need no driver call at all.  At most kCacheMax bytes are cached;
-// when the pool cannot allocate, the cache goes back to the driver and the
-// allocation is retried once.
+// repeated creations of the same hierarchy (a benchmark loop, a batch of
+// equal problems) need no driver call at all.  A miss returns the device's
+// cached blocks to the pool first (stream-ordered frees), so that a mix of
+// sizes reuses the pool's memory instead of growing it around blocks that
+// no one takes.  At most kCacheMax bytes are cached; when the pool cannot
+// allocate, the cache goes back to the driver and the allocation is retried
+// once.
 constexpr size_t kChunk = 4u << 20;
 constexpr size_t kSmallAlloc = 256u << 10;
-constexpr size_t kCacheMax = 16ull << 30;
+constexpr size_t kCacheMax = 4ull << 30;
 
 std::mutex g_cache_mu;
 std::multimap<std::pair<int, size_t>, void *> g_cache;
 size_t g_cache_bytes = 0;
 
-void *cache_take(int dev, size_t bytes) {
-    std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto it = g_cache.find({dev, bytes});
-    if (it == g_cache.end()) return nullptr;
-    void *p = it->second;
-    g_cache.erase(it);
-    g_cache_bytes -= bytes;
-    return p;
+// a block of exactly this size, else nullptr after the device's cached
+// blocks went back to the pool (freed on st, where the caller allocates next)
+void *cache_take(int dev, size_t bytes, cudaStream_t st) {
+    std::vector<void *> back;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_cache.find({dev, bytes});
+        if (it != g_cache.end()) {
+            void *p = it->second;
+            g_cache.erase(it);
+            g_cache_bytes -= bytes;
+            return p;
+        }
+        for (auto jt = g_cache.lower_bound({dev, 0}); jt != g_cache.end() && jt->first.first == dev;) {
+            back.push_back(jt->second);
+            g_cache_bytes -= jt->first.second;
+            jt = g_cache.erase(jt);
+        }
+    }
+    for (void *p : back) cudaFreeAsync(p, st);
+    return nullptr;
 }
 
 // p is idle on every stream; past the cap it is freed on st instead
@@ -89,7 +105,7 @@ void cache_drain() {
 }
 
 void *raw_alloc(Handle &H, size_t bytes, bool temp) {
-    void *p = cache_take(H.dev, bytes);
+    void *p = cache_take(H.dev, bytes, H.st);
     if (!p) {
         cudaError_t e = cudaMallocAsync(&p, bytes, H.st);
         if (e != cudaSuccess) {
@@ -195,6 +211,47 @@ void pinned_put(void *p) {
     g_pin_free.push_back(p);
 }
 
+// The side stream of a creation (with its fork and join events) is only
+// busy while the hierarchy is built: it comes from a process-wide pool per
+// device and goes back once creation has synchronised, so that handles
+// created and destroyed at a high rate make no stream or event calls for it.
+struct SideLane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+std::mutex g_side_mu;
+std::vector<std::pair<int, SideLane>> g_side_free;
+
+SideLane side_get(int dev) {
+    {
+        std::lock_guard<std::mutex> lk(g_side_mu);
+        for (size_t i = 0; i < g_side_free.size(); ++i)
+            if (g_side_free[i].first == dev) {
+                SideLane s = g_side_free[i].second;
+                g_side_free.erase(g_side_free.begin() + (int64_t)i);
+                return s;
+            }
+    }
+    SideLane s;
+    check_cuda(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking), "cudaStreamCreate");
+    check_cuda(cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming), "cudaEventCreate");
+    check_cuda(cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming), "cudaEventCreate");
+    return s;
+}
+
+// the lane is idle (its stream synchronised)
+void side_put(int dev, Handle &H) {
+    if (!H.st2) return;
+    SideLane s;
+    s.st = H.st2;
+    s.fork = H.ev_fork;
+    s.join = H.ev_join;
+    H.st2 = nullptr;
+    H.ev_fork = H.ev_join = nullptr;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    g_side_free.push_back({dev, s});
+}
+
 void destroy(Handle *H) {
     if (!H) return;
     if (H->st2) cudaStreamSynchronize(H->st2);
@@ -212,9 +269,7 @@ void destroy(Handle *H) {
     pinned_put(H->nhost);
     pinned_put(H->sing_host);
     for (cudaEvent_t e : H->pev) cudaEventDestroy(e);
-    if (H->ev_fork) cudaEventDestroy(H->ev_fork);
-    if (H->ev_join) cudaEventDestroy(H->ev_join);
-    if (H->st2) cudaStreamDestroy(H->st2);
+    side_put(H->dev, *H);  // synchronised above
     if (H->ev_in) cudaEventDestroy(H->ev_in);
     if (H->ev_out) cudaEventDestroy(H->ev_out);
     if (H->st) cudaStreamDestroy(H->st);
@@ -548,9 +603,12 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
             H->pev.resize(4 * (size_t)(H->o.nu1 + H->o.nu2), nullptr);
             for (auto &e : H->pev) check_cuda(cudaEventCreate(&e), "cudaEventCreate(profile)");
         }
-        check_cuda(cudaStreamCreateWithFlags(&H->st2, cudaStreamNonBlocking), "cudaStreamCreate");
-        check_cuda(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
-        check_cuda(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming), "cudaEventCreate");
+        {
+            SideLane sl = side_get(H->dev);
+            H->st2 = sl.st;
+            H->ev_fork = sl.fork;
+            H->ev_join = sl.join;
+        }
         H->sing_host = (int *)pinned_get();
         *H->sing_host = 0;
         enter(*H);
@@ -571,6 +629,7 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         for (auto &L : H->L) L.phi = nullptr;
         check_cuda(cudaStreamWaitEvent(H->st, H->ev_join, 0), "join wait");  // the coarsest inverse
         check_cuda(cudaStreamSynchronize(H->st), "create sync");
+        side_put(H->dev, *H);  // the join is complete: the side lane is idle
         if (*H->sing_host) throw Error{BCMG_EGEOM, "coarsest system is singular"};
         free_temps(*H);
         leave(*H);
