@@ -627,6 +627,9 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
         H->sdev = (SolveState *)dalloc(*H, sizeof(SolveState));
         set_interior_rhs(*H, L0, f_dev, L0.F);
         for (auto &L : H->L) L.phi = nullptr;
+        // the solve graph is captured here, while the device still works on
+        // the set-up (capture records launches, it runs nothing)
+        if (H->o.use_graph && !H->o.profile) H->sgraph = build_solve_graph(*H);
         check_cuda(cudaStreamWaitEvent(H->st, H->ev_join, 0), "join wait");  // the coarsest inverse
         check_cuda(cudaStreamSynchronize(H->st), "create sync");
         side_put(H->dev, *H);  // the join is complete: the side lane is idle
