@@ -106,6 +106,17 @@ class ClockSampler:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait (at most 5 s) for the first sample: nvidia-smi's start-up
+        # takes driver locks that would otherwise stall the first timed steps
+        t0 = time.time()
+        while time.time() - t0 < 5.0:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:

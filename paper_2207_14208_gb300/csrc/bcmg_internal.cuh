@@ -82,10 +82,12 @@ struct Level {
     uint32_t *boxidx = nullptr;
     // arrays
     double *u = nullptr, *F = nullptr, *r = nullptr;
+    double *Fs = nullptr;  // h^2 F / (2d + c h^2) on the interior rows (smoothing)
     double *gtmp = nullptr;  // ng
     double *bbuf = nullptr;  // 2 * nb
     // FP32 arrays of the mixed-precision inner cycle (correction equation)
     float *u32 = nullptr, *F32 = nullptr, *r32 = nullptr, *gtmp32 = nullptr, *bbuf32 = nullptr;
+    float *Fs32 = nullptr;
     // coarsest
     uint32_t *act = nullptr;
     double *Ainv = nullptr;
@@ -182,13 +184,16 @@ constexpr int kExtCap = 32;  // terms per band node of the expanded extension
 
 // ---- cycle kernels (cycle.cu); T = double (FP64) or float (inner cycles of
 // the mixed-precision refinement) ----------------------------------------
-template <typename T> void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps);
+// Fs: the level's scaled right-hand side (the cycle), or null (a caller's F)
+template <typename T> void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs = nullptr);
 template <typename T> void residual(Handle &H, Level &L, const T *u, const T *F, T *r);
 template <typename T> void extend(Handle &H, Level &L, T *a);
 // early_ok: the fine level's residual (and band extension) are the launches
 // right before
 template <typename T>
-void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero, bool early_ok = false);
+// Fsc: where the coarse interior rows' scaled right-hand side goes (or null)
+void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero, bool early_ok = false,
+                 T *Fsc = nullptr);
 // early_ok: the coarse correction's extension is the launch right before
 template <typename T> void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec, T *uf, bool early_ok = false);
 template <typename T> void coarsest_correct(Handle &H, Level &L, T *u, const T *F);

@@ -797,11 +797,12 @@ int bcmg_footprint_estimate(int dim, int64_t N, const bcmg_opts *opts, int64_t *
     bcmg_opts o;
     if (opts) o = *opts;
     else bcmg_default_opts(&o);
-    // dense per-level arrays (class byte, u, F, r; FP32 u, F, r for the mixed
-    // path) over the levels the coarsening rule allows, doubled to cover the
-    // compacted lists (ghost weights, expanded extension), which hold far
-    // fewer entries than the grid but more bytes per entry
-    const double per_node = 1.0 + 3.0 * 8.0 + (o.precision == BCMG_PREC_MIXED ? 3.0 * 4.0 : 0.0);
+    // dense per-level arrays (class byte, u, F, its scaled copy, r; FP32
+    // u, F, scaled F, r for the mixed path) over the levels the coarsening
+    // rule allows, doubled to cover the compacted lists (ghost weights,
+    // expanded extension), which hold far fewer entries than the grid but
+    // more bytes per entry
+    const double per_node = 1.0 + 4.0 * 8.0 + (o.precision == BCMG_PREC_MIXED ? 4.0 * 4.0 : 0.0);
     double total = 0.0;
     int64_t Nl = N;
     for (int l = 0; l < std::max(o.max_levels, 1); ++l) {

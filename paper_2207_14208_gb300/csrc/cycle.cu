@@ -224,6 +224,20 @@ __device__ __forceinline__ void smooth_at(int64_t X, T *u, const T *F, const G2 
     u[X] = fma((T)G.h2, F[X], s) * (T)G.inv_diag;
 }
 
+// the same update from Fs = h^2 F / (2d + c h^2), kept beside F on the
+// cycle's interior rows: s / diag + Fs, one FP64 instruction fewer
+template <int D, typename T>
+__device__ __forceinline__ void smooth_at_s(int64_t X, T *u, const T *Fs, const G2 &G) {
+    const T s = nbr_sum<D, T>(u, X, G);
+    u[X] = fma(s, (T)G.inv_diag, Fs[X]);
+}
+
+// Fs of an interior row from its F
+template <typename T>
+__device__ __forceinline__ T scaled_rhs(T f, const G2 &G) {
+    return (T)G.h2 * f * (T)G.inv_diag;
+}
+
 // fictitious-time relaxation of ghost g (eq. rel with eq. DtauOptTheta)
 template <int D, typename T>
 __device__ __forceinline__ T ghost_new(int64_t g, const uint32_t *gidx, const uint16_t *gcode, const T *gw,
@@ -462,12 +476,17 @@ __device__ __forceinline__ T extend_from(int64_t b, const EllRound<T> &R, const 
 
 // ------------------------------------------------------------ grid kernels
 template <int D, typename T>
+// Fs != null: the update from the scaled right-hand side (the cycle's
+// levels keep it); else from F (a caller's own F)
 __global__ void __launch_bounds__(kT) k_smooth(const uint32_t *__restrict__ list, int64_t n, T *u,
-                                               const T *__restrict__ F, G2 G) {
+                                               const T *__restrict__ F, const T *__restrict__ Fs, G2 G) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t X = i < n ? list[i] : 0u;
     pdl_begin();
-    if (i < n) smooth_at<D, T>(X, u, F, G);
+    if (i < n) {
+        if (Fs) smooth_at_s<D, T>(X, u, Fs, G);
+        else smooth_at<D, T>(X, u, F, G);
+    }
 }
 
 template <int D, typename T>
@@ -760,7 +779,7 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
                                                  unsigned iblocks, const uint32_t *__restrict__ gidx_c,
                                                  int64_t ng_c, const uint32_t *__restrict__ fmask_c,
                                                  const T *__restrict__ rf, T *__restrict__ Fc, T *__restrict__ uc,
-                                                 G2 Gf, G2 Gc, int early) {
+                                                 T *__restrict__ Fsc, G2 Gf, G2 Gc, int early) {
     const bool interior = blockIdx.x < iblocks;
     const int64_t i = interior ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
                                : (int64_t)(blockIdx.x - iblocks) * blockDim.x + threadIdx.x;
@@ -775,7 +794,9 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
     const bool now = early && interior;
     if (!now) pdl_begin();
     if (on) {
-        Fc[Xc] = restrict_masked<D, T>(ic, mask, rf, Gf);
+        const T fc = restrict_masked<D, T>(ic, mask, rf, Gf);
+        Fc[Xc] = fc;
+        if (Fsc && interior) Fsc[Xc] = scaled_rhs<T>(fc, Gc);
         if (uc) uc[Xc] = T(0);
     }
     if (now) pdl_begin();
@@ -1011,6 +1032,7 @@ struct TailLevel {
     const uint8_t *cls;
     const uint32_t *fmask;  // restriction families of this level's rows
     T *u, *F, *r;
+    T *Fs;  // scaled right-hand side of the interior rows
     const uint32_t *act;
     int64_t nact;
     const double *Ainv;
@@ -1077,9 +1099,9 @@ __device__ void tail_smooth(const TailLevel<T> &A, const TailSlots &S, int l, in
     const int sub = (int)(e & 3);
     const bool on = xg != kNone;
     for (int s = 0; s < nsteps; ++s) {
-        if (xr != kNone) smooth_at<D, T>(xr, A.u, A.F, A.g);
+        if (xr != kNone) smooth_at_s<D, T>(xr, A.u, A.Fs, A.g);
         tail_sync();
-        if (xb != kNone) smooth_at<D, T>(xb, A.u, A.F, A.g);
+        if (xb != kNone) smooth_at_s<D, T>(xb, A.u, A.Fs, A.g);
         tail_sync();
         const T B = ghost_B4<D, T>(on, sub, xg, code, A.gw, A.ng, g, A.u, A.g);
         T gv = T(0);
@@ -1178,7 +1200,9 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
             if (xc != kNone) {
                 int ic[3];
                 coords(xc, (uint32_t)B.g.n, D, ic);
-                B.F[xc] = restrict_masked<D, T>(ic, S.fmask[(l + 1) * kTailThreads + t], A.r, A.g);
+                const T fc = restrict_masked<D, T>(ic, S.fmask[(l + 1) * kTailThreads + t], A.r, A.g);
+                B.F[xc] = fc;
+                if (i < B.nint) B.Fs[xc] = scaled_rhs<T>(fc, B.g);
                 B.u[xc] = T(0);
             }
             tail_sync();
@@ -1240,12 +1264,14 @@ __global__ void k_solve_check(SolveState *st, const double *__restrict__ nout, c
 __global__ void __launch_bounds__(kT) k_ir_begin(const uint32_t *__restrict__ ilist, int64_t nint,
                                                  const uint32_t *__restrict__ gidx, int64_t ng,
                                                  const double *__restrict__ r, float *__restrict__ F32,
-                                                 float *__restrict__ e32) {
+                                                 float *__restrict__ Fs32, float *__restrict__ e32, G2 G) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nint + ng) return;
     const int64_t X = (i < nint) ? ilist[i] : gidx[i - nint];
-    F32[X] = (float)r[X];
+    const float f = (float)r[X];
+    F32[X] = f;
+    if (i < nint) Fs32[X] = scaled_rhs<float>(f, G);
     e32[X] = 0.0f;
 }
 
@@ -1283,12 +1309,15 @@ __global__ void k_scatter_ghosts(const uint32_t *__restrict__ gidx, int64_t ng, 
 }
 
 __global__ void __launch_bounds__(kT) k_set_interior(const uint32_t *__restrict__ ilist, int64_t nint,
-                                                     const double *__restrict__ f, double *__restrict__ F) {
+                                                     const double *__restrict__ f, double *__restrict__ F,
+                                                     double *__restrict__ Fs, G2 G) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nint) {
         const int64_t X = ilist[i];
-        F[X] = f ? f[X] : 0.0;
+        const double v = f ? f[X] : 0.0;
+        F[X] = v;
+        Fs[X] = scaled_rhs<double>(v, G);
     }
 }
 
@@ -1297,6 +1326,7 @@ template <typename T> struct Arr;
 template <> struct Arr<double> {
     static double *u(Level &L) { return L.u; }
     static double *F(Level &L) { return L.F; }
+    static double *Fs(Level &L) { return L.Fs; }
     static double *r(Level &L) { return L.r; }
     static double *gtmp(Level &L) { return L.gtmp; }
     static double *bbuf(Level &L) { return L.bbuf; }
@@ -1305,6 +1335,7 @@ template <> struct Arr<double> {
 template <> struct Arr<float> {
     static float *u(Level &L) { return L.u32; }
     static float *F(Level &L) { return L.F32; }
+    static float *Fs(Level &L) { return L.Fs32; }
     static float *r(Level &L) { return L.r32; }
     static float *gtmp(Level &L) { return L.gtmp32; }
     static float *bbuf(Level &L) { return L.bbuf32; }
@@ -1326,15 +1357,15 @@ void vcycle_t(Handle &H, int l, T *u) {
         return;
     }
     Level &B = H.L[l + 1];
-    smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu1);
+    smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu1, Arr<T>::Fs(A));
     residual<T>(H, A, u, Arr<T>::F(A), Arr<T>::r(A));
     extend<T>(H, A, Arr<T>::r(A));
-    restrict_to<T>(H, A, B, Arr<T>::r(A), Arr<T>::F(B), Arr<T>::u(B), true);
+    restrict_to<T>(H, A, B, Arr<T>::r(A), Arr<T>::F(B), Arr<T>::u(B), true, Arr<T>::Fs(B));
     const int gamma = H.o.cycle == BCMG_CYCLE_W ? 2 : 1;
     for (int g = 0; g < gamma; ++g) vcycle_t<T>(H, l + 1, Arr<T>::u(B));
     extend<T>(H, B, Arr<T>::u(B));
     prolong<T>(H, A, B, Arr<T>::u(B), u, true);
-    smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu2);
+    smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu2, Arr<T>::Fs(A));
 }
 
 template <typename T>
@@ -1359,6 +1390,7 @@ TailLevel<T> tail_level(Level &L) {
     t.fmask = L.fmask;
     t.u = Arr<T>::u(L);
     t.F = Arr<T>::F(L);
+    t.Fs = Arr<T>::Fs(L);
     t.r = Arr<T>::r(L);
     t.act = L.act;
     t.nact = L.nact;
@@ -1452,7 +1484,7 @@ void run_tail(Handle &H) {
 // ------------------------------------------------------------ host wrappers
 
 template <typename T>
-void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps) {
+void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
     const G2 G = g2_of(L);
     T *tmp = Arr<T>::gtmp(L);
     const T *gw = Arr<T>::gw(L);
@@ -1470,8 +1502,8 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps) {
                 if (n == 0) continue;
                 const int bs = bs_for(H, n);
                 const uint32_t *list = L.hlist + L.hoff[q];
-                if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, G);
-                else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, G);
+                if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
+                else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
             }
         }
         for (int c = 0; c < 2 && H.o.ordering == BCMG_ORDER_RB; ++c) {
@@ -1479,8 +1511,8 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps) {
             const int64_t n = c ? nblack : L.nred;
             const int bs = bs_for(H, n);
             if (prof) profile_mark(H, L);
-            if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, G);
-            else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, G);
+            if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
+            else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
             if (prof) profile_mark(H, L);
         }
         if (L.d == 3)
@@ -1554,7 +1586,7 @@ void extend(Handle &H, Level &L, T *a) {
 }
 
 template <typename T>
-void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero, bool early_ok) {
+void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero, bool early_ok, T *Fsc) {
     const G2 Gf = g2_of(Lf), Gc = g2_of(Lc);
     const int bs = bs_for(H, Lc.nint + Lc.ng);
     const unsigned ib = nblk(Lc.nint, bs);
@@ -1564,10 +1596,10 @@ void restrict_to(Handle &H, Level &Lf, Level &Lc, const T *rf, T *Fc, T *uc_zero
     const int early = (int)(early_ok && (Lf.ng > 0 || Lf.nb > 0));
     if (Lf.d == 3)
         launch(H, "k_restrict", k_restrict<3, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
-               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc, early);
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Fsc, Gf, Gc, early);
     else
         launch(H, "k_restrict", k_restrict<2, T>, grid, bs, (const uint32_t *)Lc.ilist, Lc.nint, ib,
-               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Gf, Gc, early);
+               (const uint32_t *)Lc.gidx, Lc.ng, (const uint32_t *)Lc.fmask, rf, Fc, uc_zero, Fsc, Gf, Gc, early);
 }
 
 template <typename T>
@@ -1631,7 +1663,7 @@ void mixed_step_enqueue(Handle &H, double *u) {
     Level &L = H.L[0];
     const unsigned grid = nblk(L.nint + L.ng, kT);
     launch(H, "k_ir_begin", k_ir_begin, grid, kT, (const uint32_t *)L.ilist, L.nint, (const uint32_t *)L.gidx, L.ng,
-           (const double *)L.r, L.F32, L.u32);
+           (const double *)L.r, L.F32, L.Fs32, L.u32, g2_of(L));
     vcycle_t<float>(H, 0, L.u32);
     launch(H, "k_ir_update", k_ir_update, grid, kT, (const uint32_t *)L.ilist, L.nint, (const uint32_t *)L.gidx,
            L.ng, (const float *)L.u32, u);
@@ -1753,19 +1785,20 @@ void scatter_ghost_values(Handle &H, Level &L, const double *g, double *F) {
 }
 
 void set_interior_rhs(Handle &H, Level &L, const double *f, double *F) {
-    launch(H, "k_set_interior", k_set_interior, nblk(L.nint, kT), kT, (const uint32_t *)L.ilist, L.nint, f, F);
+    launch(H, "k_set_interior", k_set_interior, nblk(L.nint, kT), kT, (const uint32_t *)L.ilist, L.nint, f, F,
+           L.Fs, g2_of(L));
 }
 
-template void smooth<double>(Handle &, Level &, double *, const double *, int);
+template void smooth<double>(Handle &, Level &, double *, const double *, int, const double *);
 template void residual<double>(Handle &, Level &, const double *, const double *, double *);
 template void extend<double>(Handle &, Level &, double *);
-template void restrict_to<double>(Handle &, Level &, Level &, const double *, double *, double *, bool);
+template void restrict_to<double>(Handle &, Level &, Level &, const double *, double *, double *, bool, double *);
 template void prolong<double>(Handle &, Level &, Level &, const double *, double *, bool);
 template void coarsest_correct<double>(Handle &, Level &, double *, const double *);
-template void smooth<float>(Handle &, Level &, float *, const float *, int);
+template void smooth<float>(Handle &, Level &, float *, const float *, int, const float *);
 template void residual<float>(Handle &, Level &, const float *, const float *, float *);
 template void extend<float>(Handle &, Level &, float *);
-template void restrict_to<float>(Handle &, Level &, Level &, const float *, float *, float *, bool);
+template void restrict_to<float>(Handle &, Level &, Level &, const float *, float *, float *, bool, float *);
 template void prolong<float>(Handle &, Level &, Level &, const float *, float *, bool);
 template void coarsest_correct<float>(Handle &, Level &, float *, const float *);
 

@@ -1625,10 +1625,12 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         // such row from the restriction, the finest keeps zeros until the
         // caller sets its data
         L.F = (double *)dalloc(H, sizeof(double) * L.nn, false, l == 0);
+        L.Fs = (double *)dalloc(H, sizeof(double) * L.nn, false, false);  // written before it is read
         L.r = (double *)dalloc(H, sizeof(double) * L.nn);
         if (H.o.precision == BCMG_PREC_MIXED) {
             L.u32 = (float *)dalloc(H, sizeof(float) * L.nn);
             L.F32 = (float *)dalloc(H, sizeof(float) * L.nn, false, false);
+            L.Fs32 = (float *)dalloc(H, sizeof(float) * L.nn, false, false);
             L.r32 = (float *)dalloc(H, sizeof(float) * L.nn);
             L.gtmp32 = (float *)dalloc(H, sizeof(float) * std::max<int64_t>(L.ng, 1));
             L.bbuf32 = (float *)dalloc(H, sizeof(float) * 2 * std::max<int64_t>(L.nb, 1));
