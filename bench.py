@@ -166,7 +166,7 @@ def flush_l2(buf):
 
 
 # ------------------------------------------------------------ our arm
-FP64_INSTR_PER_UPDATE = 7   # 5 adds, 1 FMA, 1 multiply per red/black update
+FP64_INSTR_PER_UPDATE = 6   # 5 adds, 1 FMA per red/black update (from the scaled right-hand side)
 FP64_PEAK_GINSTR = 152 * 2 * 2.07  # SMs x FP64 FMA pipes per clock x GHz (1.26 TFLOP/s)
 # DRAM bytes (read + write) of one finest-level k_smooth<3,double> launch at
 # N=256, from an ncu capture of that kernel (the counters belong to the
