@@ -171,7 +171,7 @@ FP64_PEAK_GINSTR = 152 * 2 * 2.07  # SMs x FP64 FMA pipes per clock x GHz (1.26 
 # DRAM bytes (read + write) of one finest-level k_smooth<3,double> launch at
 # N=256, from an ncu capture of that kernel (the counters belong to the
 # kernel as it is; set to None when the kernel changes until re-captured)
-K_SMOOTH_DRAM_BYTES = 21.59e6
+K_SMOOTH_DRAM_BYTES = 21.595e6
 K_SMOOTH_DRAM_SOURCE = ("ncu --set full capture of the first two finest-level sweeps, "
                         "dram__bytes_read.sum + dram__bytes_write.sum, cold cache")
 
