@@ -162,13 +162,6 @@ __device__ __forceinline__ T ghost_Bw(int64_t X, uint16_t code, const T *w, cons
     return (acc[0] + acc[1]) + acc[2];
 }
 
-template <int D, typename T>
-__device__ __forceinline__ T ghost_B(int64_t X, uint16_t code, const T *gw, int64_t ng, int64_t g, const T *u,
-                                     const G2 &G) {
-    T w[(D == 3) ? 27 : 9];
-    ghost_weights<D, T>(code, gw, ng, g, w);
-    return ghost_Bw<D, T>(X, code, w, u, G);
-}
 
 // One stencil row of B u~ (the terms with outermost offset `row`: o2 in 3D,
 // o1 in 2D), for lanes that share a ghost; B u~ is the sum of the rows
@@ -238,14 +231,6 @@ __device__ __forceinline__ T scaled_rhs(T f, const G2 &G) {
     return (T)G.h2 * f * (T)G.inv_diag;
 }
 
-// fictitious-time relaxation of ghost g (eq. rel with eq. DtauOptTheta)
-template <int D, typename T>
-__device__ __forceinline__ T ghost_new(int64_t g, const uint32_t *gidx, const uint16_t *gcode, const T *gw,
-                                       const double *gdt, int64_t ng, const T *u, const T *F, const G2 &G) {
-    const int64_t X = gidx[g];
-    const T B = ghost_B<D, T>(X, gcode[g], gw, ng, g, u, G);
-    return fma((T)gdt[g], F[X] - B, u[X]);
-}
 
 // interior residual (eq. Laph, with the reaction term c u)
 template <int D, typename T>
@@ -398,28 +383,6 @@ __device__ __forceinline__ T prolong_at(const int iy[3], const T *ec, const G2 &
     return v * scale;
 }
 
-// band value: the expanded extension (ELL terms of the band node), eight
-// terms per round with predicated loads so that their gathers overlap
-template <typename T>
-__device__ __forceinline__ T extend_at(int64_t b, const uint8_t *ecnt, const uint32_t *eg, const double *ew,
-                                       int64_t nb, const T *a) {
-    T v = T(0);
-    const int c = ecnt[b];
-    for (int k0 = 0; k0 < c; k0 += 8) {
-        T w[8], x[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const bool p = k0 + j < c;
-            const int64_t e = (int64_t)(k0 + j) * nb + b;
-            w[j] = p ? (T)ew[e] : T(0);
-            x[j] = p ? a[eg[e]] : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (k0 + j < c) v = fma(w[j], x[j], v);
-    }
-    return v;
-}
 
 // the map of the first kEllFirst terms of band node b (read before the
 // dependency wait)
@@ -444,8 +407,9 @@ __device__ __forceinline__ void ell_first(int64_t b, const uint8_t *ecnt, const 
     }
 }
 
-// extend_at with the first terms' map already loaded; the same terms in
-// the same order
+// band value: the expanded extension (ELL terms of band node b, term-major)
+// with the map of its first terms already loaded, the rest in rounds of
+// eight with predicated loads so that their gathers overlap
 template <typename T>
 __device__ __forceinline__ T extend_from(int64_t b, const EllRound<T> &R, const uint32_t *eg, const double *ew,
                                          int64_t nb, const T *a) {
@@ -489,6 +453,9 @@ __global__ void __launch_bounds__(kT) k_smooth(const uint32_t *__restrict__ list
     }
 }
 
+// fictitious-time relaxation of every ghost from the same u (eq. rel with
+// eq. DtauOptTheta): tmp_g = u_G + dt_g (g_G - B u~); k_ghost_scatter writes
+// tmp back once all ghosts are done (Jacobi over the ghosts)
 template <int D, typename T>
 __global__ void __launch_bounds__(kT) k_ghost_relax(const uint32_t *__restrict__ gidx,
                                                     const uint16_t *__restrict__ gcode, const T *__restrict__ gw,
