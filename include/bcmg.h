@@ -26,7 +26,12 @@
  *  - work is stream-ordered on the stream given at creation; entry points
  *    that return host data (counts, norms, host copies) synchronise it;
  *  - a call that reads or writes caller arrays must not overlap on the GPU
- *    with another call on the same handle (calls on one handle are ordered).
+ *    with another call on the same handle (calls on one handle are ordered);
+ *  - handles may be created and used from several threads at once; creation
+ *    (opts.use_graph) records the solve graph by stream capture on the
+ *    handle's own non-blocking stream, and while a capture is open CUDA
+ *    rejects a device- or context-wide synchronisation (cudaDeviceSynchronize)
+ *    from any thread: concurrent threads synchronise streams or events.
  */
 #ifndef BCMG_H
 #define BCMG_H

@@ -38,7 +38,9 @@ def _solve(B, d, N, mk, precision=None):
         s.set_boundary_values(torch.from_numpy(g).cuda())
         u = torch.zeros((N + 1) ** d, dtype=torch.float64, device="cuda")
         c, rel = s.solve(u, 1e-10, 100)
-        torch.cuda.synchronize()
+        # a stream synchronisation: a device-wide one is rejected while another
+        # thread's creation has a stream capture open
+        torch.cuda.current_stream().synchronize()
         return c, rel, u.cpu().numpy()
     finally:
         s.close()
