@@ -553,7 +553,9 @@ def run_served(args):
     count = 64
     budget = int(64e9)
     server = serve.Server(budget, workers=16)
-    server.run(served_requests(0.0, 8, seed=7))  # warm-up
+    # warm-up: the same requests once (page-locked staging buffers of every
+    # size class, device blocks, side streams)
+    server.run(served_requests(0.0, count))
     clocks = ClockSampler(0)
     clocks.start()
     launches0 = bcmg.kernel_launches()

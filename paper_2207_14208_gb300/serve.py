@@ -63,14 +63,69 @@ class Result:
         return self.done - self.arrival
 
 
+class _PinnedPool:
+    """Page-locked host staging buffers for the requests' phi and f, kept for
+    the life of the process (freeing page-locked memory waits for the whole
+    device).  Sizes are rounded up to powers of two so that buffers are
+    reused across request sizes; at most two per request in flight exist
+    per size class."""
+
+    def __init__(self):
+        self._free: list = []
+        self._lock = threading.Lock()
+
+    def get(self, n: int):
+        import torch
+        cap = 1 << max(17, (int(n) - 1).bit_length())  # doubles
+        with self._lock:
+            for i, b in enumerate(self._free):
+                if b.numel() == cap:
+                    return self._free.pop(i)
+        return torch.empty(cap, dtype=torch.float64, pin_memory=True)
+
+    def put(self, b) -> None:
+        with self._lock:
+            self._free.append(b)
+
+
+_pinned = _PinnedPool()
+
+
 def solve_one(req: Request):
     """Build, solve and free one request on the current CUDA device;
-    returns (cycles, rel, status, footprint, u or None)."""
+    returns (cycles, rel, status, footprint, u or None).  phi and f go
+    through page-locked staging buffers (pageable copies from many threads
+    serialise in the driver); creation needs phi only, so f is copied on a
+    second stream while the hierarchy is built and set afterwards."""
     import torch
-    phi = torch.from_numpy(np.ascontiguousarray(req.phi, dtype=np.float64)).cuda()
-    f = torch.from_numpy(np.ascontiguousarray(req.f, dtype=np.float64)).cuda()
-    s = bcmg.Solver(req.dim, req.N, phi, f, precision=req.precision)
+    n = req.phi.size
+    main = torch.cuda.current_stream()
+    side = _side_stream()
+    bp, bf = _pinned.get(n), _pinned.get(n)
     try:
+        np.copyto(bp[:n].numpy(), np.asarray(req.phi, dtype=np.float64).reshape(-1))
+        phi = torch.empty(n, dtype=torch.float64, device="cuda")
+        phi.copy_(bp[:n], non_blocking=True)
+        np.copyto(bf[:n].numpy(), np.asarray(req.f, dtype=np.float64).reshape(-1))
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            f = torch.empty(n, dtype=torch.float64, device="cuda")
+            f.copy_(bf[:n], non_blocking=True)
+        s = bcmg.Solver(req.dim, req.N, phi, None, precision=req.precision)
+        main.wait_stream(side)
+        f.record_stream(main)
+        s.set_rhs(f)
+    except BaseException:
+        main.synchronize()  # streams, not the device: another thread may be capturing
+        side.synchronize()
+        _pinned.put(bp)
+        _pinned.put(bf)
+        raise
+    try:
+        # the staging buffers are free once the copies are done
+        main.synchronize()
+        _pinned.put(bp)
+        _pinned.put(bf)
         Q = s.ghost_points()
         s.set_boundary_values(req.g(Q).contiguous())
         u = torch.zeros_like(phi)
@@ -145,6 +200,18 @@ class Server:
                         lock.wait(timeout=wait if not queue else 0.05 if wait is None else min(wait, 0.05))
             ex.shutdown(wait=True)
         return results
+
+
+_tls = threading.local()
+
+
+def _side_stream():
+    """This thread's second stream (the f copy during creation)."""
+    import torch
+    st = getattr(_tls, "side", None)
+    if st is None:
+        st = _tls.side = torch.cuda.Stream()
+    return st
 
 
 def percentiles(values, ps=(50, 99)):
