@@ -162,7 +162,6 @@ __device__ __forceinline__ T ghost_Bw(int64_t X, uint16_t code, const T *w, cons
     return (acc[0] + acc[1]) + acc[2];
 }
 
-
 // One stencil row of B u~ (the terms with outermost offset `row`: o2 in 3D,
 // o1 in 2D), for lanes that share a ghost; B u~ is the sum of the rows
 template <int D, typename T>
@@ -230,7 +229,6 @@ template <typename T>
 __device__ __forceinline__ T scaled_rhs(T f, const G2 &G) {
     return (T)G.h2 * f * (T)G.inv_diag;
 }
-
 
 // interior residual (eq. Laph, with the reaction term c u)
 template <int D, typename T>
@@ -382,7 +380,6 @@ __device__ __forceinline__ T prolong_at(const int iy[3], const T *ec, const G2 &
     const T scale = k == 0 ? T(1) : k == 1 ? T(0.5) : k == 2 ? T(0.25) : T(0.125);
     return v * scale;
 }
-
 
 // the map of the first kEllFirst terms of band node b (read before the
 // dependency wait)
