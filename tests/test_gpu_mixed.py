@@ -49,7 +49,9 @@ def test_mixed_matches_fp64_solution(bcmg, name, d, N, mk):
     assert c32 <= c64 + 3
 
 
-@pytest.mark.parametrize("name,d,N,mk", CASES[:1] + CASES[2:3], ids=["disk128", "ellipsoid64"])
+# ellipsoid176: a mid-size 3D case (more than 2^18 interior nodes)
+@pytest.mark.parametrize("name,d,N,mk", CASES[:1] + CASES[2:3] + [("ellipsoid176", 3, 176, W.phi_ellipsoid)],
+                         ids=["disk128", "ellipsoid64", "ellipsoid176"])
 def test_mixed_keeps_discretisation_error(bcmg, name, d, N, mk):
     B = bcmg
     s64, u64, us, c64, _ = _solve(B, d, N, mk, B.PREC_FP64, 1e-10)

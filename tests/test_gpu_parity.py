@@ -245,6 +245,35 @@ def test_nonconvergence_reported(bcmg):
     assert e.value.code == B.ENONFINITE
 
 
+# mid-size 3D cases (more than 2^18 interior nodes on the finest level), two
+# V-cycles from a random start
+MCASES = [("ellipsoid176", 3, 176, W.phi_ellipsoid), ("spheres192", 3, 192, W.phi_spheres)]
+
+
+@pytest.mark.parametrize("name,d,N,mk", MCASES, ids=[c[0] for c in MCASES])
+def test_midsize_vcycles_match_oracle(bcmg, name, d, N, mk):
+    phi = mk(N)
+    f, us = W.manufactured(d, N)
+    s, o = pair(bcmg, d, N, phi, f)
+    assert s.info(0)["n_interior"] >= 1 << 18
+    Q = o.ghosts(0)["Q"]
+    g = W.g_at(d, Q)
+    o.set_rhs(f, g)
+    s.set_boundary_values(dev(g))
+    cls = o.cls(0)
+    act = (cls == O.INTERIOR) | (cls == O.GHOST)
+    rng = np.random.default_rng(11)
+    u0 = np.where(cls == O.BOXDIR, us, rng.uniform(-1, 1, o.nn(0)))
+    uo = u0.copy()
+    ug = dev(u0)
+    for cyc in range(2):
+        uo = o.vcycle(uo, 1)
+        s.vcycle(ug, 1)
+        got = host(ug)
+        assert np.abs(got[act] - uo[act]).max() <= REL * np.abs(uo[act]).max(), cyc
+        np.testing.assert_array_equal(got[~act], u0[~act])
+
+
 @pytest.mark.slow
 def test_full_size_ellipsoid_256(bcmg):
     """The benchmark workload (3D ellipsoid, N = 256, V(2,1), FP64): set-up
