@@ -84,6 +84,10 @@ typedef struct {
     int nu1, nu2, ordering, dtau_mode, ext_sweeps, cycle, min_coarse, max_levels;
     int tgcs_maxit, rmode, ext_mode;
     int bc;
+    int band_width;  /* Chebyshev radius of the extension band (default 2) */
+    int gfam;        /* coarse-ghost family: 0 ghost + inactive, 1 ghost only */
+    int cg_rhs;      /* coarse-ghost right-hand side: 0 family restriction,
+                        1 the (extended) fine residual at the coincident node */
     double react;
     double ext_cfl;
     double dtau_const, tgcs_tol;
@@ -429,9 +433,10 @@ static void setup_ghosts(oracle_t *O, olevel *L) {
     }
 }
 
-/* inactive nodes within Chebyshev distance 2 of a ghost receive the normal
- * extension of ghost quantities (Sec. 3.3.2, transfer operators). */
-static void setup_band(olevel *L) {
+/* inactive nodes within Chebyshev distance rad (2 by default: exactly the
+ * inactive points a coarse-ghost restriction can read) of a ghost receive the
+ * normal extension of ghost quantities (Sec. 3.3.2, transfer operators). */
+static void setup_band(olevel *L, int rad) {
     int d = L->d;
     L->bpos = (int *)malloc(sizeof(int) * (size_t)L->nn);
     for (long i = 0; i < L->nn; ++i) L->bpos[i] = -1;
@@ -440,9 +445,9 @@ static void setup_band(olevel *L) {
         int ix[3];
         decode(L, L->gidx[g], ix);
         int o[3];
-        for (o[2] = (d > 2 ? -2 : 0); o[2] <= (d > 2 ? 2 : 0); ++o[2])
-            for (o[1] = (d > 1 ? -2 : 0); o[1] <= (d > 1 ? 2 : 0); ++o[1])
-                for (o[0] = -2; o[0] <= 2; ++o[0]) {
+        for (o[2] = (d > 2 ? -rad : 0); o[2] <= (d > 2 ? rad : 0); ++o[2])
+            for (o[1] = (d > 1 ? -rad : 0); o[1] <= (d > 1 ? rad : 0); ++o[1])
+                for (o[0] = -rad; o[0] <= rad; ++o[0]) {
                     int iy[3] = {ix[0] + o[0], ix[1] + o[1], ix[2] + o[2]};
                     if (!in_grid(L, iy)) continue;
                     long y = lin_of(L, iy);
@@ -636,11 +641,13 @@ static void residual(const olevel *L, const double *u, const double *F, double *
     }
 }
 
-/* Extension of ghost values into the inactive band along the normal: a fixed
- * number of explicit pseudo-time sweeps of dr/dsigma + dr/dn = 0 (Sec. 3.3.2).
- * Reading: upwind differences with the largest stable step, which makes each
- * sweep the |n_a|-weighted mean of the upwind neighbours; sources are ghosts
- * and band nodes; the band starts from zero. */
+/* The paper's own scheme for the extension (Sec. 3.3.2): explicit Euler in
+ * the pseudo-time sigma for dr/dsigma + dr/dn = 0 with the normal derivative
+ * dr/dn = sum_a n_a (r(X + e_a) - r(X - e_a)) / 2 taken by central differences
+ * (index units), step ext_cfl, over the band nodes only; ghost and interior
+ * values act as fixed data, the band starts from zero.  Kept as an option
+ * (ext_mode = 1): forward Euler with central differences is not stable for
+ * pure advection, so the default is the upwind scheme below. */
 static void extend_central(const oracle_t *O, olevel *L, double *arr) {
     long nb = L->nb;
     double *old = L->tmp, *nw = L->tmp + nb;
@@ -678,6 +685,11 @@ static void extend_central(const oracle_t *O, olevel *L, double *arr) {
     }
 }
 
+/* Default extension (reading of Sec. 3.3.2): a fixed number of explicit
+ * pseudo-time sweeps of dr/dsigma + dr/dn = 0 with upwind differences at the
+ * largest stable step, which makes each sweep the |n_a|-weighted mean of the
+ * upwind neighbours; sources are ghosts and band nodes; the band starts from
+ * zero. */
 static void extend(const oracle_t *O, olevel *L, double *arr) {
     long nb = L->nb;
     if (nb == 0) return;
@@ -711,7 +723,8 @@ static void extend(const oracle_t *O, olevel *L, double *arr) {
  * if all 3^d fine neighbours are interior, else the plain mean of the
  * interior ones; coarse ghosts take FW of the (extended) exterior residual
  * if all 3^d are ghost/inactive, else the mean of the ghost/inactive ones. */
-static void restrict_op(const olevel *Lf, const olevel *Lc, const double *rf, double *Fc, int rmode) {
+static void restrict_op(const olevel *Lf, const olevel *Lc, const double *rf, double *Fc, int rmode,
+                        int gfam, int cg_rhs) {
     int d = Lf->d;
     for (long c = 0; c < Lc->nn; ++c) {
         Fc[c] = 0.0;
@@ -739,7 +752,7 @@ static void restrict_op(const olevel *Lf, const olevel *Lc, const double *rf, do
                     long y = lin_of(Lf, iy);
                     unsigned char cy = Lf->cls[y];
                     int fam = (pc == CL_INTERIOR) ? (cy == CL_INTERIOR)
-                                                  : (cy == CL_GHOST || cy == CL_INACTIVE);
+                                                  : (cy == CL_GHOST || (cy == CL_INACTIVE && gfam == 0));
                     if (!fam) {
                         all = 0;
                         continue;
@@ -750,6 +763,15 @@ static void restrict_op(const olevel *Lf, const olevel *Lc, const double *rf, do
                     cnt++;
                 }
         int weighted = (pc == CL_INTERIOR) ? (rmode & 1) : ((rmode >> 1) & 1);
+        if (pc == CL_GHOST && cg_rhs == 1) {
+            /* injection: the fine node at the coarse ghost's position (a
+             * ghost or an extended band node, never interior since phi is
+             * injected) */
+            int iy[3] = {0, 0, 0};
+            for (int a = 0; a < d; ++a) iy[a] = 2 * ic[a];
+            Fc[c] = rf[lin_of(Lf, iy)];
+            continue;
+        }
         if (all) Fc[c] = fw;
         else if (weighted) Fc[c] = wsum > 0.0 ? fw / wsum : 0.0;
         else Fc[c] = cnt > 0 ? sum / (double)cnt : 0.0;
@@ -936,7 +958,7 @@ static void level_finish(oracle_t *O, olevel *L) {
     L->bc = O->bc;
     L->react = O->react;
     setup_ghosts(O, L);
-    setup_band(L);
+    setup_band(L, O->band_width);
     L->u = (double *)calloc((size_t)L->nn, sizeof(double));
     L->F = (double *)calloc((size_t)L->nn, sizeof(double));
     L->r = (double *)calloc((size_t)L->nn, sizeof(double));
@@ -953,7 +975,10 @@ void orc_destroy(void *hp) {
 
 /* iopts: nu1, nu2, ordering, dtau_mode, ext_sweeps, cycle, min_coarse,
  *        max_levels, tgcs_maxit, rmode, ext_mode, bc (0 Dirichlet,
- *        1 Neumann on Gamma)
+ *        1 Neumann on Gamma), band_width (Chebyshev radius of the
+ *        extension band, 2), gfam (coarse-ghost restriction family: 0 ghost
+ *        and inactive points, 1 ghost points only), cg_rhs (coarse-ghost
+ *        right-hand side: 0 the family restriction, 1 injection)
  * dopts: dtau_const (Dtau, or Dtau / h for Neumann), tgcs_tol, ext_cfl,
  *        reaction coefficient c
  * Coarsening (geometric re-discretisation, Sec. 2.1): N_{l+1} = N_l / 2
@@ -977,6 +1002,10 @@ void *orc_create(int d, int N, const double *phi, const int *iopts, const double
     O->rmode = iopts[9];
     O->ext_mode = iopts[10];
     O->bc = iopts[11];
+    O->band_width = iopts[12];
+    O->gfam = iopts[13];
+    O->cg_rhs = iopts[14];
+    if (O->band_width < 1 || O->band_width > 4) O->band_width = 2;
     O->react = dopts[3];
     O->ext_cfl = dopts[2];
     O->dtau_const = dopts[0];
@@ -1079,7 +1108,7 @@ static void cycle_rec(oracle_t *O, int l, double *u, const double *F, int gamma)
     for (int s = 0; s < O->nu1; ++s) smooth_step(O, L, u, F);
     residual(L, u, F, L->r);
     extend(O, L, L->r);
-    restrict_op(L, Lc, L->r, Lc->F, O->rmode);
+    restrict_op(L, Lc, L->r, Lc->F, O->rmode, O->gfam, O->cg_rhs);
     memset(Lc->u, 0, sizeof(double) * (size_t)Lc->nn);
     if (O->cycle == CYC_TGCS && l == 0 && O->L > 2) {
         coarse_exact(O, 1);
@@ -1202,7 +1231,7 @@ void orc_extend(void *hp, int l, double *a) {
 
 void orc_restrict(void *hp, int l, const double *rf, double *Fc) {
     oracle_t *O = (oracle_t *)hp;
-    restrict_op(&O->lv[l], &O->lv[l + 1], rf, Fc, O->rmode);
+    restrict_op(&O->lv[l], &O->lv[l + 1], rf, Fc, O->rmode, O->gfam, O->cg_rhs);
 }
 
 void orc_prolong(void *hp, int l, const double *ec, double *uf) {

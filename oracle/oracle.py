@@ -131,7 +131,8 @@ class Oracle:
                  ext_sweeps: int = 4, cycle: int = CYC_V, min_coarse: int = 8,
                  max_levels: int = 24, tgcs_tol: float = 1e-13, tgcs_maxit: int = 200,
                  rmode: int = 3, ext_mode: int = 0, ext_cfl: float = 0.5, bc: int = 0,
-                 reaction: float = 0.0):
+                 reaction: float = 0.0, band_width: int = 2, gfam: int = 0,
+                 cg_rhs: int = 0):
         self.lib = _load()
         self.d, self.N = d, N
         self.n = N + 1
@@ -139,7 +140,8 @@ class Oracle:
         phi = _f64(phi).reshape(-1)
         assert phi.size == self.n ** d
         iopts = np.array([nu1, nu2, ordering, dtau_mode, ext_sweeps, cycle, min_coarse,
-                          max_levels, tgcs_maxit, rmode, ext_mode, bc], dtype=np.int32)
+                          max_levels, tgcs_maxit, rmode, ext_mode, bc, band_width, gfam,
+                          cg_rhs], dtype=np.int32)
         dopts = np.array([dtau_const, tgcs_tol, ext_cfl, reaction], dtype=np.float64)
         self.h = self.lib.orc_create(d, N, _p(phi), _p(iopts), _p(dopts))
         if not self.h:

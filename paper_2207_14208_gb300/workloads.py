@@ -16,6 +16,7 @@ Domains, all analytic and synthetic:
   * box        phi = -1 (no curved boundary; every box node is eliminated)
   * halfspace  phi = x_0 - x_V (the paper's rectangle tests, Sec. 3.2 / 4.1)
   * circle / flower: the paper's own off-centre Circle and Flower level sets
+  * ellipsoid_paper: the paper's own off-centre ellipsoid (Sec. 4.2)
 """
 
 from __future__ import annotations
@@ -116,6 +117,15 @@ def phi_flower_paper(N: int) -> np.ndarray:
     s = np.where(r == 0, 0.0, Y / safe)
     r1, r2 = 0.5, 0.2
     return (r - r1 - r2 * (s ** 5 + 5 * c ** 4 * s - 10 * c ** 2 * s ** 3)).reshape(-1)
+
+
+def phi_ellipsoid_paper(N: int) -> np.ndarray:
+    """The paper's off-centre ellipsoid of Sec. 4.2: centre
+    (sqrt(2)/20, sqrt(3)/40, -sqrt(2)/50), semi-axes 0.686, 0.386, 0.586."""
+    X, Y, Z = coords(3, N)
+    cx, cy, cz = math.sqrt(2.0) / 20.0, math.sqrt(3.0) / 40.0, -math.sqrt(2.0) / 50.0
+    return (((X - cx) / 0.686) ** 2 + ((Y - cy) / 0.386) ** 2
+            + ((Z - cz) / 0.586) ** 2 - 1.0).reshape(-1)
 
 
 # ---------------------------------------------------- manufactured solutions
