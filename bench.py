@@ -102,7 +102,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -169,11 +169,36 @@ def flush_l2(buf):
 FP64_INSTR_PER_UPDATE = 6   # 5 adds, 1 FMA per red/black update (from the scaled right-hand side)
 FP64_PEAK_GINSTR = 152 * 2 * 2.07  # SMs x FP64 FMA pipes per clock x GHz (1.26 TFLOP/s)
 # DRAM bytes (read + write) of one finest-level k_smooth<3,double> launch at
-# N=256, from an ncu capture of that kernel (the counters belong to the
-# kernel as it is; set to None when the kernel changes until re-captured)
+# N=256, from an ncu capture of that kernel.  The counters belong to the
+# kernel source they were taken on: K_SMOOTH_SRC_SHA is the hash of the
+# smoother's device code (see smoother_source_hash) at the capture; when the
+# source no longer hashes to it, the bench reports traffic as null.
 K_SMOOTH_DRAM_BYTES = 21.595e6
+K_SMOOTH_SRC_SHA = "3c52667141ebb526"
 K_SMOOTH_DRAM_SOURCE = ("ncu --set full capture of the first two finest-level sweeps, "
                         "dram__bytes_read.sum + dram__bytes_write.sum, cold cache")
+SMOOTHER_FUNCS = ("nbr_sum", "smooth_at_s", "k_smooth")
+
+
+def smoother_source_hash():
+    """sha256 (first 16 hex digits) of the device functions the finest-level
+    sweep runs, cut out of csrc/cycle.cu by name (template head to the
+    closing brace at column 0)."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_2207_14208_gb300", "csrc", "cycle.cu")).read()
+    h = hashlib.sha256()
+    for name in SMOOTHER_FUNCS:
+        m = re.search(r"\n(template <[^\n]*>\n(?:[^\n]*\n){0,3}?[^\n]*\b" + name + r"\b\(.*?\n\})", src, re.S)
+        h.update((m.group(1) if m else name).encode())
+    return h.hexdigest()[:16]
+
+
+def smoother_traffic():
+    sha = smoother_source_hash()
+    if K_SMOOTH_SRC_SHA is not None and sha == K_SMOOTH_SRC_SHA:
+        return K_SMOOTH_DRAM_BYTES, K_SMOOTH_DRAM_SOURCE
+    return None, "stale: the smoother source (sha %s) changed since the last ncu capture" % sha
 
 
 def run_ours(args, ws, rank, local):
@@ -254,10 +279,26 @@ def run_ours(args, ws, rank, local):
 
     s = bcmg.Solver(d, N, phi, f)
     info = s.info(0)
+    act = torch.from_numpy(np.isin(s.cls(0), [bcmg.INTERIOR, bcmg.GHOST])).cuda()
+    interior = torch.from_numpy(s.cls(0) == bcmg.INTERIOR).cuda()
     s.close()
     n_int = info["n_interior"]
+    # the solutions the timed arms compute, once more outside the timed
+    # region: mixed against FP64, both against the manufactured solution
+    sols = {}
+    for prec in (bcmg.PREC_FP64, bcmg.PREC_MIXED):
+        sp, _, _ = step(prec)
+        sp.close()
+        sols[prec] = u.clone()
+    u64, u32 = sols[bcmg.PREC_FP64], sols[bcmg.PREC_MIXED]
+    us_t = torch.from_numpy(us_h).cuda()
+    scale = float(u64[act].abs().max())
+    err_mixed = float((u32 - u64)[act].abs().max()) / scale
+    disc64 = float((u64 - us_t)[interior].abs().max())
+    disc32 = float((u32 - us_t)[interior].abs().max())
+    traffic, traffic_src = smoother_traffic()
     # dominant kernel: the finest-level red/black sweep (one colour per launch,
-    # n_int / 2 updates).  FP64 is bound by the FP64 pipe (7 instructions per
+    # n_int / 2 updates).  FP64 is bound by the FP64 pipe (6 instructions per
     # update); the FP32 sweep of the mixed path by memory (12 B per update).
     upd = n_int / 2.0
     ach_instr = FP64_INSTR_PER_UPDATE * upd / (r64["sweep_ms"] / 1e3) / 1e9
@@ -282,20 +323,21 @@ def run_ours(args, ws, rank, local):
         "data": "synthetic (analytic level set and manufactured solution)",
         "config": {"workload": "3D ellipsoid Poisson N=256 (257^3), FP64 V(2,1) solve to 1e-10",
                    "N": N, "cycles_per_solve": r64["cycles"][0], "final_rel_residual": max(r64["rels"]),
-                   "interior_nodes": n_int, "ghosts": info["n_ghost"],
+                   "interior_nodes": n_int, "ghosts": info["n_ghost"], "discretisation_error": disc64,
                    "step": "create hierarchy + g(Q) + solve", "l2": "flushed (512 MiB write) before every step",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "k_smooth<3,double> (finest level, one colour)",
                      "achieved": ach_instr, "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instr/s",
                      "frac": ach_instr / FP64_PEAK_GINSTR,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (1.26 TFLOP/s)",
-                     "traffic": K_SMOOTH_DRAM_BYTES, "traffic_source": K_SMOOTH_DRAM_SOURCE,
+                     "traffic": traffic, "traffic_source": traffic_src,
                      "sweep_us": r64["sweep_ms"] * 1e3,
                      "hbm_view": {"alg_bytes_per_launch": alg_bytes64, "achieved_gbs": hbm64,
                                   "peak_gbs": peak, "frac": hbm64 / peak, "peak_source": peak_kind}},
         "mixed": {"value": r32["value"], "unit": UNIT, "dtype": "f32 cycles in f64 refinement",
                   "ms_per_step": r32["ms"] / args.steps, "cycles_per_solve": r32["cycles"][0],
                   "final_rel_residual": max(r32["rels"]),
+                  "max_rel_err_vs_fp64": err_mixed, "discretisation_error": disc32,
                   "roofline": {"bound": "hbm", "kernel": "k_smooth<3,float> (finest level, one colour)",
                                "achieved": hbm32, "peak": peak, "unit": "GB/s", "frac": hbm32 / peak,
                                "sweep_us": r32["sweep_ms"] * 1e3, "alg_bytes_per_launch": alg_bytes32}},
@@ -305,7 +347,13 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, d, N, phi_h, f_h)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, d, N, phi_h, f_h, r64["cycles"][0])
+        out["cpu_baseline"], u_orc = cpu_baseline(args, d, N, phi_h, f_h, r64["cycles"][0])
+        # the FP64 solution against the oracle's solve of the same problem
+        ah = act.cpu().numpy()
+        out["config"]["max_rel_err_vs_oracle"] = float(
+            np.abs(u64.cpu().numpy()[ah] - u_orc[ah]).max() / np.abs(u_orc[ah]).max())
+        out["mixed"]["max_rel_err_vs_oracle"] = float(
+            np.abs(u32.cpu().numpy()[ah] - u_orc[ah]).max() / np.abs(u_orc[ah]).max())
     return out
 
 
@@ -378,9 +426,9 @@ def cpu_baseline(args, d, N, phi_h, f_h, cycles_per_solve):
     o.set_rhs(f_h, W.g_at(d, o.ghosts(0)["Q"]))
     u, c, _ = o.solve(np.zeros(o.nn(0)), args.rtol, 200)
     t = time.perf_counter() - t0
-    return {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one complete oracle solve at N=%d: set-up + %d V-cycles to %.0e, %.1f s "
-                      "(1 of %d host cores)" % (N, c, args.rtol, t, os.cpu_count() or 0)}
+    return ({"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": "one complete oracle solve at N=%d: set-up + %d V-cycles to %.0e, %.1f s "
+                       "(1 of %d host cores)" % (N, c, args.rtol, t, os.cpu_count() or 0)}, u)
 
 
 # ------------------------------------------------------------ reference arm
