@@ -50,7 +50,6 @@ extern "C" {
 #define BCMG_EGEOM 4      /* no interior node, or singular / oversized coarsest system */
 #define BCMG_ENOCONV 5    /* solve hit max_cycles before rtol */
 #define BCMG_ENONFINITE 6 /* NaN or Inf in the residual */
-#define BCMG_ETIMEOUT 7   /* reserved for bounded device-side waits */
 
 #define BCMG_CLASS_INACTIVE 0
 #define BCMG_CLASS_INTERIOR 1
@@ -138,6 +137,52 @@ int bcmg_dtau_opt(int dim, int bc, int dtau_mode, double dtau_const, double thet
  * or the coarsest system is singular or has more than 4096 unknowns). */
 int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
                                const bcmg_opts *opts, void *stream, bcmg_handle *out);
+
+/* bcmg_create_grid_hierarchy on the box [lo, lo + N h]^dim with a caller's
+ * device workspace (Sec. 3 and Sec. 4 set-up: a uniform grid of (N+1)^dim
+ * nodes x_i = lo + i h on every axis; the paper's D = [-1, 1]^d is lo = -1,
+ * h = 2 / N, which is what bcmg_create_grid_hierarchy passes).
+ *   lo, h      node 0's coordinate and the finest spacing (h > 0, finite);
+ *              level l has spacing h 2^l.  h scales the interior rows
+ *              (1 / h^2), Neumann rows (1 / h) and the Neumann Delta tau
+ *              (h (Delta tau / h)_OPT); classes, projections and stencils
+ *              are index-space quantities and do not depend on lo or h.
+ *              Projection points Q (bcmg_ghost_points) are returned in
+ *              these coordinates.
+ *   workspace  NULL: the library allocates (stream-ordered pool, with its
+ *              own cache).  Otherwise a caller-owned device buffer, 256-byte
+ *              aligned, of ws_bytes bytes, from which every device array of
+ *              the hierarchy and all of its set-up scratch are carved (no
+ *              library allocation of device memory); it must stay valid and
+ *              untouched until bcmg_destroy, which does not free it.  If it
+ *              is too small, creation fails with BCMG_ENOMEM and the
+ *              message states the size reached; bcmg_workspace_size of a
+ *              hierarchy of the same geometry and options gives the size
+ *              that suffices, bcmg_footprint_estimate a guide.
+ * Other arguments and errors as bcmg_create_grid_hierarchy; EINVAL also for
+ * a non-finite lo, h <= 0, or a misaligned / empty workspace. */
+int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const double *phi_dev,
+                                  const double *f_dev, const bcmg_opts *opts, void *workspace, size_t ws_bytes,
+                                  void *stream, bcmg_handle *out);
+
+/* Bytes of device memory the creation of h drew (its arrays and its set-up
+ * scratch): a workspace of this size suffices to create a hierarchy of the
+ * same dim, N, phi and options with bcmg_create_grid_hierarchy_ex.  (No
+ * counterpart in the paper.) */
+int bcmg_workspace_size(bcmg_handle h, int64_t *bytes);
+
+/* Failure injection for tests of the callers' recovery paths (no
+ * counterpart in the paper): after this call, the k-th device allocation the
+ * library makes (counted over all handles and threads) fails as if the device
+ * memory were exhausted, and the call that needed it returns BCMG_ENOMEM
+ * after releasing what it had taken.  k = 0 disables.  Host-side only. */
+int bcmg_debug_fail_allocation(int64_t k);
+
+/* Device blocks (and their bytes) that live handles hold from the library's
+ * allocator, outside its cache of returned blocks and outside caller
+ * workspaces; 0 once every handle is destroyed (leak checks in tests; no
+ * counterpart in the paper). */
+int bcmg_debug_live_blocks(int64_t *blocks, int64_t *bytes);
 
 /* Release every resource of the handle (NULL is accepted). */
 int bcmg_destroy(bcmg_handle h);
@@ -237,6 +282,16 @@ int bcmg_profile_read(bcmg_handle h, double *out_host);
  * them (same stream or events).  Asynchronous: returns after the launches. */
 int bcmg_residual_norms_static(const double *r_dev, const uint8_t *cls_dev, int64_t count, double *out_dev,
                                void *stream);
+
+/* Self-test of the division the restriction uses for family means (no
+ * counterpart in the paper; the restriction of Sec. 3.3.2 divides by the
+ * family's FW weight sum): out_host[i] = a_host[i] / w with w = 1 + i % 64,
+ * computed on the device the way the restriction computes it (a table
+ * reciprocal and one FMA correction, Markstein's method), in FP64
+ * (fp32 = 0) or FP32 (fp32 = 1, result widened).  1 <= n <= 2^24.
+ * Synchronous; allocates and frees its own device buffer.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+int bcmg_selftest_div_wsum(int fp32, const double *a_host, int64_t n, double *out_host);
 
 /* ---- introspection (host copies, synchronous) ----------------------- */
 

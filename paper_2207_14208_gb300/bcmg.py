@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libbcmg.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "bcmg.h")
 
-OK, EINVAL, ENOMEM, ECUDA, EGEOM, ENOCONV, ENONFINITE, ETIMEOUT = range(8)
+OK, EINVAL, ENOMEM, ECUDA, EGEOM, ENOCONV, ENONFINITE = range(7)
 INACTIVE, INTERIOR, GHOST, BOXDIR = 0, 1, 2, 3
 DTAU_EXP, DTAU_POLY, DTAU_CONST = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
@@ -64,6 +64,10 @@ def load():
         sig = {
             "bcmg_default_opts": (None, [vp]),
             "bcmg_create_grid_hierarchy": (i32, [i32, i64, vp, vp, vp, vp, vp]),
+            "bcmg_create_grid_hierarchy_ex": (i32, [i32, i64, f64, f64, vp, vp, vp, vp, C.c_size_t, vp, vp]),
+            "bcmg_workspace_size": (i32, [vp, vp]),
+            "bcmg_debug_fail_allocation": (i32, [i64]),
+            "bcmg_debug_live_blocks": (i32, [vp, vp]),
             "bcmg_destroy": (i32, [vp]),
             "bcmg_ghost_count": (i32, [vp, vp]),
             "bcmg_ghost_points": (i32, [vp, vp]),
@@ -81,6 +85,7 @@ def load():
             "bcmg_kernel_launches": (i64, []),
             "bcmg_profile_read": (i32, [vp, vp]),
             "bcmg_residual_norms_static": (i32, [vp, vp, i64, vp, vp]),
+            "bcmg_selftest_div_wsum": (i32, [i32, vp, i64, vp]),
             "bcmg_num_levels": (i32, [vp, vp]),
             "bcmg_level_info": (i32, [vp, i32, vp]),
             "bcmg_get_class": (i32, [vp, i32, vp]),
@@ -106,6 +111,18 @@ def _check(rc):
         raise BcmgError(rc, load().bcmg_last_error().decode())
 
 
+def debug_fail_allocation(k: int) -> None:
+    """The k-th device allocation of the library from now on fails (0: off)."""
+    _check(load().bcmg_debug_fail_allocation(int(k)))
+
+
+def debug_live_blocks():
+    """(blocks, bytes) of device memory live handles hold from the library."""
+    b, n = C.c_int64(), C.c_int64()
+    _check(load().bcmg_debug_live_blocks(C.byref(b), C.byref(n)))
+    return b.value, n.value
+
+
 def kernel_launches() -> int:
     return int(load().bcmg_kernel_launches())
 
@@ -122,6 +139,14 @@ def residual_norms_static(r, cls, out):
         raise ValueError("size mismatch")
     _check(load().bcmg_residual_norms_static(_dptr(r), C.c_void_p(cls.data_ptr()), r.numel(), _dptr(out),
                                              _stream()))
+
+
+def selftest_div_wsum(a: np.ndarray, fp32: bool = False) -> np.ndarray:
+    """a[i] / (1 + i % 64) as the library's restriction divides (host arrays)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.empty_like(a)
+    _check(load().bcmg_selftest_div_wsum(int(fp32), _hptr(a), a.size, _hptr(out)))
+    return out
 
 
 def _dptr(t):
@@ -188,7 +213,10 @@ class Solver:
 
     phi, f: CUDA float64 tensors with (N+1)^dim entries (x fastest)."""
 
-    def __init__(self, dim: int, N: int, phi, f=None, **opts):
+    def __init__(self, dim: int, N: int, phi, f=None, lo=None, h=None, workspace=None, **opts):
+        """lo, h: the box [lo, lo + N h]^dim (default [-1, 1]^dim); workspace:
+        a CUDA tensor whose storage holds every device array of the
+        hierarchy (kept referenced by the solver)."""
         self.lib = load()
         self.dim, self.N = dim, N
         self.n = N + 1
@@ -196,12 +224,26 @@ class Solver:
         if phi.numel() != self.nn:
             raise ValueError("phi must have (N+1)^dim entries")
         o = default_opts(**opts)
-        h = C.c_void_p()
+        hd = C.c_void_p()
         fp = _dptr(f) if f is not None else None
-        _check(self.lib.bcmg_create_grid_hierarchy(dim, N, _dptr(phi), fp, C.byref(o), _stream(),
-                                                   C.byref(h)))
-        self.h = h
+        if lo is None and h is None and workspace is None:
+            _check(self.lib.bcmg_create_grid_hierarchy(dim, N, _dptr(phi), fp, C.byref(o), _stream(),
+                                                       C.byref(hd)))
+        else:
+            lo = -1.0 if lo is None else float(lo)
+            h = 2.0 / N if h is None else float(h)
+            wp, wb = (None, 0) if workspace is None else \
+                (C.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size())
+            _check(self.lib.bcmg_create_grid_hierarchy_ex(dim, N, lo, h, _dptr(phi), fp, C.byref(o), wp, wb,
+                                                          _stream(), C.byref(hd)))
+        self._workspace = workspace
+        self.h = hd
         self.levels = self._num_levels()
+
+    def workspace_size(self) -> int:
+        v = C.c_int64()
+        _check(self.lib.bcmg_workspace_size(self.h, C.byref(v)))
+        return v.value
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

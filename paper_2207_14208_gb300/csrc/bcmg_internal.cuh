@@ -42,6 +42,7 @@ struct Level {
     int64_t nn = 0;
     int64_t st[3] = {0, 0, 0};
     double h = 0.0;
+    double lo = -1.0;  // coordinate of node 0 on every axis (x_i = lo + i h)
     double react = 0.0;  // reaction coefficient c of c u - Lap u = f
     uint8_t *cls = nullptr;
     int64_t nint = 0, nbox = 0, ng = 0, nb = 0, nclamp = 0, nfall = 0, nact = 0;
@@ -150,6 +151,13 @@ struct Handle {
     int64_t captured = 0;
     std::vector<std::pair<void *, size_t>> allocs;
     int64_t dev_bytes = 0;      // device memory the handle holds
+    double lo = -1.0;           // domain box [lo, lo + N h0]^d
+    double h0 = 0.0;            // finest grid spacing
+    // caller-supplied workspace: every device array of the handle (set-up
+    // scratch included) is carved from it; no pool allocation
+    char *ws_base = nullptr;
+    size_t ws_cap = 0, ws_used = 0;
+    int64_t alloc_total = 0;    // bytes drawn during creation (perm + scratch)
     Arena arena_perm, arena_temp;
     std::vector<std::pair<void *, size_t>> temps;  // set-up scratch, freed when creation ends
     // profiling of the finest-level sweeps (opts.profile)
@@ -175,6 +183,7 @@ void count_launch(Handle &H);
 int64_t launches_total();
 void add_launches(int64_t n);
 int report(int code, const std::string &msg);  // sets the thread's last error
+int selftest_div_wsum(int fp32, const double *a_host, int64_t n, double *out_host, std::string *msg);
 
 // ---- set-up (setup.cu) -------------------------------------------------
 void setup_hierarchy(Handle &H, const double *phi0);

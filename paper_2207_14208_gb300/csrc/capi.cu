@@ -104,8 +104,50 @@ void cache_drain() {
     (void)cudaSetDevice(cur);
 }
 
+bool in_workspace(const Handle &H, const void *p) {
+    return H.ws_base && (const char *)p >= H.ws_base && (const char *)p < H.ws_base + H.ws_cap;
+}
+
+// Allocation-failure injection (bcmg_debug_fail_allocation): when the
+// countdown reaches zero the device allocation fails as if the pool were
+// exhausted.  Host-side only: no GPU fault is involved.
+std::atomic<int64_t> g_fail_countdown{0};
+// device blocks (and bytes) held by live handles, outside the cache
+std::atomic<int64_t> g_live_blocks{0}, g_live_bytes{0};
+
+void release_block(Handle &H, void *p, size_t bytes) {
+    if (in_workspace(H, p)) return;
+    g_live_blocks.fetch_sub(1);
+    g_live_bytes.fetch_sub((int64_t)bytes);
+    cache_put(H.dev, bytes, p, H.st);
+}
+
+bool injected_failure() {
+    int64_t c = g_fail_countdown.load();
+    while (c > 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+
 void *raw_alloc(Handle &H, size_t bytes, bool temp) {
-    void *p = cache_take(H.dev, bytes, H.st);
+    if (injected_failure())
+        throw Error{BCMG_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (injected)"};
+    void *p = nullptr;
+    if (H.ws_base) {
+        // the caller's workspace: bump allocation, 256-byte aligned
+        const size_t off = (H.ws_used + 255) & ~(size_t)255;
+        if (off + bytes > H.ws_cap)
+            throw Error{BCMG_ENOMEM, "workspace too small: " + std::to_string(H.ws_cap) + " bytes given, more than " +
+                                         std::to_string(off + bytes) + " needed"};
+        p = H.ws_base + off;
+        H.ws_used = off + bytes;
+        H.alloc_total = (int64_t)H.ws_used;
+        (temp ? H.temps : H.allocs).push_back({p, bytes});
+        if (!temp) H.dev_bytes += (int64_t)bytes;
+        return p;
+    }
+    p = cache_take(H.dev, bytes, H.st);
     if (!p) {
         cudaError_t e = cudaMallocAsync(&p, bytes, H.st);
         if (e != cudaSuccess) {
@@ -120,6 +162,9 @@ void *raw_alloc(Handle &H, size_t bytes, bool temp) {
     }
     (temp ? H.temps : H.allocs).push_back({p, bytes});
     if (!temp) H.dev_bytes += (int64_t)bytes;
+    H.alloc_total += (int64_t)bytes;
+    g_live_blocks.fetch_add(1);
+    g_live_bytes.fetch_add((int64_t)bytes);
     return p;
 }
 
@@ -169,7 +214,7 @@ namespace {
 
 // H's streams are synchronised (creation's closing sync, or destroy)
 void free_temps(Handle &H) {
-    for (auto &pb : H.temps) cache_put(H.dev, pb.second, pb.first, H.st);
+    for (auto &pb : H.temps) release_block(H, pb.first, pb.second);
     H.temps.clear();
     H.arena_temp = Arena{};
 }
@@ -262,7 +307,7 @@ void destroy(Handle *H) {
     pinned_put(H->shost);
     if (H->st) {
         free_temps(*H);
-        for (auto &pb : H->allocs) cache_put(H->dev, pb.second, pb.first, H->st);
+        for (auto &pb : H->allocs) release_block(*H, pb.first, pb.second);
         H->allocs.clear();
         cudaStreamSynchronize(H->st);
     }
@@ -571,6 +616,13 @@ void bcmg_default_opts(bcmg_opts *o) {
 
 int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
                                const bcmg_opts *opts, void *stream, bcmg_handle *out) {
+    return bcmg_create_grid_hierarchy_ex(dim, N, -1.0, N > 0 ? 2.0 / (double)N : 0.0, phi_dev, f_dev, opts,
+                                         nullptr, 0, stream, out);
+}
+
+int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const double *phi_dev,
+                                  const double *f_dev, const bcmg_opts *opts, void *workspace, size_t ws_bytes,
+                                  void *stream, bcmg_handle *out) {
     if (!out) return fail(BCMG_EINVAL, "out is null");
     *out = nullptr;
     if (dim != 2 && dim != 3) return fail(BCMG_EINVAL, "dim must be 2 or 3");
@@ -578,11 +630,19 @@ int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const 
     double nn_d = std::pow((double)(N + 1), dim);
     if (nn_d >= 4294967295.0) return fail(BCMG_EINVAL, "grid has 2^32 nodes or more");
     if (!phi_dev) return fail(BCMG_EINVAL, "phi is null");
+    if (!std::isfinite(lo) || !(h > 0.0) || !std::isfinite(h) || !std::isfinite(lo + (double)N * h))
+        return fail(BCMG_EINVAL, "lo must be finite and h positive and finite");
+    if (workspace && (ws_bytes == 0 || ((uintptr_t)workspace & 255u) != 0))
+        return fail(BCMG_EINVAL, "workspace must be 256-byte aligned with ws_bytes > 0");
     Handle *H = nullptr;
     int rc = guarded([&] {
         H = new Handle();
         H->d = dim;
         H->N = N;
+        H->lo = lo;
+        H->h0 = h;
+        H->ws_base = (char *)workspace;
+        H->ws_cap = workspace ? ws_bytes : 0;
         if (opts) H->o = *opts;
         else bcmg_default_opts(&H->o);
         if (H->o.nu1 < 0 || H->o.nu2 < 0 || H->o.ext_sweeps < 1 || H->o.min_coarse < 2 ||
@@ -779,6 +839,29 @@ int bcmg_dtau_opt(int dim, int bc, int dtau_mode, double dtau_const, double thet
         dtau_mode > 2 || !(theta >= 0.0 && theta <= 1.0))
         return fail(BCMG_EINVAL, "bad dim, bc, dtau_mode or theta");
     *out = dtau_of(dim, bc, dtau_mode, dtau_const, theta);
+    g_last_error.clear();
+    return BCMG_OK;
+}
+
+int bcmg_workspace_size(bcmg_handle h, int64_t *bytes) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!bytes) throw Error{BCMG_EINVAL, "bytes is null"};
+        *bytes = H.alloc_total;
+    });
+}
+
+int bcmg_debug_live_blocks(int64_t *blocks, int64_t *bytes) {
+    if (!blocks || !bytes) return fail(BCMG_EINVAL, "null pointer");
+    *blocks = g_live_blocks.load();
+    *bytes = g_live_bytes.load();
+    g_last_error.clear();
+    return BCMG_OK;
+}
+
+int bcmg_debug_fail_allocation(int64_t k) {
+    if (k < 0) return fail(BCMG_EINVAL, "k must be >= 0");
+    g_fail_countdown.store(k);
     g_last_error.clear();
     return BCMG_OK;
 }

@@ -282,9 +282,15 @@ __device__ const float c_rcp32[65] = {
     1.0f / 47, 1.0f / 48, 1.0f / 49, 1.0f / 50, 1.0f / 51, 1.0f / 52, 1.0f / 53, 1.0f / 54, 1.0f / 55,
     1.0f / 56, 1.0f / 57, 1.0f / 58, 1.0f / 59, 1.0f / 60, 1.0f / 61, 1.0f / 62, 1.0f / 63, 1.0f / 64};
 
-// a / w for an integer weight sum 1 <= w <= 64: q = a y with y = 1/w from
-// the table, then one FMA correction with the exact remainder a - q w (a
-// divide subroutine costs tens of FP64 instructions)
+// a / w for an integer weight sum 1 <= w <= 64 by Markstein's correction
+// (P. W. Markstein, IBM J. Res. Dev. 34(1), 1990; the theorem in Muller et
+// al., Handbook of Floating-Point Arithmetic, on correcting a quotient with
+// one FMA): y = RN(1/w) from the table, q = RN(a y), the remainder
+// r = a - q w is exact in one FMA, and RN(q + r y) is the correctly rounded
+// a / w whenever y is the correctly rounded reciprocal, q lies within one
+// ulp of a / w and nothing underflows.  A divide subroutine costs tens of
+// FP64 instructions; this costs one multiply and two FMAs
+// (bcmg_selftest_div_wsum checks it against true division).
 template <typename T>
 __device__ __forceinline__ T div_wsum(T a, int w) {
     const T y = sizeof(T) == 8 ? (T)c_rcp64[w] : (T)c_rcp32[w];
@@ -1753,6 +1759,42 @@ void set_interior_rhs(Handle &H, Level &L, const double *f, double *F) {
            L.Fs, g2_of(L));
 }
 
+namespace {
+template <typename T>
+__global__ void k_div_wsum_test(const double *__restrict__ a, int64_t n, double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)div_wsum<T>((T)a[i], (int)(1 + i % 64));
+}
+}  // namespace
+
+int selftest_div_wsum(int fp32, const double *a_host, int64_t n, double *out_host, std::string *msg) {
+    if (!a_host || !out_host || n < 1 || n > (1 << 24)) {
+        *msg = "null pointer or n outside [1, 2^24]";
+        return BCMG_EINVAL;
+    }
+    double *buf = nullptr;
+    const size_t bytes = (size_t)n * sizeof(double);
+    if (cudaMalloc(&buf, 2 * bytes) != cudaSuccess) {
+        *msg = "cudaMalloc failed";
+        return BCMG_ENOMEM;
+    }
+    int rc = BCMG_OK;
+    cudaError_t e = cudaMemcpy(buf, a_host, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (fp32) k_div_wsum_test<float><<<nblk(n, 256), 256>>>(buf, n, buf + n);
+        else k_div_wsum_test<double><<<nblk(n, 256), 256>>>(buf, n, buf + n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, buf + n, bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        *msg = std::string("selftest_div_wsum: ") + cudaGetErrorString(e);
+        rc = BCMG_ECUDA;
+    }
+    cudaFree(buf);
+    add_launches(1);
+    return rc;
+}
+
 template void smooth<double>(Handle &, Level &, double *, const double *, int, const double *);
 template void residual<double>(Handle &, Level &, const double *, const double *, double *);
 template void extend<double>(Handle &, Level &, double *);
@@ -1767,3 +1809,9 @@ template void prolong<float>(Handle &, Level &, Level &, const float *, float *,
 template void coarsest_correct<float>(Handle &, Level &, float *, const float *);
 
 }  // namespace bcmg
+
+extern "C" int bcmg_selftest_div_wsum(int fp32, const double *a_host, int64_t n, double *out_host) {
+    std::string msg;
+    int rc = bcmg::selftest_div_wsum(fp32, a_host, n, out_host, &msg);
+    return bcmg::report(rc, msg);
+}

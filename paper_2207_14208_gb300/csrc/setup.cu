@@ -18,7 +18,7 @@ namespace {
 struct Geo {
     int d, N, n;
     int64_t st[3];
-    double h;
+    double h, lo;
 };
 
 Geo geo_of(const Level &L) {
@@ -28,6 +28,7 @@ Geo geo_of(const Level &L) {
     g.n = L.n;
     for (int a = 0; a < 3; ++a) g.st[a] = L.st[a];
     g.h = L.h;
+    g.lo = L.lo;
     return g;
 }
 
@@ -614,7 +615,7 @@ __device__ __forceinline__ void ghost_one(int bc, const uint32_t *__restrict__ g
         out.nrm[(int64_t)a * ng + g] = n[a];
         if (s[a] < 0) code |= (uint16_t)(1u << a);
         code |= (uint16_t)((unsigned)q[a] << (3 + 2 * a));
-        double xg = __dadd_rn(-1.0, __dmul_rn((double)ix[a], G.h));
+        double xg = __dadd_rn(G.lo, __dmul_rn((double)ix[a], G.h));
         out.Q[g * d + a] = __dsub_rn(xg, __dmul_rn(__dmul_rn(eta, G.h), n[a]));
     }
     out.code[g] = code;
@@ -1255,7 +1256,9 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             L.d = H.d;
             L.N = (int)Nl;
             L.n = (int)Nl + 1;
-            L.h = 2.0 / (double)Nl;
+            // h_l = h_0 2^l (exact: a power-of-two scaling)
+            L.h = std::ldexp(H.h0, l);
+            L.lo = H.lo;
             L.react = H.o.reaction;
             L.nn = 1;
             for (int a = 0; a < H.d; ++a) {

@@ -139,55 +139,101 @@ def solve_one(req: Request):
 
 class Server:
     """Admits requests by estimated footprint and runs up to `workers` of
-    them at once, each on its own stream."""
+    them at once, each on its own stream.
 
-    def __init__(self, mem_budget: int, workers: int = 8):
+    If a creation still runs out of device memory (BCMG_ENOMEM: the estimate
+    was low for that geometry, or other users hold memory), the request is
+    not failed: its budget is released, the admission limit backs off to the
+    memory the other requests in flight hold, and the request goes back to
+    the head of the queue (its arrival order is kept) to be admitted again
+    once enough of them have finished.  After `max_retries` such returns, or
+    if it fails with nothing else in flight, its result carries the ENOMEM
+    status.  The limit returns to `mem_budget` after the next success."""
+
+    def __init__(self, mem_budget: int, workers: int = 8, max_retries: int = 8):
         self.mem_budget = int(mem_budget)
         self.workers = int(workers)
+        self.max_retries = int(max_retries)
+        self.backoffs = 0  # ENOMEM returns of the last run
+
+    # device-facing parts (a test replaces them to drive the admission logic
+    # without a GPU)
+    def estimate(self, req: Request) -> int:
+        return bcmg.footprint_estimate(req.dim, req.N, precision=req.precision)
+
+    def execute(self, req: Request):
+        """(cycles, rel, status, footprint, u) of one request; raises
+        bcmg.BcmgError on a failed creation."""
+        import torch
+        torch.cuda.set_device(self._dev)
+        with torch.cuda.stream(torch.cuda.Stream()):  # its own caller stream
+            return solve_one(req)
+
+    def _prepare(self):
+        import torch
+        self._dev = torch.cuda.current_device()
 
     def run(self, requests: list[Request]) -> list[Result]:
         """Replay the requests at their arrival times; return their results
         in completion order."""
-        import torch
-        dev = torch.cuda.current_device()
+        self._prepare()
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
         for r in pending:
-            est = bcmg.footprint_estimate(r.dim, r.N, precision=r.precision)
+            est = self.estimate(r)
             if est > self.mem_budget:
                 raise ValueError("request %d needs %d bytes, more than the budget" % (r.rid, est))
         lock = threading.Condition()
-        state = {"in_use": 0, "busy": 0}
+        state = {"in_use": 0, "busy": 0, "limit": self.mem_budget}
+        retries: dict = {}
         results: list[Result] = []
+        queue: list = []  # arrived, not yet admitted: (arrival, rid, req, est)
+        self.backoffs = 0
         t0 = time.perf_counter()
 
         def work(req: Request, est: int, start: float):
-            torch.cuda.set_device(dev)
             try:
-                with torch.cuda.stream(torch.cuda.Stream()):  # its own caller stream
-                    cyc, rel, st, fp, u = solve_one(req)
+                cyc, rel, st, fp, u = self.execute(req)
             except bcmg.BcmgError as e:
+                with lock:
+                    others = state["in_use"] - est
+                    if e.code == bcmg.ENOMEM and others > 0 and retries.get(req.rid, 0) < self.max_retries:
+                        # back off: admit no more than what the others hold
+                        # until one of them finishes, and queue it again
+                        retries[req.rid] = retries.get(req.rid, 0) + 1
+                        self.backoffs += 1
+                        state["in_use"] -= est
+                        state["busy"] -= 1
+                        state["limit"] = max(others, est)
+                        heapq.heappush(queue, (req.arrival, req.rid, req, est))
+                        lock.notify_all()
+                        return
                 cyc, rel, st, fp, u = 0, float("nan"), e.code, 0, None
             done = time.perf_counter() - t0
             with lock:
                 results.append(Result(req.rid, cyc, rel, st, req.arrival, start, done, fp, u))
                 state["in_use"] -= est
                 state["busy"] -= 1
+                if st != bcmg.ENOMEM:
+                    state["limit"] = self.mem_budget
                 lock.notify_all()
 
-        queue: list = []  # arrived, not yet admitted: (arrival, rid, req, est)
         i = 0
         with ThreadPoolExecutor(self.workers) as ex:
-            while i < len(pending) or queue:
+            while True:
+                with lock:
+                    if i >= len(pending) and not queue and state["busy"] == 0:
+                        break
                 now = time.perf_counter() - t0
                 while i < len(pending) and pending[i].arrival <= now:
                     r = pending[i]
-                    heapq.heappush(queue, (r.arrival, r.rid, r,
-                                           bcmg.footprint_estimate(r.dim, r.N, precision=r.precision)))
+                    est = self.estimate(r)
+                    with lock:
+                        heapq.heappush(queue, (r.arrival, r.rid, r, est))
                     i += 1
                 with lock:
                     # first come, first served; the head waits for memory
                     while queue and state["busy"] < self.workers and \
-                            state["in_use"] + queue[0][3] <= self.mem_budget:
+                            (state["in_use"] + queue[0][3] <= state["limit"] or state["busy"] == 0):
                         _, _, r, est = heapq.heappop(queue)
                         state["in_use"] += est
                         state["busy"] += 1
@@ -196,8 +242,7 @@ class Server:
                         wait = max(0.0, pending[i].arrival - (time.perf_counter() - t0))
                     else:
                         wait = None
-                    if queue or i < len(pending):
-                        lock.wait(timeout=wait if not queue else 0.05 if wait is None else min(wait, 0.05))
+                    lock.wait(timeout=0.05 if wait is None else min(wait, 0.05))
             ex.shutdown(wait=True)
         return results
 

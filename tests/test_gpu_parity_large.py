@@ -6,7 +6,7 @@ coarsening stops at the odd N = 15), and 3D ellipsoids whose level sizes are
 not powers of two (N = 320 down to 10, N = 336 down to the odd 21): set-up
 identical to the oracle's on every level, then V-cycles from zero and from a
 random start within 1e-12 of the oracle's, and the mixed-precision solve on
-the FP64 solution to 1e-10.
+the FP64 solution to 1e-10 (both solved to a relative residual of 1e-10).
 """
 
 import numpy as np
@@ -103,8 +103,10 @@ def test_large_mixed_matches_fp64(bcmg, name, d, N, mk):
         g = W.g_at(d, host(s.ghost_points()))
         s.set_boundary_values(dev(g))
         u = torch.zeros((N + 1) ** d, dtype=torch.float64, device="cuda")
-        c, rel = s.solve(u, 1e-13, 200)
-        assert rel <= 1e-13
+        # 1e-10 is the workloads' tolerance; far below it the FP64 residual of
+        # these grids reaches its rounding floor (rows of size 2d |u| / h^2)
+        c, rel = s.solve(u, 1e-10, 100)
+        assert rel <= 1e-10
         out[prec] = (host(u), c, s.cls(0))
     u64, c64, cls = out[B.PREC_FP64]
     u32, c32, _ = out[B.PREC_MIXED]

@@ -78,3 +78,20 @@ def test_static_norms_reject_oversized_input(bcmg):
                                              big, ctypes.c_void_p(out.data_ptr()), None)
     assert rc == B.EINVAL
     assert "capacity" in B.load().bcmg_last_error().decode()
+
+
+def test_static_norms_large_input(bcmg):
+    # 257^3 entries: more than 1024 partial blocks, so the final reduction
+    # walks its partials in strides; checked against a torch reduction of the
+    # interior and ghost entries, on two different inputs in a row
+    B = bcmg
+    n = 257 ** 3
+    g = torch.Generator(device="cuda").manual_seed(5)
+    cls = torch.randint(0, 4, (n,), generator=g, device="cuda", dtype=torch.uint8)
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    for call in range(2):
+        r = torch.rand(n, generator=g, device="cuda", dtype=torch.float64) * 2 - 1
+        B.residual_norms_static(r, cls, out)
+        ri, rg = r[cls == B.INTERIOR], r[cls == B.GHOST]
+        want = torch.stack([ri.norm(), rg.norm(), ri.abs().max(), rg.abs().max()]).cpu().numpy()
+        np.testing.assert_allclose(out.cpu().numpy(), want, rtol=RTOL, atol=0)
