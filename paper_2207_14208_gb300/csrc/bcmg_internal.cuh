@@ -1,7 +1,8 @@
 // Internal declarations of the GB300 BCMG library (not part of the C ABI).
 //
 // Data layout in HBM, per level l (N_l = N >> l cells, n_l = N_l + 1 nodes per
-// axis, dense x-fastest arrays of n_l^d entries):
+// axis; node X = i + n j + n^2 k; cls dense x-fastest, the value arrays u, F,
+// Fs, r parity-split, see split_ho below):
 //   cls  uint8 node class (INACTIVE / INTERIOR / GHOST / BOXDIR)
 //   u    FP64 solution (level 0: internal copy) or correction e (l > 0)
 //   F    FP64 right-hand side: f on interior rows, g on ghost rows (level 0),
@@ -37,9 +38,33 @@ constexpr int kTailNodes = BCMG_TAIL_NODES;  // coarse levels up to this many in
 constexpr int kTailCoarse = 1024;  // largest coarsest system the tail inverts
 constexpr int32_t kNoRef = INT32_MIN;
 
+// Level arrays of values (u, F, Fs, r and their FP32 copies) are stored
+// parity-split: node X (linear index i + n j + n^2 k) lives at position
+// (X >> 1) + (X & 1) ho, the even-index nodes first, the odd-index nodes
+// from offset ho on.  Every smoothed level has an odd n = N + 1, and then
+// the parity of X is the red-black colour (i + j + k) mod 2, so each colour
+// is one contiguous half: a sweep reads the other colour's half and writes
+// its own densely.  ho is ceil(nn / 2) rounded up to 32 entries.
+__host__ __device__ __forceinline__ int64_t split_ho(int64_t nn) { return ((nn + 1) / 2 + 31) / 32 * 32; }
+__host__ __device__ __forceinline__ int64_t split_len(int64_t nn) { return split_ho(nn) + nn / 2; }
+// A level's layout: position of node X = (X >> s) + ((X & m) ? ho : 0):
+// s = m = 1 and ho = split_ho(nn) for the parity-split layout (the grid
+// levels), s = m = ho = 0 for the dense one (the small levels of the cluster
+// tail, where the split layout only lengthens latency-bound gathers).  Node
+// indices and positions are below 2^32 (checked at creation); 32-bit
+// arithmetic keeps the address chains short.
+struct Lay {
+    uint32_t s = 1, m = 1, ho = 0;
+};
+__host__ __device__ __forceinline__ uint32_t pos(int64_t X, const Lay &y) {
+    const uint32_t x = (uint32_t)X;
+    return (x >> y.s) + ((x & y.m) ? y.ho : 0u);
+}
+
 struct Level {
     int d = 0, N = 0, n = 0;
     int64_t nn = 0;
+    Lay lay;  // layout of the value arrays (parity-split unless a tail level)
     int64_t st[3] = {0, 0, 0};
     double h = 0.0;
     double lo = -1.0;  // coordinate of node 0 on every axis (x_i = lo + i h)
@@ -158,6 +183,7 @@ struct Handle {
     char *ws_base = nullptr;
     size_t ws_cap = 0, ws_used = 0;
     int64_t alloc_total = 0;    // bytes drawn during creation (perm + scratch)
+    double *stage[3] = {nullptr, nullptr, nullptr};  // split scratch of the stage operators
     Arena arena_perm, arena_temp;
     std::vector<std::pair<void *, size_t>> temps;  // set-up scratch, freed when creation ends
     // profiling of the finest-level sweeps (opts.profile)
@@ -220,7 +246,13 @@ void vcycle_enqueue(Handle &H, int l, double *u);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,
 // u += correction; r must hold the FP64 residual of u
 void mixed_step_enqueue(Handle &H, double *u);
-void copy_active(Handle &H, const double *src, double *dst, bool with_boxdir);
+// in: the caller's dense u (interior, ghost and eliminated box nodes) into
+// the finest working copy (parity-split); otherwise the working copy's
+// interior and ghost nodes back into the caller's dense array
+void copy_active(Handle &H, const double *src, double *dst, bool in);
+// whole level arrays between the caller's dense layout and the split one
+void dense_to_split(Handle &H, const Level &L, const double *dense, double *split);
+void split_to_dense(Handle &H, const Level &L, const double *split, double *dense);
 void scatter_ghost_values(Handle &H, Level &L, const double *g, double *F);
 void set_interior_rhs(Handle &H, Level &L, const double *f, double *F);
 

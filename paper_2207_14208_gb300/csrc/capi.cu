@@ -589,6 +589,26 @@ int solve_status(int status) {
     return BCMG_OK;
 }
 
+// The stage operators take the caller's arrays in the dense layout; the
+// kernels work on the parity-split one, so the arrays go through the
+// handle's stage scratch (allocated on the first stage call, three arrays
+// of the finest level's split length, from the library's allocator even
+// when the hierarchy lives in a caller workspace).
+double *stage_buf(Handle &H, int k) {
+    if (!H.stage[k]) {
+        char *ws = H.ws_base;
+        H.ws_base = nullptr;
+        try {
+            H.stage[k] = (double *)dalloc(H, sizeof(double) * split_len(H.L[0].nn), false, false);
+        } catch (...) {
+            H.ws_base = ws;
+            throw;
+        }
+        H.ws_base = ws;
+    }
+    return H.stage[k];
+}
+
 }  // namespace
 }  // namespace bcmg
 
@@ -676,7 +696,7 @@ int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const
         // the coarser level still has interior nodes (Sec. 2.1)
         setup_hierarchy(*H, phi_dev);
         Level &L0 = H->L[0];
-        H->u0 = (double *)dalloc(*H, sizeof(double) * L0.nn, false, false);
+        H->u0 = (double *)dalloc(*H, sizeof(double) * split_len(L0.nn), false, false);
         H->npart = (double *)dalloc(*H, sizeof(double) * 4 * (norm_parts(L0) + 1));
         H->ncount = (unsigned *)dalloc(*H, sizeof(unsigned));
         setup_cycle(*H);
@@ -1007,7 +1027,11 @@ int bcmg_smooth(bcmg_handle h, int level, double *u_dev, const double *F_dev, in
         Level &L = level_of(H, level);
         if (!u_dev || !F_dev || nsteps < 0) throw Error{BCMG_EINVAL, "bad argument"};
         enter(H);
-        smooth(H, L, u_dev, F_dev, nsteps);
+        double *u = stage_buf(H, 0), *F = stage_buf(H, 1);
+        dense_to_split(H, L, u_dev, u);
+        dense_to_split(H, L, F_dev, F);
+        smooth(H, L, u, (const double *)F, nsteps);
+        split_to_dense(H, L, u, u_dev);
         leave(H);
     });
 }
@@ -1018,7 +1042,12 @@ int bcmg_residual(bcmg_handle h, int level, const double *u_dev, const double *F
         Level &L = level_of(H, level);
         if (!u_dev || !F_dev || !r_dev) throw Error{BCMG_EINVAL, "bad argument"};
         enter(H);
-        residual(H, L, u_dev, F_dev, r_dev);
+        double *u = stage_buf(H, 0), *F = stage_buf(H, 1), *r = stage_buf(H, 2);
+        dense_to_split(H, L, u_dev, u);
+        dense_to_split(H, L, F_dev, F);
+        dense_to_split(H, L, r_dev, r);
+        residual(H, L, (const double *)u, (const double *)F, r);
+        split_to_dense(H, L, r, r_dev);
         leave(H);
     });
 }
@@ -1029,7 +1058,10 @@ int bcmg_extend(bcmg_handle h, int level, double *a_dev) {
         Level &L = level_of(H, level);
         if (!a_dev) throw Error{BCMG_EINVAL, "bad argument"};
         enter(H);
-        extend(H, L, a_dev);
+        double *a = stage_buf(H, 0);
+        dense_to_split(H, L, a_dev, a);
+        extend(H, L, a);
+        split_to_dense(H, L, a, a_dev);
         leave(H);
     });
 }
@@ -1040,7 +1072,12 @@ int bcmg_restrict(bcmg_handle h, int level, const double *r_fine_dev, double *F_
         if (level < 0 || level + 1 >= (int)H.L.size()) throw Error{BCMG_EINVAL, "level out of range"};
         if (!r_fine_dev || !F_coarse_dev) throw Error{BCMG_EINVAL, "bad argument"};
         enter(H);
-        restrict_to<double>(H, H.L[level], H.L[level + 1], r_fine_dev, F_coarse_dev, nullptr);
+        Level &Lf = H.L[level], &Lc = H.L[level + 1];
+        double *rf = stage_buf(H, 0), *Fc = stage_buf(H, 1);
+        dense_to_split(H, Lf, r_fine_dev, rf);
+        dense_to_split(H, Lc, F_coarse_dev, Fc);
+        restrict_to<double>(H, Lf, Lc, (const double *)rf, Fc, nullptr);
+        split_to_dense(H, Lc, Fc, F_coarse_dev);
         leave(H);
     });
 }
@@ -1051,7 +1088,12 @@ int bcmg_prolong(bcmg_handle h, int level, const double *e_coarse_dev, double *u
         if (level < 0 || level + 1 >= (int)H.L.size()) throw Error{BCMG_EINVAL, "level out of range"};
         if (!e_coarse_dev || !u_fine_dev) throw Error{BCMG_EINVAL, "bad argument"};
         enter(H);
-        prolong(H, H.L[level], H.L[level + 1], e_coarse_dev, u_fine_dev);
+        Level &Lf = H.L[level], &Lc = H.L[level + 1];
+        double *ec = stage_buf(H, 0), *uf = stage_buf(H, 1);
+        dense_to_split(H, Lc, e_coarse_dev, ec);
+        dense_to_split(H, Lf, u_fine_dev, uf);
+        prolong(H, Lf, Lc, (const double *)ec, uf);
+        split_to_dense(H, Lf, uf, u_fine_dev);
         leave(H);
     });
 }
@@ -1061,7 +1103,12 @@ int bcmg_coarsest_solve(bcmg_handle h, double *u_dev, const double *F_dev) {
         Handle &H = *checked(h);
         if (!u_dev || !F_dev) throw Error{BCMG_EINVAL, "bad argument"};
         enter(H);
-        coarsest_correct(H, H.L.back(), u_dev, F_dev);
+        Level &L = H.L.back();
+        double *u = stage_buf(H, 0), *F = stage_buf(H, 1);
+        dense_to_split(H, L, u_dev, u);
+        dense_to_split(H, L, F_dev, F);
+        coarsest_correct(H, L, u, (const double *)F);
+        split_to_dense(H, L, u, u_dev);
         leave(H);
     });
 }

@@ -28,6 +28,7 @@ namespace {
 struct G2 {
     int d, N, n;
     int64_t sy, sz;
+    Lay lay;  // layout of the level's value arrays
     double h2, ih2;
     double diag, inv_diag;  // 2d + c h^2 of c u - Lap_h u = f, and its inverse
 };
@@ -39,6 +40,7 @@ G2 g2_of(const Level &L) {
     g.n = L.n;
     g.sy = L.st[1];
     g.sz = L.st[2];
+    g.lay = L.lay;
     g.h2 = L.h * L.h;
     g.ih2 = 1.0 / g.h2;
     g.diag = 2.0 * L.d + L.react * g.h2;  // exactly 2d without reaction
@@ -48,6 +50,8 @@ G2 g2_of(const Level &L) {
 
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 constexpr int kT = 256;           // largest block of the grid kernels
+constexpr int kMultiMin = 2048;   // sweeps with more entries per SM than this
+                                  // take several entries per thread (FP32)
 constexpr int kTailThreads = 512; // threads per CTA of the cluster tail
 
 // block size for n independent work items: the largest of 256, 128, 64 that
@@ -154,7 +158,7 @@ __device__ __forceinline__ T ghost_Bw(int64_t X, uint16_t code, const T *w, cons
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
         const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
-        v[k] = ghost_term<D>(code, k) ? u[X + o2 * oz + o1 * oy + o0 * ox] : T(0);
+        v[k] = ghost_term<D>(code, k) ? u[pos(X + o2 * oz + o1 * oy + o0 * ox, G.lay)] : T(0);
     }
     T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -179,7 +183,7 @@ __device__ __forceinline__ T ghost_row(int64_t X, uint16_t code, const T *gw, in
         const int o0 = j % 3, o1 = (D == 3) ? j / 3 : 0;
         const bool p = ghost_term<D>(code, k);
         w[j] = p ? gw[(int64_t)k * ng + g] : T(0);
-        v[j] = p ? u[base + o1 * oy + o0 * ox] : T(0);
+        v[j] = p ? u[pos(base + o1 * oy + o0 * ox, G.lay)] : T(0);
     }
     T acc = T(0);
 #pragma unroll
@@ -201,8 +205,8 @@ __device__ __forceinline__ T ghost_B4(bool on, int sub, int64_t X, uint16_t code
 
 template <int D, typename T>
 __device__ __forceinline__ T nbr_sum(const T *u, int64_t X, const G2 &G) {
-    T s = (u[X - 1] + u[X + 1]) + (u[X - G.sy] + u[X + G.sy]);
-    if (D == 3) s += u[X - G.sz] + u[X + G.sz];
+    T s = (u[pos(X - 1, G.lay)] + u[pos(X + 1, G.lay)]) + (u[pos(X - G.sy, G.lay)] + u[pos(X + G.sy, G.lay)]);
+    if (D == 3) s += u[pos(X - G.sz, G.lay)] + u[pos(X + G.sz, G.lay)];
     return s;
 }
 
@@ -213,7 +217,8 @@ __device__ __forceinline__ T nbr_sum(const T *u, int64_t X, const G2 &G) {
 template <int D, typename T>
 __device__ __forceinline__ void smooth_at(int64_t X, T *u, const T *F, const G2 &G) {
     const T s = nbr_sum<D, T>(u, X, G);
-    u[X] = fma((T)G.h2, F[X], s) * (T)G.inv_diag;
+    const int64_t x = pos(X, G.lay);
+    u[x] = fma((T)G.h2, F[x], s) * (T)G.inv_diag;
 }
 
 // the same update from Fs = h^2 F / (2d + c h^2), kept beside F on the
@@ -221,7 +226,29 @@ __device__ __forceinline__ void smooth_at(int64_t X, T *u, const T *F, const G2 
 template <int D, typename T>
 __device__ __forceinline__ void smooth_at_s(int64_t X, T *u, const T *Fs, const G2 &G) {
     const T s = nbr_sum<D, T>(u, X, G);
-    u[X] = fma(s, (T)G.inv_diag, Fs[X]);
+    const int64_t x = pos(X, G.lay);
+    u[x] = fma(s, (T)G.inv_diag, Fs[x]);
+}
+
+// The same update when every node of the list has the parity par of its
+// index and n is odd (the red and black lists of every smoothed level): with
+// m = X >> 1 the node sits at m in its own half and its 2d neighbours, all
+// of the other parity, at fixed offsets from m in the other half, so the
+// sweep reads one contiguous run of the other colour per axis direction and
+// writes its own colour densely.  Same terms, same order as nbr_sum.
+template <int D, typename T>
+__device__ __forceinline__ void smooth_at_par(uint32_t X, T *u, const T *Fs, const G2 &G, int par) {
+    const uint32_t m = X >> 1;
+    const T *v = u + (par ? 0 : G.lay.ho) + m;
+    const int64_t sy = G.sy, sz = G.sz;
+    const int64_t xm = par - 1, xp = par, ym = par - ((sy + 1) >> 1), yp = par + ((sy - 1) >> 1);
+    T s = (v[xm] + v[xp]) + (v[ym] + v[yp]);
+    if (D == 3) {
+        const int64_t zm = par - ((sz + 1) >> 1), zp = par + ((sz - 1) >> 1);
+        s += v[zm] + v[zp];
+    }
+    const int64_t x = (par ? G.lay.ho : 0) + m;
+    u[x] = fma(s, (T)G.inv_diag, Fs[x]);
 }
 
 // Fs of an interior row from its F
@@ -234,7 +261,8 @@ __device__ __forceinline__ T scaled_rhs(T f, const G2 &G) {
 template <int D, typename T>
 __device__ __forceinline__ T residual_int(int64_t X, const T *u, const T *F, const G2 &G) {
     const T s = nbr_sum<D, T>(u, X, G);
-    return F[X] - ((T)G.diag * u[X] - s) * (T)G.ih2;
+    const int64_t x = pos(X, G.lay);
+    return F[x] - ((T)G.diag * u[x] - s) * (T)G.ih2;
 }
 
 // Restriction (Sec. 2.1 eq. coarseFW, Sec. 3.3.2): FW if all 3^d fine
@@ -341,7 +369,7 @@ __device__ __forceinline__ T restrict_masked(const int ic[3], uint32_t mask, con
         const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
         const int64_t Y = (int64_t)(2 * ic[0] + ox) + (int64_t)(2 * ic[1] + oy) * Gf.sy +
                           (int64_t)(2 * ic[2] + oz) * Gf.sz;
-        v[k] = ((mask >> k) & 1u) ? rf[Y] : T(0);
+        v[k] = ((mask >> k) & 1u) ? rf[pos(Y, Gf.lay)] : T(0);
     }
     T fw = T(0);
 #pragma unroll
@@ -366,7 +394,7 @@ __device__ __forceinline__ T prolong_at(const int iy[3], const T *ec, const G2 &
     for (int k = 0; k < NC; ++k) {
         const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
         const bool p = b0 <= t0 && b1 <= t1 && b2 <= t2;
-        c[k] = p ? ec[C0 + b0 + b1 * Gc.sy + b2 * Gc.sz] : T(0);
+        c[k] = p ? ec[pos(C0 + b0 + b1 * Gc.sy + b2 * Gc.sz, Gc.lay)] : T(0);
     }
     T v = c[0];
     if (t0) v += c[1];
@@ -415,12 +443,12 @@ __device__ __forceinline__ void ell_first(int64_t b, const uint8_t *ecnt, const 
 // eight with predicated loads so that their gathers overlap
 template <typename T>
 __device__ __forceinline__ T extend_from(int64_t b, const EllRound<T> &R, const uint32_t *eg, const double *ew,
-                                         int64_t nb, const T *a) {
+                                         int64_t nb, const T *a, Lay ly) {
     T v = T(0);
     {
         T x[kEllFirst];
 #pragma unroll
-        for (int j = 0; j < kEllFirst; ++j) x[j] = j < R.c ? a[R.g[j]] : T(0);
+        for (int j = 0; j < kEllFirst; ++j) x[j] = j < R.c ? a[pos(R.g[j], ly)] : T(0);
 #pragma unroll
         for (int j = 0; j < kEllFirst; ++j)
             if (j < R.c) v = fma(R.w[j], x[j], v);
@@ -432,7 +460,7 @@ __device__ __forceinline__ T extend_from(int64_t b, const EllRound<T> &R, const 
             const bool p = k0 + j < R.c;
             const int64_t e = (int64_t)(k0 + j) * nb + b;
             w[j] = p ? (T)ew[e] : T(0);
-            x[j] = p ? a[eg[e]] : T(0);
+            x[j] = p ? a[pos(eg[e], ly)] : T(0);
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -444,15 +472,63 @@ __device__ __forceinline__ T extend_from(int64_t b, const EllRound<T> &R, const 
 // ------------------------------------------------------------ grid kernels
 template <int D, typename T>
 // Fs != null: the update from the scaled right-hand side (the cycle's
-// levels keep it); else from F (a caller's own F)
+// levels keep it); else from F (a caller's own F).  par 0 / 1: every node of
+// the list has that index parity and n is odd; -1: no such promise
 __global__ void __launch_bounds__(kT) k_smooth(const uint32_t *__restrict__ list, int64_t n, T *u,
-                                               const T *__restrict__ F, const T *__restrict__ Fs, G2 G) {
+                                               const T *__restrict__ F, const T *__restrict__ Fs, G2 G, int par) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t X = i < n ? list[i] : 0u;
     pdl_begin();
     if (i < n) {
-        if (Fs) smooth_at_s<D, T>(X, u, Fs, G);
+        if (Fs && par >= 0) smooth_at_par<D, T>(X, u, Fs, G, par);
+        else if (Fs) smooth_at_s<D, T>(X, u, Fs, G);
         else smooth_at<D, T>(X, u, F, G);
+    }
+}
+
+// The same sweep with NPT list entries per thread (entries i0 + j blockDim,
+// coalesced per j) on a parity-split level with odd n: all entries' loads
+// are issued before any update, which multiplies the loads a thread has in
+// flight (the FP32 sweep on large grids is bound by memory latency, not by
+// arithmetic).  A colour sweep reads only the other colour and writes only
+// its own, so the entries of a thread never depend on one another.
+template <int D, typename T, int NPT>
+__global__ void __launch_bounds__(kT) k_smooth_multi(const uint32_t *__restrict__ list, int64_t n, T *u,
+                                                     const T *__restrict__ Fs, G2 G, int par) {
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * NPT + threadIdx.x;
+    uint32_t m[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = i0 + (int64_t)j * blockDim.x;
+        m[j] = i < n ? (list[i] >> 1) : 0u;
+    }
+    pdl_begin();
+    const int64_t sy = G.sy, sz = G.sz;
+    const int64_t xm = par - 1, xp = par, ym = par - ((sy + 1) >> 1), yp = par + ((sy - 1) >> 1);
+    const int64_t zm = par - ((sz + 1) >> 1), zp = par + ((sz - 1) >> 1);
+    const T *v = u + (par ? 0 : G.lay.ho);
+    const int64_t own = par ? G.lay.ho : 0;
+    T a[NPT][D == 3 ? 6 : 4], f[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const bool on = i0 + (int64_t)j * blockDim.x < n;
+        const T *w = v + m[j];
+        a[j][0] = on ? w[xm] : T(0);
+        a[j][1] = on ? w[xp] : T(0);
+        a[j][2] = on ? w[ym] : T(0);
+        a[j][3] = on ? w[yp] : T(0);
+        if (D == 3) {
+            a[j][4] = on ? w[zm] : T(0);
+            a[j][5] = on ? w[zp] : T(0);
+        }
+        f[j] = on ? Fs[own + m[j]] : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        if (i0 + (int64_t)j * blockDim.x >= n) continue;
+        T s = (a[j][0] + a[j][1]) + (a[j][2] + a[j][3]);
+        if (D == 3) s += a[j][4] + a[j][5];
+        u[own + m[j]] = fma(s, (T)G.inv_diag, f[j]);
     }
 }
 
@@ -472,16 +548,19 @@ __global__ void __launch_bounds__(kT) k_ghost_relax(const uint32_t *__restrict__
     T w[(D == 3) ? 27 : 9];
     ghost_weights<D, T>(code, gw, ng, on ? g : 0, w);
     pdl_begin();
-    if (on) tmp[g] = fma(dt, F[X] - ghost_Bw<D, T>(X, code, w, u, G), u[X]);
+    if (on) {
+        const int64_t x = pos(X, G.lay);
+        tmp[g] = fma(dt, F[x] - ghost_Bw<D, T>(X, code, w, u, G), u[x]);
+    }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kT) k_ghost_scatter(const uint32_t *__restrict__ gidx, int64_t ng,
-                                                      const T *__restrict__ tmp, T *__restrict__ u) {
+                                                      const T *__restrict__ tmp, T *__restrict__ u, Lay ly) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t X = g < ng ? gidx[g] : 0u;
     pdl_begin();
-    if (g < ng) u[X] = tmp[g];
+    if (g < ng) u[pos(X, ly)] = tmp[g];
 }
 
 // the block's norm partials (sum r^2, max|r|) of one row class, reduced in
@@ -661,7 +740,7 @@ __global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict_
     for (int j = 0; j < NPT; ++j) {
         if (i0 + (int64_t)j * blockDim.x < nint) {
             const T v = residual_int<D, T>(X[j], u, F, G);
-            r[X[j]] = v;
+            r[pos(X[j], G.lay)] = v;
             s2 = fma((double)v, (double)v, s2);
             mxb = max(mxb, abs_bits((double)v));
         }
@@ -693,8 +772,9 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
     // the interior rows still run; only the final reduction waits for them.
     if (!early) pdl_begin();
     if (on) {
-        const T v = F[X] - ghost_Bw<D, T>(X, code, w, u, G);
-        r[X] = v;
+        const int64_t x = pos(X, G.lay);
+        const T v = F[x] - ghost_Bw<D, T>(X, code, w, u, G);
+        r[x] = v;
         s2 = (double)v * (double)v;
         mxb = abs_bits((double)v);
     }
@@ -707,7 +787,7 @@ template <typename T>
 __global__ void __launch_bounds__(kT) k_extend_ell(const uint32_t *__restrict__ bidx,
                                                    const uint8_t *__restrict__ ecnt,
                                                    const uint32_t *__restrict__ eg, const double *__restrict__ ew,
-                                                   int64_t nb, T *a) {
+                                                   int64_t nb, T *a, Lay ly) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool on = b < nb;
     const uint32_t X = on ? bidx[b] : 0u;
@@ -715,7 +795,7 @@ __global__ void __launch_bounds__(kT) k_extend_ell(const uint32_t *__restrict__ 
     R.c = 0;
     if (on) ell_first<T>(b, ecnt, eg, ew, nb, R);
     pdl_begin();
-    if (on) a[X] = extend_from<T>(b, R, eg, ew, nb, a);
+    if (on) a[pos(X, ly)] = extend_from<T>(b, R, eg, ew, nb, a, ly);
 }
 
 // One explicit pseudo-time sweep of dr/dsigma + dr/dn = 0 with upwind
@@ -724,7 +804,7 @@ __global__ void __launch_bounds__(kT) k_extend_ell(const uint32_t *__restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(kT) k_extend(const uint32_t *__restrict__ bidx, const int32_t *__restrict__ bref,
                                                const double *__restrict__ bw, int64_t nb, int d, T *a,
-                                               const T *__restrict__ in, T *__restrict__ out, int last) {
+                                               const T *__restrict__ in, T *__restrict__ out, int last, Lay ly) {
     pdl_begin();
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -733,11 +813,11 @@ __global__ void __launch_bounds__(kT) k_extend(const uint32_t *__restrict__ bidx
         const int32_t ref = bref[(int64_t)ax * nb + b];
         if (ref == kNoRef) continue;
         T s;
-        if (ref < 0) s = a[-(int64_t)ref - 1];
+        if (ref < 0) s = a[pos(-(int64_t)ref - 1, ly)];
         else s = in ? in[ref] : T(0);
         v = fma((T)bw[(int64_t)ax * nb + b], s, v);
     }
-    if (last) a[bidx[b]] = v;
+    if (last) a[pos(bidx[b], ly)] = v;
     else out[b] = v;
 }
 
@@ -765,9 +845,10 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
     if (!now) pdl_begin();
     if (on) {
         const T fc = restrict_masked<D, T>(ic, mask, rf, Gf);
-        Fc[Xc] = fc;
-        if (Fsc && interior) Fsc[Xc] = scaled_rhs<T>(fc, Gc);
-        if (uc) uc[Xc] = T(0);
+        const int64_t xc = pos(Xc, Gc.lay);
+        Fc[xc] = fc;
+        if (Fsc && interior) Fsc[xc] = scaled_rhs<T>(fc, Gc);
+        if (uc) uc[xc] = T(0);
     }
     if (now) pdl_begin();
 }
@@ -831,25 +912,26 @@ __global__ void __launch_bounds__(kT) k_prolong(const uint32_t *__restrict__ ili
     // warp-uniform (no lane does its FP64 work twice): early only when the
     // whole warp can go
     now = __all_sync(0xffffffffu, now || !on) && early;
-    if (now && on) uf[X] += prolong_at<D, T>(iy, ec, Gc);
+    if (now && on) uf[pos(X, Gf.lay)] += prolong_at<D, T>(iy, ec, Gc);
     pdl_begin();
-    if (on && !now) uf[X] += prolong_at<D, T>(iy, ec, Gc);
+    if (on && !now) uf[pos(X, Gf.lay)] += prolong_at<D, T>(iy, ec, Gc);
 }
 
 template <typename T>
 __global__ void k_coarse_gather(const uint32_t *__restrict__ act, int64_t nact, const T *__restrict__ r,
-                                double *__restrict__ rhs) {
+                                double *__restrict__ rhs, Lay ly) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t X = j < nact ? act[j] : 0u;
     pdl_begin();
-    if (j < nact) rhs[j] = (double)r[X];
+    if (j < nact) rhs[j] = (double)r[pos(X, ly)];
 }
 
 // u[act[i]] += (A^-1 rhs)_i, one warp per row (FP64 accumulation)
 template <typename T>
 __global__ void __launch_bounds__(kT) k_coarse_gemv(const uint32_t *__restrict__ act, int64_t nact,
                                                     const double *__restrict__ Ainv,
-                                                    const double *__restrict__ rhs, T *__restrict__ u) {
+                                                    const double *__restrict__ rhs, T *__restrict__ u,
+                                                    Lay ly) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (i >= nact) return;
@@ -858,7 +940,7 @@ __global__ void __launch_bounds__(kT) k_coarse_gemv(const uint32_t *__restrict__
     for (int64_t j = lane; j < nact; j += 32) s = fma(Ainv[i * nact + j], rhs[j], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) u[act[i]] += (T)s;
+    if (lane == 0) u[pos(act[i], ly)] += (T)s;
 }
 
 // reduce the residual kernel's block partials in block order (deterministic)
@@ -1035,7 +1117,7 @@ __device__ __forceinline__ int64_t tail_entry() {
 // costs two dependent round trips
 template <typename T>
 __device__ __forceinline__ T extend_fixed(int64_t b, int rounds, const uint8_t *ecnt, const uint32_t *eg,
-                                          const double *ew, int64_t nb, const T *a) {
+                                          const double *ew, int64_t nb, const T *a, Lay ly) {
     const int c = ecnt[b];
     T v = T(0);
     for (int r0 = 0; r0 < rounds; r0 += 2) {
@@ -1050,7 +1132,7 @@ __device__ __forceinline__ T extend_fixed(int64_t b, int rounds, const uint8_t *
         }
         T x[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) x[j] = (r0 * 8 + j < c) ? a[e[j]] : T(0);
+        for (int j = 0; j < 16; ++j) x[j] = (r0 * 8 + j < c) ? a[pos(e[j], ly)] : T(0);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
             if (r0 * 8 + j < c) v = fma((T)w[j], x[j], v);
@@ -1068,16 +1150,33 @@ __device__ void tail_smooth(const TailLevel<T> &A, const TailSlots &S, int l, in
     const int64_t e = tail_entry(), g = e >> 2;
     const int sub = (int)(e & 3);
     const bool on = xg != kNone;
+    // register copies of the level's constants and pointers: the table lives
+    // in global memory, and the phases' stores would otherwise force the
+    // compiler to read it again for every access
+    const G2 G = A.g;
+    T *const u = A.u;
+    const T *const Fs = A.Fs, *const F = A.F, *const gw = A.gw;
+    const double *const gdt = A.gdt;
+    const int64_t ng = A.ng;
+    // split layout with odd n: red = even index, black = odd
+    const bool odd_n = (G.n & 1) && G.lay.s == 1;
+    const int64_t xs = pos(xg, G.lay);
     for (int s = 0; s < nsteps; ++s) {
-        if (xr != kNone) smooth_at_s<D, T>(xr, A.u, A.Fs, A.g);
+        if (xr != kNone) {
+            if (odd_n) smooth_at_par<D, T>(xr, u, Fs, G, 0);
+            else smooth_at_s<D, T>(xr, u, Fs, G);
+        }
         tail_sync();
-        if (xb != kNone) smooth_at_s<D, T>(xb, A.u, A.Fs, A.g);
+        if (xb != kNone) {
+            if (odd_n) smooth_at_par<D, T>(xb, u, Fs, G, 1);
+            else smooth_at_s<D, T>(xb, u, Fs, G);
+        }
         tail_sync();
-        const T B = ghost_B4<D, T>(on, sub, xg, code, A.gw, A.ng, g, A.u, A.g);
+        const T B = ghost_B4<D, T>(on, sub, xg, code, gw, ng, g, u, G);
         T gv = T(0);
-        if (on && sub == 0) gv = fma((T)A.gdt[g], A.F[xg] - B, A.u[xg]);
+        if (on && sub == 0) gv = fma((T)gdt[g], F[xs] - B, u[xs]);
         tail_sync();
-        if (on && sub == 0) A.u[xg] = gv;
+        if (on && sub == 0) u[xs] = gv;
         tail_sync();
     }
 }
@@ -1087,13 +1186,16 @@ __device__ void tail_residual(const TailLevel<T> &A, const TailSlots &S, int l) 
     const int t = threadIdx.x;
     const int64_t i = tail_entry();
     const uint32_t xa = S.act[l * kTailThreads + t];
-    if (xa != kNone && i < A.nint) A.r[xa] = residual_int<D, T>(xa, A.u, A.F, A.g);
+    const G2 G = A.g;
+    const T *const u = A.u, *const F = A.F;
+    T *const r = A.r;
+    if (xa != kNone && i < A.nint) r[pos(xa, G.lay)] = residual_int<D, T>(xa, u, F, G);
     // ghost rows four lanes each, as in the relaxation
     const uint32_t xg = S.gh[l * kTailThreads + t];
     const int64_t g = i >> 2;
     const int sub = (int)(i & 3);
-    const T B = ghost_B4<D, T>(xg != kNone, sub, xg, S.gcode[l * kTailThreads + t], A.gw, A.ng, g, A.u, A.g);
-    if (xg != kNone && sub == 0) A.r[xg] = A.F[xg] - B;
+    const T B = ghost_B4<D, T>(xg != kNone, sub, xg, S.gcode[l * kTailThreads + t], A.gw, A.ng, g, u, G);
+    if (xg != kNone && sub == 0) r[pos(xg, G.lay)] = F[pos(xg, G.lay)] - B;
     tail_sync();
 }
 
@@ -1101,8 +1203,8 @@ template <typename T>
 __device__ void tail_extend(const TailLevel<T> &A, const TailSlots &S, int l, T *a) {
     const int t = threadIdx.x;
     const uint32_t xb = S.band[l * kTailThreads + t];
-    if (xb != kNone)
-        a[xb] = extend_fixed<T>(tail_entry(), A.ell_rounds, A.ecnt, A.eg, A.ew, A.nb, a);
+    const Lay ly = A.g.lay;
+    if (xb != kNone) a[pos(xb, ly)] = extend_fixed<T>(tail_entry(), A.ell_rounds, A.ecnt, A.eg, A.ew, A.nb, a, ly);
     tail_sync();
 }
 
@@ -1153,10 +1255,11 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
             const TailLevel<T> &B = tl[l + 1];
             tail_extend<T>(B, S, l + 1, B.u);
             const uint32_t xa = S.act[l * kTailThreads + t];
+            const G2 Ag = A.g, Bg = B.g;
             if (xa != kNone) {
                 int iy[3];
-                coords(xa, (uint32_t)A.g.n, D, iy);
-                A.u[xa] += prolong_at<D, T>(iy, B.u, B.g);
+                coords(xa, (uint32_t)Ag.n, D, iy);
+                A.u[pos(xa, Ag.lay)] += prolong_at<D, T>(iy, B.u, Bg);
             }
             tail_sync();
         }
@@ -1167,17 +1270,20 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
             const TailLevel<T> &B = tl[l + 1];
             tail_extend<T>(A, S, l, A.r);
             const uint32_t xc = S.act[(l + 1) * kTailThreads + t];
+            const G2 Ag = A.g, Bg = B.g;
             if (xc != kNone) {
                 int ic[3];
-                coords(xc, (uint32_t)B.g.n, D, ic);
-                const T fc = restrict_masked<D, T>(ic, S.fmask[(l + 1) * kTailThreads + t], A.r, A.g);
-                B.F[xc] = fc;
-                if (i < B.nint) B.Fs[xc] = scaled_rhs<T>(fc, B.g);
-                B.u[xc] = T(0);
+                coords(xc, (uint32_t)Bg.n, D, ic);
+                const T fc = restrict_masked<D, T>(ic, S.fmask[(l + 1) * kTailThreads + t], A.r, Ag);
+                const int64_t xs = pos(xc, Bg.lay);
+                B.F[xs] = fc;
+                if (i < B.nint) B.Fs[xs] = scaled_rhs<T>(fc, Bg);
+                B.u[xs] = T(0);
             }
             tail_sync();
         } else {  // coarsest: u += A^-1 r on the active rows
-            if (i < A.nact) A.crhs[i] = (double)A.r[A.act[i]];
+            const Lay ly = A.g.lay;
+            if (i < A.nact) A.crhs[i] = (double)A.r[pos(A.act[i], ly)];
             tail_sync();
             const int lane = t & 31;
             const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
@@ -1186,7 +1292,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_tail(const TailLevel<T> *__
                 for (int64_t j = lane; j < A.nact; j += 32) sum = fma(A.Ainv[row * A.nact + j], A.crhs[j], sum);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-                if (lane == 0) A.u[A.act[row]] += (T)sum;
+                if (lane == 0) A.u[pos(A.act[row], ly)] += (T)sum;
             }
             tail_sync();
         }
@@ -1238,29 +1344,31 @@ __global__ void __launch_bounds__(kT) k_ir_begin(const uint32_t *__restrict__ il
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nint + ng) return;
-    const int64_t X = (i < nint) ? ilist[i] : gidx[i - nint];
-    const float f = (float)r[X];
-    F32[X] = f;
-    if (i < nint) Fs32[X] = scaled_rhs<float>(f, G);
-    e32[X] = 0.0f;
+    const int64_t x = pos((i < nint) ? ilist[i] : gidx[i - nint], G.lay);
+    const float f = (float)r[x];
+    F32[x] = f;
+    if (i < nint) Fs32[x] = scaled_rhs<float>(f, G);
+    e32[x] = 0.0f;
 }
 
 // End of a refinement step: u += e on interior and ghost nodes (FP64).
 __global__ void __launch_bounds__(kT) k_ir_update(const uint32_t *__restrict__ ilist, int64_t nint,
                                                   const uint32_t *__restrict__ gidx, int64_t ng,
-                                                  const float *__restrict__ e32, double *__restrict__ u) {
+                                                  const float *__restrict__ e32, double *__restrict__ u,
+                                                  Lay ly) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nint + ng) return;
-    const int64_t X = (i < nint) ? ilist[i] : gidx[i - nint];
-    u[X] += (double)e32[X];
+    const int64_t x = pos((i < nint) ? ilist[i] : gidx[i - nint], ly);
+    u[x] += (double)e32[x];
 }
 
 // ------------------------------------------------------------ data movement
 __global__ void __launch_bounds__(kT) k_copy_active(const uint32_t *__restrict__ ilist, int64_t nint,
                                                     const uint32_t *__restrict__ gidx, int64_t ng,
                                                     const uint32_t *__restrict__ box, int64_t nbox,
-                                                    const double *__restrict__ src, double *__restrict__ dst) {
+                                                    const double *__restrict__ src, double *__restrict__ dst,
+                                                    Lay ly, int to_split) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nint + ng + nbox) return;
@@ -1268,14 +1376,15 @@ __global__ void __launch_bounds__(kT) k_copy_active(const uint32_t *__restrict__
     if (i < nint) X = ilist[i];
     else if (i < nint + ng) X = gidx[i - nint];
     else X = box[i - nint - ng];
-    dst[X] = src[X];
+    if (to_split) dst[pos(X, ly)] = src[X];
+    else dst[X] = src[pos(X, ly)];
 }
 
 __global__ void k_scatter_ghosts(const uint32_t *__restrict__ gidx, int64_t ng, const double *__restrict__ g,
-                                 double *__restrict__ F) {
+                                 double *__restrict__ F, Lay ly) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ng) F[gidx[i]] = g[i];
+    if (i < ng) F[pos(gidx[i], ly)] = g[i];
 }
 
 __global__ void __launch_bounds__(kT) k_set_interior(const uint32_t *__restrict__ ilist, int64_t nint,
@@ -1285,9 +1394,9 @@ __global__ void __launch_bounds__(kT) k_set_interior(const uint32_t *__restrict_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nint) {
         const int64_t X = ilist[i];
-        const double v = f ? f[X] : 0.0;
-        F[X] = v;
-        Fs[X] = scaled_rhs<double>(v, G);
+        const double v = f ? f[X] : 0.0;  // the caller's array: dense
+        F[pos(X, G.lay)] = v;
+        Fs[pos(X, G.lay)] = scaled_rhs<double>(v, G);
     }
 }
 
@@ -1472,8 +1581,10 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
                 if (n == 0) continue;
                 const int bs = bs_for(H, n);
                 const uint32_t *list = L.hlist + L.hoff[q];
-                if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
-                else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
+                // hyperplane p = i + j (+ k) = q: one index parity when n is odd
+                const int par = ((L.n & 1) && L.lay.s == 1) ? (int)(q & 1) : -1;
+                if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
+                else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
             }
         }
         for (int c = 0; c < 2 && H.o.ordering == BCMG_ORDER_RB; ++c) {
@@ -1481,8 +1592,20 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
             const int64_t n = c ? nblack : L.nred;
             const int bs = bs_for(H, n);
             if (prof) profile_mark(H, L);
-            if (L.d == 3) launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
-            else launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G);
+            // red (c = 0) = even index, black = odd, when n is odd
+            const int par = ((L.n & 1) && L.lay.s == 1) ? c : -1;
+            if (sizeof(T) == 4 && Fs && par >= 0 && n >= kMultiMin * (int64_t)H.nsm) {
+                // FP32 sweep of a large level: four entries per thread
+                constexpr int NPT = 4;
+                if (L.d == 3)
+                    launch(H, "k_smooth", k_smooth_multi<3, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
+                else
+                    launch(H, "k_smooth", k_smooth_multi<2, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
+            } else if (L.d == 3) {
+                launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
+            } else {
+                launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
+            }
             if (prof) profile_mark(H, L);
         }
         if (L.d == 3)
@@ -1492,7 +1615,7 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
             launch(H, "k_ghost_relax", k_ghost_relax<2, T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx,
                    (const uint16_t *)L.gcode, gw, (const double *)L.gdt, L.ng, (const T *)u, F, tmp, G);
         launch(H, "k_ghost_scatter", k_ghost_scatter<T>, nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, L.ng,
-               (const T *)tmp, u);
+               (const T *)tmp, u, L.lay);
     }
 }
 
@@ -1540,7 +1663,7 @@ void extend(Handle &H, Level &L, T *a) {
     const int bs = bs_for(H, L.nb);
     if (L.ecnt) {
         launch(H, "k_extend_ell", k_extend_ell<T>, nblk(L.nb, bs), bs, (const uint32_t *)L.bidx,
-               (const uint8_t *)L.ecnt, (const uint32_t *)L.eg, (const double *)L.ew, L.nb, a);
+               (const uint8_t *)L.ecnt, (const uint32_t *)L.eg, (const double *)L.ew, L.nb, a, L.lay);
         return;
     }
     const int K = std::max(H.o.ext_sweeps, 1);
@@ -1550,7 +1673,7 @@ void extend(Handle &H, Level &L, T *a) {
         const int last = (k == K - 1);
         T *out = (k % 2 == 0) ? b0 : b1;
         launch(H, "k_extend", k_extend<T>, nblk(L.nb, bs), bs, (const uint32_t *)L.bidx, (const int32_t *)L.bref,
-               (const double *)L.bw, L.nb, L.d, a, in, out, last);
+               (const double *)L.bw, L.nb, L.d, a, in, out, last, L.lay);
         in = out;
     }
 }
@@ -1594,9 +1717,9 @@ template <typename T>
 void coarsest_correct(Handle &H, Level &L, T *u, const T *F) {
     residual<T>(H, L, u, F, Arr<T>::r(L));
     launch(H, "k_coarse_gather", k_coarse_gather<T>, nblk(L.nact, 64), 64, (const uint32_t *)L.act, L.nact,
-           (const T *)Arr<T>::r(L), L.crhs);
+           (const T *)Arr<T>::r(L), L.crhs, L.lay);
     launch(H, "k_coarse_gemv", k_coarse_gemv<T>, nblk(L.nact, 2), 64, (const uint32_t *)L.act, L.nact,
-           (const double *)L.Ainv, (const double *)L.crhs, u);
+           (const double *)L.Ainv, (const double *)L.crhs, u, L.lay);
 }
 
 // residual of the finest level and its four norms, optionally followed by
@@ -1636,7 +1759,7 @@ void mixed_step_enqueue(Handle &H, double *u) {
            (const double *)L.r, L.F32, L.Fs32, L.u32, g2_of(L));
     vcycle_t<float>(H, 0, L.u32);
     launch(H, "k_ir_update", k_ir_update, grid, kT, (const uint32_t *)L.ilist, L.nint, (const uint32_t *)L.gidx,
-           L.ng, (const float *)L.u32, u);
+           L.ng, (const float *)L.u32, u, L.lay);
 }
 
 // Cycle tables made once after the hierarchy: the ghost interpolation
@@ -1714,6 +1837,9 @@ void setup_cycle(Handle &H) {
     H.tail_cluster = cs;
     H.tail_start = lt;
     const int nl = L - lt;
+    // the tail's levels keep the dense layout (nothing has been written to
+    // their value arrays yet; zeros read the same in either layout)
+    for (int l = lt; l < L; ++l) H.L[l].lay = Lay{0u, 0u, 0u};
     std::vector<uint8_t> ops;
     tail_schedule(0, nl, H.o.cycle == BCMG_CYCLE_W ? 2 : 1, ops);
     H.tail_nops = (int)(ops.size() / 2);
@@ -1743,15 +1869,35 @@ void solve_check_enqueue(Handle &H, unsigned long long cond) {
            (cudaGraphConditionalHandle)cond);
 }
 
-void copy_active(Handle &H, const double *src, double *dst, bool with_boxdir) {
+void copy_active(Handle &H, const double *src, double *dst, bool in) {
     Level &L = H.L[0];
+    const bool with_boxdir = in;
     const int64_t nbox = with_boxdir ? L.nbox : 0;
     launch(H, "k_copy_active", k_copy_active, nblk(L.nint + L.ng + nbox, kT), kT, (const uint32_t *)L.ilist, L.nint,
-           (const uint32_t *)L.gidx, L.ng, (const uint32_t *)L.boxidx, nbox, src, dst);
+           (const uint32_t *)L.gidx, L.ng, (const uint32_t *)L.boxidx, nbox, src, dst, L.lay, (int)with_boxdir);
+}
+
+namespace {
+__global__ void __launch_bounds__(kT) k_permute(const double *__restrict__ src, double *__restrict__ dst, int64_t nn,
+                                                Lay ly, int to_split) {
+    pdl_begin();
+    const int64_t X = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= nn) return;
+    if (to_split) dst[pos(X, ly)] = src[X];
+    else dst[X] = src[pos(X, ly)];
+}
+}  // namespace
+
+void dense_to_split(Handle &H, const Level &L, const double *dense, double *split) {
+    launch(H, "k_permute", k_permute, nblk(L.nn, kT), kT, dense, split, L.nn, L.lay, 1);
+}
+
+void split_to_dense(Handle &H, const Level &L, const double *split, double *dense) {
+    launch(H, "k_permute", k_permute, nblk(L.nn, kT), kT, split, dense, L.nn, L.lay, 0);
 }
 
 void scatter_ghost_values(Handle &H, Level &L, const double *g, double *F) {
-    launch(H, "k_scatter_ghosts", k_scatter_ghosts, nblk(L.ng, kT), kT, (const uint32_t *)L.gidx, L.ng, g, F);
+    launch(H, "k_scatter_ghosts", k_scatter_ghosts, nblk(L.ng, kT), kT, (const uint32_t *)L.gidx, L.ng, g, F, L.lay);
 }
 
 void set_interior_rhs(Handle &H, Level &L, const double *f, double *F) {

@@ -1265,6 +1265,8 @@ void setup_hierarchy(Handle &H, const double *phi0) {
                 L.st[a] = L.nn;
                 L.nn *= L.n;
             }
+            L.lay.s = L.lay.m = 1;
+            L.lay.ho = (uint32_t)split_ho(L.nn);
             H.L.push_back(L);
             if (Nl % 2 != 0 || Nl / 2 < H.o.min_coarse) break;
             Nl /= 2;
@@ -1623,18 +1625,20 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     // level arrays
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
-        if (l > 0) L.u = (double *)dalloc(H, sizeof(double) * L.nn);
+        // value arrays in the parity-split layout (split_len entries)
+        const int64_t sl = split_len(L.nn);
+        if (l > 0) L.u = (double *)dalloc(H, sizeof(double) * sl);
         // F is read on interior and ghost rows only; coarse levels get every
         // such row from the restriction, the finest keeps zeros until the
         // caller sets its data
-        L.F = (double *)dalloc(H, sizeof(double) * L.nn, false, l == 0);
-        L.Fs = (double *)dalloc(H, sizeof(double) * L.nn, false, false);  // written before it is read
-        L.r = (double *)dalloc(H, sizeof(double) * L.nn);
+        L.F = (double *)dalloc(H, sizeof(double) * sl, false, l == 0);
+        L.Fs = (double *)dalloc(H, sizeof(double) * sl, false, false);  // written before it is read
+        L.r = (double *)dalloc(H, sizeof(double) * sl);
         if (H.o.precision == BCMG_PREC_MIXED) {
-            L.u32 = (float *)dalloc(H, sizeof(float) * L.nn);
-            L.F32 = (float *)dalloc(H, sizeof(float) * L.nn, false, false);
-            L.Fs32 = (float *)dalloc(H, sizeof(float) * L.nn, false, false);
-            L.r32 = (float *)dalloc(H, sizeof(float) * L.nn);
+            L.u32 = (float *)dalloc(H, sizeof(float) * sl);
+            L.F32 = (float *)dalloc(H, sizeof(float) * sl, false, false);
+            L.Fs32 = (float *)dalloc(H, sizeof(float) * sl, false, false);
+            L.r32 = (float *)dalloc(H, sizeof(float) * sl);
             L.gtmp32 = (float *)dalloc(H, sizeof(float) * std::max<int64_t>(L.ng, 1));
             L.bbuf32 = (float *)dalloc(H, sizeof(float) * 2 * std::max<int64_t>(L.nb, 1));
         }
