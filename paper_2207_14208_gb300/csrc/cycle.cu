@@ -64,17 +64,25 @@ int bs_for(const Handle &H, int64_t n) {
 
 // Programmatic dependent launch: every cycle kernel is launched with
 // programmatic stream serialisation, so its CTAs may be scheduled while its
-// predecessor drains; each kernel waits (griddepcontrol.wait, a hardware
-// dependency wait that returns once the preceding grid has completed and its
-// writes are visible) and then allows its own successor to be scheduled.
-// Since every kernel waits before it triggers, a kernel that has started
-// knows that all grids before its predecessor are complete.  Before the wait
-// a kernel therefore reads only the level tables that are fixed once the
+// predecessor drains; each kernel waits (griddepcontrol.wait: per the PTX ISA
+// it returns once the prerequisite grid has completed and its memory
+// operations are performed and made visible to the waiting grid) and then
+// allows its own successor to be scheduled (griddepcontrol.launch_dependents).
+// Before the wait a kernel reads the level tables that are fixed once the
 // hierarchy exists (node lists, ghost codes, weights and steps, class bytes,
-// extension maps; creation ends with a stream synchronisation), never u, F,
-// r or other data a cycle writes, and writes nothing -- except the ghost
-// rows of a residual, whose predecessor is the interior rows of the same
-// residual (k_residual_gh).
+// family masks, extension maps; creation ends with a stream
+// synchronisation), and three kernels also do part of their work: the ghost
+// rows of a residual, the coarse interior rows of a restriction and the
+// prolongation of rows with no band corner.  That work reads only values
+// written by grids two or more launches back and writes only what its
+// predecessor neither reads nor writes.  Why those values are visible: a
+// kernel's CTAs are launched only after every CTA of its predecessor has
+// executed launch_dependents, which each does right after its own wait, so
+// the grid two back has completed and its writes were performed and made
+// visible to the predecessor's threads on every SM -- device scope, whose
+// point of coherence is L2 -- before this kernel starts.  The early work reads
+// those values with ld.global.cg, which caches in L2 and not in L1, so no SM
+// can serve it a line cached before they were written.
 __device__ __forceinline__ void pdl_begin() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -129,6 +137,17 @@ __device__ __forceinline__ void coords(uint32_t X, uint32_t n, int D, int ic[3])
     }
 }
 
+// Loads of values a cycle writes.  CG = false: ordinary loads (after the
+// dependency wait).  CG = true: ld.global.cg, cached in L2 only, for the work
+// a few kernels do before their wait on data that grids two or more
+// launches back wrote (see pdl_begin): L2 is the device-wide point of
+// coherence, so those loads cannot hit a stale line of an SM's L1.
+template <bool CG, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // B u~ at a ghost: the (tri/bi)quadratic interpolant on ST_G at Q (eq. BCh),
 // with the tensor-product Lagrange weights tabulated per ghost (gw, term
 // (o2 * 3 + o1) * 3 + o0, term-major).  Branch-free: every term's loads are
@@ -148,7 +167,7 @@ __device__ __forceinline__ void ghost_weights(uint16_t code, const T *gw, int64_
     for (int k = 0; k < ((D == 3) ? 27 : 9); ++k) w[k] = ghost_term<D>(code, k) ? gw[(int64_t)k * ng + g] : T(0);
 }
 
-template <int D, typename T>
+template <int D, typename T, bool CG = false>
 __device__ __forceinline__ T ghost_Bw(int64_t X, uint16_t code, const T *w, const T *u, const G2 &G) {
     const int64_t ox = (code & 1) ? 1 : -1;
     const int64_t oy = (code & 2) ? G.sy : -G.sy;
@@ -158,7 +177,7 @@ __device__ __forceinline__ T ghost_Bw(int64_t X, uint16_t code, const T *w, cons
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
         const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
-        v[k] = ghost_term<D>(code, k) ? u[pos(X + o2 * oz + o1 * oy + o0 * ox, G.lay)] : T(0);
+        v[k] = ghost_term<D>(code, k) ? ldv<CG>(u + pos(X + o2 * oz + o1 * oy + o0 * ox, G.lay)) : T(0);
     }
     T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -360,7 +379,7 @@ __device__ __forceinline__ uint32_t family_mask(const int ic[3], bool interior, 
 
 // restrict_with from the family mask: the same terms in the same order (a
 // non-member adds an exact zero), the weight sum from population counts
-template <int D, typename T>
+template <int D, typename T, bool CG = false>
 __device__ __forceinline__ T restrict_masked(const int ic[3], uint32_t mask, const T *rf, const G2 &Gf) {
     constexpr int NT = (D == 3) ? 27 : 9;
     T v[NT];
@@ -369,7 +388,7 @@ __device__ __forceinline__ T restrict_masked(const int ic[3], uint32_t mask, con
         const int ox = k % 3 - 1, oy = (k / 3) % 3 - 1, oz = (D == 3) ? k / 9 - 1 : 0;
         const int64_t Y = (int64_t)(2 * ic[0] + ox) + (int64_t)(2 * ic[1] + oy) * Gf.sy +
                           (int64_t)(2 * ic[2] + oz) * Gf.sz;
-        v[k] = ((mask >> k) & 1u) ? rf[pos(Y, Gf.lay)] : T(0);
+        v[k] = ((mask >> k) & 1u) ? ldv<CG>(rf + pos(Y, Gf.lay)) : T(0);
     }
     T fw = T(0);
 #pragma unroll
@@ -383,7 +402,7 @@ __device__ __forceinline__ T restrict_masked(const int ic[3], uint32_t mask, con
 // multilinear prolongation at fine node iy (Sec. 2.1, 3.2, 3.3.2): the 2^k
 // coarse neighbours (k = number of odd coordinates) all weigh 2^-k, so their
 // sum is scaled once; the corner loads are predicated, not branched
-template <int D, typename T>
+template <int D, typename T, bool CG = false>
 __device__ __forceinline__ T prolong_at(const int iy[3], const T *ec, const G2 &Gc) {
     const int t0 = iy[0] & 1, t1 = iy[1] & 1, t2 = (D == 3) ? (iy[2] & 1) : 0;
     const int64_t C0 = (int64_t)(iy[0] >> 1) + (int64_t)(iy[1] >> 1) * Gc.sy +
@@ -394,7 +413,7 @@ __device__ __forceinline__ T prolong_at(const int iy[3], const T *ec, const G2 &
     for (int k = 0; k < NC; ++k) {
         const int b0 = k & 1, b1 = (k >> 1) & 1, b2 = (k >> 2) & 1;
         const bool p = b0 <= t0 && b1 <= t1 && b2 <= t2;
-        c[k] = p ? ec[pos(C0 + b0 + b1 * Gc.sy + b2 * Gc.sz, Gc.lay)] : T(0);
+        c[k] = p ? ldv<CG>(ec + pos(C0 + b0 + b1 * Gc.sy + b2 * Gc.sz, Gc.lay)) : T(0);
     }
     T v = c[0];
     if (t0) v += c[1];
@@ -768,12 +787,14 @@ __global__ void __launch_bounds__(kT) k_residual_gh(const uint32_t *__restrict__
     // early: the predecessor is the interior-row kernel of the same
     // residual, which neither reads nor writes what the ghost rows touch; u
     // and F were written by grids before it, which are complete once this
-    // grid runs.  So the ghost rows (and their partials) are computed while
-    // the interior rows still run; only the final reduction waits for them.
+    // grid runs (see pdl_begin).  So the ghost rows (and their partials) are
+    // computed while the interior rows still run, reading u and F through L2;
+    // only the final reduction waits for them.
     if (!early) pdl_begin();
     if (on) {
         const int64_t x = pos(X, G.lay);
-        const T v = F[x] - ghost_Bw<D, T>(X, code, w, u, G);
+        const T v = early ? ldv<true>(F + x) - ghost_Bw<D, T, true>(X, code, w, u, G)
+                          : F[x] - ghost_Bw<D, T>(X, code, w, u, G);
         r[x] = v;
         s2 = (double)v * (double)v;
         mxb = abs_bits((double)v);
@@ -840,11 +861,12 @@ __global__ void __launch_bounds__(kT) k_restrict(const uint32_t *__restrict__ il
     coords(Xc, (uint32_t)Gc.n, D, ic);
     // early (the predecessor is the fine level's ghost residual or band
     // extension): coarse interior rows read fine interior residuals only,
-    // which complete grids wrote, and are restricted before the wait
+    // which complete grids wrote (see pdl_begin), and are restricted before
+    // the wait, reading them through L2
     const bool now = early && interior;
     if (!now) pdl_begin();
     if (on) {
-        const T fc = restrict_masked<D, T>(ic, mask, rf, Gf);
+        const T fc = now ? restrict_masked<D, T, true>(ic, mask, rf, Gf) : restrict_masked<D, T>(ic, mask, rf, Gf);
         const int64_t xc = pos(Xc, Gc.lay);
         Fc[xc] = fc;
         if (Fsc && interior) Fsc[xc] = scaled_rhs<T>(fc, Gc);
@@ -912,7 +934,11 @@ __global__ void __launch_bounds__(kT) k_prolong(const uint32_t *__restrict__ ili
     // warp-uniform (no lane does its FP64 work twice): early only when the
     // whole warp can go
     now = __all_sync(0xffffffffu, now || !on) && early;
-    if (now && on) uf[pos(X, Gf.lay)] += prolong_at<D, T>(iy, ec, Gc);
+    if (now && on) {
+        // before the wait: corners and u_f through L2 (see pdl_begin)
+        const int64_t xf = pos(X, Gf.lay);
+        uf[xf] = ldv<true>(uf + xf) + prolong_at<D, T, true>(iy, ec, Gc);
+    }
     pdl_begin();
     if (on && !now) uf[pos(X, Gf.lay)] += prolong_at<D, T>(iy, ec, Gc);
 }
