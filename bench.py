@@ -55,10 +55,12 @@ def parse():
     p.add_argument("--rtol", type=float, default=1e-10)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-sizes", action="store_true")
     p.add_argument("--arms", choices=["both", "fp64", "mixed"], default="both")
     # the default workload is the 3D ellipsoid at 257^3; the other two are the
     # batched and the served workloads (single GPU, extra lines, not defaults)
-    p.add_argument("--config", choices=["ellipsoid256", "stars_batched", "served"], default="ellipsoid256")
+    p.add_argument("--config", choices=["ellipsoid256", "stars_batched", "served", "large512"],
+                   default="ellipsoid256")
     return p.parse_args()
 
 
@@ -167,6 +169,7 @@ def flush_l2(buf):
 
 # ------------------------------------------------------------ our arm
 FP64_INSTR_PER_UPDATE = 6   # 5 adds, 1 FMA per red/black update (from the scaled right-hand side)
+SWEEPS = 200                # back-to-back sweeps timed for the roofline
 FP64_PEAK_GINSTR = 152 * 2 * 2.07  # SMs x FP64 FMA pipes per clock x GHz (1.26 TFLOP/s)
 # DRAM bytes (read + write) of one finest-level k_smooth<3,double> launch at
 # N=256, from an ncu capture of that kernel.  The counters belong to the
@@ -255,18 +258,17 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         launches = bcmg.kernel_launches() - launches0
         clk = clocks.stop()
-        # the finest-level sweep durations come from one more solve, outside
-        # the timed steps, with event records around those sweeps (a solve
-        # with profiling runs its cycles from a host loop)
-        flush_l2(flush)
-        s, _, _ = step(precision, profile=True)
-        prof.append(s.profile())
+        # the finest-level sweep duration: after one more solve (outside the
+        # timed steps), 200 sweeps back to back between two CUDA events, the
+        # way the sweeps run inside a cycle (each one's start overlapping its
+        # predecessor's end)
+        s, _, _ = step(precision)
+        sweep_ms = s.time_sweeps(SWEEPS) / SWEEPS
         s.close()
         if ws > 1:
             import torch.distributed as dist
             dist.barrier()
         total_ms_max = max_over_ranks(sum(times), ws)
-        sweep_ms = sum(p["smooth_ms"] for p in prof) / max(1, sum(p["smooth_launches"] for p in prof))
         return dict(ms=total_ms_max, cycles=cycles, rels=rels, sweep_ms=sweep_ms, launches=launches,
                     clocks=clk, value=sum(cycles) * ws / (total_ms_max / 1e3))
 
@@ -344,6 +346,8 @@ def run_ours(args, ws, rank, local):
         "clocks": r64["clocks"],
         "gpu_launches": r64["launches"],
     }
+    if rank == 0 and not args.no_sizes:
+        out["sweep_roofline_by_size"] = sweep_rooflines()
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(args, d, N, phi_h, f_h)
     if rank == 0 and not args.no_cpu_baseline:
@@ -354,6 +358,44 @@ def run_ours(args, ws, rank, local):
             np.abs(u64.cpu().numpy()[ah] - u_orc[ah]).max() / np.abs(u_orc[ah]).max())
         out["mixed"]["max_rel_err_vs_oracle"] = float(
             np.abs(u32.cpu().numpy()[ah] - u_orc[ah]).max() / np.abs(u_orc[ah]).max())
+    return out
+
+
+def sweep_rooflines(sizes=(256, 384, 512), nsweeps=100):
+    """The finest-level sweep on the ellipsoid at several grid sizes, timed
+    back to back (bcmg_time_sweeps) after one V-cycle: FP64 against the
+    FP64-pipe peak (6 instructions per update), FP32 (the mixed path's inner
+    sweep) against the measured HBM peak (12 B per update: Fs, the own value,
+    one neighbour value amortised)."""
+    import torch
+    from paper_2207_14208_gb300 import bcmg
+    peak, peak_kind = measured_peaks()
+    out = {}
+    for N in sizes:
+        phi = torch.from_numpy(W.phi_ellipsoid(N)).cuda()
+        f = torch.from_numpy(W.manufactured(3, N)[0]).cuda()
+        row = {}
+        for prec, key in ((bcmg.PREC_FP64, "fp64"), (bcmg.PREC_MIXED, "fp32")):
+            s = bcmg.Solver(3, N, phi, f, precision=prec)
+            s.set_boundary_values(u_exact_torch(s.ghost_points()).contiguous())
+            u = torch.zeros_like(phi)
+            s.vcycle(u, 1)
+            upd = s.info(0)["n_interior"] / 2.0
+            us = s.time_sweeps(nsweeps) / nsweeps * 1e3
+            s.close()
+            if key == "fp64":
+                ach = FP64_INSTR_PER_UPDATE * upd / (us * 1e-6) / 1e9
+                row[key] = {"sweep_us": us, "updates": upd, "achieved": ach, "peak": FP64_PEAK_GINSTR,
+                            "unit": "G FP64 instr/s", "frac": ach / FP64_PEAK_GINSTR,
+                            "hbm_frac": 24.0 * upd / (us * 1e-6) / 1e9 / peak}
+            else:
+                ach = 12.0 * upd / (us * 1e-6) / 1e9
+                row[key] = {"sweep_us": us, "updates": upd, "achieved": ach, "peak": peak, "unit": "GB/s",
+                            "frac": ach / peak}
+        del phi, f
+        torch.cuda.empty_cache()
+        out[str(N)] = row
+    out["peak_source"] = "FP64: derived 152 SMs x 2 FMA/clk x 2.07 GHz; HBM: %s" % peak_kind
     return out
 
 
@@ -638,13 +680,88 @@ def run_served(args):
             "clocks": clk, "gpu_launches": launches}
 
 
+def run_large512(args, steps=3):
+    """The 512^3 grids: (a) the ellipsoid at N = 512 solved to 1e-10 by FP32
+    V-cycles inside FP64 refinement and by FP64 V-cycles (each step a whole
+    solve with creation), with the mixed solution's error against the FP64
+    one and both discretisation errors; (b) the union of 64 seeded spheres
+    at N = 512 (the 512^3 sphere-union workload), on which the V-cycle does
+    not converge (coarse levels under-resolve the spheres): its creation time
+    and its time per V-cycle in both precisions."""
+    import torch
+    from paper_2207_14208_gb300 import bcmg
+    from paper_2207_14208_gb300 import build as B
+    B.build()
+    N, d = 512, 3
+    out = {"config": {"workload": "3D ellipsoid N=512 (513^3) solve to 1e-10; 64-sphere union N=512 cycles",
+                      "N": N}}
+    phi = torch.from_numpy(W.phi_ellipsoid(N)).cuda()
+    f_h, us_h = W.manufactured(d, N)
+    f = torch.from_numpy(f_h).cuda()
+    us_t = torch.from_numpy(us_h).cuda()
+    sols = {}
+    for prec, key in ((bcmg.PREC_MIXED, "mixed"), (bcmg.PREC_FP64, "fp64")):
+        times, cyc = [], 0
+        for it in range(steps + 1):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s = bcmg.Solver(d, N, phi, f, precision=prec)
+            s.set_boundary_values(u_exact_torch(s.ghost_points()).contiguous())
+            u = torch.zeros_like(phi)
+            c, rel = s.solve(u, 1e-10, 200)
+            e1.record()
+            e1.synchronize()
+            if it > 0:
+                times.append(e0.elapsed_time(e1))
+                cyc += c
+            cls = s.cls(0)
+            s.close()
+        sols[key] = u
+        act = torch.from_numpy(np.isin(cls, [bcmg.INTERIOR, bcmg.GHOST])).cuda()
+        interior = torch.from_numpy(cls == bcmg.INTERIOR).cuda()
+        out[key] = {"value": cyc / (sum(times) / 1e3), "unit": UNIT, "ms_per_solve": sum(times) / len(times),
+                    "cycles_per_solve": c, "final_rel_residual": rel,
+                    "discretisation_error": float((u - us_t)[interior].abs().max())}
+    out["mixed"]["max_rel_err_vs_fp64"] = float((sols["mixed"] - sols["fp64"])[act].abs().max() /
+                                                sols["fp64"][act].abs().max())
+    del sols, phi, f, us_t
+    torch.cuda.empty_cache()
+    # the sphere union: time per V-cycle (it diverges; 10 cycles timed)
+    phi = torch.from_numpy(W.phi_spheres(N)).cuda()
+    f = torch.from_numpy(W.manufactured(d, N)[0]).cuda()
+    sph = {}
+    for prec, key in ((bcmg.PREC_MIXED, "mixed"), (bcmg.PREC_FP64, "fp64")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = bcmg.Solver(d, N, phi, f, precision=prec)
+        torch.cuda.synchronize()
+        create_ms = (time.perf_counter() - t0) * 1e3
+        s.set_boundary_values(u_exact_torch(s.ghost_points()).contiguous())
+        u = torch.zeros_like(phi)
+        s.vcycle(u, 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        s.vcycle(u, 10)
+        e1.record()
+        e1.synchronize()
+        sph[key] = {"ms_per_cycle": e0.elapsed_time(e1) / 10, "create_ms": create_ms,
+                    "interior_nodes": s.info(0)["n_interior"], "ghosts": s.info(0)["n_ghost"],
+                    "memory_bytes": s.memory_footprint()}
+        s.close()
+    out["spheres64"] = sph
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_info()
     if args.impl == "ours" and args.config != "ellipsoid256":
         if ws > 1 and rank != 0:
             return
-        out = run_stars_batched(args) if args.config == "stars_batched" else run_served(args)
+        out = (run_stars_batched(args) if args.config == "stars_batched" else
+               run_large512(args) if args.config == "large512" else run_served(args))
         print(json.dumps(out))
         return
     if args.impl == "reference":

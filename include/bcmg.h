@@ -293,6 +293,16 @@ int bcmg_residual_norms_static(const double *r_dev, const uint8_t *cls_dev, int6
  * ENOMEM, ECUDA. */
 int bcmg_selftest_div_wsum(int fp32, const double *a_host, int64_t n, double *out_host);
 
+/* Timing of the finest-level interior sweep (eq. GSLEX_2D in red-black
+ * order, the dominant kernel of a cycle): nsweeps alternating red and black
+ * sweeps of the finest level, in the handle's working precision, launched
+ * back to back on the handle's stream between two CUDA events, as they run
+ * inside a cycle; *ms_host receives their summed device time (ms).  The
+ * sweeps act on the handle's internal working copy only (the next vcycle or
+ * solve copies the caller's u in again).  Red-black ordering only.
+ * Synchronous.  Errors: EINVAL, ECUDA. */
+int bcmg_time_sweeps(bcmg_handle h, int nsweeps, double *ms_host);
+
 /* ---- introspection (host copies, synchronous) ----------------------- */
 
 int bcmg_num_levels(bcmg_handle h, int *levels);

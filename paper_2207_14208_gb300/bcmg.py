@@ -84,6 +84,7 @@ def load():
             "bcmg_last_error": (C.c_char_p, []),
             "bcmg_kernel_launches": (i64, []),
             "bcmg_profile_read": (i32, [vp, vp]),
+            "bcmg_time_sweeps": (i32, [vp, i32, vp]),
             "bcmg_residual_norms_static": (i32, [vp, vp, i64, vp, vp]),
             "bcmg_selftest_div_wsum": (i32, [i32, vp, i64, vp]),
             "bcmg_num_levels": (i32, [vp, vp]),
@@ -302,6 +303,12 @@ class Solver:
         out = np.zeros(2)
         _check(self.lib.bcmg_profile_read(self.h, _hptr(out)))
         return {"smooth_ms": float(out[0]), "smooth_launches": int(out[1])}
+
+    def time_sweeps(self, nsweeps: int) -> float:
+        """Summed device time (ms) of nsweeps back-to-back finest-level sweeps."""
+        v = C.c_double()
+        _check(self.lib.bcmg_time_sweeps(self.h, int(nsweeps), C.byref(v)))
+        return v.value
 
     def memory_footprint(self) -> int:
         """Device memory (bytes) this hierarchy holds."""

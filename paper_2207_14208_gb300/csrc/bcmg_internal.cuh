@@ -243,6 +243,8 @@ void setup_cycle(Handle &H);
 void solve_init_enqueue(Handle &H, unsigned long long cond);
 void solve_check_enqueue(Handle &H, unsigned long long cond);
 void vcycle_enqueue(Handle &H, int l, double *u);
+// summed device time (ms) of nsweeps back-to-back finest-level colour sweeps
+double time_sweeps(Handle &H, int nsweeps);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,
 // u += correction; r must hold the FP64 residual of u
 void mixed_step_enqueue(Handle &H, double *u);

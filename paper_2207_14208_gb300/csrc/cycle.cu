@@ -1588,6 +1588,51 @@ void run_tail(Handle &H) {
 
 // ------------------------------------------------------------ host wrappers
 
+// one red (c = 0) or black (c = 1) interior sweep of level L
+template <typename T>
+static void sweep_colour(Handle &H, Level &L, T *u, const T *F, const T *Fs, int c) {
+    const G2 G = g2_of(L);
+    const uint32_t *list = L.ilist + (c ? L.nred : 0);
+    const int64_t n = c ? L.nint - L.nred : L.nred;
+    const int bs = bs_for(H, n);
+    // red (c = 0) = even index, black = odd, when n is odd
+    const int par = ((L.n & 1) && L.lay.s == 1) ? c : -1;
+    if (sizeof(T) == 4 && Fs && par >= 0 && n >= kMultiMin * (int64_t)H.nsm) {
+        // FP32 sweep of a large level: four entries per thread
+        constexpr int NPT = 4;
+        if (L.d == 3) launch(H, "k_smooth", k_smooth_multi<3, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
+        else launch(H, "k_smooth", k_smooth_multi<2, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
+    } else if (L.d == 3) {
+        launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
+    } else {
+        launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
+    }
+}
+
+// nsweeps alternating red / black sweeps of the finest level on the handle's
+// working arrays (of its working precision), back to back between two
+// events; returns their summed device time (ms).  A measurement of the
+// sweep as it runs inside a cycle, where each sweep's start overlaps its
+// predecessor's end; it changes only the working copy.
+double time_sweeps(Handle &H, int nsweeps) {
+    Level &L = H.L[0];
+    cudaEvent_t e0, e1;
+    check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+    check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+    check_cuda(cudaEventRecord(e0, H.st), "event");
+    for (int k = 0; k < nsweeps; ++k) {
+        if (H.o.precision == BCMG_PREC_MIXED) sweep_colour<float>(H, L, L.u32, L.F32, L.Fs32, k & 1);
+        else sweep_colour<double>(H, L, H.u0, L.F, L.Fs, k & 1);
+    }
+    check_cuda(cudaEventRecord(e1, H.st), "event");
+    check_cuda(cudaEventSynchronize(e1), "event sync");
+    float ms = 0.0f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (double)ms;
+}
+
 template <typename T>
 void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
     const G2 G = g2_of(L);
@@ -1595,7 +1640,6 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
     const T *gw = Arr<T>::gw(L);
     // the timed sweeps are the finest-level ones of the solve's working precision
     const bool prof = (sizeof(T) == 8) == (H.o.precision == BCMG_PREC_FP64);
-    const int64_t nblack = L.nint - L.nred;
     const int bg = bs_for(H, L.ng);
     for (int s = 0; s < nsteps; ++s) {
         if (H.o.ordering == BCMG_ORDER_LEX) {
@@ -1614,24 +1658,8 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
             }
         }
         for (int c = 0; c < 2 && H.o.ordering == BCMG_ORDER_RB; ++c) {
-            const uint32_t *list = L.ilist + (c ? L.nred : 0);
-            const int64_t n = c ? nblack : L.nred;
-            const int bs = bs_for(H, n);
             if (prof) profile_mark(H, L);
-            // red (c = 0) = even index, black = odd, when n is odd
-            const int par = ((L.n & 1) && L.lay.s == 1) ? c : -1;
-            if (sizeof(T) == 4 && Fs && par >= 0 && n >= kMultiMin * (int64_t)H.nsm) {
-                // FP32 sweep of a large level: four entries per thread
-                constexpr int NPT = 4;
-                if (L.d == 3)
-                    launch(H, "k_smooth", k_smooth_multi<3, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
-                else
-                    launch(H, "k_smooth", k_smooth_multi<2, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
-            } else if (L.d == 3) {
-                launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
-            } else {
-                launch(H, "k_smooth", k_smooth<2, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
-            }
+            sweep_colour<T>(H, L, u, F, Fs, c);
             if (prof) profile_mark(H, L);
         }
         if (L.d == 3)
