@@ -522,8 +522,10 @@ def run_stars_batched(args):
     """256 seeded star domains (N log-uniform 64..1024), FP32 cycles inside
     FP64 refinement: per step every hierarchy is built (16 host threads, one
     library stream each), its g(Q) set, and all 256 solved by one
-    bcmg_solve_batch call (the solves run concurrently on the device).  The
-    same domains solved one after another give the single-solve rate."""
+    bcmg_solve_batch call (one launch per stage for all 256: the batched
+    kernels).  The same domains solved one after another give the
+    single-solve rate; the line also splits the step into creation and the
+    batched solve.""" 
     import torch
     from concurrent.futures import ThreadPoolExecutor
     from paper_2207_14208_gb300 import bcmg
@@ -548,10 +550,17 @@ def run_stars_batched(args):
             cs.synchronize()
         return s, u, cs
 
+    split = {"create": 0.0, "solve": 0.0}
+
     def step(pool):
+        t0 = time.perf_counter()
         trip = list(pool.map(make, range(len(data))))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         cyc, rel, st = bcmg.solve_batch([t[0] for t in trip], [t[1] for t in trip], args.rtol, 100)
         torch.cuda.synchronize()
+        split["create"] += t1 - t0
+        split["solve"] += time.perf_counter() - t1
         for t in trip:
             t[0].close()
         return cyc, st
@@ -563,6 +572,7 @@ def run_stars_batched(args):
         torch.cuda.synchronize()
         clocks = ClockSampler(0)
         clocks.start()
+        split["create"] = split["solve"] = 0.0
         launches0 = bcmg.kernel_launches()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -597,6 +607,9 @@ def run_stars_batched(args):
                        "mean_cycles": float(np.mean(cycles)), "single_solves_per_s": single,
                        "batch_over_single": value / single,
                        "step": "threaded create x256 + g(Q) + one bcmg_solve_batch + destroy",
+                       "create_ms_per_step": split["create"] * 1e3 / steps,
+                       "solve_batch_ms_per_step": split["solve"] * 1e3 / steps,
+                       "batched_solves_per_s": len(data) * steps / split["solve"],
                        "parallelism": "single"},
             "clocks": clk, "gpu_launches": launches}
 

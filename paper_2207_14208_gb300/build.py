@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libbcmg.so")
-SOURCES = ["setup.cu", "cycle.cu", "capi.cu", "static_norms.cu"]
+SOURCES = ["setup.cu", "cycle.cu", "batch.cu", "capi.cu", "static_norms.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,6 +32,7 @@ def nvcc() -> str:
 def _inputs():
     files = [os.path.join(SRC_DIR, s) for s in SOURCES]
     files.append(os.path.join(SRC_DIR, "bcmg_internal.cuh"))
+    files.append(os.path.join(SRC_DIR, "nodeops.cuh"))
     files.append(os.path.join(ROOT, "include", "bcmg.h"))
     return files
 

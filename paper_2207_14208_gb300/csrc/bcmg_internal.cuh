@@ -245,6 +245,14 @@ void solve_check_enqueue(Handle &H, unsigned long long cond);
 void vcycle_enqueue(Handle &H, int l, double *u);
 // summed device time (ms) of nsweeps back-to-back finest-level colour sweeps
 double time_sweeps(Handle &H, int nsweeps);
+// batched solves (batch.cu): can these hierarchies advance together (same
+// dimension, precision, device, red-black V(nu1, nu2) cycles, expanded
+// extensions)?  Then solve all of them from their working copies u0, ordered
+// on st; per-hierarchy cycles, relative residuals and statuses into the host
+// arrays; returns the kernels launched.
+bool batch_eligible(const std::vector<Handle *> &hs);
+int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rtol, int max_cycles, int *cycles,
+                    double *rels, int *statuses);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,
 // u += correction; r must hold the FP64 residual of u
 void mixed_step_enqueue(Handle &H, double *u);

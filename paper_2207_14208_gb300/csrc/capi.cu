@@ -829,6 +829,35 @@ int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, 
             for (int j = 0; j < i; ++j)
                 if (hs[j] == hs[i]) throw Error{BCMG_EINVAL, "a handle appears twice in the batch"};
         }
+        if (batch_eligible(hs)) {
+            // one launch per stage for the whole batch (batch.cu), on the
+            // first handle's stream after every handle's copy-in
+            cudaStream_t bst = hs[0]->st;
+            for (int i = 0; i < n; ++i) {
+                Handle &H = *hs[i];
+                enter(H);
+                copy_active(H, u_devs[i], H.u0, true);
+                if (i > 0) {
+                    check_cuda(cudaEventRecord(H.ev_out, H.st), "batch fork");
+                    check_cuda(cudaStreamWaitEvent(bst, H.ev_out, 0), "batch fork wait");
+                }
+            }
+            std::vector<int> cyc(n), st(n);
+            std::vector<double> rel(n);
+            add_launches(batch_solve(hs, bst, rtol, max_cycles, cyc.data(), rel.data(), st.data()));
+            check_cuda(cudaEventRecord(hs[0]->ev_in, bst), "batch join");
+            for (int i = 0; i < n; ++i) {
+                Handle &H = *hs[i];
+                if (i > 0) check_cuda(cudaStreamWaitEvent(H.st, hs[0]->ev_in, 0), "batch join wait");
+                copy_active(H, H.u0, u_devs[i], false);
+                leave(H);
+                if (cycles_done) cycles_done[i] = cyc[i];
+                if (final_rel_res) final_rel_res[i] = rel[i];
+                if (statuses) statuses[i] = st[i];
+                if (first == BCMG_OK && st[i] != BCMG_OK) first = st[i];
+            }
+            return;
+        }
         // the solve graphs are built first (no capture while other solves
         // run), then every device-driven solve is enqueued on its handle's
         // own stream before any is waited for, so the solves run concurrently
