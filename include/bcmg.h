@@ -71,7 +71,12 @@ typedef struct {
     int ext_sweeps;    /* pseudo-time sweeps of the normal extension (4) */
     int min_coarse;    /* coarsening stops before N_l / 2 < min_coarse (8) */
     int max_levels;    /* upper bound on the number of levels (24) */
-    int use_graph;     /* replay the V-cycle from a captured CUDA graph (1) */
+    int use_graph;     /* replay the V-cycle from a captured CUDA graph:
+                          1 the solve graph is captured at creation
+                          (default), 2 at the first bcmg_solve that needs
+                          it (creation costs less when the handle is only
+                          solved through the batched kernels of
+                          bcmg_solve_batch), 0 never (host-driven loop) */
     int profile;       /* time every finest-level smoothing sweep with CUDA
                           events during bcmg_solve (0) */
     int precision;     /* BCMG_PREC_FP64 (default) or BCMG_PREC_MIXED */
@@ -219,18 +224,30 @@ int bcmg_vcycle(bcmg_handle h, double *u_dev, int ncycles);
 int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *cycles_done,
                double *final_rel_res);
 
-/* Many solves at once (uneven sizes and geometries welcome): every handle's
- * solve is enqueued on that handle's own stream before any is waited for,
- * so the GPU runs them concurrently; then each is finished in order.
+/* Many solves at once (uneven sizes and geometries welcome).
  *   handles[n], u_devs[n]  distinct handles and their u arrays (as for
  *                          bcmg_solve); rtol, max_cycles shared by all
  *   cycles_done[n], final_rel_res[n], statuses[n]   per-solve results
  *                          (host arrays, each may be NULL)
- * A solve whose handle was created with profile = 1 or use_graph = 0 runs
- * its host-driven loop in the second pass.  Results are identical to
- * bcmg_solve on each handle alone.  Returns BCMG_OK if every solve
- * converged, else the first failing status (per-solve ones in statuses);
- * EINVAL for null arrays or a handle that appears twice. */
+ * Batched kernels: when n >= 2 and every handle has the same dimension,
+ * working precision, device, nu1 and nu2, red-black ordering and V-cycles,
+ * the solves run together, one launch per stage of the V-cycle for all
+ * hierarchies (levels aligned by depth), in a CUDA graph whose loop runs
+ * while any solve is unfinished; a finished hierarchy's work is skipped.
+ * The launch shape (block size, items per thread) is measured once per
+ * batch shape on the first call (an autotuner; it runs batched cycles on
+ * the hierarchies' working copies only).  Per node the arithmetic is that
+ * of bcmg_solve; the coarse levels and the norm reduction sum in another
+ * order, so results agree with bcmg_solve alone to rounding (and a cycle
+ * count within a few cycles of it), not bit for bit.  The work is ordered
+ * after every handle's stream and every handle's stream after it.
+ * Otherwise (mixed batches) every handle's solve is enqueued on its own
+ * stream before any is waited for, so the GPU runs them concurrently, and
+ * results are identical to bcmg_solve on each handle alone; a handle created
+ * with profile = 1 or use_graph = 0 runs its host-driven loop in a second
+ * pass.  Returns BCMG_OK if every solve converged, else the first failing
+ * status (per-solve ones in statuses); EINVAL for null arrays or a handle
+ * that appears twice. */
 int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, int max_cycles,
                      int *cycles_done, double *final_rel_res, int *statuses);
 

@@ -263,9 +263,18 @@ class Solver:
         _check(self.lib.bcmg_ghost_count(self.h, C.byref(n)))
         return n.value
 
-    def ghost_points(self):
+    def ghost_points(self, out=None):
+        """Q of the finest-level ghosts (count x dim CUDA float64 tensor); with
+        out (a contiguous tensor of that shape, e.g. a slice of one array that
+        gathers the ghosts of many hierarchies) written there."""
         import torch
         ng = self.ghost_count()
+        if out is not None:
+            if tuple(out.shape) != (ng, self.dim) or not out.is_contiguous() or out.dtype != torch.float64:
+                raise ValueError("out must be a contiguous float64 tensor of shape (ghost_count, dim)")
+            if ng > 0:
+                _check(self.lib.bcmg_ghost_points(self.h, _dptr(out)))
+            return out
         Q = torch.empty((max(ng, 1), self.dim), dtype=torch.float64, device="cuda")
         _check(self.lib.bcmg_ghost_points(self.h, _dptr(Q)))
         return Q[:ng]

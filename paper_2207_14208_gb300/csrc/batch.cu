@@ -13,12 +13,17 @@
 // The coarse levels that a single hierarchy runs in its thread-block-cluster
 // tail run here as ordinary stages, shared by the batch.  Each hierarchy
 // keeps its own convergence state on the device; once it has converged (or
-// hit its limit) its blocks return right after the dependency wait, and the
+// hit its limit) its blocks return before the dependency wait, and the
 // whole solve -- initial norms, then a WHILE loop of (cycle, norms, check)
 // -- is one CUDA graph whose condition is "some hierarchy still runs".  The
-// block size of the stage launches is chosen by measurement (a small
-// autotuner): one batched cycle is timed for 64, 128 and 256 threads and the
-// fastest kept for batches of the same shape.
+// launch shape of the stages is chosen by measurement (a small autotuner):
+// one batched cycle is timed for block sizes of 64, 128 and 256 threads,
+// each with one or four items per thread in the node-parallel stages, and
+// the fastest kept for batches of the same shape.  Several items per thread
+// put several independent load chains of a thread in flight at once: a
+// block's work is a short chain of dependent loads (task map, list entry,
+// neighbours), so on the large levels one item per thread leaves the memory
+// system idle between waves of blocks.
 //
 // Every node is updated by the same device functions as in a single solve
 // (nodeops.cuh).  The differences from a single solve are the coarse levels,
@@ -105,7 +110,34 @@ struct BShared {  // batch-wide counters of the check kernel
 
 __device__ __forceinline__ bool bdone(const BCtl *ctl, int h) { return *(volatile const int *)&ctl[h].done; }
 
-template <int D, typename T>
+// Entry of a stage kernel after its fixed-table prologue; true when the
+// block is to return because its hierarchy has finished.  The flag was
+// written by the check that ends a cycle, in an earlier launch of the loop
+// body (or before the graph), which completed before this launch began, so
+// it is read before the dependency wait (a volatile load, served by L2) and
+// a finished hierarchy's block leaves without waiting.  Block 0 always
+// waits: every grid then completes only after its predecessor, and starts
+// only after its predecessor's block 0 has passed the wait, so the ordering
+// pdl_begin relies on holds even for a stage whose hierarchies have all
+// finished.
+__device__ __forceinline__ bool bskip(const BCtl *ctl, int h) {
+    const bool d = bdone(ctl, h);
+    if (d && blockIdx.x != 0) return true;
+    pdl_begin();
+    return d;
+}
+
+// item j of this thread when a block takes NPT items per thread (strided by
+// the block size, so a warp's loads of one item index stay contiguous)
+template <int NPT>
+__device__ __forceinline__ int64_t bitem(const BTask &t, int j) {
+    return ((int64_t)t.blk * NPT + j) * blockDim.x + threadIdx.x;
+}
+
+// One colour sweep, NPT nodes per thread: every load of the thread's nodes
+// is issued before its first store (a colour sweep reads only the other
+// colour, so the nodes of a thread never depend on one another).
+template <int D, typename T, int NPT>
 __global__ void __launch_bounds__(kT) kb_smooth(const BLev<T> *__restrict__ lv, const BRange *__restrict__ rg, int nr,
                                                 const BCtl *__restrict__ ctl, int colour) {
     const BTask t = block_task(rg, nr);
@@ -113,15 +145,34 @@ __global__ void __launch_bounds__(kT) kb_smooth(const BLev<T> *__restrict__ lv, 
     const G2 G = A.g;
     const int64_t n = colour ? A.nint - A.nred : A.nred;
     const uint32_t *list = A.ilist + (colour ? A.nred : 0);
-    const int64_t i = (int64_t)t.blk * blockDim.x + threadIdx.x;
-    const uint32_t X = i < n ? list[i] : 0u;
+    uint32_t X[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = bitem<NPT>(t, j);
+        X[j] = i < n ? list[i] : 0u;
+    }
     T *u = A.u;
     const T *Fs = A.Fs;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h) || i >= n) return;
-    if ((G.n & 1) && G.lay.s == 1) smooth_at_par<D, T>(X, u, Fs, G, colour);
-    else smooth_at_s<D, T>(X, u, Fs, G);
+    if (bskip(ctl, A.h)) return;
+    const bool par = (G.n & 1) && G.lay.s == 1;
+    T s[NPT], f[NPT];
+    int64_t x[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        s[j] = f[j] = T(0);
+        x[j] = 0;
+        if (bitem<NPT>(t, j) >= n) continue;
+        if (par) {
+            s[j] = nbr_sum_par<D, T>(X[j], u, G, colour, x[j]);
+        } else {
+            s[j] = nbr_sum<D, T>(u, X[j], G);
+            x[j] = pos(X[j], G.lay);
+        }
+        f[j] = Fs[x[j]];
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+        if (bitem<NPT>(t, j) < n) u[x[j]] = fma(s[j], (T)G.inv_diag, f[j]);
 }
 
 template <int D, typename T>
@@ -140,9 +191,7 @@ __global__ void __launch_bounds__(kT) kb_ghost_relax(const BLev<T> *__restrict__
     ghost_weights<D, T>(code, A.gw, ng, on ? g : 0, w);
     const T *u = A.u, *F = A.F;
     T *tmp = A.tmp;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
+    if (bskip(ctl, A.h) || !on) return;
     const int64_t x = pos(X, G.lay);
     tmp[g] = fma(dt, F[x] - ghost_Bw<D, T>(X, code, w, u, G), u[x]);
 }
@@ -158,42 +207,61 @@ __global__ void __launch_bounds__(kT) kb_ghost_scatter(const BLev<T> *__restrict
     const Lay ly = A.g.lay;
     const T *tmp = A.tmp;
     T *u = A.u;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
+    if (bskip(ctl, A.h) || !on) return;
     u[pos(X, ly)] = tmp[g];
 }
 
-// residual rows: interior rows (sub 0) or ghost rows (sub 1); with part,
-// every block writes its norm partials at its launch slot
-template <int D, typename T>
+// residual rows: interior rows (sub 0, NPT rows per thread) or ghost rows
+// (sub 1, one row per thread); with part, every block writes its norm
+// partials at its launch slot (a finished hierarchy's slots are left as they
+// are: the check does not read them)
+template <int D, typename T, int NPT>
 __global__ void __launch_bounds__(kT) kb_residual(const BLev<T> *__restrict__ lv, const BRange *__restrict__ rg, int nr,
                                                   const BCtl *__restrict__ ctl, double *__restrict__ part) {
     const BTask t = block_task(rg, nr);
     const BLev<T> &A = lv[t.lev];
     const G2 G = A.g;
-    const bool gh = t.sub != 0;
-    const int64_t i = (int64_t)t.blk * blockDim.x + threadIdx.x;
-    const bool on = i < (gh ? A.ng : A.nint);
-    const int64_t X = on ? (gh ? A.gidx[i] : A.ilist[i]) : 0;
-    const uint16_t code = (on && gh) ? A.gcode[i] : 0;
     const T *u = A.u, *F = A.F;
     T *r = A.r;
-    const int h = A.h;
-    T w[(D == 3) ? 27 : 9];
-    if (gh) ghost_weights<D, T>(code, A.gw, A.ng, on ? i : 0, w);
-    pdl_begin();
-    const bool skip = bdone(ctl, h);  // uniform over the block (one hierarchy)
     double s2 = 0.0;
     long long mxb = 0;
-    if (!skip && on) {
-        const int64_t x = pos(X, G.lay);
-        const T v = gh ? F[x] - ghost_Bw<D, T>(X, code, w, u, G) : residual_int<D, T>(X, u, F, G);
-        r[x] = v;
-        s2 = (double)v * (double)v;
-        mxb = abs_bits((double)v);
+    if (t.sub != 0) {  // ghost rows
+        const int64_t i = (int64_t)t.blk * blockDim.x + threadIdx.x;
+        const bool on = i < A.ng;
+        const int64_t X = on ? A.gidx[i] : 0;
+        const uint16_t code = on ? A.gcode[i] : 0;
+        T w[(D == 3) ? 27 : 9];
+        ghost_weights<D, T>(code, A.gw, A.ng, on ? i : 0, w);
+        if (bskip(ctl, A.h)) return;  // uniform over the block (one hierarchy)
+        if (on) {
+            const int64_t x = pos(X, G.lay);
+            const T v = F[x] - ghost_Bw<D, T>(X, code, w, u, G);
+            r[x] = v;
+            s2 = (double)v * (double)v;
+            mxb = abs_bits((double)v);
+        }
+        if (part) block_partials(s2, mxb, part, blockIdx.x, false);
+        return;
     }
-    if (part) block_partials(s2, mxb, part, blockIdx.x, !gh);
+    const int64_t nint = A.nint;
+    uint32_t X[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = bitem<NPT>(t, j);
+        X[j] = i < nint ? A.ilist[i] : 0u;
+    }
+    if (bskip(ctl, A.h)) return;
+    T v[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) v[j] = bitem<NPT>(t, j) < nint ? residual_int<D, T>(X[j], u, F, G) : T(0);
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        if (bitem<NPT>(t, j) >= nint) continue;
+        r[pos(X[j], G.lay)] = v[j];
+        s2 = fma((double)v[j], (double)v[j], s2);
+        mxb = max(mxb, abs_bits((double)v[j]));
+    }
+    if (part) block_partials(s2, mxb, part, blockIdx.x, true);
 }
 
 // expanded extension of the level's r (which = 0) or u (which = 1) into its band
@@ -213,62 +281,83 @@ __global__ void __launch_bounds__(kT) kb_extend(const BLev<T> *__restrict__ lv, 
     if (on) ell_first<T>(b, A.ecnt, eg, ew, nb, R);
     T *a = which ? A.u : A.r;
     const Lay ly = A.g.lay;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
+    if (bskip(ctl, A.h) || !on) return;
     a[pos(X, ly)] = extend_from<T>(b, R, eg, ew, nb, a, ly);
 }
 
 // restriction to the coarse level t.lev from the fine level t.lev - 1 (rows:
-// coarse interior rows, then coarse ghost rows); the coarse correction is
-// zeroed on the same rows
-template <int D, typename T>
+// coarse interior rows, then coarse ghost rows; NPT rows per thread); the
+// coarse correction is zeroed on the same rows
+template <int D, typename T, int NPT>
 __global__ void __launch_bounds__(kT) kb_restrict(const BLev<T> *__restrict__ lv, const BRange *__restrict__ rg, int nr,
                                                   const BCtl *__restrict__ ctl) {
     const BTask t = block_task(rg, nr);
     const BLev<T> &C = lv[t.lev];
     const BLev<T> &Fl = lv[t.lev - 1];
     const G2 Gc = C.g, Gf = Fl.g;
-    const int64_t row = (int64_t)t.blk * blockDim.x + threadIdx.x;
-    const int64_t nint_c = C.nint;
-    const bool on = row < nint_c + C.ng;
-    const uint32_t Xc = on ? (row < nint_c ? C.ilist[row] : C.gidx[row - nint_c]) : 0u;
-    const uint32_t mask = on ? C.fmask[row] : 0u;
+    const int64_t nint_c = C.nint, nrow = C.nint + C.ng;
+    uint32_t Xc[NPT], mask[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t row = bitem<NPT>(t, j);
+        const bool on = row < nrow;
+        Xc[j] = on ? (row < nint_c ? C.ilist[row] : C.gidx[row - nint_c]) : 0u;
+        mask[j] = on ? C.fmask[row] : 0u;
+    }
     const T *rf = Fl.r;
     T *Fc = C.F, *Fsc = C.Fs, *uc = C.u;
-    const int h = C.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
-    int ic[3];
-    coords(Xc, (uint32_t)Gc.n, D, ic);
-    const T fc = restrict_masked<D, T>(ic, mask, rf, Gf);
-    const int64_t xc = pos(Xc, Gc.lay);
-    Fc[xc] = fc;
-    if (row < nint_c) Fsc[xc] = scaled_rhs<T>(fc, Gc);
-    uc[xc] = T(0);
+    if (bskip(ctl, C.h)) return;
+    T fc[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        int ic[3];
+        coords(Xc[j], (uint32_t)Gc.n, D, ic);
+        fc[j] = bitem<NPT>(t, j) < nrow ? restrict_masked<D, T>(ic, mask[j], rf, Gf) : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t row = bitem<NPT>(t, j);
+        if (row >= nrow) continue;
+        const int64_t xc = pos(Xc[j], Gc.lay);
+        Fc[xc] = fc[j];
+        if (row < nint_c) Fsc[xc] = scaled_rhs<T>(fc[j], Gc);
+        uc[xc] = T(0);
+    }
 }
 
 // prolongation into the fine level t.lev from t.lev + 1 (rows: interior
-// rows, then ghost rows)
-template <int D, typename T>
+// rows, then ghost rows; NPT rows per thread)
+template <int D, typename T, int NPT>
 __global__ void __launch_bounds__(kT) kb_prolong(const BLev<T> *__restrict__ lv, const BRange *__restrict__ rg, int nr,
                                                  const BCtl *__restrict__ ctl) {
     const BTask t = block_task(rg, nr);
     const BLev<T> &Fl = lv[t.lev];
     const BLev<T> &C = lv[t.lev + 1];
     const G2 Gf = Fl.g, Gc = C.g;
-    const int64_t i = (int64_t)t.blk * blockDim.x + threadIdx.x;
-    const int64_t nint = Fl.nint;
-    const bool on = i < nint + Fl.ng;
-    const uint32_t X = on ? (i < nint ? Fl.ilist[i] : Fl.gidx[i - nint]) : 0u;
+    const int64_t nint = Fl.nint, nrow = Fl.nint + Fl.ng;
+    uint32_t X[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = bitem<NPT>(t, j);
+        X[j] = i < nrow ? (i < nint ? Fl.ilist[i] : Fl.gidx[i - nint]) : 0u;
+    }
     const T *ec = C.u;
     T *uf = Fl.u;
-    const int h = Fl.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
-    int iy[3];
-    coords(X, (uint32_t)Gf.n, D, iy);
-    uf[pos(X, Gf.lay)] += prolong_at<D, T>(iy, ec, Gc);
+    if (bskip(ctl, Fl.h)) return;
+    T v[NPT];
+    int64_t x[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        v[j] = T(0);
+        x[j] = pos(X[j], Gf.lay);
+        if (bitem<NPT>(t, j) >= nrow) continue;
+        int iy[3];
+        coords(X[j], (uint32_t)Gf.n, D, iy);
+        v[j] = uf[x[j]] + prolong_at<D, T>(iy, ec, Gc);
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+        if (bitem<NPT>(t, j) < nrow) uf[x[j]] = v[j];
 }
 
 template <typename T>
@@ -282,9 +371,7 @@ __global__ void __launch_bounds__(kT) kb_coarse_gather(const BLev<T> *__restrict
     const Lay ly = A.g.lay;
     const T *r = A.r;
     double *rhs = A.crhs;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
+    if (bskip(ctl, A.h) || !on) return;
     rhs[j] = (double)r[pos(X, ly)];
 }
 
@@ -299,9 +386,7 @@ __global__ void __launch_bounds__(kT) kb_coarse_gemv(const BLev<T> *__restrict__
     const Lay ly = A.g.lay;
     T *u = A.u;
     const uint32_t *act = A.act;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h)) return;
+    if (bskip(ctl, A.h)) return;
     const int64_t i = (int64_t)t.blk * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (i >= nact) return;
     const int lane = threadIdx.x & 31;
@@ -314,7 +399,8 @@ __global__ void __launch_bounds__(kT) kb_coarse_gemv(const BLev<T> *__restrict__
 
 // start of a refinement step on the finest level: F32 = (float) r64, the
 // scaled copy on interior rows, e32 = 0 (level entries of the FP64 and FP32
-// tables are the same index)
+// tables are the same index); NPT rows per thread
+template <int NPT>
 __global__ void __launch_bounds__(kT) kb_ir_begin(const BLev<double> *__restrict__ l64,
                                                   const BLev<float> *__restrict__ l32,
                                                   const BRange *__restrict__ rg, int nr, const BCtl *__restrict__ ctl) {
@@ -322,40 +408,58 @@ __global__ void __launch_bounds__(kT) kb_ir_begin(const BLev<double> *__restrict
     const BLev<double> &A = l64[t.lev];
     const BLev<float> &B = l32[t.lev];
     const G2 G = A.g;
-    const int64_t i = (int64_t)t.blk * blockDim.x + threadIdx.x;
-    const int64_t nint = A.nint;
-    const bool on = i < nint + A.ng;
-    const uint32_t X = on ? (i < nint ? A.ilist[i] : A.gidx[i - nint]) : 0u;
+    const int64_t nint = A.nint, nrow = A.nint + A.ng;
+    uint32_t X[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = bitem<NPT>(t, j);
+        X[j] = i < nrow ? (i < nint ? A.ilist[i] : A.gidx[i - nint]) : 0u;
+    }
     const double *r = A.r;
     float *F32 = B.F, *Fs32 = B.Fs, *e32 = B.u;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
-    const int64_t x = pos(X, G.lay);
-    const float f = (float)r[x];
-    F32[x] = f;
-    if (i < nint) Fs32[x] = scaled_rhs<float>(f, G);
-    e32[x] = 0.0f;
+    if (bskip(ctl, A.h)) return;
+    float f[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) f[j] = bitem<NPT>(t, j) < nrow ? (float)r[pos(X[j], G.lay)] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = bitem<NPT>(t, j);
+        if (i >= nrow) continue;
+        const int64_t x = pos(X[j], G.lay);
+        F32[x] = f[j];
+        if (i < nint) Fs32[x] = scaled_rhs<float>(f[j], G);
+        e32[x] = 0.0f;
+    }
 }
 
+// end of a refinement step: u += e on interior and ghost rows (FP64)
+template <int NPT>
 __global__ void __launch_bounds__(kT) kb_ir_update(const BLev<double> *__restrict__ l64,
                                                    const BLev<float> *__restrict__ l32,
                                                    const BRange *__restrict__ rg, int nr, const BCtl *__restrict__ ctl) {
     const BTask t = block_task(rg, nr);
     const BLev<double> &A = l64[t.lev];
     const BLev<float> &B = l32[t.lev];
-    const int64_t i = (int64_t)t.blk * blockDim.x + threadIdx.x;
-    const int64_t nint = A.nint;
-    const bool on = i < nint + A.ng;
-    const uint32_t X = on ? (i < nint ? A.ilist[i] : A.gidx[i - nint]) : 0u;
+    const int64_t nint = A.nint, nrow = A.nint + A.ng;
+    uint32_t X[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = bitem<NPT>(t, j);
+        X[j] = i < nrow ? (i < nint ? A.ilist[i] : A.gidx[i - nint]) : 0u;
+    }
     const Lay ly = A.g.lay;
     const float *e32 = B.u;
     double *u = A.u;
-    const int h = A.h;
-    pdl_begin();
-    if (bdone(ctl, h) || !on) return;
-    const int64_t x = pos(X, ly);
-    u[x] += (double)e32[x];
+    if (bskip(ctl, A.h)) return;
+    double v[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t x = pos(X[j], ly);
+        v[j] = bitem<NPT>(t, j) < nrow ? u[x] + (double)e32[x] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+        if (bitem<NPT>(t, j) < nrow) u[pos(X[j], ly)] = v[j];
 }
 
 // One block per hierarchy: reduce its norm partials (slots p0[h] .. p0[h+1]
@@ -479,12 +583,14 @@ BLev<T> blev_of(Handle &H, int l, int h) {
 struct Stage {
     int kind, arg;
     int64_t first, nr, blocks;
+    int npt;  // items per thread of the stage's kernel (1 or 4)
 };
 enum { S_RED, S_BLACK, S_RELAX, S_SCATTER, S_RES, S_EXT_R, S_EXT_U, S_RESTRICT, S_PROLONG, S_GATHER, S_GEMV,
        S_IR_BEGIN, S_IR_UPDATE, S_NORMRES, S_CHECK };
 
 struct Plan {
     int bs = 128;
+    int npt = 1;  // items per thread of the node-parallel stages
     std::vector<BRange> ranges;
     std::vector<Stage> cycle;  // one cycle (precision of the V-cycle)
     std::vector<Stage> norms;  // finest FP64 residual with partials; refinement rows
@@ -507,7 +613,8 @@ struct StageBuilder {
     Plan &P;
     int64_t first;
     uint32_t blocks = 0;
-    explicit StageBuilder(Plan &p) : P(p), first((int64_t)p.ranges.size()) {}
+    int npt;
+    explicit StageBuilder(Plan &p, int npt_ = 1) : P(p), first((int64_t)p.ranges.size()), npt(npt_) {}
     template <class Fn>
     void add(const std::vector<int> &levs, int per_block, Fn n_of, uint32_t sub = 0) {
         for (int lv : levs) {
@@ -519,13 +626,19 @@ struct StageBuilder {
         }
     }
     void push(std::vector<Stage> &seq, int kind, int arg) {
-        if (blocks > 0) seq.push_back(Stage{kind, arg, first, (int64_t)P.ranges.size() - first, (int64_t)blocks});
+        if (blocks > 0) seq.push_back(Stage{kind, arg, first, (int64_t)P.ranges.size() - first, (int64_t)blocks, npt});
     }
 };
 
-Plan make_plan(const Batch &B, int bs, int nu1, int nu2) {
+// the stages of one cycle and of the norms; node-parallel stages (colour
+// sweeps, interior residual rows, restriction and prolongation in 2D, the
+// refinement rows) take npt items per thread, the ghost, band and coarsest
+// stages one
+Plan make_plan(const Batch &B, int bs, int npt, int nu1, int nu2) {
     Plan P;
     P.bs = bs;
+    P.npt = npt;
+    const int nptr = B.d == 2 ? npt : 1;  // 3^d-point restriction rows: one per thread in 3D
     const int nh = (int)B.hs.size();
     int depth = 0;
     for (Handle *H : B.hs) depth = std::max(depth, (int)H->L.size());
@@ -541,11 +654,11 @@ Plan make_plan(const Batch &B, int bs, int nu1, int nu2) {
     std::vector<Stage> &C = P.cycle;
     auto smooth_steps = [&](const std::vector<int> &S, int steps) {
         for (int s = 0; s < steps; ++s) {
-            StageBuilder r(P);
-            r.add(S, bs, nred);
+            StageBuilder r(P, npt);
+            r.add(S, bs * npt, nred);
             r.push(C, S_RED, 0);
-            StageBuilder b(P);
-            b.add(S, bs, nblack);
+            StageBuilder b(P, npt);
+            b.add(S, bs * npt, nblack);
             b.push(C, S_BLACK, 1);
             StageBuilder g(P);
             g.add(S, bs, ng);
@@ -569,20 +682,20 @@ Plan make_plan(const Batch &B, int bs, int nu1, int nu2) {
         }
         smooth_steps(S, nu1);
         {
-            StageBuilder r(P);
-            r.add(S, bs, nint, 0);
+            StageBuilder r(P, npt);
+            r.add(S, bs * npt, nint, 0);
             r.add(S, bs, ng, 1);
             r.push(C, S_RES, 0);
             StageBuilder e(P);
             e.add(S, bs, nband);
             e.push(C, S_EXT_R, 0);
-            StageBuilder q(P);
-            q.add(Sc, bs, nrows);
+            StageBuilder q(P, nptr);
+            q.add(Sc, bs * nptr, nrows);
             q.push(C, S_RESTRICT, 0);
         }
         if (!Co.empty()) {
-            StageBuilder r(P);
-            r.add(Co, bs, nint, 0);
+            StageBuilder r(P, npt);
+            r.add(Co, bs * npt, nint, 0);
             r.add(Co, bs, ng, 1);
             r.push(C, S_RES, 0);
             StageBuilder g(P);
@@ -604,29 +717,29 @@ Plan make_plan(const Batch &B, int bs, int nu1, int nu2) {
         StageBuilder e(P);
         e.add(Cb, bs, nband);
         e.push(C, S_EXT_U, 1);
-        StageBuilder q(P);
-        q.add(S, bs, nrows);
+        StageBuilder q(P, nptr);
+        q.add(S, bs * nptr, nrows);
         q.push(C, S_PROLONG, 0);
         smooth_steps(S, nu2);
     }
     // the finest FP64 residual with norm partials, hierarchy by hierarchy
     // (partial slot = block), then the refinement rows of the finest levels
     {
-        StageBuilder r(P);
+        StageBuilder r(P, npt);
         P.p0.assign((size_t)nh + 1, 0);
         std::vector<int> L0;
         for (int h = 0; h < nh; ++h) {
             P.p0[h] = r.blocks;
             std::vector<int> one{lev(h, 0)};
-            r.add(one, bs, nint, 0);
+            r.add(one, bs * npt, nint, 0);
             r.add(one, bs, ng, 1);
             L0.push_back(lev(h, 0));
         }
         P.p0[nh] = r.blocks;
         P.nparts = r.blocks;
         r.push(P.norms, S_NORMRES, 0);
-        StageBuilder ir(P);
-        ir.add(L0, bs, nrows);
+        StageBuilder ir(P, npt);
+        ir.add(L0, bs * npt, nrows);
         ir.push(P.norms, S_IR_BEGIN, 0);
     }
     return P;
@@ -656,7 +769,8 @@ void enqueue_stages(const Plan &P, const DevPlan &Dv, const BLev<T> *lv, const s
         switch (s.kind) {
             case S_RED:
             case S_BLACK:
-                blaunch(st, kb_smooth<D, T>, grid, bs, count, lv, rg, nr, ctl, s.arg);
+                if (s.npt == 4) blaunch(st, kb_smooth<D, T, 4>, grid, bs, count, lv, rg, nr, ctl, s.arg);
+                else blaunch(st, kb_smooth<D, T, 1>, grid, bs, count, lv, rg, nr, ctl, s.arg);
                 break;
             case S_RELAX:
                 blaunch(st, kb_ghost_relax<D, T>, grid, bs, count, lv, rg, nr, ctl);
@@ -665,17 +779,28 @@ void enqueue_stages(const Plan &P, const DevPlan &Dv, const BLev<T> *lv, const s
                 blaunch(st, kb_ghost_scatter<T>, grid, bs, count, lv, rg, nr, ctl);
                 break;
             case S_RES:
-                blaunch(st, kb_residual<D, T>, grid, bs, count, lv, rg, nr, ctl, (double *)nullptr);
+                if (s.npt == 4) blaunch(st, kb_residual<D, T, 4>, grid, bs, count, lv, rg, nr, ctl, (double *)nullptr);
+                else blaunch(st, kb_residual<D, T, 1>, grid, bs, count, lv, rg, nr, ctl, (double *)nullptr);
                 break;
             case S_EXT_R:
             case S_EXT_U:
                 blaunch(st, kb_extend<T>, grid, bs, count, lv, rg, nr, ctl, s.arg);
                 break;
             case S_RESTRICT:
-                blaunch(st, kb_restrict<D, T>, grid, bs, count, lv, rg, nr, ctl);
+                if constexpr (D == 2)
+                    if (s.npt == 4) {
+                        blaunch(st, kb_restrict<D, T, 4>, grid, bs, count, lv, rg, nr, ctl);
+                        break;
+                    }
+                blaunch(st, kb_restrict<D, T, 1>, grid, bs, count, lv, rg, nr, ctl);
                 break;
             case S_PROLONG:
-                blaunch(st, kb_prolong<D, T>, grid, bs, count, lv, rg, nr, ctl);
+                if constexpr (D == 2)
+                    if (s.npt == 4) {
+                        blaunch(st, kb_prolong<D, T, 4>, grid, bs, count, lv, rg, nr, ctl);
+                        break;
+                    }
+                blaunch(st, kb_prolong<D, T, 1>, grid, bs, count, lv, rg, nr, ctl);
                 break;
             case S_GATHER:
                 blaunch(st, kb_coarse_gather<T>, grid, bs, count, lv, rg, nr, ctl);
@@ -695,7 +820,8 @@ template <int D>
 void enqueue_norms(const Batch &B, const Plan &P, const DevPlan &Dv, cudaStream_t st, int mode, unsigned stop_at,
                    cudaGraphConditionalHandle cond, int64_t *count) {
     const Stage &s = P.norms[0];
-    blaunch(st, kb_residual<D, double>, (unsigned)s.blocks, (unsigned)P.bs, count, (const BLev<double> *)Dv.l64,
+    auto kern = s.npt == 4 ? kb_residual<D, double, 4> : kb_residual<D, double, 1>;
+    blaunch(st, kern, (unsigned)s.blocks, (unsigned)P.bs, count, (const BLev<double> *)Dv.l64,
             (const BRange *)(Dv.ranges + s.first), (int)s.nr, (const BCtl *)Dv.ctl, Dv.part);
     blaunch(st, kb_norm_check, (unsigned)B.hs.size(), 256u, count, Dv.ctl, (const double *)Dv.part,
             (const int64_t *)Dv.p0, Dv.sh, mode, stop_at, cond);
@@ -709,11 +835,12 @@ void enqueue_cycle(const Batch &B, const Plan &P, const DevPlan &Dv, cudaStream_
     }
     const Stage &ir = P.norms[1];
     const BRange *rg = Dv.ranges + ir.first;
-    blaunch(st, kb_ir_begin, (unsigned)ir.blocks, (unsigned)P.bs, count, (const BLev<double> *)Dv.l64,
-            (const BLev<float> *)Dv.l32, rg, (int)ir.nr, (const BCtl *)Dv.ctl);
+    const bool four = ir.npt == 4;
+    blaunch(st, four ? kb_ir_begin<4> : kb_ir_begin<1>, (unsigned)ir.blocks, (unsigned)P.bs, count,
+            (const BLev<double> *)Dv.l64, (const BLev<float> *)Dv.l32, rg, (int)ir.nr, (const BCtl *)Dv.ctl);
     enqueue_stages<D, float>(P, Dv, Dv.l32, P.cycle, st, count);
-    blaunch(st, kb_ir_update, (unsigned)ir.blocks, (unsigned)P.bs, count, (const BLev<double> *)Dv.l64,
-            (const BLev<float> *)Dv.l32, rg, (int)ir.nr, (const BCtl *)Dv.ctl);
+    blaunch(st, four ? kb_ir_update<4> : kb_ir_update<1>, (unsigned)ir.blocks, (unsigned)P.bs, count,
+            (const BLev<double> *)Dv.l64, (const BLev<float> *)Dv.l32, rg, (int)ir.nr, (const BCtl *)Dv.ctl);
 }
 
 void *dev_alloc(DevPlan &Dv, size_t bytes, cudaStream_t st) {
@@ -817,7 +944,8 @@ cudaGraphExec_t build_cycle_graph(const Batch &B, const Plan &P, const DevPlan &
 }
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int64_t, int64_t>, int> g_tuned;  // (dev, d, mixed, nh, nodes) -> bs
+// (dev, d, mixed, nh, nodes) -> (block size, items per thread)
+std::map<std::tuple<int, int, int, int64_t, int64_t>, std::pair<int, int>> g_tuned;
 
 Batch make_batch(const std::vector<Handle *> &hs) {
     Batch B;
@@ -835,9 +963,12 @@ Batch make_batch(const std::vector<Handle *> &hs) {
     return B;
 }
 
-// the autotuner: one batched cycle per candidate block size, timed after a
-// warm replay, on the working copies (saved before and restored after)
-int tune_block_size(const Batch &B, cudaStream_t st, double rtol, int max_cycles, int64_t *launched) {
+// the autotuner: one batched cycle per candidate launch shape (block size
+// 64, 128 or 256 threads; one or four items per thread in the node-parallel
+// stages), timed after a warm replay, on the working copies (saved before
+// and restored after); returns the fastest shape
+std::pair<int, int> tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cycles,
+                                      int64_t *launched) {
     const int nu1 = B.hs[0]->o.nu1, nu2 = B.hs[0]->o.nu2;
     std::vector<double *> saved;
     for (Handle *H : B.hs) {
@@ -847,10 +978,11 @@ int tune_block_size(const Batch &B, cudaStream_t st, double rtol, int max_cycles
         check_cuda(cudaMemcpyAsync(p, H->u0, bytes, cudaMemcpyDeviceToDevice, st), "tune save copy");
         saved.push_back(p);
     }
-    int bs = 0;
+    std::pair<int, int> shape{0, 0};
     float best = 0.0f;
-    for (int cand : {64, 128, 256}) {
-        Plan P = make_plan(B, cand, nu1, nu2);
+    for (const auto cand : {std::make_pair(64, 1), std::make_pair(128, 1), std::make_pair(256, 1),
+                            std::make_pair(64, 4), std::make_pair(128, 4), std::make_pair(256, 4)}) {
+        Plan P = make_plan(B, cand.first, cand.second, nu1, nu2);
         DevPlan Dv = upload_plan(B, P, st);
         std::vector<BCtl> c0(B.hs.size());
         for (auto &c : c0) c = BCtl{rtol, max_cycles, 0, 1.0, 1.0, 0, 0};
@@ -871,9 +1003,9 @@ int tune_block_size(const Batch &B, cudaStream_t st, double rtol, int max_cycles
         cudaGraphExecDestroy(ex);
         free_plan(Dv, st);
         *launched += 2 * (int64_t)(P.cycle.size() + (B.mixed ? 2 : 0));
-        if (bs == 0 || ms < best) {
+        if (shape.first == 0 || ms < best) {
             best = ms;
-            bs = cand;
+            shape = cand;
         }
     }
     for (size_t h = 0; h < B.hs.size(); ++h) {
@@ -882,7 +1014,7 @@ int tune_block_size(const Batch &B, cudaStream_t st, double rtol, int max_cycles
                    "tune restore");
         cudaFreeAsync(saved[h], st);
     }
-    return bs;
+    return shape;
 }
 
 }  // namespace
@@ -917,16 +1049,16 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
     check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     const auto key = std::make_tuple(dev, hs[0]->d, (int)(hs[0]->o.precision == BCMG_PREC_MIXED), (int64_t)n, nodes);
     int64_t launched = 0;
-    int bs = 0;
+    std::pair<int, int> shape{0, 0};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) bs = it->second;
+        if (it != g_tuned.end()) shape = it->second;
     }
-    if (bs == 0) {
-        bs = tune_block_size(make_batch(hs), st, rtol, max_cycles, &launched);
+    if (shape.first == 0) {
+        shape = tune_launch_shape(make_batch(hs), st, rtol, max_cycles, &launched);
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = bs;
+        g_tuned[key] = shape;
     }
     std::vector<BCtl> state(n, BCtl{rtol, max_cycles, 0, 0.0, 0.0, 0, 0});
     std::vector<int> active(n);
@@ -940,7 +1072,7 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
             cs.push_back(state[i]);
         }
         const Batch B = make_batch(sub);
-        const Plan P = make_plan(B, bs, hs[0]->o.nu1, hs[0]->o.nu2);
+        const Plan P = make_plan(B, shape.first, shape.second, hs[0]->o.nu1, hs[0]->o.nu2);
         DevPlan Dv = upload_plan(B, P, st);
         upload(cs, Dv.ctl, st);
         const unsigned stop_at = active.size() > 8 ? (unsigned)(active.size() / 8) : 0u;

@@ -256,10 +256,14 @@ void pinned_put(void *p) {
     g_pin_free.push_back(p);
 }
 
-// The side stream of a creation (with its fork and join events) is only
-// busy while the hierarchy is built: it comes from a process-wide pool per
-// device and goes back once creation has synchronised, so that handles
-// created and destroyed at a high rate make no stream or event calls for it.
+// Streams with two events each ("lanes") come from a process-wide pool per
+// device: a handle's own stream (with its enter and leave events) for its
+// lifetime, and the side stream of a creation (with its fork and join
+// events) while the hierarchy is built.  A lane goes back idle (its stream
+// synchronised), so that handles created and destroyed at a high rate make
+// no stream or event calls, which take driver locks that concurrent
+// creations would contend for.  A recorded event may be reused at once: a
+// stream that waits on it waits for the record made before its wait call.
 struct SideLane {
     cudaStream_t st = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -282,6 +286,11 @@ SideLane side_get(int dev) {
     check_cuda(cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming), "cudaEventCreate");
     check_cuda(cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming), "cudaEventCreate");
     return s;
+}
+
+void lane_put(int dev, SideLane s) {
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    g_side_free.push_back({dev, s});
 }
 
 // the lane is idle (its stream synchronised)
@@ -315,9 +324,15 @@ void destroy(Handle *H) {
     pinned_put(H->sing_host);
     for (cudaEvent_t e : H->pev) cudaEventDestroy(e);
     side_put(H->dev, *H);  // synchronised above
-    if (H->ev_in) cudaEventDestroy(H->ev_in);
-    if (H->ev_out) cudaEventDestroy(H->ev_out);
-    if (H->st) cudaStreamDestroy(H->st);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (H->st && cudaStreamIsCapturing(H->st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusInvalidated;
+    if (H->st && H->ev_in && H->ev_out && cap == cudaStreamCaptureStatusNone) {  // synchronised above
+        lane_put(H->dev, SideLane{H->st, H->ev_in, H->ev_out});
+    } else {
+        if (H->ev_in) cudaEventDestroy(H->ev_in);
+        if (H->ev_out) cudaEventDestroy(H->ev_out);
+        if (H->st) cudaStreamDestroy(H->st);
+    }
     H->magic = 0;
     delete H;
 }
@@ -671,14 +686,18 @@ int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const
             (H->o.bc != BCMG_BC_DIRICHLET && H->o.bc != BCMG_BC_NEUMANN) ||
             !(H->o.reaction >= 0.0 && H->o.reaction < 1e300) ||
             (H->o.cycle != BCMG_CYCLE_V && H->o.cycle != BCMG_CYCLE_W) ||
-            (H->o.ordering != BCMG_ORDER_RB && H->o.ordering != BCMG_ORDER_LEX))
+            (H->o.ordering != BCMG_ORDER_RB && H->o.ordering != BCMG_ORDER_LEX) || H->o.use_graph < 0 ||
+            H->o.use_graph > 2)
             throw Error{BCMG_EINVAL, "invalid options"};
         H->user = (cudaStream_t)stream;
         check_cuda(cudaGetDevice(&H->dev), "cudaGetDevice");
         keep_pool_memory();
-        check_cuda(cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking), "cudaStreamCreate");
-        check_cuda(cudaEventCreateWithFlags(&H->ev_in, cudaEventDisableTiming), "cudaEventCreate");
-        check_cuda(cudaEventCreateWithFlags(&H->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+        {
+            SideLane ml = side_get(H->dev);
+            H->st = ml.st;
+            H->ev_in = ml.fork;
+            H->ev_out = ml.join;
+        }
         if (H->o.profile) {
             H->pev.resize(4 * (size_t)(H->o.nu1 + H->o.nu2), nullptr);
             for (auto &e : H->pev) check_cuda(cudaEventCreate(&e), "cudaEventCreate(profile)");
@@ -709,7 +728,7 @@ int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const
         for (auto &L : H->L) L.phi = nullptr;
         // the solve graph is captured here, while the device still works on
         // the set-up (capture records launches, it runs nothing)
-        if (H->o.use_graph && !H->o.profile) H->sgraph = build_solve_graph(*H);
+        if (H->o.use_graph == 1 && !H->o.profile) H->sgraph = build_solve_graph(*H);
         check_cuda(cudaStreamWaitEvent(H->st, H->ev_join, 0), "join wait");  // the coarsest inverse
         check_cuda(cudaStreamSynchronize(H->st), "create sync");
         side_put(H->dev, *H);  // the join is complete: the side lane is idle

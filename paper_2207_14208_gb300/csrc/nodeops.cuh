@@ -242,7 +242,7 @@ __device__ __forceinline__ void smooth_at_s(int64_t X, T *u, const T *Fs, const 
 // sweep reads one contiguous run of the other colour per axis direction and
 // writes its own colour densely.  Same terms, same order as nbr_sum.
 template <int D, typename T>
-__device__ __forceinline__ void smooth_at_par(uint32_t X, T *u, const T *Fs, const G2 &G, int par) {
+__device__ __forceinline__ T nbr_sum_par(uint32_t X, const T *u, const G2 &G, int par, int64_t &x) {
     const uint32_t m = X >> 1;
     const T *v = u + (par ? 0 : G.lay.ho) + m;
     const int64_t sy = G.sy, sz = G.sz;
@@ -252,7 +252,14 @@ __device__ __forceinline__ void smooth_at_par(uint32_t X, T *u, const T *Fs, con
         const int64_t zm = par - ((sz + 1) >> 1), zp = par + ((sz - 1) >> 1);
         s += v[zm] + v[zp];
     }
-    const int64_t x = (par ? G.lay.ho : 0) + m;
+    x = (par ? G.lay.ho : 0) + m;  // the node's own slot
+    return s;
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void smooth_at_par(uint32_t X, T *u, const T *Fs, const G2 &G, int par) {
+    int64_t x;
+    const T s = nbr_sum_par<D, T>(X, u, G, par, x);
     u[x] = fma(s, (T)G.inv_diag, Fs[x]);
 }
 
