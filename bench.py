@@ -59,7 +59,11 @@ def parse():
     p.add_argument("--arms", choices=["both", "fp64", "mixed"], default="both")
     # the default workload is the 3D ellipsoid at 257^3; the other two are the
     # batched and the served workloads (single GPU, extra lines, not defaults)
-    p.add_argument("--config", choices=["ellipsoid256", "stars_batched", "served", "large512"],
+    # "sweeps": only the finest-level colour sweeps of the ellipsoid at --N,
+    # --steps of them per precision from the created hierarchy (no cycle
+    # before them), for a profiler's capture of the smoother; "trace": one
+    # host-driven solve per precision of --arms, for a profiler's launch list
+    p.add_argument("--config", choices=["ellipsoid256", "stars_batched", "served", "large512", "sweeps", "trace"],
                    default="ellipsoid256")
     return p.parse_args()
 
@@ -169,38 +173,48 @@ def flush_l2(buf):
 
 # ------------------------------------------------------------ our arm
 FP64_INSTR_PER_UPDATE = 6   # 5 adds, 1 FMA per red/black update (from the scaled right-hand side)
+# algorithmic bytes of one colour pass per interior node of the level: u read
+# (the whole level), f read and u written for the pass's colour -- 32 B per
+# node for the two separate colour passes of a sweep in FP64, half in FP32
+SWEEP_BYTES_PER_NODE = {"fp64": 16.0, "fp32": 8.0}
 SWEEPS = 200                # back-to-back sweeps timed for the roofline
 FP64_PEAK_GINSTR = 152 * 2 * 2.07  # SMs x FP64 FMA pipes per clock x GHz (1.26 TFLOP/s)
-# DRAM bytes (read + write) of one finest-level k_smooth<3,double> launch at
-# N=256, from an ncu capture of that kernel.  The counters belong to the
-# kernel source they were taken on: K_SMOOTH_SRC_SHA is the hash of the
-# smoother's device code (see smoother_source_hash) at the capture; when the
-# source no longer hashes to it, the bench reports traffic as null.
-K_SMOOTH_DRAM_BYTES = 21.595e6
-K_SMOOTH_SRC_SHA = "3c52667141ebb526"
-K_SMOOTH_DRAM_SOURCE = ("ncu --set full capture of the first two finest-level sweeps, "
+# DRAM bytes (read + write) of one finest-level sweep launch at N=256 (FP64
+# k_smooth<3,double>, FP32 k_smooth_pers<3,float,2>), from an ncu capture of
+# those kernels (bench.py --config sweeps --N 256 --steps 2; the first two
+# launches of each, cold cache).  The counters belong to the kernel source
+# they were taken on: the hash of the sweep's device code (smoother_source_hash)
+# at the capture; when the source no longer hashes to it, the bench reports
+# traffic as null.
+SMOOTHER = {
+    "fp64": {"funcs": ("nbr_sum", "smooth_at_par", "nbr_sum_par", "k_smooth"),
+             "dram_bytes": 13.313e6, "sha": "8f8f4093add23f68"},
+    "fp32": {"funcs": ("nbr_sum_par", "k_smooth_pers"),
+             "dram_bytes": 9.028e6, "sha": "0550b80d7b412c4a"},
+}
+SMOOTHER_DRAM_SOURCE = ("ncu --set full capture of the first two finest-level sweeps, "
                         "dram__bytes_read.sum + dram__bytes_write.sum, cold cache")
-SMOOTHER_FUNCS = ("nbr_sum", "smooth_at_s", "k_smooth")
 
 
-def smoother_source_hash():
+def smoother_source_hash(key="fp64"):
     """sha256 (first 16 hex digits) of the device functions the finest-level
-    sweep runs, cut out of csrc/cycle.cu by name (template head to the
-    closing brace at column 0)."""
+    sweep runs, cut out of csrc/cycle.cu and csrc/nodeops.cuh by name
+    (template head to the closing brace at column 0)."""
     import hashlib
     import re
-    src = open(os.path.join(ROOT, "paper_2207_14208_gb300", "csrc", "cycle.cu")).read()
+    csrc = os.path.join(ROOT, "paper_2207_14208_gb300", "csrc")
+    src = "".join(open(os.path.join(csrc, f)).read() for f in ("nodeops.cuh", "cycle.cu"))
     h = hashlib.sha256()
-    for name in SMOOTHER_FUNCS:
+    for name in SMOOTHER[key]["funcs"]:
         m = re.search(r"\n(template <[^\n]*>\n(?:[^\n]*\n){0,3}?[^\n]*\b" + name + r"\b\(.*?\n\})", src, re.S)
         h.update((m.group(1) if m else name).encode())
     return h.hexdigest()[:16]
 
 
-def smoother_traffic():
-    sha = smoother_source_hash()
-    if K_SMOOTH_SRC_SHA is not None and sha == K_SMOOTH_SRC_SHA:
-        return K_SMOOTH_DRAM_BYTES, K_SMOOTH_DRAM_SOURCE
+def smoother_traffic(key="fp64"):
+    sha = smoother_source_hash(key)
+    if SMOOTHER[key]["sha"] is not None and sha == SMOOTHER[key]["sha"]:
+        return SMOOTHER[key]["dram_bytes"], SMOOTHER_DRAM_SOURCE
     return None, "stale: the smoother source (sha %s) changed since the last ncu capture" % sha
 
 
@@ -298,14 +312,16 @@ def run_ours(args, ws, rank, local):
     err_mixed = float((u32 - u64)[act].abs().max()) / scale
     disc64 = float((u64 - us_t)[interior].abs().max())
     disc32 = float((u32 - us_t)[interior].abs().max())
-    traffic, traffic_src = smoother_traffic()
+    traffic, traffic_src = smoother_traffic("fp64")
+    traffic32, traffic32_src = smoother_traffic("fp32")
     # dominant kernel: the finest-level red/black sweep (one colour per launch,
     # n_int / 2 updates).  FP64 is bound by the FP64 pipe (6 instructions per
-    # update); the FP32 sweep of the mixed path by memory (12 B per update).
+    # update); the FP32 sweep of the mixed path by memory (SWEEP_BYTES_PER_NODE
+    # per interior node).
     upd = n_int / 2.0
     ach_instr = FP64_INSTR_PER_UPDATE * upd / (r64["sweep_ms"] / 1e3) / 1e9
-    alg_bytes64 = 24.0 * upd
-    alg_bytes32 = 12.0 * upd
+    alg_bytes64 = SWEEP_BYTES_PER_NODE["fp64"] * n_int
+    alg_bytes32 = SWEEP_BYTES_PER_NODE["fp32"] * n_int
     peak, peak_kind = measured_peaks()
     hbm64 = alg_bytes64 / (r64["sweep_ms"] / 1e3) / 1e9
     hbm32 = alg_bytes32 / (r32["sweep_ms"] / 1e3) / 1e9
@@ -340,9 +356,10 @@ def run_ours(args, ws, rank, local):
                   "ms_per_step": r32["ms"] / args.steps, "cycles_per_solve": r32["cycles"][0],
                   "final_rel_residual": max(r32["rels"]),
                   "max_rel_err_vs_fp64": err_mixed, "discretisation_error": disc32,
-                  "roofline": {"bound": "hbm", "kernel": "k_smooth<3,float> (finest level, one colour)",
+                  "roofline": {"bound": "hbm", "kernel": "k_smooth_pers<3,float,2> (finest level, one colour)",
                                "achieved": hbm32, "peak": peak, "unit": "GB/s", "frac": hbm32 / peak,
-                               "sweep_us": r32["sweep_ms"] * 1e3, "alg_bytes_per_launch": alg_bytes32}},
+                               "sweep_us": r32["sweep_ms"] * 1e3, "alg_bytes_per_launch": alg_bytes32,
+                               "traffic": traffic32, "traffic_source": traffic32_src}},
         "clocks": r64["clocks"],
         "gpu_launches": r64["launches"],
     }
@@ -361,12 +378,12 @@ def run_ours(args, ws, rank, local):
     return out
 
 
-def sweep_rooflines(sizes=(256, 384, 512), nsweeps=100):
+def sweep_rooflines(sizes=(256, 384, 512), nsweeps=100, warm=True):
     """The finest-level sweep on the ellipsoid at several grid sizes, timed
-    back to back (bcmg_time_sweeps) after one V-cycle: FP64 against the
+    back to back (bcmg_time_sweeps) after one V-cycle (warm): FP64 against the
     FP64-pipe peak (6 instructions per update), FP32 (the mixed path's inner
-    sweep) against the measured HBM peak (12 B per update: Fs, the own value,
-    one neighbour value amortised)."""
+    sweep) against the measured HBM peak (SWEEP_BYTES_PER_NODE per interior
+    node and colour pass)."""
     import torch
     from paper_2207_14208_gb300 import bcmg
     peak, peak_kind = measured_peaks()
@@ -378,18 +395,20 @@ def sweep_rooflines(sizes=(256, 384, 512), nsweeps=100):
         for prec, key in ((bcmg.PREC_FP64, "fp64"), (bcmg.PREC_MIXED, "fp32")):
             s = bcmg.Solver(3, N, phi, f, precision=prec)
             s.set_boundary_values(u_exact_torch(s.ghost_points()).contiguous())
-            u = torch.zeros_like(phi)
-            s.vcycle(u, 1)
-            upd = s.info(0)["n_interior"] / 2.0
+            if warm:
+                u = torch.zeros_like(phi)
+                s.vcycle(u, 1)
+            nint = s.info(0)["n_interior"]
+            upd = nint / 2.0
             us = s.time_sweeps(nsweeps) / nsweeps * 1e3
             s.close()
             if key == "fp64":
                 ach = FP64_INSTR_PER_UPDATE * upd / (us * 1e-6) / 1e9
                 row[key] = {"sweep_us": us, "updates": upd, "achieved": ach, "peak": FP64_PEAK_GINSTR,
                             "unit": "G FP64 instr/s", "frac": ach / FP64_PEAK_GINSTR,
-                            "hbm_frac": 24.0 * upd / (us * 1e-6) / 1e9 / peak}
+                            "hbm_frac": SWEEP_BYTES_PER_NODE["fp64"] * nint / (us * 1e-6) / 1e9 / peak}
             else:
-                ach = 12.0 * upd / (us * 1e-6) / 1e9
+                ach = SWEEP_BYTES_PER_NODE["fp32"] * nint / (us * 1e-6) / 1e9
                 row[key] = {"sweep_us": us, "updates": upd, "achieved": ach, "peak": peak, "unit": "GB/s",
                             "frac": ach / peak}
         del phi, f
@@ -713,6 +732,32 @@ def run_served(args):
             "clocks": clk, "gpu_launches": launches}
 
 
+def run_trace(args):
+    """One solve of the ellipsoid workload at --N per precision in --arms,
+    driven from the host (use_graph = 0: one launch per kernel, the same
+    kernels and launch shapes as the graph solve), so that a profiler's
+    launch list shows every kernel of the cycles; no timing claims."""
+    import torch
+    from paper_2207_14208_gb300 import bcmg
+    from paper_2207_14208_gb300 import build as B
+    B.build()
+    N = args.N
+    phi = torch.from_numpy(W.phi_ellipsoid(N)).cuda()
+    f = torch.from_numpy(W.manufactured(3, N)[0]).cuda()
+    out = {"metric": "host-driven solve of the 3D ellipsoid (launch trace)", "N": N}
+    arms = {"both": ("fp64", "mixed"), "fp64": ("fp64",), "mixed": ("mixed",)}[args.arms]
+    for key in arms:
+        prec = bcmg.PREC_FP64 if key == "fp64" else bcmg.PREC_MIXED
+        s = bcmg.Solver(3, N, phi, f, precision=prec, use_graph=0)
+        s.set_boundary_values(u_exact_torch(s.ghost_points()).contiguous())
+        u = torch.zeros_like(phi)
+        c, rel = s.solve(u, args.rtol, 100)
+        torch.cuda.synchronize()
+        out[key] = {"cycles": c, "rel": rel}
+        s.close()
+    return out
+
+
 def run_large512(args, steps=3):
     """The 512^3 grids: (a) the ellipsoid at N = 512 solved to 1e-10 by FP32
     V-cycles inside FP64 refinement and by FP64 V-cycles (each step a whole
@@ -793,8 +838,16 @@ def main():
     if args.impl == "ours" and args.config != "ellipsoid256":
         if ws > 1 and rank != 0:
             return
-        out = (run_stars_batched(args) if args.config == "stars_batched" else
-               run_large512(args) if args.config == "large512" else run_served(args))
+        if args.config == "trace":
+            out = run_trace(args)
+        elif args.config == "sweeps":
+            from paper_2207_14208_gb300 import build as B
+            B.build()
+            out = {"metric": "finest-level colour sweep time (3D ellipsoid), back to back",
+                   "sweeps": sweep_rooflines((args.N,), max(1, args.steps), warm=False)}
+        else:
+            out = (run_stars_batched(args) if args.config == "stars_batched" else
+                   run_large512(args) if args.config == "large512" else run_served(args))
         print(json.dumps(out))
         return
     if args.impl == "reference":

@@ -171,6 +171,7 @@ struct Handle {
     void *tail_ops = nullptr;  // (kind, level) schedule of the tail
     int tail_nops = 0;
     int nsm = 152;  // SMs of the device (block sizes of the FP64 kernels)
+    int pers_blocks = 0;  // resident blocks of the persistent FP32 sweep (0: not yet queried)
     int dev = 0;    // the device the handle was created on
     bool capturing = false;
     int64_t captured = 0;

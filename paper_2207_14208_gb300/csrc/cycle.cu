@@ -43,20 +43,25 @@ __global__ void __launch_bounds__(kT) k_smooth(const uint32_t *__restrict__ list
     }
 }
 
-// The same sweep with NPT list entries per thread (entries i0 + j blockDim,
-// coalesced per j) on a parity-split level with odd n: all entries' loads
-// are issued before any update, which multiplies the loads a thread has in
-// flight (the FP32 sweep on large grids is bound by memory latency, not by
-// arithmetic).  A colour sweep reads only the other colour and writes only
-// its own, so the entries of a thread never depend on one another.
+// The colour sweep of a large FP32 level on a parity-split level with odd n,
+// as a persistent grid: the SMs' resident blocks walk the list in chunks of
+// NPT x blockDim entries (chunks blockIdx, blockIdx + gridDim, ...; entry
+// i0 + j blockDim, coalesced per j).  A thread's NPT entries' loads are all
+// issued before any update, and the list entries of its next chunk are
+// loaded while the values of the current one are in flight, so past its
+// first chunk a block waits for one round trip per chunk, not two (the sweep
+// is bound by memory latency, not by arithmetic).  A colour sweep reads only
+// the other colour and writes only its own, so no entry depends on another.
+// Same terms, same order as smooth_at_par.
 template <int D, typename T, int NPT>
-__global__ void __launch_bounds__(kT) k_smooth_multi(const uint32_t *__restrict__ list, int64_t n, T *u,
-                                                     const T *__restrict__ Fs, G2 G, int par) {
-    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * NPT + threadIdx.x;
+__global__ void __launch_bounds__(kT) k_smooth_pers(const uint32_t *__restrict__ list, int64_t n, T *u,
+                                                    const T *__restrict__ Fs, G2 G, int par) {
+    const int64_t chunk = (int64_t)blockDim.x * NPT;
+    int64_t c = blockIdx.x;
     uint32_t m[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
-        const int64_t i = i0 + (int64_t)j * blockDim.x;
+        const int64_t i = c * chunk + (int64_t)j * blockDim.x + threadIdx.x;
         m[j] = i < n ? (list[i] >> 1) : 0u;
     }
     pdl_begin();
@@ -65,27 +70,39 @@ __global__ void __launch_bounds__(kT) k_smooth_multi(const uint32_t *__restrict_
     const int64_t zm = par - ((sz + 1) >> 1), zp = par + ((sz - 1) >> 1);
     const T *v = u + (par ? 0 : G.lay.ho);
     const int64_t own = par ? G.lay.ho : 0;
-    T a[NPT][D == 3 ? 6 : 4], f[NPT];
+    for (; c * chunk < n; c += gridDim.x) {
+        const int64_t i0 = c * chunk + threadIdx.x;
+        T a[NPT][D == 3 ? 6 : 4], f[NPT];
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-        const bool on = i0 + (int64_t)j * blockDim.x < n;
-        const T *w = v + m[j];
-        a[j][0] = on ? w[xm] : T(0);
-        a[j][1] = on ? w[xp] : T(0);
-        a[j][2] = on ? w[ym] : T(0);
-        a[j][3] = on ? w[yp] : T(0);
-        if (D == 3) {
-            a[j][4] = on ? w[zm] : T(0);
-            a[j][5] = on ? w[zp] : T(0);
+        for (int j = 0; j < NPT; ++j) {
+            const bool on = i0 + (int64_t)j * blockDim.x < n;
+            const T *w = v + m[j];
+            a[j][0] = on ? w[xm] : T(0);
+            a[j][1] = on ? w[xp] : T(0);
+            a[j][2] = on ? w[ym] : T(0);
+            a[j][3] = on ? w[yp] : T(0);
+            if (D == 3) {
+                a[j][4] = on ? w[zm] : T(0);
+                a[j][5] = on ? w[zp] : T(0);
+            }
+            f[j] = on ? Fs[own + m[j]] : T(0);
         }
-        f[j] = on ? Fs[own + m[j]] : T(0);
-    }
+        uint32_t mn[NPT];
+        const int64_t i1 = (c + gridDim.x) * chunk + threadIdx.x;
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-        if (i0 + (int64_t)j * blockDim.x >= n) continue;
-        T s = (a[j][0] + a[j][1]) + (a[j][2] + a[j][3]);
-        if (D == 3) s += a[j][4] + a[j][5];
-        u[own + m[j]] = fma(s, (T)G.inv_diag, f[j]);
+        for (int j = 0; j < NPT; ++j) {
+            const int64_t i = i1 + (int64_t)j * blockDim.x;
+            mn[j] = i < n ? (list[i] >> 1) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            if (i0 + (int64_t)j * blockDim.x >= n) continue;
+            T s = (a[j][0] + a[j][1]) + (a[j][2] + a[j][3]);
+            if (D == 3) s += a[j][4] + a[j][5];
+            u[own + m[j]] = fma(s, (T)G.inv_diag, f[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) m[j] = mn[j];
     }
 }
 
@@ -1086,10 +1103,16 @@ static void sweep_colour(Handle &H, Level &L, T *u, const T *F, const T *Fs, int
     // red (c = 0) = even index, black = odd, when n is odd
     const int par = ((L.n & 1) && L.lay.s == 1) ? c : -1;
     if (sizeof(T) == 4 && Fs && par >= 0 && n >= kMultiMin * (int64_t)H.nsm) {
-        // FP32 sweep of a large level: four entries per thread
-        constexpr int NPT = 4;
-        if (L.d == 3) launch(H, "k_smooth", k_smooth_multi<3, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
-        else launch(H, "k_smooth", k_smooth_multi<2, T, NPT>, nblk(n, kT * NPT), kT, list, n, u, Fs, G, par);
+        // FP32 sweep of a large level: a persistent grid (the SMs' resident
+        // blocks), two entries per thread and chunk
+        constexpr int NPT = 2;
+        auto k = L.d == 3 ? k_smooth_pers<3, T, NPT> : k_smooth_pers<2, T, NPT>;
+        if (H.pers_blocks == 0) {
+            int b = 0;
+            check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kT, 0), "occupancy");
+            H.pers_blocks = std::max(1, b) * H.nsm;
+        }
+        launch(H, "k_smooth", k, std::min((unsigned)H.pers_blocks, nblk(n, kT * NPT)), kT, list, n, u, Fs, G, par);
     } else if (L.d == 3) {
         launch(H, "k_smooth", k_smooth<3, T>, nblk(n, bs), bs, list, n, u, F, Fs, G, par);
     } else {
