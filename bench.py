@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-sizes", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched and served workloads that follow the default line at N=1")
     p.add_argument("--arms", choices=["both", "fp64", "mixed"], default="both")
     # the default workload is the 3D ellipsoid at 257^3; the other two are the
     # batched and the served workloads (single GPU, extra lines, not defaults)
@@ -758,6 +760,19 @@ def run_trace(args):
     return out
 
 
+def extra_workloads(args):
+    """The batched and the served workloads, measured after the default
+    workload in the same run (N=1): their own lines' headline numbers, each
+    from its own timed region with its own clock record."""
+    out = {}
+    for key, fn in (("stars_batched", run_stars_batched), ("served", run_served)):
+        line = fn(args)
+        keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "clocks", "gpu_launches")
+        out[key] = {k: line[k] for k in keep if k in line}
+        out[key]["config"] = line.get("config")
+    return out
+
+
 def run_large512(args, steps=3):
     """The 512^3 grids: (a) the ellipsoid at N = 512 solved to 1e-10 by FP32
     V-cycles inside FP64 refinement and by FP64 V-cycles (each step a whole
@@ -859,11 +874,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     out = run_ours(args, ws, rank, local)
-    if rank == 0:
-        print(json.dumps(out))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    if rank == 0:
+        if ws == 1 and not args.no_extras:
+            out["workloads"] = extra_workloads(args)
+        print(json.dumps(out))
 
 
 if __name__ == "__main__":
