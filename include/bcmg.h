@@ -176,6 +176,18 @@ int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const
  * counterpart in the paper.) */
 int bcmg_workspace_size(bcmg_handle h, int64_t *bytes);
 
+/* Fixes the launch shape of the batched kernels of bcmg_solve_batch for the
+ * calls that follow, in place of the autotuner's choice (no counterpart in
+ * the paper; for tests and measurements):
+ *   block      threads per block of the stage kernels: 64, 128 or 256; 0
+ *              returns to the autotuner
+ *   items      items per thread of the node-parallel stages: 1 or 4
+ *   tail_rows  coarse levels whose lists all have at most this many entries
+ *              run in one block per hierarchy (the block tail); 0: none
+ * Results do not depend on the shape (the same per-node arithmetic in the
+ * same order).  Process-wide.  EINVAL for other values. */
+int bcmg_debug_batch_shape(int block, int items, int64_t tail_rows);
+
 /* Failure injection for tests of the callers' recovery paths (no
  * counterpart in the paper): after this call, the k-th device allocation the
  * library makes (counted over all handles and threads) fails as if the device

@@ -67,6 +67,7 @@ def load():
             "bcmg_create_grid_hierarchy_ex": (i32, [i32, i64, f64, f64, vp, vp, vp, vp, C.c_size_t, vp, vp]),
             "bcmg_workspace_size": (i32, [vp, vp]),
             "bcmg_debug_fail_allocation": (i32, [i64]),
+            "bcmg_debug_batch_shape": (i32, [i32, i32, i64]),
             "bcmg_debug_live_blocks": (i32, [vp, vp]),
             "bcmg_destroy": (i32, [vp]),
             "bcmg_ghost_count": (i32, [vp, vp]),
@@ -110,6 +111,12 @@ def load():
 def _check(rc):
     if rc != OK:
         raise BcmgError(rc, load().bcmg_last_error().decode())
+
+
+def debug_batch_shape(block: int = 0, items: int = 1, tail_rows: int = 0) -> None:
+    """Launch shape of the batched kernels for the following batched solves
+    (block 0: the autotuner's choice again)."""
+    _check(load().bcmg_debug_batch_shape(int(block), int(items), int(tail_rows)))
 
 
 def debug_fail_allocation(k: int) -> None:

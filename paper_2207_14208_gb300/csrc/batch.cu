@@ -462,6 +462,232 @@ __global__ void __launch_bounds__(kT) kb_ir_update(const BLev<double> *__restric
         if (bitem<NPT>(t, j) < nrow) u[pos(X[j], ly)] = v[j];
 }
 
+// ------------------------------------------------------------ block tail
+// The coarse levels of a hierarchy in one block: the levels from the tail's
+// top down to the coarsest, every stage of the cycle on them as a phase of
+// the block, phases separated by the block barrier.  Per node the same
+// device functions as the stage kernels, in the same phase order, so the
+// results are those of the stage path.  One launch (one block per
+// hierarchy with a tail) replaces the seventeen or so stage launches per
+// coarse level.  Lists of a tail level are walked in chunks of kBTEnt
+// entries per thread, every load of a chunk before its first store.
+constexpr int kBT = 256;     // threads of a tail block (two blocks per SM)
+constexpr int kBTEnt = 4;    // entries per thread and chunk
+constexpr int64_t kBTMaxCoarse = 192;  // coarsest unknowns of a tail (its dense GEMV runs on one SM)
+
+struct BTail {
+    uint32_t lev0;  // level descriptor of the tail's top level
+    uint32_t nl;    // tail levels (the last one is the coarsest)
+};
+
+__device__ __forceinline__ int64_t bt_entry(int64_t b0, int j) {
+    return b0 + (int64_t)j * blockDim.x + threadIdx.x;
+}
+
+template <int D, typename T>
+__device__ void bt_sweep(const BLev<T> &A, int colour) {
+    const G2 G = A.g;
+    const int64_t n = colour ? A.nint - A.nred : A.nred;
+    const uint32_t *list = A.ilist + (colour ? A.nred : 0);
+    T *const u = A.u;
+    const T *const Fs = A.Fs;
+    const bool par = (G.n & 1) && G.lay.s == 1;
+    for (int64_t b0 = 0; b0 < n; b0 += (int64_t)kBTEnt * blockDim.x) {
+        uint32_t X[kBTEnt];
+#pragma unroll
+        for (int j = 0; j < kBTEnt; ++j) X[j] = bt_entry(b0, j) < n ? list[bt_entry(b0, j)] : 0u;
+        T s[kBTEnt], f[kBTEnt];
+        int64_t x[kBTEnt];
+#pragma unroll
+        for (int j = 0; j < kBTEnt; ++j) {
+            s[j] = f[j] = T(0);
+            x[j] = 0;
+            if (bt_entry(b0, j) >= n) continue;
+            if (par) {
+                s[j] = nbr_sum_par<D, T>(X[j], u, G, colour, x[j]);
+            } else {
+                s[j] = nbr_sum<D, T>(u, X[j], G);
+                x[j] = pos(X[j], G.lay);
+            }
+            f[j] = Fs[x[j]];
+        }
+#pragma unroll
+        for (int j = 0; j < kBTEnt; ++j)
+            if (bt_entry(b0, j) < n) u[x[j]] = fma(s[j], (T)G.inv_diag, f[j]);
+    }
+    __syncthreads();
+}
+
+// ghost relaxation from the same u, then the write-back
+template <int D, typename T>
+__device__ void bt_relax(const BLev<T> &A) {
+    const G2 G = A.g;
+    const int64_t ng = A.ng;
+    const T *const F = A.F;
+    T *const u = A.u;
+    T *const tmp = A.tmp;
+    const uint32_t *const gidx = A.gidx;
+    const uint16_t *const gcode = A.gcode;
+    const double *const gdt = A.gdt;
+    const T *const gw = A.gw;
+    for (int64_t g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int64_t X = gidx[g];
+        const uint16_t code = gcode[g];
+        const T dt = (T)gdt[g];
+        T w[(D == 3) ? 27 : 9];
+        ghost_weights<D, T>(code, gw, ng, g, w);
+        const int64_t x = pos(X, G.lay);
+        tmp[g] = fma(dt, F[x] - ghost_Bw<D, T>(X, code, w, u, G), u[x]);
+    }
+    __syncthreads();
+    for (int64_t g = threadIdx.x; g < ng; g += blockDim.x) u[pos(gidx[g], G.lay)] = tmp[g];
+    __syncthreads();
+}
+
+template <int D, typename T>
+__device__ void bt_residual(const BLev<T> &A) {
+    const G2 G = A.g;
+    const int64_t nint = A.nint, ng = A.ng;
+    const T *const u = A.u, *const F = A.F;
+    T *const r = A.r;
+    const uint32_t *const ilist = A.ilist, *const gidx = A.gidx;
+    const uint16_t *const gcode = A.gcode;
+    const T *const gw = A.gw;
+    for (int64_t b0 = 0; b0 < nint; b0 += (int64_t)kBTEnt * blockDim.x) {
+        uint32_t X[kBTEnt];
+#pragma unroll
+        for (int j = 0; j < kBTEnt; ++j) X[j] = bt_entry(b0, j) < nint ? ilist[bt_entry(b0, j)] : 0u;
+        T v[kBTEnt];
+#pragma unroll
+        for (int j = 0; j < kBTEnt; ++j) v[j] = bt_entry(b0, j) < nint ? residual_int<D, T>(X[j], u, F, G) : T(0);
+#pragma unroll
+        for (int j = 0; j < kBTEnt; ++j)
+            if (bt_entry(b0, j) < nint) r[pos(X[j], G.lay)] = v[j];
+    }
+    for (int64_t g = threadIdx.x; g < ng; g += blockDim.x) {
+        const int64_t X = gidx[g];
+        const uint16_t code = gcode[g];
+        T w[(D == 3) ? 27 : 9];
+        ghost_weights<D, T>(code, gw, ng, g, w);
+        const int64_t x = pos(X, G.lay);
+        r[x] = F[x] - ghost_Bw<D, T>(X, code, w, u, G);
+    }
+    __syncthreads();
+}
+
+// expanded extension of a (the level's r or u) into its band
+template <typename T>
+__device__ void bt_extend(const BLev<T> &A, T *a) {
+    const int64_t nb = A.nb;
+    const Lay ly = A.g.lay;
+    const uint8_t *const ecnt = A.ecnt;
+    const uint32_t *const eg = A.eg, *const bidx = A.bidx;
+    const double *const ew = A.ew;
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+        EllRound<T> R;
+        R.c = 0;
+        ell_first<T>(b, ecnt, eg, ew, nb, R);
+        a[pos(bidx[b], ly)] = extend_from<T>(b, R, eg, ew, nb, a, ly);
+    }
+    __syncthreads();
+}
+
+// restriction into C from its fine level Fl, the coarse correction zeroed
+template <int D, typename T>
+__device__ void bt_restrict(const BLev<T> &C, const BLev<T> &Fl) {
+    const G2 Gc = C.g, Gf = Fl.g;
+    const int64_t nint_c = C.nint, nrow = C.nint + C.ng;
+    const T *const rf = Fl.r;
+    T *const Fc = C.F, *const Fsc = C.Fs, *const uc = C.u;
+    const uint32_t *const ilist = C.ilist, *const gidx = C.gidx, *const fmask = C.fmask;
+    for (int64_t row = threadIdx.x; row < nrow; row += blockDim.x) {
+        const uint32_t Xc = row < nint_c ? ilist[row] : gidx[row - nint_c];
+        int ic[3];
+        coords(Xc, (uint32_t)Gc.n, D, ic);
+        const T fc = restrict_masked<D, T>(ic, fmask[row], rf, Gf);
+        const int64_t xc = pos(Xc, Gc.lay);
+        Fc[xc] = fc;
+        if (row < nint_c) Fsc[xc] = scaled_rhs<T>(fc, Gc);
+        uc[xc] = T(0);
+    }
+    __syncthreads();
+}
+
+// prolongation of C's correction into its fine level Fl
+template <int D, typename T>
+__device__ void bt_prolong(const BLev<T> &Fl, const BLev<T> &C) {
+    const G2 Gf = Fl.g, Gc = C.g;
+    const int64_t nint = Fl.nint, nrow = Fl.nint + Fl.ng;
+    const T *const ec = C.u;
+    T *const uf = Fl.u;
+    const uint32_t *const ilist = Fl.ilist, *const gidx = Fl.gidx;
+    for (int64_t i = threadIdx.x; i < nrow; i += blockDim.x) {
+        const uint32_t X = i < nint ? ilist[i] : gidx[i - nint];
+        int iy[3];
+        coords(X, (uint32_t)Gf.n, D, iy);
+        const int64_t x = pos(X, Gf.lay);
+        uf[x] = uf[x] + prolong_at<D, T>(iy, ec, Gc);
+    }
+    __syncthreads();
+}
+
+// coarsest level: u += A^-1 r on the active rows (one warp per row, FP64
+// accumulation in the order of kb_coarse_gemv)
+template <typename T>
+__device__ void bt_coarsest(const BLev<T> &A) {
+    const int64_t nact = A.nact;
+    const Lay ly = A.g.lay;
+    double *const rhs = A.crhs;
+    T *const u = A.u;
+    const T *const r = A.r;
+    const uint32_t *const act = A.act;
+    const double *const Ainv = A.Ainv;
+    for (int64_t j = threadIdx.x; j < nact; j += blockDim.x) rhs[j] = (double)r[pos(act[j], ly)];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = threadIdx.x >> 5; i < nact; i += blockDim.x >> 5) {
+        double s = 0.0;
+        for (int64_t j = lane; j < nact; j += 32) s = fma(Ainv[i * nact + j], rhs[j], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) u[pos(act[i], ly)] += (T)s;
+    }
+    __syncthreads();
+}
+
+// one block per hierarchy with a tail: its V-cycle from the tail's top
+// level down to the coarsest and back (nu1 pre- and nu2 post-smoothing
+// steps, each red, black, ghost relaxation)
+template <int D, typename T>
+__global__ void __launch_bounds__(kBT, 2) kb_btail(const BLev<T> *__restrict__ lv, const BTail *__restrict__ tails,
+                                                const BCtl *__restrict__ ctl, int nu1, int nu2) {
+    const BTail tl = tails[blockIdx.x];
+    const BLev<T> *const L = lv + tl.lev0;
+    const int nl = (int)tl.nl;
+    if (bskip(ctl, L[0].h)) return;  // uniform over the block (one hierarchy)
+    for (int l = 0; l + 1 < nl; ++l) {
+        for (int s = 0; s < nu1; ++s) {
+            bt_sweep<D, T>(L[l], 0);
+            bt_sweep<D, T>(L[l], 1);
+            bt_relax<D, T>(L[l]);
+        }
+        bt_residual<D, T>(L[l]);
+        bt_extend<T>(L[l], L[l].r);
+        bt_restrict<D, T>(L[l + 1], L[l]);
+    }
+    bt_residual<D, T>(L[nl - 1]);
+    bt_coarsest<T>(L[nl - 1]);
+    for (int l = nl - 2; l >= 0; --l) {
+        bt_extend<T>(L[l + 1], L[l + 1].u);
+        bt_prolong<D, T>(L[l], L[l + 1]);
+        for (int s = 0; s < nu2; ++s) {
+            bt_sweep<D, T>(L[l], 0);
+            bt_sweep<D, T>(L[l], 1);
+            bt_relax<D, T>(L[l]);
+        }
+    }
+}
+
 // One block per hierarchy: reduce its norm partials (slots p0[h] .. p0[h+1]
 // of the norm residual launch) in slot order, then start (mode 0) or check
 // (mode 1) its solve; the last block to finish sets the WHILE condition to
@@ -586,12 +812,14 @@ struct Stage {
     int npt;  // items per thread of the stage's kernel (1 or 4)
 };
 enum { S_RED, S_BLACK, S_RELAX, S_SCATTER, S_RES, S_EXT_R, S_EXT_U, S_RESTRICT, S_PROLONG, S_GATHER, S_GEMV,
-       S_IR_BEGIN, S_IR_UPDATE, S_NORMRES, S_CHECK };
+       S_IR_BEGIN, S_IR_UPDATE, S_NORMRES, S_CHECK, S_TAIL };
 
 struct Plan {
     int bs = 128;
     int npt = 1;  // items per thread of the node-parallel stages
     std::vector<BRange> ranges;
+    std::vector<BTail> tails;  // block-tail blocks (one per hierarchy with a tail)
+    int nu1 = 2, nu2 = 1;
     std::vector<Stage> cycle;  // one cycle (precision of the V-cycle)
     std::vector<Stage> norms;  // finest FP64 residual with partials; refinement rows
     std::vector<int64_t> p0;   // partial slots per hierarchy (norms)
@@ -634,10 +862,12 @@ struct StageBuilder {
 // sweeps, interior residual rows, restriction and prolongation in 2D, the
 // refinement rows) take npt items per thread, the ghost, band and coarsest
 // stages one
-Plan make_plan(const Batch &B, int bs, int npt, int nu1, int nu2) {
+Plan make_plan(const Batch &B, int bs, int npt, int nu1, int nu2, int64_t tail_rows = 0) {
     Plan P;
     P.bs = bs;
     P.npt = npt;
+    P.nu1 = nu1;
+    P.nu2 = nu2;
     const int nptr = B.d == 2 ? npt : 1;  // 3^d-point restriction rows: one per thread in 3D
     const int nh = (int)B.hs.size();
     int depth = 0;
@@ -651,6 +881,28 @@ Plan make_plan(const Batch &B, int bs, int npt, int nu1, int nu2) {
     auto nrows = [&](int lv) { return info(lv).nint + info(lv).ng; };
     auto nband = [&](int lv) { return info(lv).nb; };
     auto nact = [&](int lv) { return info(lv).nact; };
+    // the block tail of each hierarchy: its levels from st[h] down to the
+    // coarsest, when every list of each of them has at most tail_rows
+    // entries (the coarsest at most kBTMaxCoarse unknowns) and there are at
+    // least two; st[h] = L - 1 (no tail) otherwise
+    std::vector<int> st(nh);
+    std::vector<bool> tailed(nh, false);
+    auto fits = [&](int lv) {
+        const BLev<double> &A = info(lv);
+        const int64_t m = std::max({A.nred, A.nint - A.nred, A.nint + A.ng, A.nb, A.nact});
+        return m <= tail_rows && (A.nb == 0 || A.ecnt != nullptr);
+    };
+    for (int h = 0; h < nh; ++h) {
+        const int Lh = (int)B.hs[h]->L.size();
+        st[h] = Lh - 1;
+        if (tail_rows <= 0 || Lh < 2 || !fits(lev(h, Lh - 1)) || info(lev(h, Lh - 1)).nact > kBTMaxCoarse) continue;
+        int t = Lh - 1;
+        while (t - 1 >= 1 && fits(lev(h, t - 1))) --t;
+        if (t > Lh - 2) continue;
+        st[h] = t;
+        tailed[h] = true;
+        P.tails.push_back(BTail{(uint32_t)lev(h, t), (uint32_t)(Lh - t)});
+    }
     std::vector<Stage> &C = P.cycle;
     auto smooth_steps = [&](const std::vector<int> &S, int steps) {
         for (int s = 0; s < steps; ++s) {
@@ -673,10 +925,10 @@ Plan make_plan(const Batch &B, int bs, int npt, int nu1, int nu2) {
         std::vector<int> S, Co, Sc;
         for (int h = 0; h < nh; ++h) {
             const int Lh = (int)B.hs[h]->L.size();
-            if (k < Lh - 1) {
+            if (k < st[h]) {
                 S.push_back(lev(h, k));
                 Sc.push_back(lev(h, k + 1));
-            } else if (k == Lh - 1) {
+            } else if (k == Lh - 1 && !tailed[h]) {
                 Co.push_back(lev(h, k));
             }
         }
@@ -706,11 +958,14 @@ Plan make_plan(const Batch &B, int bs, int npt, int nu1, int nu2) {
             m.push(C, S_GEMV, 0);
         }
     }
+    // the block tails, between the two legs
+    if (!P.tails.empty())
+        C.push_back(Stage{S_TAIL, 0, 0, (int64_t)P.tails.size(), (int64_t)P.tails.size(), 1});
     // the way up
     for (int k = depth - 2; k >= 0; --k) {
         std::vector<int> S, Cb;
         for (int h = 0; h < nh; ++h)
-            if (k < (int)B.hs[h]->L.size() - 1) {
+            if (k < st[h]) {
                 S.push_back(lev(h, k));
                 Cb.push_back(lev(h, k + 1));
             }
@@ -747,6 +1002,7 @@ Plan make_plan(const Batch &B, int bs, int npt, int nu1, int nu2) {
 
 // device copies of a batch's tables
 struct DevPlan {
+    BTail *tails = nullptr;
     BLev<double> *l64 = nullptr;
     BLev<float> *l32 = nullptr;
     BRange *ranges = nullptr;
@@ -808,6 +1064,10 @@ void enqueue_stages(const Plan &P, const DevPlan &Dv, const BLev<T> *lv, const s
             case S_GEMV:
                 blaunch(st, kb_coarse_gemv<T>, grid, bs, count, lv, rg, nr, ctl);
                 break;
+            case S_TAIL:
+                blaunch(st, kb_btail<D, T>, grid, (unsigned)kBT, count, lv, (const BTail *)Dv.tails, ctl, P.nu1,
+                        P.nu2);
+                break;
             default:
                 break;
         }
@@ -867,6 +1127,8 @@ DevPlan upload_plan(const Batch &B, const Plan &P, cudaStream_t st) {
     }
     Dv.ranges = (BRange *)dev_alloc(Dv, sizeof(BRange) * P.ranges.size(), st);
     upload(P.ranges, Dv.ranges, st);
+    Dv.tails = (BTail *)dev_alloc(Dv, sizeof(BTail) * std::max<size_t>(P.tails.size(), 1), st);
+    upload(P.tails, Dv.tails, st);
     Dv.ctl = (BCtl *)dev_alloc(Dv, sizeof(BCtl) * B.hs.size(), st);
     Dv.sh = (BShared *)dev_alloc(Dv, sizeof(BShared), st);
     check_cuda(cudaMemsetAsync(Dv.sh, 0, sizeof(BShared), st), "batch counters");
@@ -944,8 +1206,9 @@ cudaGraphExec_t build_cycle_graph(const Batch &B, const Plan &P, const DevPlan &
 }
 
 std::mutex g_tune_mu;
-// (dev, d, mixed, nh, nodes) -> (block size, items per thread)
-std::map<std::tuple<int, int, int, int64_t, int64_t>, std::pair<int, int>> g_tuned;
+std::tuple<int, int, int64_t> g_shape_override{0, 1, 0};  // block 0: none (guarded by g_tune_mu)
+// (dev, d, mixed, nh, nodes) -> (block size, items per thread, tail rows)
+std::map<std::tuple<int, int, int, int64_t, int64_t>, std::tuple<int, int, int64_t>> g_tuned;
 
 Batch make_batch(const std::vector<Handle *> &hs) {
     Batch B;
@@ -963,12 +1226,19 @@ Batch make_batch(const std::vector<Handle *> &hs) {
     return B;
 }
 
-// the autotuner: one batched cycle per candidate launch shape (block size
-// 64, 128 or 256 threads; one or four items per thread in the node-parallel
-// stages), timed after a warm replay, on the working copies (saved before
-// and restored after); returns the fastest shape
-std::pair<int, int> tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cycles,
-                                      int64_t *launched) {
+// A batch's launch shape: block size and items per thread of the stages,
+// and the largest list of a level that runs in the block tail (0: no tail)
+struct Shape {
+    int bs = 0, npt = 1;
+    int64_t tail = 0;
+};
+
+// the autotuner: one batched cycle per candidate launch shape, timed after a
+// warm replay, on the working copies (saved before and restored after).
+// First block size 64, 128 or 256 threads, each with one or four items per
+// thread in the node-parallel stages; then, with the fastest of those, the
+// block tail for levels of at most 512 or 2048 list entries, kept if faster.
+Shape tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cycles, int64_t *launched) {
     const int nu1 = B.hs[0]->o.nu1, nu2 = B.hs[0]->o.nu2;
     std::vector<double *> saved;
     for (Handle *H : B.hs) {
@@ -978,14 +1248,13 @@ std::pair<int, int> tune_launch_shape(const Batch &B, cudaStream_t st, double rt
         check_cuda(cudaMemcpyAsync(p, H->u0, bytes, cudaMemcpyDeviceToDevice, st), "tune save copy");
         saved.push_back(p);
     }
-    std::pair<int, int> shape{0, 0};
-    float best = 0.0f;
-    for (const auto cand : {std::make_pair(64, 1), std::make_pair(128, 1), std::make_pair(256, 1),
-                            std::make_pair(64, 4), std::make_pair(128, 4), std::make_pair(256, 4)}) {
-        Plan P = make_plan(B, cand.first, cand.second, nu1, nu2);
+    // the second replay's time; < 0 when the shape gives the batch no tail
+    auto time_shape = [&](const Shape &c) -> float {
+        Plan P = make_plan(B, c.bs, c.npt, nu1, nu2, c.tail);
+        if (c.tail > 0 && P.tails.empty()) return -1.0f;
         DevPlan Dv = upload_plan(B, P, st);
         std::vector<BCtl> c0(B.hs.size());
-        for (auto &c : c0) c = BCtl{rtol, max_cycles, 0, 1.0, 1.0, 0, 0};
+        for (auto &x : c0) x = BCtl{rtol, max_cycles, 0, 1.0, 1.0, 0, 0};
         upload(c0, Dv.ctl, st);
         cudaGraphExec_t ex = B.d == 3 ? build_cycle_graph<3>(B, P, Dv, st) : build_cycle_graph<2>(B, P, Dv, st);
         cudaEvent_t e0, e1;
@@ -1003,9 +1272,26 @@ std::pair<int, int> tune_launch_shape(const Batch &B, cudaStream_t st, double rt
         cudaGraphExecDestroy(ex);
         free_plan(Dv, st);
         *launched += 2 * (int64_t)(P.cycle.size() + (B.mixed ? 2 : 0));
-        if (shape.first == 0 || ms < best) {
-            best = ms;
-            shape = cand;
+        return ms;
+    };
+    Shape best;
+    float best_ms = 0.0f;
+    for (const auto cand : {std::make_pair(64, 1), std::make_pair(128, 1), std::make_pair(256, 1),
+                            std::make_pair(64, 4), std::make_pair(128, 4), std::make_pair(256, 4)}) {
+        const Shape c{cand.first, cand.second, 0};
+        const float ms = time_shape(c);
+        if (best.bs == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    const Shape base = best;
+    for (const int64_t tail : {(int64_t)512, (int64_t)2048}) {
+        const Shape c{base.bs, base.npt, tail};
+        const float ms = time_shape(c);
+        if (ms >= 0.0f && ms < best_ms) {
+            best_ms = ms;
+            best = c;
         }
     }
     for (size_t h = 0; h < B.hs.size(); ++h) {
@@ -1014,10 +1300,15 @@ std::pair<int, int> tune_launch_shape(const Batch &B, cudaStream_t st, double rt
                    "tune restore");
         cudaFreeAsync(saved[h], st);
     }
-    return shape;
+    return best;
 }
 
 }  // namespace
+
+void batch_shape_override(int block, int items, int64_t tail_rows) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_shape_override = std::make_tuple(block, items, tail_rows);
+}
 
 bool batch_eligible(const std::vector<Handle *> &hs) {
     if (hs.size() < 2) return false;
@@ -1049,16 +1340,20 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
     check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     const auto key = std::make_tuple(dev, hs[0]->d, (int)(hs[0]->o.precision == BCMG_PREC_MIXED), (int64_t)n, nodes);
     int64_t launched = 0;
-    std::pair<int, int> shape{0, 0};
+    Shape shape;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (std::get<0>(g_shape_override) > 0)
+            shape = Shape{std::get<0>(g_shape_override), std::get<1>(g_shape_override),
+                          std::get<2>(g_shape_override)};
         auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) shape = it->second;
+        if (shape.bs == 0 && it != g_tuned.end())
+            shape = Shape{std::get<0>(it->second), std::get<1>(it->second), std::get<2>(it->second)};
     }
-    if (shape.first == 0) {
+    if (shape.bs == 0) {
         shape = tune_launch_shape(make_batch(hs), st, rtol, max_cycles, &launched);
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = shape;
+        g_tuned[key] = std::make_tuple(shape.bs, shape.npt, shape.tail);
     }
     std::vector<BCtl> state(n, BCtl{rtol, max_cycles, 0, 0.0, 0.0, 0, 0});
     std::vector<int> active(n);
@@ -1072,7 +1367,7 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
             cs.push_back(state[i]);
         }
         const Batch B = make_batch(sub);
-        const Plan P = make_plan(B, shape.first, shape.second, hs[0]->o.nu1, hs[0]->o.nu2);
+        const Plan P = make_plan(B, shape.bs, shape.npt, hs[0]->o.nu1, hs[0]->o.nu2, shape.tail);
         DevPlan Dv = upload_plan(B, P, st);
         upload(cs, Dv.ctl, st);
         const unsigned stop_at = active.size() > 8 ? (unsigned)(active.size() / 8) : 0u;

@@ -927,6 +927,16 @@ int bcmg_debug_live_blocks(int64_t *blocks, int64_t *bytes) {
     return BCMG_OK;
 }
 
+int bcmg_debug_batch_shape(int block, int items, int64_t tail_rows) {
+    if (block != 0 && block != 64 && block != 128 && block != 256)
+        return fail(BCMG_EINVAL, "block must be 0, 64, 128 or 256");
+    if (items != 1 && items != 4) return fail(BCMG_EINVAL, "items must be 1 or 4");
+    if (tail_rows < 0) return fail(BCMG_EINVAL, "tail_rows must be >= 0");
+    bcmg::batch_shape_override(block, items, tail_rows);
+    g_last_error.clear();
+    return BCMG_OK;
+}
+
 int bcmg_debug_fail_allocation(int64_t k) {
     if (k < 0) return fail(BCMG_EINVAL, "k must be >= 0");
     g_fail_countdown.store(k);

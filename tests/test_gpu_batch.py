@@ -1,10 +1,14 @@
 """Batched solves (bcmg_solve_batch) and device-memory footprints.
 
-Many hierarchies of uneven size and shape are solved in one call; their
-solves run concurrently on the device (each on its own stream).  Each result
-must be bit-identical to the same solve alone, in FP64 and in mixed
-precision, and the footprint estimate used for admission must cover what a
-hierarchy actually holds."""
+Many hierarchies of uneven size and shape are solved in one call.  A batch
+of one dimension and precision runs through the batched kernels (one launch
+per stage of the cycle for all hierarchies): one batched cycle must match
+the oracle's cycle, whole solves must match the same solves alone to
+rounding, and the result must not depend on the launch shape (block size,
+items per thread, block tail).  A mixed batch (2D and 3D) runs each solve on
+its own stream and must be bit-identical to the same solve alone.  The
+footprint estimate used for admission must cover what a hierarchy actually
+holds."""
 
 import numpy as np
 import pytest
@@ -104,11 +108,27 @@ def _ellipsoid_set():
     return [(3, N, W.phi_ellipsoid(N)) for N in (40, 48, 64, 96)]
 
 
+# launch shapes of the batched kernels: (block, items per thread, tail rows);
+# None = the autotuner's choice
+SHAPES = [None, (128, 1, 0), (64, 4, 0), (128, 4, 512), (256, 4, 2048)]
+
+
+@pytest.fixture
+def shape(bcmg, request):
+    s = request.param
+    if s is not None:
+        bcmg.debug_batch_shape(*s)
+    yield s
+    bcmg.debug_batch_shape(0)
+
+
+@pytest.mark.parametrize("shape", SHAPES, indirect=True, ids=lambda s: "tuned" if s is None else "%d-%d-%d" % s)
 @pytest.mark.parametrize("which", ["stars", "ellipsoids"])
-def test_batched_cycle_matches_oracle(bcmg, which):
+def test_batched_cycle_matches_oracle(bcmg, which, shape):
     # one batched V-cycle per hierarchy (max_cycles = 1) against the oracle's
-    # V-cycle from the same start: the batched stages run the same per-node
-    # steps, the coarse levels included (no cluster tail in a batch)
+    # V-cycle from the same start: the batched stages (and the block tail,
+    # where the shape has one) run the same per-node steps, the coarse levels
+    # included
     from oracle import oracle as O
     O.build()
     B = bcmg
@@ -128,8 +148,10 @@ def test_batched_cycle_matches_oracle(bcmg, which):
         s.close()
 
 
+@pytest.mark.parametrize("shape", [None, (128, 4, 2048)], indirect=True,
+                         ids=lambda s: "tuned" if s is None else "%d-%d-%d" % s)
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batched_solves_match_alone(bcmg, prec):
+def test_batched_solves_match_alone(bcmg, prec, shape):
     B = bcmg
     p = B.PREC_FP64 if prec == "fp64" else B.PREC_MIXED
     probs = _star_set(12, 640)
@@ -167,3 +189,40 @@ def test_batched_limits_and_mixed_convergence(bcmg):
     assert all(c < 60 for c in cyc2) and st2 == [B.OK] * len(probs)
     for s, _ in pairs:
         s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_block_tail_is_shape_independent(bcmg, prec):
+    # the same batched cycles with and without the block tail: identical u
+    # (the tail runs the stages' per-node steps in the stages' order), and
+    # the tail takes stage launches off every cycle
+    B = bcmg
+    p = B.PREC_FP64 if prec == "fp64" else B.PREC_MIXED
+    probs = _star_set(10, 640)
+    res = {}
+    try:
+        for shp in ((128, 4, 0), (128, 4, 2048), (64, 1, 512)):
+            B.debug_batch_shape(*shp)
+            pairs = [_make(B, d, N, phi, p) for d, N, phi in probs]
+            k0 = B.kernel_launches()
+            cyc, rel, st = B.solve_batch([s for s, _ in pairs], [u for _, u in pairs], 0.0, 3)
+            torch.cuda.synchronize()
+            res[shp] = (B.kernel_launches() - k0, [u.cpu().numpy() for _, u in pairs])
+            for s, _ in pairs:
+                s.close()
+    finally:
+        B.debug_batch_shape(0)
+    base = res[(128, 4, 0)][1]
+    for shp in ((128, 4, 2048), (64, 1, 512)):
+        for a, b in zip(base, res[shp][1]):
+            np.testing.assert_array_equal(a, b)
+    assert res[(128, 4, 2048)][0] < res[(128, 4, 0)][0]
+
+
+def test_batch_shape_rejects_bad_values(bcmg):
+    B = bcmg
+    for bad in ((100, 1, 0), (128, 3, 0), (128, 1, -1)):
+        with pytest.raises(B.BcmgError) as e:
+            B.debug_batch_shape(*bad)
+        assert e.value.code == B.EINVAL
+    B.debug_batch_shape(0)
