@@ -84,13 +84,18 @@ typedef struct {
                           (default) or BCMG_BC_NEUMANN */
     double reaction;   /* c >= 0 of the interior equation c u - Lap u = f
                           (0: Poisson, the default; Sec. 4.2 Test2N: 1) */
-    int cycle;         /* BCMG_CYCLE_V (gamma = 1, default) or BCMG_CYCLE_W
-                          (gamma = 2), Sec. 2.1 */
+    int cycle;         /* BCMG_CYCLE_V (gamma = 1, default), BCMG_CYCLE_W
+                          (gamma = 2) or BCMG_CYCLE_TG (the two-grid
+                          correction scheme: the level-1 problem solved by
+                          tg_inner V-cycles), Sec. 2.1 */
     int ordering;      /* interior Gauss-Seidel order: BCMG_ORDER_RB
                           (red-black, default) or BCMG_ORDER_LEX
                           (lexicographic, the paper's GS-LEX, eq. GSLEX_2D,
                           run as a sweep over the hyperplanes i+j(+k) = p;
                           one launch per hyperplane, for comparisons) */
+    int tg_inner;      /* V-cycles of the level-1 solve of BCMG_CYCLE_TG
+                          (30: at the method's contraction the coarse
+                          problem is then solved to rounding) */
 } bcmg_opts;
 
 #define BCMG_ORDER_RB 0
@@ -98,6 +103,7 @@ typedef struct {
 
 #define BCMG_CYCLE_V 0
 #define BCMG_CYCLE_W 1
+#define BCMG_CYCLE_TG 2
 
 /* Boundary conditions on Gamma (Sec. 3): Dirichlet u = g; Neumann
  * grad u . n = g with n the ghost's outward unit normal (bcmg_ghost_normals),

@@ -24,7 +24,7 @@ INACTIVE, INTERIOR, GHOST, BOXDIR = 0, 1, 2, 3
 DTAU_EXP, DTAU_POLY, DTAU_CONST = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 BC_DIRICHLET, BC_NEUMANN = 0, 1
-CYCLE_V, CYCLE_W = 0, 1
+CYCLE_V, CYCLE_W, CYCLE_TG = 0, 1, 2
 ORDER_RB, ORDER_LEX = 0, 1
 
 _lib = None
@@ -42,7 +42,7 @@ class Opts(C.Structure):
                 ("dtau_const", C.c_double), ("ext_sweeps", C.c_int), ("min_coarse", C.c_int),
                 ("max_levels", C.c_int), ("use_graph", C.c_int), ("profile", C.c_int),
                 ("precision", C.c_int), ("bc", C.c_int), ("reaction", C.c_double), ("cycle", C.c_int),
-                ("ordering", C.c_int)]
+                ("ordering", C.c_int), ("tg_inner", C.c_int)]
 
 
 def declared_functions():

@@ -647,6 +647,7 @@ void bcmg_default_opts(bcmg_opts *o) {
     o->reaction = 0.0;
     o->cycle = BCMG_CYCLE_V;
     o->ordering = BCMG_ORDER_RB;
+    o->tg_inner = 30;
 }
 
 int bcmg_create_grid_hierarchy(int dim, int64_t N, const double *phi_dev, const double *f_dev,
@@ -685,7 +686,8 @@ int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const
             (H->o.precision != BCMG_PREC_FP64 && H->o.precision != BCMG_PREC_MIXED) ||
             (H->o.bc != BCMG_BC_DIRICHLET && H->o.bc != BCMG_BC_NEUMANN) ||
             !(H->o.reaction >= 0.0 && H->o.reaction < 1e300) ||
-            (H->o.cycle != BCMG_CYCLE_V && H->o.cycle != BCMG_CYCLE_W) ||
+            (H->o.cycle != BCMG_CYCLE_V && H->o.cycle != BCMG_CYCLE_W && H->o.cycle != BCMG_CYCLE_TG) ||
+            (H->o.cycle == BCMG_CYCLE_TG && (H->o.tg_inner < 1 || H->o.tg_inner > 10000)) ||
             (H->o.ordering != BCMG_ORDER_RB && H->o.ordering != BCMG_ORDER_LEX) || H->o.use_graph < 0 ||
             H->o.use_graph > 2)
             throw Error{BCMG_EINVAL, "invalid options"};

@@ -971,7 +971,11 @@ void vcycle_t(Handle &H, int l, T *u) {
     residual<T>(H, A, u, Arr<T>::F(A), Arr<T>::r(A));
     extend<T>(H, A, Arr<T>::r(A));
     restrict_to<T>(H, A, B, Arr<T>::r(A), Arr<T>::F(B), Arr<T>::u(B), true, Arr<T>::Fs(B));
-    const int gamma = H.o.cycle == BCMG_CYCLE_W ? 2 : 1;
+    // two-grid correction scheme (Sec. 2.1): the level-1 problem solved by
+    // tg_inner V-cycles from zero (with more than two levels; else the
+    // coarsest solve below is already exact); otherwise gamma visits
+    const bool tg = H.o.cycle == BCMG_CYCLE_TG && l == 0 && H.L.size() > 2;
+    const int gamma = tg ? H.o.tg_inner : H.o.cycle == BCMG_CYCLE_W ? 2 : 1;
     for (int g = 0; g < gamma; ++g) vcycle_t<T>(H, l + 1, Arr<T>::u(B));
     extend<T>(H, B, Arr<T>::u(B));
     prolong<T>(H, A, B, Arr<T>::u(B), u, true);

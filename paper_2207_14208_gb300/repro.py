@@ -138,6 +138,15 @@ def main():
                  lambda r, N: "%.3f" % rho(2, N, (W.phi_circle_paper if r.startswith("circle") else
                                                   W.phi_flower_paper)(N),
                                           ordering=bcmg.ORDER_LEX if r.endswith("LEX") else bcmg.ORDER_RB)))
+    print("\nTwo-grid correction scheme (the paper's protocol, Sec. 2.1: the level-1 problem solved by 30 "
+          "V-cycles), (2,1) smoothing: rho")
+    tg = dict(cycle=bcmg.CYCLE_TG, tg_inner=30)
+    print(_table(["circle Dtau_OPT exp", "circle Dtau = 1.75", "flower Dtau_OPT exp", "flower Dtau = 1.75"],
+                 Ns2[:4],
+                 lambda r, N: "%.3f" % rho(2, N, (W.phi_circle_paper if r.startswith("circle") else
+                                                  W.phi_flower_paper)(N),
+                                          **tg, **(dict(dtau_mode=bcmg.DTAU_CONST, dtau_const=1.75)
+                                                   if r.endswith("1.75") else dict(dtau_mode=bcmg.DTAU_EXP)))))
     print("\nW(2,1) against V(2,1), Dtau_OPT exp: rho")
     print(_table(["circle V", "circle W"], Ns2[:4],
                  lambda r, N: "%.3f" % rho(2, N, W.phi_circle_paper(N),

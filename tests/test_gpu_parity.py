@@ -328,6 +328,46 @@ def test_wcycle_matches_oracle(bcmg, name, d, N, mk):
     assert rel <= 1e-10
 
 
+@pytest.mark.parametrize("name,d,N,mk", [("disk128", 2, 128, W.phi_disk), ("ellipsoid48", 3, 48, W.phi_ellipsoid),
+                                         ("flower96", 2, 96, W.phi_flower_paper)],
+                         ids=["disk128", "ellipsoid48", "flower96"])
+def test_tgcs_matches_oracle(bcmg, name, d, N, mk):
+    # two-grid correction scheme (Sec. 2.1): the level-1 problem solved by K
+    # V-cycles from zero (the grid path and the cluster tail below level 1);
+    # the oracle's TGCS with tolerance 0 runs exactly K
+    B = bcmg
+    K = 12
+    phi = mk(N)
+    f, us = W.manufactured(d, N)
+    s = B.Solver(d, N, dev(phi), dev(f), cycle=B.CYCLE_TG, tg_inner=K)
+    o = O.Oracle(d, N, phi, cycle=O.CYC_TGCS, tgcs_tol=0.0, tgcs_maxit=K)
+    assert s.levels == o.L > 2
+    g = W.g_at(d, o.ghosts(0)["Q"])
+    o.set_rhs(f, g)
+    s.set_boundary_values(dev(g))
+    act = np.isin(o.cls(0), [O.INTERIOR, O.GHOST])
+    uo = np.zeros(o.nn(0))
+    ug = dev(uo)
+    for cyc in range(3):
+        uo = o.vcycle(uo, 1)
+        s.vcycle(ug, 1)
+        assert np.abs(host(ug)[act] - uo[act]).max() <= REL * np.abs(uo[act]).max(), cyc
+    c, rel = s.solve(dev(np.zeros(o.nn(0))), 1e-10, 60)
+    assert rel <= 1e-10
+    cv, _ = B.Solver(d, N, dev(phi), dev(f)).solve(dev(np.zeros(o.nn(0))), 1e-10, 60)
+    assert c <= cv  # an exact coarse solve needs no more cycles than the V-cycle
+
+
+def test_tgcs_rho_harness_matches_oracle(bcmg):
+    from paper_2207_14208_gb300 import repro
+    N = 64
+    phi = W.phi_circle_paper(N)
+    r_gpu = repro.rho(2, N, phi, cycle=bcmg.CYCLE_TG, tg_inner=30)
+    o = O.Oracle(2, N, phi, cycle=O.CYC_TGCS, tgcs_tol=0.0, tgcs_maxit=30)
+    r_orc, _ = o.rho(np.random.Generator(np.random.PCG64(3)).uniform(-1.0, 1.0, (N + 1) ** 2))
+    assert r_gpu == pytest.approx(r_orc, rel=1e-6)
+
+
 def test_rho_harness_matches_oracle(bcmg):
     # the reproduction harness's rho (Sec. 2.2 protocol) against the oracle's
     from paper_2207_14208_gb300 import repro
