@@ -178,7 +178,7 @@ FP64_INSTR_PER_UPDATE = 6   # 5 adds, 1 FMA per red/black update (from the scale
 # algorithmic bytes of one colour pass per interior node of the level: u read
 # (the whole level), f read and u written for the pass's colour -- 32 B per
 # node for the two separate colour passes of a sweep in FP64, half in FP32
-SWEEP_BYTES_PER_NODE = {"fp64": 16.0, "fp32": 8.0}
+SWEEP_BYTES_PER_NODE = {"fp64": 16.0, "fp32": 8.0, "bf16": 4.0}
 SWEEPS = 200                # back-to-back sweeps timed for the roofline
 FP64_PEAK_GINSTR = 152 * 2 * 2.07  # SMs x FP64 FMA pipes per clock x GHz (1.26 TFLOP/s)
 # DRAM bytes (read + write) of one finest-level sweep launch at N=256 (FP64
@@ -403,6 +403,9 @@ def sweep_rooflines(sizes=(256, 384, 512), nsweeps=100, warm=True):
             nint = s.info(0)["n_interior"]
             upd = nint / 2.0
             us = s.time_sweeps(nsweeps) / nsweeps * 1e3
+            # the same sweeps with 16-bit storage (FP32 arithmetic): what
+            # bfloat16 would gain on this kernel
+            us16 = s.time_sweeps_bf16(nsweeps) / nsweeps * 1e3 if key == "fp32" else None
             s.close()
             if key == "fp64":
                 ach = FP64_INSTR_PER_UPDATE * upd / (us * 1e-6) / 1e9
@@ -413,6 +416,9 @@ def sweep_rooflines(sizes=(256, 384, 512), nsweeps=100, warm=True):
                 ach = SWEEP_BYTES_PER_NODE["fp32"] * nint / (us * 1e-6) / 1e9
                 row[key] = {"sweep_us": us, "updates": upd, "achieved": ach, "peak": peak, "unit": "GB/s",
                             "frac": ach / peak}
+                ach16 = SWEEP_BYTES_PER_NODE["bf16"] * nint / (us16 * 1e-6) / 1e9
+                row["bf16"] = {"sweep_us": us16, "achieved": ach16, "peak": peak, "unit": "GB/s",
+                               "frac": ach16 / peak, "speedup_vs_fp32": us / us16}
         del phi, f
         torch.cuda.empty_cache()
         out[str(N)] = row

@@ -338,6 +338,15 @@ int bcmg_selftest_div_wsum(int fp32, const double *a_host, int64_t n, double *ou
  * Synchronous.  Errors: EINVAL, ECUDA. */
 int bcmg_time_sweeps(bcmg_handle h, int nsweeps, double *ms_host);
 
+/* The same sweeps with u and the scaled right-hand side stored as bfloat16
+ * (8-bit significand; sums and updates in FP32, results rounded to nearest)
+ * on temporary copies of the working arrays, which are freed again; the
+ * handle is left unchanged.  A measurement of what 16-bit storage would
+ * gain on the dominant kernel (the paper computes in double precision
+ * throughout; no counterpart there).  The finest level must be split by
+ * parity (even N).  Synchronous.  Errors: EINVAL, ENOMEM, ECUDA. */
+int bcmg_time_sweeps_bf16(bcmg_handle h, int nsweeps, double *ms_host);
+
 /* ---- introspection (host copies, synchronous) ----------------------- */
 
 int bcmg_num_levels(bcmg_handle h, int *levels);

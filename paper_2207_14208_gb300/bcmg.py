@@ -86,6 +86,7 @@ def load():
             "bcmg_kernel_launches": (i64, []),
             "bcmg_profile_read": (i32, [vp, vp]),
             "bcmg_time_sweeps": (i32, [vp, i32, vp]),
+            "bcmg_time_sweeps_bf16": (i32, [vp, i32, vp]),
             "bcmg_residual_norms_static": (i32, [vp, vp, i64, vp, vp]),
             "bcmg_selftest_div_wsum": (i32, [i32, vp, i64, vp]),
             "bcmg_num_levels": (i32, [vp, vp]),
@@ -324,6 +325,13 @@ class Solver:
         """Summed device time (ms) of nsweeps back-to-back finest-level sweeps."""
         v = C.c_double()
         _check(self.lib.bcmg_time_sweeps(self.h, int(nsweeps), C.byref(v)))
+        return v.value
+
+    def time_sweeps_bf16(self, nsweeps: int) -> float:
+        """The same sweeps with bfloat16 storage of u and Fs (FP32 arithmetic),
+        on temporary copies: summed device time (ms)."""
+        v = C.c_double()
+        _check(self.lib.bcmg_time_sweeps_bf16(self.h, int(nsweeps), C.byref(v)))
         return v.value
 
     def memory_footprint(self) -> int:

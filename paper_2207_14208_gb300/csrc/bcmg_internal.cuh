@@ -246,6 +246,7 @@ void solve_check_enqueue(Handle &H, unsigned long long cond);
 void vcycle_enqueue(Handle &H, int l, double *u);
 // summed device time (ms) of nsweeps back-to-back finest-level colour sweeps
 double time_sweeps(Handle &H, int nsweeps);
+double time_sweeps_bf16(Handle &H, int nsweeps);
 // batched solves (batch.cu): can these hierarchies advance together (same
 // dimension, precision, device, red-black V(nu1, nu2) cycles, expanded
 // extensions)?  Then solve all of them from their working copies u0, ordered

@@ -1015,6 +1015,17 @@ int bcmg_time_sweeps(bcmg_handle h, int nsweeps, double *ms_host) {
     });
 }
 
+int bcmg_time_sweeps_bf16(bcmg_handle h, int nsweeps, double *ms_host) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        if (!ms_host || nsweeps < 1) throw Error{BCMG_EINVAL, "bad argument"};
+        if (H.o.ordering != BCMG_ORDER_RB) throw Error{BCMG_EINVAL, "red-black ordering only"};
+        enter(H);
+        *ms_host = time_sweeps_bf16(H, nsweeps);
+        leave(H);
+    });
+}
+
 int bcmg_num_levels(bcmg_handle h, int *levels) {
     return guarded([&] {
         Handle &H = *checked(h);

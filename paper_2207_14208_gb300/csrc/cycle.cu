@@ -13,6 +13,7 @@
 // hardware cluster barrier.  None of these kernels is a dense contraction,
 // so no tensor-core path is used.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <map>
@@ -104,6 +105,72 @@ __global__ void __launch_bounds__(kT) k_smooth_pers(const uint32_t *__restrict__
 #pragma unroll
         for (int j = 0; j < NPT; ++j) m[j] = mn[j];
     }
+}
+
+// k_smooth_pers with 16-bit storage: u and Fs held as bfloat16 (8-bit
+// significand), every sum and the update in FP32, the new value rounded to
+// bfloat16 (round to nearest even).  Used only to measure what 16-bit
+// storage would gain on the dominant kernel (time_sweeps_bf16).
+template <int D, int NPT>
+__global__ void __launch_bounds__(kT) k_smooth_pers_bf16(const uint32_t *__restrict__ list, int64_t n,
+                                                         __nv_bfloat16 *u, const __nv_bfloat16 *__restrict__ Fs,
+                                                         G2 G, int par) {
+    const int64_t chunk = (int64_t)blockDim.x * NPT;
+    int64_t c = blockIdx.x;
+    uint32_t m[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const int64_t i = c * chunk + (int64_t)j * blockDim.x + threadIdx.x;
+        m[j] = i < n ? (list[i] >> 1) : 0u;
+    }
+    pdl_begin();
+    const int64_t sy = G.sy, sz = G.sz;
+    const int64_t xm = par - 1, xp = par, ym = par - ((sy + 1) >> 1), yp = par + ((sy - 1) >> 1);
+    const int64_t zm = par - ((sz + 1) >> 1), zp = par + ((sz - 1) >> 1);
+    const __nv_bfloat16 *v = u + (par ? 0 : G.lay.ho);
+    const int64_t own = par ? G.lay.ho : 0;
+    const float inv_diag = (float)G.inv_diag;
+    for (; c * chunk < n; c += gridDim.x) {
+        const int64_t i0 = c * chunk + threadIdx.x;
+        float a[NPT][D == 3 ? 6 : 4], f[NPT];
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const bool on = i0 + (int64_t)j * blockDim.x < n;
+            const __nv_bfloat16 *w = v + m[j];
+            a[j][0] = on ? __bfloat162float(w[xm]) : 0.0f;
+            a[j][1] = on ? __bfloat162float(w[xp]) : 0.0f;
+            a[j][2] = on ? __bfloat162float(w[ym]) : 0.0f;
+            a[j][3] = on ? __bfloat162float(w[yp]) : 0.0f;
+            if (D == 3) {
+                a[j][4] = on ? __bfloat162float(w[zm]) : 0.0f;
+                a[j][5] = on ? __bfloat162float(w[zp]) : 0.0f;
+            }
+            f[j] = on ? __bfloat162float(Fs[own + m[j]]) : 0.0f;
+        }
+        uint32_t mn[NPT];
+        const int64_t i1 = (c + gridDim.x) * chunk + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const int64_t i = i1 + (int64_t)j * blockDim.x;
+            mn[j] = i < n ? (list[i] >> 1) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            if (i0 + (int64_t)j * blockDim.x >= n) continue;
+            float s = (a[j][0] + a[j][1]) + (a[j][2] + a[j][3]);
+            if (D == 3) s += a[j][4] + a[j][5];
+            u[own + m[j]] = __float2bfloat16_rn(fmaf(s, inv_diag, f[j]));
+        }
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) m[j] = mn[j];
+    }
+}
+
+template <typename S>
+__global__ void k_to_bf16(const S *__restrict__ src, __nv_bfloat16 *__restrict__ dst, int64_t n) {
+    pdl_begin();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn((float)src[i]);
 }
 
 // fictitious-time relaxation of every ghost from the same u (eq. rel with
@@ -1145,6 +1212,52 @@ double time_sweeps(Handle &H, int nsweeps) {
     check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    return (double)ms;
+}
+
+// The sweeps of time_sweeps with u and Fs stored as bfloat16 (temporary
+// copies of the working arrays; arithmetic in FP32): a measurement of the
+// dominant kernel with 16-bit storage.  The level must be parity-split with
+// odd n (the grid levels of an even N).
+double time_sweeps_bf16(Handle &H, int nsweeps) {
+    Level &L = H.L[0];
+    if (!((L.n & 1) && L.lay.s == 1)) throw Error{BCMG_EINVAL, "the finest level is not parity-split with odd n"};
+    const int64_t len = split_len(L.nn);
+    __nv_bfloat16 *u16 = nullptr, *fs16 = nullptr;
+    check_cuda(cudaMallocAsync(&u16, sizeof(__nv_bfloat16) * (size_t)len, H.st), "bf16 copy");
+    check_cuda(cudaMallocAsync(&fs16, sizeof(__nv_bfloat16) * (size_t)len, H.st), "bf16 copy");
+    const bool mixed = H.o.precision == BCMG_PREC_MIXED;
+    if (mixed) {
+        launch(H, "k_to_bf16", k_to_bf16<float>, nblk(len, kT), kT, (const float *)L.u32, u16, len);
+        launch(H, "k_to_bf16", k_to_bf16<float>, nblk(len, kT), kT, (const float *)L.Fs32, fs16, len);
+    } else {
+        launch(H, "k_to_bf16", k_to_bf16<double>, nblk(len, kT), kT, (const double *)H.u0, u16, len);
+        launch(H, "k_to_bf16", k_to_bf16<double>, nblk(len, kT), kT, (const double *)L.Fs, fs16, len);
+    }
+    constexpr int NPT = 2;
+    auto k = L.d == 3 ? k_smooth_pers_bf16<3, NPT> : k_smooth_pers_bf16<2, NPT>;
+    int b = 0;
+    check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kT, 0), "occupancy");
+    const unsigned resident = (unsigned)(std::max(1, b) * H.nsm);
+    const G2 G = g2_of(L);
+    cudaEvent_t e0, e1;
+    check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+    check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+    check_cuda(cudaEventRecord(e0, H.st), "event");
+    for (int s = 0; s < nsweeps; ++s) {
+        const int c = s & 1;
+        const int64_t n = c ? L.nint - L.nred : L.nred;
+        launch(H, "k_smooth", k, std::min(resident, nblk(n, kT * NPT)), kT, (const uint32_t *)(L.ilist + (c ? L.nred : 0)),
+               n, u16, (const __nv_bfloat16 *)fs16, G, c);
+    }
+    check_cuda(cudaEventRecord(e1, H.st), "event");
+    check_cuda(cudaEventSynchronize(e1), "event sync");
+    float ms = 0.0f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(u16, H.st);
+    cudaFreeAsync(fs16, H.st);
     return (double)ms;
 }
 
