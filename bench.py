@@ -566,7 +566,7 @@ def run_stars_batched(args):
                      torch.from_numpy(W.manufactured(2, N)[0]).cuda()))
     stream = torch.cuda.current_stream()
 
-    def make(i, use_graph=2):
+    def make(i, use_graph=2, prec=bcmg.PREC_MIXED):
         # the hierarchy is ordered on the stream current at its creation, so
         # that stream is kept with it; these handles are solved through the
         # batched kernels, so their own solve graphs are left to a first
@@ -574,7 +574,7 @@ def run_stars_batched(args):
         N, phi, f = data[i]
         cs = torch.cuda.Stream()
         with torch.cuda.stream(cs):
-            s = bcmg.Solver(2, N, phi, f, precision=bcmg.PREC_MIXED, use_graph=use_graph)
+            s = bcmg.Solver(2, N, phi, f, precision=prec, use_graph=use_graph)
             u = torch.zeros((N + 1) ** 2, dtype=torch.float64, device="cuda")
         return s, u, cs
 
@@ -597,7 +597,7 @@ def run_stars_batched(args):
 
     split = {"create": 0.0, "solve": 0.0}
 
-    def step(pool):
+    def step(pool, keep=()):
         t0 = time.perf_counter()
         trip = list(pool.map(make, range(len(data))))
         boundary_values(trip)
@@ -607,9 +607,10 @@ def run_stars_batched(args):
         torch.cuda.synchronize()
         split["create"] += t1 - t0
         split["solve"] += time.perf_counter() - t1
+        kept = {i: trip[i][1].cpu().numpy() for i in keep if st[i] == bcmg.OK}
         for t in trip:
             t[0].close()
-        return cyc, st
+        return (cyc, st, kept) if keep else (cyc, st)
 
     steps = max(1, min(args.steps, 5))
     with ThreadPoolExecutor(16) as pool:
@@ -634,16 +635,32 @@ def run_stars_batched(args):
         ms = e0.elapsed_time(e1)
         launches = bcmg.kernel_launches() - launches0
         clk = clocks.stop()
-    # single solves, one after another (same work)
-    t0 = time.perf_counter()
-    for i in range(len(data)):
-        s, u, cs = make(i, use_graph=1)
+        # one more step, untimed, keeping every 16th solution for the error
+        # against the FP64 single solves below
+        sample = list(range(0, len(data), 16))
+        _, _, kept = step(pool, keep=sample)
+    # plain FP64 single solves, one after another (same problems, same
+    # tolerance): the baseline the batched mixed-precision rate is set against
+    def single_fp64(i):
+        s, u, cs = make(i, use_graph=1, prec=bcmg.PREC_FP64)
         with torch.cuda.stream(cs):
             s.set_boundary_values(_g2_torch(s.ghost_points()).contiguous())
-            s.solve(u, args.rtol, 100, raise_noconv=False)
-        s.close()
+            c, r = s.solve(u, args.rtol, 100, raise_noconv=False)
+        return s, u, r
+
+    t0 = time.perf_counter()
+    for i in range(len(data)):
+        single_fp64(i)[0].close()
     torch.cuda.synchronize()
     single = len(data) / (time.perf_counter() - t0)
+    errs = []
+    for i in kept:  # untimed: the sampled stars again, for the error
+        s, u, r = single_fp64(i)
+        if r <= args.rtol:
+            act = np.isin(s.cls(0), [bcmg.INTERIOR, bcmg.GHOST])
+            u64 = u.cpu().numpy()
+            errs.append(float(np.abs(kept[i][act] - u64[act]).max() / np.abs(u64[act]).max()))
+        s.close()
     value = ok / (ms / 1e3)
     return {"metric": "solves/s, 256 batched 2D star domains (N 64..1024), FP32 cycles in FP64 refinement to 1e-10",
             "value": value, "unit": "solves/s", "n_gpus": 1, "steps": steps, "warmup": max(1, args.warmup),
@@ -651,8 +668,11 @@ def run_stars_batched(args):
             "dtype": "f32 cycles in f64 refinement", "data": "synthetic (seeded star level sets, manufactured solution)",
             "config": {"workload": "256 star domains r = 0.5 + a sin(k theta + psi), PCG64 seed 1, N 64..1024",
                        "solves_per_step": len(data), "converged_per_step": ok / steps,
-                       "mean_cycles": float(np.mean(cycles)), "single_solves_per_s": single,
-                       "batch_over_single": value / single,
+                       "mean_cycles": float(np.mean(cycles)), "single_fp64_solves_per_s": single,
+                       "batch_over_single_fp64": value / single,
+                       "max_rel_err_vs_fp64_single": max(errs) if errs else None,
+                       "error_sample": "every 16th star that converges (%d of %d), interior and ghost nodes"
+                                       % (len(errs), len(data)),
                        "step": "threaded create x256 + one gathered g(Q) + one bcmg_solve_batch + destroy",
                        "create_ms_per_step": split["create"] * 1e3 / steps,
                        "solve_batch_ms_per_step": split["solve"] * 1e3 / steps,
@@ -710,6 +730,9 @@ def run_served(args):
     clocks.start()
     launches0 = bcmg.kernel_launches()
     reqs = served_requests(0.0, count)  # built on the host before the clock starts
+    sample = set(range(0, count, 8))  # solutions kept for the error against FP64 single solves
+    for r in reqs:
+        r.keep_u = r.rid in sample
     t0 = time.perf_counter()
     res = server.run(reqs)
     sat_s = time.perf_counter() - t0
@@ -729,6 +752,26 @@ def run_served(args):
     launches = bcmg.kernel_launches() - launches0
     clk = clocks.stop()
     torch.cuda.synchronize()
+    # plain FP64 single solves of the same requests, one after another (same
+    # tolerance): the baseline the served rate is set against; then, untimed,
+    # the sampled requests again for the error of the served solutions
+    import dataclasses
+    fp64_reqs = [dataclasses.replace(r, precision=bcmg.PREC_FP64, keep_u=False) for r in served_requests(0.0, count)]
+    t0 = time.perf_counter()
+    for r in fp64_reqs:
+        with torch.cuda.stream(torch.cuda.Stream()):
+            serve.solve_one(r)
+    torch.cuda.synchronize()
+    single = count / (time.perf_counter() - t0)
+    kept = {r.rid: r for r in res if r.u is not None and r.status == bcmg.OK}
+    errs = []
+    for r in fp64_reqs:
+        if r.rid not in kept:
+            continue
+        with torch.cuda.stream(torch.cuda.Stream()):
+            _, rel64, st64, _, u64 = serve.solve_one(dataclasses.replace(r, keep_u=True))
+        if st64 == bcmg.OK:
+            errs.append(float(np.abs(kept[r.rid].u - u64).max() / np.abs(u64).max()))
     return {"metric": "solves/s and p50/p99 latency, served stream (Poisson arrivals, 2D stars + 3D ellipsoids, "
                       "FP64 and mixed, rtol 1e-10)",
             "value": sat, "unit": "solves/s", "n_gpus": 1, "steps": count, "warmup": 8,
@@ -736,7 +779,11 @@ def run_served(args):
             "dtype": "f64 and f32-in-f64 mix", "data": "synthetic (seeded level sets, manufactured solutions)",
             "config": {"workload": "64 requests, PCG64 seed 2: 2D stars N 64..2048, 3D ellipsoids N 64..256",
                        "admission": "estimated footprint within a %d GB budget, 16 workers" % (budget // 10 ** 9),
-                       "rates": lines, "converged_at_saturation": len(ok), "parallelism": "single"},
+                       "rates": lines, "converged_at_saturation": len(ok),
+                       "single_fp64_solves_per_s": single, "saturation_over_single_fp64": sat / single,
+                       "max_rel_err_vs_fp64_single": max(errs) if errs else None,
+                       "error_sample": "every 8th request (%d), whole grid" % len(errs),
+                       "parallelism": "single"},
             "clocks": clk, "gpu_launches": launches}
 
 
