@@ -736,6 +736,7 @@ def run_served(args):
     t0 = time.perf_counter()
     res = server.run(reqs)
     sat_s = time.perf_counter() - t0
+    res_sat = res
     ok = [r for r in res if r.status == bcmg.OK]
     sat = len(ok) / sat_s
     lines = {"saturation": {"solves_per_s": sat, **{"p%d_ms" % p: v * 1e3 for p, v in
@@ -763,7 +764,7 @@ def run_served(args):
             serve.solve_one(r)
     torch.cuda.synchronize()
     single = count / (time.perf_counter() - t0)
-    kept = {r.rid: r for r in res if r.u is not None and r.status == bcmg.OK}
+    kept = {r.rid: r for r in res_sat if r.u is not None and r.status == bcmg.OK}
     errs = []
     for r in fp64_reqs:
         if r.rid not in kept:
