@@ -730,7 +730,11 @@ def run_served(args):
     clocks.start()
     launches0 = bcmg.kernel_launches()
     reqs = served_requests(0.0, count)  # built on the host before the clock starts
-    sample = set(range(0, count, 8))  # solutions kept for the error against FP64 single solves
+    # solutions kept for the error against FP64 single solves: the first four
+    # requests of each precision
+    sample = set()
+    for prec in (bcmg.PREC_FP64, bcmg.PREC_MIXED):
+        sample |= set(sorted(r.rid for r in reqs if r.precision == prec)[:4])
     for r in reqs:
         r.keep_u = r.rid in sample
     t0 = time.perf_counter()
@@ -783,7 +787,7 @@ def run_served(args):
                        "rates": lines, "converged_at_saturation": len(ok),
                        "single_fp64_solves_per_s": single, "saturation_over_single_fp64": sat / single,
                        "max_rel_err_vs_fp64_single": max(errs) if errs else None,
-                       "error_sample": "every 8th request (%d), whole grid" % len(errs),
+                       "error_sample": "the first four requests of each precision (%d), whole grid" % len(errs),
                        "parallelism": "single"},
             "clocks": clk, "gpu_launches": launches}
 

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 
 #include "bcmg_internal.cuh"
 
@@ -879,6 +881,55 @@ __global__ void k_assemble(const uint32_t *__restrict__ act, int64_t nact, const
             }
 }
 
+// Device-to-device copies of several arrays in one launch, in 32-bit words
+// (job j: n words from src to dst; blockIdx.y is the job).  Creation copies a
+// handful of arrays per level; one launch instead of one driver call each
+// keeps concurrent creations from contending for the driver.
+struct CopyJob {
+    const uint32_t *src;
+    uint32_t *dst;
+    int64_t n;
+};
+constexpr int kMaxCopyJobs = 64;
+struct CopyBatch {
+    int nj;
+    CopyJob j[kMaxCopyJobs];
+};
+
+__global__ void k_copy_words(CopyBatch B) {
+    const CopyJob c = B.j[blockIdx.y];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.n; i += (int64_t)gridDim.x * blockDim.x)
+        c.dst[i] = c.src[i];
+}
+
+struct Copier {
+    Handle &H;
+    CopyBatch b{};
+    int64_t maxn = 0;
+    explicit Copier(Handle &h) : H(h) {}
+    // bytes: a multiple of 4; both pointers 4-byte aligned
+    void add(const void *src, void *dst, size_t bytes) {
+        if (bytes == 0) return;
+        if (b.nj == kMaxCopyJobs) flush();
+        const int64_t n = (int64_t)(bytes / 4);
+        b.j[b.nj++] = CopyJob{(const uint32_t *)src, (uint32_t *)dst, n};
+        maxn = std::max(maxn, n);
+    }
+    void flush() {
+        if (b.nj == 0) return;
+        const unsigned gx = (unsigned)std::min<int64_t>((maxn + 255) / 256, 1024);
+        k_copy_words<<<dim3(gx, (unsigned)b.nj), 256, 0, H.st>>>(b);
+        count_launch(H);
+        check_cuda(cudaGetLastError(), "array copies");
+        b.nj = 0;
+        maxn = 0;
+    }
+};
+
+// the shared-memory limits of the LU kernels are per kernel and device for
+// the whole process: set once per device, always to the largest size
+void lu_attributes_once();
+
 __global__ void k_identity(double *__restrict__ M, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n * n) return;
@@ -1382,16 +1433,10 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             // shared-memory limits are per kernel for the whole process: always
             // the largest size (n = kLuSmall), never one handle's n
             const size_t smem = sizeof(double) * (size_t)(n * n + n);
-            check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(sizeof(double) * (kLuSmall * kLuSmall + kLuSmall))),
-                       "LU shared memory");
+            lu_attributes_once();
             k_lu_small<<<1, 1024, smem, H.st2>>>(A, (int)n, LU, perm, sing);
             count_launch(H);
             const size_t smem2 = sizeof(double) * (size_t)(n * n + n + kLuColsPerBlock * n);
-            check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(sizeof(double) * (kLuSmall * kLuSmall + (2 + kLuColsPerBlock) *
-                                                                                            kLuSmall))),
-                       "LU inverse shared memory");
             k_lu_inverse<<<nblocks(n, kLuColsPerBlock), 32 * kLuColsPerBlock, smem2, H.st2>>>(LU, (int)n, perm, L.Ainv);
             count_launch(H);
         } else {
@@ -1414,6 +1459,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     // and band marks of every level in one launch
     std::vector<LevelTab> tab(keep);
     int64_t gblocks = 0;
+    Copier lists(H);
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
         LevelScratch &s = S[l];
@@ -1421,13 +1467,8 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         // arrays every entry of which a set-up kernel or copy writes take
         // no zero-fill
         L.ilist = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(L.nint, 1), false, false);
-        if (L.nred > 0)
-            check_cuda(cudaMemcpyAsync(L.ilist, s.red, sizeof(uint32_t) * L.nred, cudaMemcpyDeviceToDevice, H.st),
-                       "red list");
-        if (L.nint > L.nred)
-            check_cuda(cudaMemcpyAsync(L.ilist + L.nred, s.black, sizeof(uint32_t) * (L.nint - L.nred),
-                                       cudaMemcpyDeviceToDevice, H.st),
-                       "black list");
+        lists.add(s.red, L.ilist, sizeof(uint32_t) * (size_t)L.nred);
+        lists.add(s.black, L.ilist + L.nred, sizeof(uint32_t) * (size_t)(L.nint - L.nred));
         int64_t ng1 = std::max<int64_t>(L.ng, 1);
         L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1, false, false);
         L.gxi = (double *)dalloc(H, sizeof(double) * 3 * ng1);
@@ -1450,6 +1491,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         t.blk_g = gblocks;
         gblocks += nblocks(L.ng, 128);
     }
+    lists.flush();
     LevelTab *tab_d = (LevelTab *)dalloc(H, sizeof(LevelTab) * keep, true);
     check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(LevelTab) * keep, cudaMemcpyHostToDevice, H.st), "tab");
     if (gblocks > 0) {
@@ -1555,6 +1597,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         int *hov = (int *)(hc + 2 * keep);
         check_cuda(cudaMemcpyAsync(hov, ovf, sizeof(int) * 2 * keep, cudaMemcpyDeviceToHost, H.st), "overflow");
         check_cuda(cudaStreamSynchronize(H.st), "set-up sync 3");
+        Copier ell(H);
         for (int l = 0; l < keep; ++l) {
             Level &L = H.L[l];
             L.nclamp = hc[2 * l];
@@ -1569,16 +1612,13 @@ void setup_hierarchy(Handle &H, const double *phi0) {
                 const int slots = std::min(kExtCap, ((std::max(L.ell_max, 1) + 7) / 8) * 8);
                 uint32_t *eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * slots * nb1);
                 double *ew = (double *)dalloc(H, sizeof(double) * slots * nb1);
-                check_cuda(cudaMemcpyAsync(eg, L.eg, sizeof(uint32_t) * (size_t)L.ell_max * nb1,
-                                           cudaMemcpyDeviceToDevice, H.st),
-                           "ELL copy");
-                check_cuda(cudaMemcpyAsync(ew, L.ew, sizeof(double) * (size_t)L.ell_max * nb1,
-                                           cudaMemcpyDeviceToDevice, H.st),
-                           "ELL copy");
+                ell.add(L.eg, eg, sizeof(uint32_t) * (size_t)L.ell_max * nb1);
+                ell.add(L.ew, ew, sizeof(double) * (size_t)L.ell_max * nb1);
                 L.eg = eg;
                 L.ew = ew;
             }
         }
+        ell.flush();
     }
     // GS-LEX: interior nodes grouped by hyperplane on every level (one sync)
     if (H.o.ordering == BCMG_ORDER_LEX) {
@@ -1645,4 +1685,25 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     }
 }
 
+}  // namespace bcmg
+
+namespace bcmg {
+namespace {
+std::mutex g_lu_attr_mu;
+std::set<int> g_lu_attr_devs;
+
+void lu_attributes_once() {
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_lu_attr_mu);
+    if (g_lu_attr_devs.count(dev)) return;
+    check_cuda(cudaFuncSetAttribute(k_lu_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(double) * (kLuSmall * kLuSmall + kLuSmall))),
+               "LU shared memory");
+    check_cuda(cudaFuncSetAttribute(k_lu_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(double) * (kLuSmall * kLuSmall + (2 + kLuColsPerBlock) * kLuSmall))),
+               "LU inverse shared memory");
+    g_lu_attr_devs.insert(dev);
+}
+}  // namespace
 }  // namespace bcmg

@@ -226,3 +226,50 @@ def test_batch_shape_rejects_bad_values(bcmg):
             B.debug_batch_shape(*bad)
         assert e.value.code == B.EINVAL
     B.debug_batch_shape(0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_degenerate_hierarchies(bcmg, prec):
+    # one level only (odd N: the finest level is the coarsest, solved
+    # directly), two levels, a zero problem (r0 = 0: done before any cycle)
+    # and an ordinary star in one batch; every result as alone
+    B = bcmg
+    p = B.PREC_FP64 if prec == "fp64" else B.PREC_MIXED
+    probs = [(2, 15, W.phi_disk(15)), (2, 30, W.phi_disk(30)), (2, 64, W.phi_star(64, 0.12, 5, 0.4)),
+             (2, 48, W.phi_disk(48))]
+
+    def build(i, d, N, phi):
+        if i == 3:  # zero data
+            s = B.Solver(d, N, torch.from_numpy(phi).cuda(), None, precision=p)
+            s.set_boundary_values(torch.zeros(s.ghost_count(), dtype=torch.float64, device="cuda"))
+            return s, torch.zeros((N + 1) ** d, dtype=torch.float64, device="cuda")
+        return _make(B, d, N, phi, p)
+
+    alone = []
+    for i, (d, N, phi) in enumerate(probs):
+        s, u = build(i, d, N, phi)
+        c, rel, st = B.solve_batch([s], [u], 1e-10, 60)
+        torch.cuda.synchronize()
+        alone.append((c[0], rel[0], st[0], u.cpu().numpy(), s.levels))
+        s.close()
+    assert alone[0][4] == 1 and alone[1][4] == 2
+    assert alone[3][0] == 0 and alone[3][2] == B.OK
+    pairs = [build(i, d, N, phi) for i, (d, N, phi) in enumerate(probs)]
+    cyc, rel, st = B.solve_batch([s for s, _ in pairs], [u for _, u in pairs], 1e-10, 60)
+    torch.cuda.synchronize()
+    for i, (s, u) in enumerate(pairs):
+        c0, r0, s0, u0, _ = alone[i]
+        assert st[i] == s0
+        assert abs(cyc[i] - c0) <= (1 if prec == "fp64" else 3)
+        got = u.cpu().numpy()
+        scale = max(np.abs(u0).max(), 1e-300)
+        assert np.abs(got - u0).max() <= 1e-9 * scale, i
+        s.close()
+    # no cycle allowed: every non-trivial solve ends unconverged, the zero
+    # problem converged, in the batch as alone
+    pairs = [build(i, d, N, phi) for i, (d, N, phi) in enumerate(probs)]
+    cyc, rel, st = B.solve_batch([s for s, _ in pairs], [u for _, u in pairs], 1e-10, 0)
+    assert cyc == [0, 0, 0, 0]
+    assert st == [B.ENOCONV, B.ENOCONV, B.ENOCONV, B.OK]
+    for s, _ in pairs:
+        s.close()
