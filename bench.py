@@ -635,6 +635,8 @@ def run_stars_batched(args):
         ms = e0.elapsed_time(e1)
         launches = bcmg.kernel_launches() - launches0
         clk = clocks.stop()
+        tuned_shape = bcmg.batch_last_shape()  # the autotuner's choice for this batch
+        timed_split = dict(split)  # the timed steps' creation / solve split
         # one more step, untimed, keeping every 16th solution for the error
         # against the FP64 single solves below
         sample = list(range(0, len(data), 16))
@@ -674,9 +676,10 @@ def run_stars_batched(args):
                        "error_sample": "every 16th star that converges (%d of %d), interior and ghost nodes"
                                        % (len(errs), len(data)),
                        "step": "threaded create x256 + one gathered g(Q) + one bcmg_solve_batch + destroy",
-                       "create_ms_per_step": split["create"] * 1e3 / steps,
-                       "solve_batch_ms_per_step": split["solve"] * 1e3 / steps,
-                       "batched_solves_per_s": len(data) * steps / split["solve"],
+                       "create_ms_per_step": timed_split["create"] * 1e3 / steps,
+                       "solve_batch_ms_per_step": timed_split["solve"] * 1e3 / steps,
+                       "batched_solves_per_s": len(data) * steps / timed_split["solve"],
+                       "launch_shape": dict(zip(("block", "items_per_thread", "tail_rows"), tuned_shape)),
                        "parallelism": "single"},
             "clocks": clk, "gpu_launches": launches}
 

@@ -194,6 +194,12 @@ int bcmg_workspace_size(bcmg_handle h, int64_t *bytes);
  * same order).  Process-wide.  EINVAL for other values. */
 int bcmg_debug_batch_shape(int block, int items, int64_t tail_rows);
 
+/* The launch shape (block size, items per thread, tail rows; see
+ * bcmg_debug_batch_shape) the process's last batched solve used: the
+ * autotuner's choice for that batch's shape, or the fixed one.  block = 0
+ * when no batched solve has run.  (No counterpart in the paper.) */
+int bcmg_batch_last_shape(int *block, int *items, int64_t *tail_rows);
+
 /* Failure injection for tests of the callers' recovery paths (no
  * counterpart in the paper): after this call, the k-th device allocation the
  * library makes (counted over all handles and threads) fails as if the device

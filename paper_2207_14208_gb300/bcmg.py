@@ -68,6 +68,7 @@ def load():
             "bcmg_workspace_size": (i32, [vp, vp]),
             "bcmg_debug_fail_allocation": (i32, [i64]),
             "bcmg_debug_batch_shape": (i32, [i32, i32, i64]),
+            "bcmg_batch_last_shape": (i32, [vp, vp, vp]),
             "bcmg_debug_live_blocks": (i32, [vp, vp]),
             "bcmg_destroy": (i32, [vp]),
             "bcmg_ghost_count": (i32, [vp, vp]),
@@ -118,6 +119,13 @@ def debug_batch_shape(block: int = 0, items: int = 1, tail_rows: int = 0) -> Non
     """Launch shape of the batched kernels for the following batched solves
     (block 0: the autotuner's choice again)."""
     _check(load().bcmg_debug_batch_shape(int(block), int(items), int(tail_rows)))
+
+
+def batch_last_shape():
+    """(block, items per thread, tail rows) the last batched solve used."""
+    b, i, t = C.c_int(), C.c_int(), C.c_int64()
+    _check(load().bcmg_batch_last_shape(C.byref(b), C.byref(i), C.byref(t)))
+    return b.value, i.value, t.value
 
 
 def debug_fail_allocation(k: int) -> None:

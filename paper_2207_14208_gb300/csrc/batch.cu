@@ -1207,6 +1207,7 @@ cudaGraphExec_t build_cycle_graph(const Batch &B, const Plan &P, const DevPlan &
 
 std::mutex g_tune_mu;
 std::tuple<int, int, int64_t> g_shape_override{0, 1, 0};  // block 0: none (guarded by g_tune_mu)
+std::tuple<int, int, int64_t> g_last_shape{0, 1, 0};      // of the last batched solve (g_tune_mu)
 // (dev, d, mixed, nh, nodes) -> (block size, items per thread, tail rows)
 std::map<std::tuple<int, int, int, int64_t, int64_t>, std::tuple<int, int, int64_t>> g_tuned;
 
@@ -1226,6 +1227,9 @@ Batch make_batch(const std::vector<Handle *> &hs) {
     return B;
 }
 
+constexpr int kTuneReplays = 3;       // timed replays per candidate (the fastest counts)
+constexpr float kTailSlack = 1.03f;   // the block tail is kept within 3 % of the fastest stage-only shape
+
 // A batch's launch shape: block size and items per thread of the stages,
 // and the largest list of a level that runs in the block tail (0: no tail)
 struct Shape {
@@ -1237,7 +1241,8 @@ struct Shape {
 // warm replay, on the working copies (saved before and restored after).
 // First block size 64, 128 or 256 threads, each with one or four items per
 // thread in the node-parallel stages; then, with the fastest of those, the
-// block tail for levels of at most 512 or 2048 list entries, kept if faster.
+// block tail for levels of at most 512 or 2048 list entries (the faster of
+// the two), kept unless slower than kTailSlack times the stage-only shape.
 Shape tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cycles, int64_t *launched) {
     const int nu1 = B.hs[0]->o.nu1, nu2 = B.hs[0]->o.nu2;
     std::vector<double *> saved;
@@ -1261,17 +1266,21 @@ Shape tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cy
         check_cuda(cudaEventCreate(&e0), "event");
         check_cuda(cudaEventCreate(&e1), "event");
         check_cuda(cudaGraphLaunch(ex, st), "tune warm");
-        check_cuda(cudaEventRecord(e0, st), "event");
-        check_cuda(cudaGraphLaunch(ex, st), "tune timed");
-        check_cuda(cudaEventRecord(e1, st), "event");
-        check_cuda(cudaEventSynchronize(e1), "tune sync");
         float ms = 0.0f;
-        check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+        for (int rep = 0; rep < kTuneReplays; ++rep) {
+            check_cuda(cudaEventRecord(e0, st), "event");
+            check_cuda(cudaGraphLaunch(ex, st), "tune timed");
+            check_cuda(cudaEventRecord(e1, st), "event");
+            check_cuda(cudaEventSynchronize(e1), "tune sync");
+            float t = 0.0f;
+            check_cuda(cudaEventElapsedTime(&t, e0, e1), "event time");
+            ms = rep == 0 ? t : std::min(ms, t);
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         cudaGraphExecDestroy(ex);
         free_plan(Dv, st);
-        *launched += 2 * (int64_t)(P.cycle.size() + (B.mixed ? 2 : 0));
+        *launched += (1 + kTuneReplays) * (int64_t)(P.cycle.size() + (B.mixed ? 2 : 0));
         return ms;
     };
     Shape best;
@@ -1285,12 +1294,17 @@ Shape tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cy
             best = c;
         }
     }
+    // the replay runs every hierarchy; later rounds run few, where a cycle is
+    // bound by its launches, which the tail removes: the tail is kept unless
+    // it is measurably slower on the full batch
     const Shape base = best;
+    const float base_ms = best_ms;
+    float tail_ms = 0.0f;
     for (const int64_t tail : {(int64_t)512, (int64_t)2048}) {
         const Shape c{base.bs, base.npt, tail};
         const float ms = time_shape(c);
-        if (ms >= 0.0f && ms < best_ms) {
-            best_ms = ms;
+        if (ms >= 0.0f && ms <= base_ms * kTailSlack && (best.tail == 0 || ms < tail_ms)) {
+            tail_ms = ms;
             best = c;
         }
     }
@@ -1304,6 +1318,13 @@ Shape tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cy
 }
 
 }  // namespace
+
+void batch_last_shape(int *block, int *items, int64_t *tail_rows) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *block = std::get<0>(g_last_shape);
+    *items = std::get<1>(g_last_shape);
+    *tail_rows = std::get<2>(g_last_shape);
+}
 
 void batch_shape_override(int block, int items, int64_t tail_rows) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1354,6 +1375,10 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
         shape = tune_launch_shape(make_batch(hs), st, rtol, max_cycles, &launched);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = std::make_tuple(shape.bs, shape.npt, shape.tail);
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_last_shape = std::make_tuple(shape.bs, shape.npt, shape.tail);
     }
     std::vector<BCtl> state(n, BCtl{rtol, max_cycles, 0, 0.0, 0.0, 0, 0});
     std::vector<int> active(n);

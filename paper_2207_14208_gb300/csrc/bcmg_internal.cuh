@@ -256,6 +256,8 @@ bool batch_eligible(const std::vector<Handle *> &hs);
 // launch shape of the batched kernels for the following batched solves
 // instead of the autotuner's (block <= 0: back to the autotuner)
 void batch_shape_override(int block, int items, int64_t tail_rows);
+// the launch shape the last batched solve of the process used (block 0: none yet)
+void batch_last_shape(int *block, int *items, int64_t *tail_rows);
 int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rtol, int max_cycles, int *cycles,
                     double *rels, int *statuses);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,

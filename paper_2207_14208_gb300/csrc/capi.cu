@@ -1,5 +1,6 @@
 // C ABI of the GB300 BCMG library: handle life cycle, argument checks,
 // stream ordering, CUDA-graph replay of the V-cycle, and error reporting.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -219,13 +220,19 @@ void free_temps(Handle &H) {
     H.arena_temp = Arena{};
 }
 
+// once per device (an attribute of the device's default pool)
+std::mutex g_pool_mu;
+std::vector<int> g_pool_devs;
+
 void keep_pool_memory() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (std::find(g_pool_devs.begin(), g_pool_devs.end(), dev) != g_pool_devs.end()) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
     uint64_t thr = UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) == cudaSuccess) g_pool_devs.push_back(dev);
 }
 
 // Small pinned host blocks (norms, solve state) come from a process-wide
@@ -925,6 +932,13 @@ int bcmg_debug_live_blocks(int64_t *blocks, int64_t *bytes) {
     if (!blocks || !bytes) return fail(BCMG_EINVAL, "null pointer");
     *blocks = g_live_blocks.load();
     *bytes = g_live_bytes.load();
+    g_last_error.clear();
+    return BCMG_OK;
+}
+
+int bcmg_batch_last_shape(int *block, int *items, int64_t *tail_rows) {
+    if (!block || !items || !tail_rows) return fail(BCMG_EINVAL, "null pointer");
+    bcmg::batch_last_shape(block, items, tail_rows);
     g_last_error.clear();
     return BCMG_OK;
 }

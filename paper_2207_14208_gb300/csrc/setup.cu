@@ -1460,6 +1460,10 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     std::vector<LevelTab> tab(keep);
     int64_t gblocks = 0;
     Copier lists(H);
+    // the ghost counters of every level (two each) and the extension's
+    // overflow flags and longest rows (two ints per level), contiguous, so
+    // that round 3 reads them back with one copy
+    char *ctr = (char *)dalloc(H, (sizeof(unsigned long long) * 2 + sizeof(int) * 2) * (size_t)keep, true);
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
         LevelScratch &s = S[l];
@@ -1477,7 +1481,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         L.geta = (double *)dalloc(H, sizeof(double) * ng1, false, false);
         L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
         L.gtmp = (double *)dalloc(H, sizeof(double) * ng1, false, false);
-        s.cnt = (unsigned long long *)dalloc(H, 2 * sizeof(unsigned long long), true);
+        s.cnt = (unsigned long long *)ctr + 2 * l;
         s.fband = (uint8_t *)dalloc(H, (size_t)L.nn, true);  // zero-filled
         LevelTab &t = tab[l];
         t = LevelTab{};
@@ -1542,7 +1546,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     // level in one launch each
     const bool ell = ext_ell_ok(H.d, H.o.ext_sweeps);
     int64_t bblocks = 0;
-    int *ovf = (int *)dalloc(H, sizeof(int) * 2 * keep, true);  // overflow flags, longest rows
+    int *ovf = (int *)(ctr + sizeof(unsigned long long) * 2 * keep);  // overflow flags, longest rows
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
         int64_t nb1 = std::max<int64_t>(L.nb, 1);
@@ -1591,11 +1595,10 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     // round 3: clamp / fall-back counters and ELL overflows (one sync)
     {
         int64_t *hc = pinned_scratch(H, 3 * (size_t)keep + 2);
-        for (int l = 0; l < keep; ++l)
-            check_cuda(cudaMemcpyAsync(hc + 2 * l, S[l].cnt, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, H.st),
-                       "ghost counters");
+        check_cuda(cudaMemcpyAsync(hc, ctr, (sizeof(int64_t) * 2 + sizeof(int) * 2) * (size_t)keep,
+                                   cudaMemcpyDeviceToHost, H.st),
+                   "ghost counters, overflow");
         int *hov = (int *)(hc + 2 * keep);
-        check_cuda(cudaMemcpyAsync(hov, ovf, sizeof(int) * 2 * keep, cudaMemcpyDeviceToHost, H.st), "overflow");
         check_cuda(cudaStreamSynchronize(H.st), "set-up sync 3");
         Copier ell(H);
         for (int l = 0; l < keep; ++l) {

@@ -219,6 +219,20 @@ def test_block_tail_is_shape_independent(bcmg, prec):
     assert res[(128, 4, 2048)][0] < res[(128, 4, 0)][0]
 
 
+def test_last_shape_reports_the_fixed_shape(bcmg):
+    B = bcmg
+    probs = _star_set(3, 200)
+    try:
+        B.debug_batch_shape(64, 4, 512)
+        pairs = [_make(B, d, N, phi, B.PREC_FP64) for d, N, phi in probs]
+        B.solve_batch([s for s, _ in pairs], [u for _, u in pairs], 1e-10, 5)
+        assert B.batch_last_shape() == (64, 4, 512)
+        for s, _ in pairs:
+            s.close()
+    finally:
+        B.debug_batch_shape(0)
+
+
 def test_batch_shape_rejects_bad_values(bcmg):
     B = bcmg
     for bad in ((100, 1, 0), (128, 3, 0), (128, 1, -1)):
