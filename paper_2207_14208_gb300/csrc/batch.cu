@@ -1319,6 +1319,73 @@ Shape tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cy
 
 }  // namespace
 
+namespace {
+// a handle's part of a batched copy of the caller's u in or out
+struct BCopy {
+    const uint32_t *ilist, *gidx, *box;
+    int64_t nint, ng, nbox;
+    const double *src;
+    double *dst;
+    Lay lay;
+    uint32_t blk0;  // first block of this handle
+};
+
+// in (to_split): the caller's dense u of interior, ghost and eliminated box
+// nodes into the working copy; out: interior and ghost nodes back (the
+// per-handle copy_active, for every handle of the batch in one launch)
+__global__ void __launch_bounds__(256) kb_copy_active(const BCopy *__restrict__ tab, int n, int to_split) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].blk0 <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const BCopy &c = tab[lo];
+    const int64_t i = (int64_t)(blockIdx.x - c.blk0) * blockDim.x + threadIdx.x;
+    const int64_t nbox = to_split ? c.nbox : 0;
+    if (i >= c.nint + c.ng + nbox) return;
+    int64_t X;
+    if (i < c.nint) X = c.ilist[i];
+    else if (i < c.nint + c.ng) X = c.gidx[i - c.nint];
+    else X = c.box[i - c.nint - c.ng];
+    if (to_split) c.dst[pos(X, c.lay)] = c.src[X];
+    else c.dst[X] = c.src[pos(X, c.lay)];
+}
+}  // namespace
+
+// every handle's u between the caller's arrays and the working copies, one
+// launch on st (the table goes up with one copy)
+void batch_copy_active(const std::vector<Handle *> &hs, double *const *u_devs, cudaStream_t st, bool in) {
+    std::vector<BCopy> tab;
+    uint32_t blocks = 0;
+    for (size_t i = 0; i < hs.size(); ++i) {
+        Handle &H = *hs[i];
+        const Level &L = H.L[0];
+        BCopy c;
+        c.ilist = L.ilist;
+        c.gidx = L.gidx;
+        c.box = L.boxidx;
+        c.nint = L.nint;
+        c.ng = L.ng;
+        c.nbox = L.nbox;
+        c.src = in ? u_devs[i] : H.u0;
+        c.dst = in ? H.u0 : u_devs[i];
+        c.lay = L.lay;
+        c.blk0 = blocks;
+        tab.push_back(c);
+        blocks += (uint32_t)((L.nint + L.ng + (in ? L.nbox : 0) + 255) / 256);
+    }
+    if (blocks == 0) return;
+    BCopy *tab_d = nullptr;
+    check_cuda(cudaMallocAsync(&tab_d, sizeof(BCopy) * tab.size(), st), "batch copy table");
+    check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(BCopy) * tab.size(), cudaMemcpyHostToDevice, st),
+               "batch copy table");
+    kb_copy_active<<<blocks, 256, 0, st>>>(tab_d, (int)tab.size(), in ? 1 : 0);
+    check_cuda(cudaGetLastError(), "batch copy");
+    add_launches(1);
+    cudaFreeAsync(tab_d, st);
+}
+
 void batch_last_shape(int *block, int *items, int64_t *tail_rows) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     *block = std::get<0>(g_last_shape);

@@ -258,6 +258,10 @@ bool batch_eligible(const std::vector<Handle *> &hs);
 void batch_shape_override(int block, int items, int64_t tail_rows);
 // the launch shape the last batched solve of the process used (block 0: none yet)
 void batch_last_shape(int *block, int *items, int64_t *tail_rows);
+// every handle's u between the caller's arrays and the working copies (in:
+// interior, ghost and eliminated box nodes; out: interior and ghost nodes),
+// one launch on st
+void batch_copy_active(const std::vector<Handle *> &hs, double *const *u_devs, cudaStream_t st, bool in);
 int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rtol, int max_cycles, int *cycles,
                     double *rels, int *statuses);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,

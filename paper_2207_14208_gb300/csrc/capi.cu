@@ -858,27 +858,28 @@ int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, 
                 if (hs[j] == hs[i]) throw Error{BCMG_EINVAL, "a handle appears twice in the batch"};
         }
         if (batch_eligible(hs)) {
-            // one launch per stage for the whole batch (batch.cu), on the
-            // first handle's stream after every handle's copy-in
+            // one launch per stage for the whole batch (batch.cu) on the first
+            // handle's stream.  It waits once for every distinct caller stream
+            // (each handle's earlier work is ordered before its caller's
+            // stream), copies every u in with one launch and out with one,
+            // and is synchronised before the return, so each caller stream
+            // finds its u written and each handle's stream its arrays idle.
             cudaStream_t bst = hs[0]->st;
+            std::vector<cudaStream_t> users;
             for (int i = 0; i < n; ++i) {
                 Handle &H = *hs[i];
-                enter(H);
-                copy_active(H, u_devs[i], H.u0, true);
-                if (i > 0) {
-                    check_cuda(cudaEventRecord(H.ev_out, H.st), "batch fork");
-                    check_cuda(cudaStreamWaitEvent(bst, H.ev_out, 0), "batch fork wait");
-                }
+                if (std::find(users.begin(), users.end(), H.user) != users.end()) continue;
+                users.push_back(H.user);
+                check_cuda(cudaEventRecord(H.ev_in, H.user), "batch fork");
+                check_cuda(cudaStreamWaitEvent(bst, H.ev_in, 0), "batch fork wait");
             }
+            batch_copy_active(hs, u_devs, bst, true);
             std::vector<int> cyc(n), st(n);
             std::vector<double> rel(n);
             add_launches(batch_solve(hs, bst, rtol, max_cycles, cyc.data(), rel.data(), st.data()));
-            check_cuda(cudaEventRecord(hs[0]->ev_in, bst), "batch join");
+            batch_copy_active(hs, u_devs, bst, false);
+            check_cuda(cudaStreamSynchronize(bst), "batch sync");
             for (int i = 0; i < n; ++i) {
-                Handle &H = *hs[i];
-                if (i > 0) check_cuda(cudaStreamWaitEvent(H.st, hs[0]->ev_in, 0), "batch join wait");
-                copy_active(H, H.u0, u_devs[i], false);
-                leave(H);
                 if (cycles_done) cycles_done[i] = cyc[i];
                 if (final_rel_res) final_rel_res[i] = rel[i];
                 if (statuses) statuses[i] = st[i];
