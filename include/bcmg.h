@@ -264,7 +264,8 @@ int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *c
  * of bcmg_solve; the coarse levels and the norm reduction sum in another
  * order, so results agree with bcmg_solve alone to rounding (and a cycle
  * count within a few cycles of it), not bit for bit.  The work is ordered
- * after every handle's stream and every handle's stream after it.
+ * after each handle's stream (the stream given at its creation) and is
+ * complete when the call returns.
  * Otherwise (mixed batches) every handle's solve is enqueued on its own
  * stream before any is waited for, so the GPU runs them concurrently, and
  * results are identical to bcmg_solve on each handle alone; a handle created
