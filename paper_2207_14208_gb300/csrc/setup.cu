@@ -1665,23 +1665,43 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         // the pageable cursor copy must be done before the vector goes
         check_cuda(cudaStreamSynchronize(H.st), "hp sync 2");
     }
-    // level arrays
+    // level arrays: value arrays in the parity-split layout (split_len
+    // entries).  Those that must start at zero -- u of the coarse levels, F
+    // of the finest (it keeps zeros until the caller sets its data; coarse
+    // levels get every row they read from the restriction), r, and their
+    // FP32 copies -- are slices of one zero-filled block (one allocation and
+    // one fill for the whole hierarchy); the others are written before they
+    // are read.
+    const bool mixed = H.o.precision == BCMG_PREC_MIXED;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t zbytes = 0;
+    for (int l = 0; l < keep; ++l) {
+        const size_t sl = (size_t)split_len(H.L[l].nn);
+        zbytes += 2 * al(sizeof(double) * sl);                  // u (coarse) or F (finest), and r
+        if (mixed) zbytes += 2 * al(sizeof(float) * sl);        // u32, r32
+    }
+    char *z = (char *)dalloc(H, zbytes);
+    auto take = [&](size_t b) {
+        char *p = z;
+        z += al(b);
+        return p;
+    };
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
-        // value arrays in the parity-split layout (split_len entries)
         const int64_t sl = split_len(L.nn);
-        if (l > 0) L.u = (double *)dalloc(H, sizeof(double) * sl);
-        // F is read on interior and ghost rows only; coarse levels get every
-        // such row from the restriction, the finest keeps zeros until the
-        // caller sets its data
-        L.F = (double *)dalloc(H, sizeof(double) * sl, false, l == 0);
-        L.Fs = (double *)dalloc(H, sizeof(double) * sl, false, false);  // written before it is read
-        L.r = (double *)dalloc(H, sizeof(double) * sl);
-        if (H.o.precision == BCMG_PREC_MIXED) {
-            L.u32 = (float *)dalloc(H, sizeof(float) * sl);
+        if (l > 0) {
+            L.u = (double *)take(sizeof(double) * sl);
+            L.F = (double *)dalloc(H, sizeof(double) * sl, false, false);
+        } else {
+            L.F = (double *)take(sizeof(double) * sl);
+        }
+        L.Fs = (double *)dalloc(H, sizeof(double) * sl, false, false);
+        L.r = (double *)take(sizeof(double) * sl);
+        if (mixed) {
+            L.u32 = (float *)take(sizeof(float) * sl);
             L.F32 = (float *)dalloc(H, sizeof(float) * sl, false, false);
             L.Fs32 = (float *)dalloc(H, sizeof(float) * sl, false, false);
-            L.r32 = (float *)dalloc(H, sizeof(float) * sl);
+            L.r32 = (float *)take(sizeof(float) * sl);
             L.gtmp32 = (float *)dalloc(H, sizeof(float) * std::max<int64_t>(L.ng, 1));
             L.bbuf32 = (float *)dalloc(H, sizeof(float) * 2 * std::max<int64_t>(L.nb, 1));
         }
