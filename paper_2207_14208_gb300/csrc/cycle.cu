@@ -1459,11 +1459,24 @@ void setup_cycle(Handle &H) {
     const int nterm = H.d == 3 ? 27 : 9;
     std::vector<GwTab> gt(L);
     int64_t blocks = 0;
+    // the weight tables of every level (zero outside each ghost's stencil
+    // degrees): slices of one zero-filled block
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t wbytes = 0;
+    for (int l = 0; l < L; ++l) {
+        const size_t n1 = (size_t)std::max<int64_t>(H.L[l].ng, 1) * nterm;
+        wbytes += al(sizeof(double) * n1) + (mixed ? al(sizeof(float) * n1) : 0);
+    }
+    char *wnext = (char *)dalloc(H, wbytes);
     for (int l = 0; l < L; ++l) {
         Level &A = H.L[l];
         const size_t n1 = (size_t)std::max<int64_t>(A.ng, 1) * nterm;
-        A.gw = (double *)dalloc(H, sizeof(double) * n1);
-        if (mixed) A.gw32 = (float *)dalloc(H, sizeof(float) * n1);
+        A.gw = (double *)wnext;
+        wnext += al(sizeof(double) * n1);
+        if (mixed) {
+            A.gw32 = (float *)wnext;
+            wnext += al(sizeof(float) * n1);
+        }
         gt[l] = GwTab{A.gcode, A.gxi, A.gn, A.ng, A.h, A.gw, A.gw32, blocks};
         blocks += nblk(A.ng, kT);
     }

@@ -1460,6 +1460,10 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     std::vector<LevelTab> tab(keep);
     int64_t gblocks = 0;
     Copier lists(H);
+    // the band marks of every level: slices of one zero-filled block
+    size_t fb_bytes = 0;
+    for (int l = 0; l < keep; ++l) fb_bytes += ((size_t)H.L[l].nn + 255) & ~(size_t)255;
+    uint8_t *fb_next = (uint8_t *)dalloc(H, fb_bytes, true);
     // the ghost counters of every level (two each) and the extension's
     // overflow flags and longest rows (two ints per level), contiguous, so
     // that round 3 reads them back with one copy
@@ -1482,7 +1486,8 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         L.gQ = (double *)dalloc(H, sizeof(double) * 3 * ng1);
         L.gtmp = (double *)dalloc(H, sizeof(double) * ng1, false, false);
         s.cnt = (unsigned long long *)ctr + 2 * l;
-        s.fband = (uint8_t *)dalloc(H, (size_t)L.nn, true);  // zero-filled
+        s.fband = fb_next;  // zero-filled
+        fb_next += ((size_t)L.nn + 255) & ~(size_t)255;
         LevelTab &t = tab[l];
         t = LevelTab{};
         t.G = G;
@@ -1601,6 +1606,13 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         int *hov = (int *)(hc + 2 * keep);
         check_cuda(cudaStreamSynchronize(H.st), "set-up sync 3");
         Copier ell(H);
+        // term-major ELL: the first ell_max slabs are the whole map; keep a
+        // multiple of 8 slots (the tail reads 8-term rounds), the extra slots
+        // zero -- the kept maps of every level are slices of one zero-filled
+        // block
+        auto slots_of = [&](const Level &L) { return std::min(kExtCap, ((std::max(L.ell_max, 1) + 7) / 8) * 8); };
+        auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        size_t ebytes = 0;
         for (int l = 0; l < keep; ++l) {
             Level &L = H.L[l];
             L.nclamp = hc[2 * l];
@@ -1608,13 +1620,20 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             if (hov[l]) L.ecnt = nullptr;  // a row longer than kExtCap: sweep by sweep
             L.ell_max = hov[keep + l];
             if (L.ecnt) {
-                // term-major ELL: the first ell_max slabs are the whole map;
-                // keep a multiple of 8 slots (the tail reads 8-term rounds),
-                // the extra slots zero
+                const size_t nb1 = (size_t)std::max<int64_t>(L.nb, 1);
+                ebytes += al(sizeof(uint32_t) * slots_of(L) * nb1) + al(sizeof(double) * slots_of(L) * nb1);
+            }
+        }
+        char *enext = ebytes > 0 ? (char *)dalloc(H, ebytes) : nullptr;
+        for (int l = 0; l < keep; ++l) {
+            Level &L = H.L[l];
+            if (L.ecnt) {
                 const int64_t nb1 = std::max<int64_t>(L.nb, 1);
-                const int slots = std::min(kExtCap, ((std::max(L.ell_max, 1) + 7) / 8) * 8);
-                uint32_t *eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * slots * nb1);
-                double *ew = (double *)dalloc(H, sizeof(double) * slots * nb1);
+                const int slots = slots_of(L);
+                uint32_t *eg = (uint32_t *)enext;
+                enext += al(sizeof(uint32_t) * slots * nb1);
+                double *ew = (double *)enext;
+                enext += al(sizeof(double) * slots * nb1);
                 ell.add(L.eg, eg, sizeof(uint32_t) * (size_t)L.ell_max * nb1);
                 ell.add(L.ew, ew, sizeof(double) * (size_t)L.ell_max * nb1);
                 L.eg = eg;
