@@ -220,9 +220,11 @@ int bcmg_destroy(bcmg_handle h);
 int bcmg_ghost_count(bcmg_handle h, int64_t *n);
 
 /* Projection points Q of the finest-level ghosts (Sec. 3.3), ghost-list order
- * (increasing node index), written as count x dim FP64 (x, y[, z]) to the
- * device buffer Q_dev.  The caller evaluates its boundary data there. */
-int bcmg_ghost_points(bcmg_handle h, double *Q_dev);
+ * (increasing node index), written as count x dim FP64 (x, y[, z]) to Q: a
+ * device buffer (stream-ordered) or host memory (pageable or page-locked;
+ * filled when the call returns, which then synchronises the handle's
+ * stream).  The caller evaluates its boundary data there. */
+int bcmg_ghost_points(bcmg_handle h, double *Q);
 
 /* Outward unit normals n (computed from phi at each ghost G, Sec. 3.3) of
  * the finest-level ghosts, ghost-list order, count x dim FP64 to the device
@@ -231,8 +233,9 @@ int bcmg_ghost_normals(bcmg_handle h, double *n_dev);
 
 /* Boundary data for the finest-level ghosts (eq. BCh right-hand side):
  * Dirichlet values g(Q), or Neumann values grad u(Q) . n with n from
- * bcmg_ghost_normals; count FP64 values in ghost-list order, device pointer. */
-int bcmg_set_boundary_values(bcmg_handle h, const double *g_dev);
+ * bcmg_ghost_normals; count FP64 values in ghost-list order, from device
+ * memory (stream-ordered) or host memory (read before the call returns). */
+int bcmg_set_boundary_values(bcmg_handle h, const double *g);
 
 /* Replace the interior right-hand side f (n^dim, device; NULL = 0). */
 int bcmg_set_rhs(bcmg_handle h, const double *f_dev);
@@ -275,6 +278,16 @@ int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *c
  * that appears twice. */
 int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, int max_cycles,
                      int *cycles_done, double *final_rel_res, int *statuses);
+
+/* ncycles V-cycles (as bcmg_vcycle) on each of n hierarchies at once:
+ * handles[n], u_devs[n] as for bcmg_solve_batch.  An eligible batch (see
+ * bcmg_solve_batch) runs through the batched kernels, exactly ncycles
+ * cycles per hierarchy whatever its residual, complete when the call
+ * returns; other batches enqueue each handle's cycles on its own stream
+ * before any is waited for (results identical to bcmg_vcycle on each
+ * handle).  EINVAL for null arrays, a handle that appears twice or
+ * ncycles < 0. */
+int bcmg_vcycle_batch(bcmg_handle *handles, double **u_devs, int n, int ncycles);
 
 /* Device memory (bytes) the handle holds: every level's arrays, lists and
  * tables (not the caller's phi, f or u). */

@@ -68,6 +68,7 @@ def load():
             "bcmg_workspace_size": (i32, [vp, vp]),
             "bcmg_debug_fail_allocation": (i32, [i64]),
             "bcmg_debug_batch_shape": (i32, [i32, i32, i64]),
+            "bcmg_vcycle_batch": (i32, [vp, vp, i32, i32]),
             "bcmg_batch_last_shape": (i32, [vp, vp, vp]),
             "bcmg_debug_live_blocks": (i32, [vp, vp]),
             "bcmg_destroy": (i32, [vp]),
@@ -207,6 +208,16 @@ def footprint_estimate(dim: int, N: int, **opts) -> int:
     return out.value
 
 
+def vcycle_batch(solvers, us, ncycles: int = 1) -> None:
+    """ncycles V-cycles on many hierarchies at once (bcmg_vcycle_batch)."""
+    n = len(solvers)
+    if len(us) != n:
+        raise ValueError("one u per solver")
+    hs = (C.c_void_p * n)(*[s.h.value for s in solvers])
+    ps = (C.c_void_p * n)(*[_dptr(u).value for u in us])
+    _check(load().bcmg_vcycle_batch(hs, ps, n, int(ncycles)))
+
+
 def solve_batch(solvers, us, rtol: float = 1e-10, max_cycles: int = 100):
     """Solve on many hierarchies at once (bcmg_solve_batch): the solves run
     concurrently on the device.  Returns (cycles, rel, statuses) lists; does
@@ -282,9 +293,16 @@ class Solver:
     def ghost_points(self, out=None):
         """Q of the finest-level ghosts (count x dim CUDA float64 tensor); with
         out (a contiguous tensor of that shape, e.g. a slice of one array that
-        gathers the ghosts of many hierarchies) written there."""
+        gathers the ghosts of many hierarchies, or a float64 numpy array of
+        that shape in host memory) written there."""
         import torch
         ng = self.ghost_count()
+        if isinstance(out, np.ndarray):
+            if out.shape != (ng, self.dim) or out.dtype != np.float64 or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous float64 array of shape (ghost_count, dim)")
+            if ng > 0:
+                _check(self.lib.bcmg_ghost_points(self.h, _hptr(out)))
+            return out
         if out is not None:
             if tuple(out.shape) != (ng, self.dim) or not out.is_contiguous() or out.dtype != torch.float64:
                 raise ValueError("out must be a contiguous float64 tensor of shape (ghost_count, dim)")
@@ -305,6 +323,13 @@ class Solver:
         return n[:ng]
 
     def set_boundary_values(self, g):
+        """g: ghost_count float64 values, a CUDA tensor or a numpy array."""
+        if isinstance(g, np.ndarray):
+            g = np.ascontiguousarray(g, dtype=np.float64)
+            if g.size != self.ghost_count():
+                raise ValueError("g must have ghost_count entries")
+            _check(self.lib.bcmg_set_boundary_values(self.h, _hptr(g)))
+            return
         _check(self.lib.bcmg_set_boundary_values(self.h, _dptr(g)))
 
     def set_rhs(self, f):

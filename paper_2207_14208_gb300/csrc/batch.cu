@@ -101,6 +101,7 @@ struct BCtl {
     double r0, rel;
     int status;
     int done;
+    int fixed;  // run exactly max_cycles (batched V-cycles), whatever the residual
 };
 
 struct BShared {  // batch-wide counters of the check kernel
@@ -724,14 +725,14 @@ __global__ void __launch_bounds__(256) kb_norm_check(BCtl *__restrict__ ctl, con
             c.cycles = 0;
             c.rel = rn > 0.0 ? 1.0 : 0.0;
             c.status = fin ? BCMG_OK : BCMG_ENONFINITE;
-            c.done = !(fin && rn > 0.0 && c.max_cycles > 0);
+            c.done = !(fin && (rn > 0.0 || c.fixed) && c.max_cycles > 0);
         } else if (!c.done) {
             const int cyc = c.cycles + 1;
             c.cycles = cyc;
-            const double rel = rn / c.r0;
+            const double rel = c.r0 > 0.0 ? rn / c.r0 : 0.0;
             c.rel = rel;
             if (!fin) c.status = BCMG_ENONFINITE;
-            c.done = !(fin && rel > c.rtol && cyc < c.max_cycles);
+            c.done = !(fin && (c.fixed || rel > c.rtol) && cyc < c.max_cycles);
         }
         if (!c.done) atomicAdd(&sh->active, 1u);
         __threadfence();
@@ -1259,7 +1260,7 @@ Shape tune_launch_shape(const Batch &B, cudaStream_t st, double rtol, int max_cy
         if (c.tail > 0 && P.tails.empty()) return -1.0f;
         DevPlan Dv = upload_plan(B, P, st);
         std::vector<BCtl> c0(B.hs.size());
-        for (auto &x : c0) x = BCtl{rtol, max_cycles, 0, 1.0, 1.0, 0, 0};
+        for (auto &x : c0) x = BCtl{rtol, max_cycles, 0, 1.0, 1.0, 0, 0, 0};
         upload(c0, Dv.ctl, st);
         cudaGraphExec_t ex = B.d == 3 ? build_cycle_graph<3>(B, P, Dv, st) : build_cycle_graph<2>(B, P, Dv, st);
         cudaEvent_t e0, e1;
@@ -1416,10 +1417,11 @@ bool batch_eligible(const std::vector<Handle *> &hs) {
 // arrays.  The solve runs in rounds: a round's loop stops once at most an
 // eighth of its hierarchies still run, and the next round is planned for
 // those only, so hierarchies that need many more cycles than the rest (or
-// never converge) do not keep every launch of the batch going.  Returns the
-// number of kernels launched.
+// never converge) do not keep every launch of the batch going.  With fixed,
+// every hierarchy runs exactly max_cycles cycles (batched V-cycles; only a
+// non-finite norm stops one early).  Returns the number of kernels launched.
 int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rtol, int max_cycles, int *cycles,
-                    double *rels, int *statuses) {
+                    double *rels, int *statuses, bool fixed) {
     const int n = (int)hs.size();
     int64_t nodes = 0;
     for (Handle *H : hs)
@@ -1447,7 +1449,7 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_last_shape = std::make_tuple(shape.bs, shape.npt, shape.tail);
     }
-    std::vector<BCtl> state(n, BCtl{rtol, max_cycles, 0, 0.0, 0.0, 0, 0});
+    std::vector<BCtl> state(n, BCtl{rtol, max_cycles, 0, 0.0, 0.0, 0, 0, fixed ? 1 : 0});
     std::vector<int> active(n);
     for (int i = 0; i < n; ++i) active[i] = i;
     bool start = true;
@@ -1489,7 +1491,7 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
         cycles[i] = c.cycles;
         rels[i] = c.rel;
         int status = c.status;
-        if (status == BCMG_OK && c.r0 > 0.0 && c.rel > rtol) status = BCMG_ENOCONV;
+        if (!fixed && status == BCMG_OK && c.r0 > 0.0 && c.rel > rtol) status = BCMG_ENOCONV;
         statuses[i] = status;
     }
     return launched;

@@ -263,7 +263,7 @@ void batch_last_shape(int *block, int *items, int64_t *tail_rows);
 // one launch on st
 void batch_copy_active(const std::vector<Handle *> &hs, double *const *u_devs, cudaStream_t st, bool in);
 int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rtol, int max_cycles, int *cycles,
-                    double *rels, int *statuses);
+                    double *rels, int *statuses, bool fixed = false);
 // one refinement step: F32 = r (finest), FP32 V-cycle on the correction,
 // u += correction; r must hold the FP64 residual of u
 void mixed_step_enqueue(Handle &H, double *u);

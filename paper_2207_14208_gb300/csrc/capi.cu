@@ -631,6 +631,50 @@ double *stage_buf(Handle &H, int k) {
     return H.stage[k];
 }
 
+// host memory (pageable or page-locked), as opposed to device or managed
+bool is_host_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered || a.type == cudaMemoryTypeHost;
+}
+
+// the handles of a batch call: live, distinct, each with its u
+std::vector<Handle *> batch_handles(bcmg_handle *handles, double **u_devs, int n) {
+    std::vector<Handle *> hs(n);
+    for (int i = 0; i < n; ++i) {
+        hs[i] = checked(handles[i]);
+        if (!u_devs[i]) throw Error{BCMG_EINVAL, "null u in batch"};
+        for (int j = 0; j < i; ++j)
+            if (hs[j] == hs[i]) throw Error{BCMG_EINVAL, "a handle appears twice in the batch"};
+    }
+    return hs;
+}
+
+// An eligible batch through the batched kernels (batch.cu), on the first
+// handle's stream.  It waits once for every distinct caller stream (each
+// handle's earlier work is ordered before its caller's stream), copies every
+// u in with one launch and out with one, and is synchronised before the
+// return, so each caller stream finds its u written and each handle's stream
+// its arrays idle.  fixed: exactly max_cycles cycles (batched V-cycles).
+void batched_run(const std::vector<Handle *> &hs, double **u_devs, double rtol, int max_cycles, bool fixed,
+                 int *cyc, double *rel, int *st) {
+    cudaStream_t bst = hs[0]->st;
+    std::vector<cudaStream_t> users;
+    for (Handle *H : hs) {
+        if (std::find(users.begin(), users.end(), H->user) != users.end()) continue;
+        users.push_back(H->user);
+        check_cuda(cudaEventRecord(H->ev_in, H->user), "batch fork");
+        check_cuda(cudaStreamWaitEvent(bst, H->ev_in, 0), "batch fork wait");
+    }
+    batch_copy_active(hs, u_devs, bst, true);
+    add_launches(batch_solve(hs, bst, rtol, max_cycles, cyc, rel, st, fixed));
+    batch_copy_active(hs, u_devs, bst, false);
+    check_cuda(cudaStreamSynchronize(bst), "batch sync");
+}
+
 }  // namespace
 }  // namespace bcmg
 
@@ -768,15 +812,18 @@ int bcmg_ghost_count(bcmg_handle h, int64_t *n) {
     });
 }
 
-int bcmg_ghost_points(bcmg_handle h, double *Q_dev) {
+int bcmg_ghost_points(bcmg_handle h, double *Q) {
     return guarded([&] {
         Handle &H = *checked(h);
-        if (!Q_dev) throw Error{BCMG_EINVAL, "Q is null"};
+        if (!Q) throw Error{BCMG_EINVAL, "Q is null"};
+        const bool host = is_host_ptr(Q);
         enter(H);
         Level &L = H.L[0];
         if (L.ng > 0)
-            check_cuda(cudaMemcpyAsync(Q_dev, L.gQ, sizeof(double) * L.ng * H.d, cudaMemcpyDeviceToDevice, H.st),
+            check_cuda(cudaMemcpyAsync(Q, L.gQ, sizeof(double) * L.ng * H.d,
+                                       host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, H.st),
                        "ghost points copy");
+        if (host) check_cuda(cudaStreamSynchronize(H.st), "ghost points sync");  // filled on return
         leave(H);
     });
 }
@@ -796,12 +843,22 @@ int bcmg_ghost_normals(bcmg_handle h, double *n_dev) {
     });
 }
 
-int bcmg_set_boundary_values(bcmg_handle h, const double *g_dev) {
+int bcmg_set_boundary_values(bcmg_handle h, const double *g) {
     return guarded([&] {
         Handle &H = *checked(h);
-        if (!g_dev) throw Error{BCMG_EINVAL, "g is null"};
+        if (!g) throw Error{BCMG_EINVAL, "g is null"};
         enter(H);
-        scatter_ghost_values(H, H.L[0], g_dev, H.L[0].F);
+        Level &L = H.L[0];
+        const double *src = g;
+        if (is_host_ptr(g) && L.ng > 0) {
+            // staged through the level's ghost buffer (idle between calls);
+            // the caller's array may be reused on return
+            check_cuda(cudaMemcpyAsync(L.gtmp, g, sizeof(double) * L.ng, cudaMemcpyHostToDevice, H.st),
+                       "boundary values copy");
+            check_cuda(cudaStreamSynchronize(H.st), "boundary values sync");
+            src = L.gtmp;
+        }
+        scatter_ghost_values(H, L, src, L.F);
         leave(H);
     });
 }
@@ -844,41 +901,41 @@ int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *c
     return solve_status(status);
 }
 
+int bcmg_vcycle_batch(bcmg_handle *handles, double **u_devs, int n, int ncycles) {
+    if (n < 0 || (n > 0 && (!handles || !u_devs))) return fail(BCMG_EINVAL, "bad batch arrays");
+    return guarded([&] {
+        if (ncycles < 0) throw Error{BCMG_EINVAL, "ncycles must be >= 0"};
+        std::vector<Handle *> hs = batch_handles(handles, u_devs, n);
+        if (batch_eligible(hs)) {
+            std::vector<int> cyc(n), st(n);
+            std::vector<double> rel(n);
+            batched_run(hs, u_devs, 0.0, ncycles, true, cyc.data(), rel.data(), st.data());
+            return;
+        }
+        // each handle's cycles on its own stream, all enqueued before any
+        // is waited for
+        for (int i = 0; i < n; ++i) {
+            Handle &H = *hs[i];
+            enter(H);
+            copy_active(H, u_devs[i], H.u0, true);
+            for (int c = 0; c < ncycles; ++c) run_vcycle(H);
+            copy_active(H, H.u0, u_devs[i], false);
+            leave(H);
+        }
+    });
+}
+
 int bcmg_solve_batch(bcmg_handle *handles, double **u_devs, int n, double rtol, int max_cycles,
                      int *cycles_done, double *final_rel_res, int *statuses) {
     if (n < 0 || (n > 0 && (!handles || !u_devs))) return fail(BCMG_EINVAL, "bad batch arrays");
     int first = BCMG_OK;
     int rc = guarded([&] {
         if (max_cycles < 0 || !(rtol >= 0.0)) throw Error{BCMG_EINVAL, "bad rtol or max_cycles"};
-        std::vector<Handle *> hs(n);
-        for (int i = 0; i < n; ++i) {
-            hs[i] = checked(handles[i]);
-            if (!u_devs[i]) throw Error{BCMG_EINVAL, "null u in batch"};
-            for (int j = 0; j < i; ++j)
-                if (hs[j] == hs[i]) throw Error{BCMG_EINVAL, "a handle appears twice in the batch"};
-        }
+        std::vector<Handle *> hs = batch_handles(handles, u_devs, n);
         if (batch_eligible(hs)) {
-            // one launch per stage for the whole batch (batch.cu) on the first
-            // handle's stream.  It waits once for every distinct caller stream
-            // (each handle's earlier work is ordered before its caller's
-            // stream), copies every u in with one launch and out with one,
-            // and is synchronised before the return, so each caller stream
-            // finds its u written and each handle's stream its arrays idle.
-            cudaStream_t bst = hs[0]->st;
-            std::vector<cudaStream_t> users;
-            for (int i = 0; i < n; ++i) {
-                Handle &H = *hs[i];
-                if (std::find(users.begin(), users.end(), H.user) != users.end()) continue;
-                users.push_back(H.user);
-                check_cuda(cudaEventRecord(H.ev_in, H.user), "batch fork");
-                check_cuda(cudaStreamWaitEvent(bst, H.ev_in, 0), "batch fork wait");
-            }
-            batch_copy_active(hs, u_devs, bst, true);
             std::vector<int> cyc(n), st(n);
             std::vector<double> rel(n);
-            add_launches(batch_solve(hs, bst, rtol, max_cycles, cyc.data(), rel.data(), st.data()));
-            batch_copy_active(hs, u_devs, bst, false);
-            check_cuda(cudaStreamSynchronize(bst), "batch sync");
+            batched_run(hs, u_devs, rtol, max_cycles, false, cyc.data(), rel.data(), st.data());
             for (int i = 0; i < n; ++i) {
                 if (cycles_done) cycles_done[i] = cyc[i];
                 if (final_rel_res) final_rel_res[i] = rel[i];

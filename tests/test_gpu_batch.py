@@ -287,3 +287,75 @@ def test_batched_degenerate_hierarchies(bcmg, prec):
     assert st == [B.ENOCONV, B.ENOCONV, B.ENOCONV, B.OK]
     for s, _ in pairs:
         s.close()
+
+
+def test_vcycle_batch_matches_oracle_and_alone(bcmg):
+    # batched V-cycles (bcmg_vcycle_batch): on an eligible batch exactly
+    # ncycles cycles per hierarchy, each within 1e-12 of the oracle's cycles
+    # (also a zero problem, whose cycles keep u at zero); on a mixed 2D / 3D
+    # batch identical to bcmg_vcycle on each handle
+    from oracle import oracle as O
+    O.build()
+    B = bcmg
+    probs = _star_set(5, 300)
+    pairs = [_make(B, d, N, phi, B.PREC_FP64) for d, N, phi in probs]
+    B.vcycle_batch([s for s, _ in pairs], [u for _, u in pairs], 2)
+    torch.cuda.synchronize()
+    for (d, N, phi), (s, u) in zip(probs, pairs):
+        o = O.Oracle(d, N, phi)
+        f, _ = W.manufactured(d, N)
+        o.set_rhs(f, W.g_at(d, o.ghosts(0)["Q"]))
+        uo = o.vcycle(np.zeros(o.nn(0)), 2)
+        act = np.isin(o.cls(0), [O.INTERIOR, O.GHOST])
+        assert np.abs(u.cpu().numpy()[act] - uo[act]).max() <= 1e-12 * np.abs(uo[act]).max(), N
+        s.close()
+    zs = B.Solver(2, 64, torch.from_numpy(W.phi_disk(64)).cuda(), None)
+    zs.set_boundary_values(torch.zeros(zs.ghost_count(), dtype=torch.float64, device="cuda"))
+    zu = torch.zeros(65 * 65, dtype=torch.float64, device="cuda")
+    s2, u2 = _make(B, 2, 96, W.phi_disk(96), B.PREC_FP64)
+    B.vcycle_batch([zs, s2], [zu, u2], 3)
+    assert float(zu.abs().max()) == 0.0 and float(u2.abs().max()) > 0.0
+    zs.close()
+    s2.close()
+    mixed = [(2, 64, W.phi_disk(64)), (3, 24, W.phi_ellipsoid(24)), (2, 80, W.phi_flower_paper(80))]
+    alone = []
+    for d, N, phi in mixed:
+        s, u = _make(B, d, N, phi, B.PREC_FP64)
+        s.vcycle(u, 2)
+        torch.cuda.synchronize()
+        alone.append(u.cpu().numpy())
+        s.close()
+    pairs = [_make(B, d, N, phi, B.PREC_FP64) for d, N, phi in mixed]
+    B.vcycle_batch([s for s, _ in pairs], [u for _, u in pairs], 2)
+    torch.cuda.synchronize()
+    with pytest.raises(B.BcmgError) as e:
+        B.vcycle_batch([pairs[0][0]], [pairs[0][1]], -1)
+    assert e.value.code == B.EINVAL
+    for a, (s, u) in zip(alone, pairs):
+        np.testing.assert_array_equal(u.cpu().numpy(), a)
+        s.close()
+
+
+def test_host_boundary_data_equals_device(bcmg):
+    # bcmg_ghost_points into host memory and bcmg_set_boundary_values from
+    # host memory give what the device buffers give
+    B = bcmg
+    d, N = 2, 96
+    phi = torch.from_numpy(W.phi_flower_paper(N)).cuda()
+    f = torch.from_numpy(W.manufactured(d, N)[0]).cuda()
+    out = []
+    for host in (False, True):
+        s = B.Solver(d, N, phi, f)
+        if host:
+            Q = s.ghost_points(out=np.empty((s.ghost_count(), d)))
+            s.set_boundary_values(W.g_at(d, Q))
+        else:
+            Q = s.ghost_points().cpu().numpy()
+            s.set_boundary_values(torch.from_numpy(W.g_at(d, Q)).cuda())
+        u = torch.zeros((N + 1) ** d, dtype=torch.float64, device="cuda")
+        c, rel = s.solve(u, 1e-10, 60)
+        out.append((Q.copy(), c, u.cpu().numpy()))
+        s.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    np.testing.assert_array_equal(out[0][2], out[1][2])
