@@ -689,9 +689,12 @@ def served_requests(rate, count, seed=2):
     (N log-uniform 64..2048), half 3D ellipsoids with random semi-axes
     (N log-uniform 64..256; stand-in for the sphere unions, whose coarse
     levels do not converge with the paper's re-discretised hierarchy), half
-    FP64 and half mixed precision."""
+    FP64 and half mixed precision.  The requests themselves come from
+    their own generator (PCG64 seed) and the arrival gaps from another
+    (PCG64 seed + 1000), so every rate serves the same requests."""
     from paper_2207_14208_gb300 import bcmg, serve
     rng = np.random.Generator(np.random.PCG64(seed))
+    arr = np.random.Generator(np.random.PCG64(seed + 1000))
     cands = sorted({m << k for m in range(8, 16) for k in range(0, 12)})
 
     def pick(lo, hi):
@@ -700,7 +703,7 @@ def served_requests(rate, count, seed=2):
 
     reqs, t = [], 0.0
     for i in range(count):
-        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        t += arr.exponential(1.0 / rate) if rate > 0 else 0.0
         prec = bcmg.PREC_FP64 if rng.uniform() < 0.5 else bcmg.PREC_MIXED
         if rng.uniform() < 0.5:
             N = pick(64, 2048)
