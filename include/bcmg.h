@@ -301,6 +301,11 @@ int bcmg_memory_footprint(bcmg_handle h, int64_t *bytes);
  * exceed it.  opts may be NULL (defaults). */
 int bcmg_footprint_estimate(int dim, int64_t N, const bcmg_opts *opts, int64_t *bytes);
 
+/* The same estimate with the grid size given per axis (N[dim]; size_t
+ * result): the library's grids are cubic, so every entry must equal N[0]
+ * (EINVAL otherwise). */
+int bcmg_footprint(int dim, const int64_t *N, const bcmg_opts *opts, size_t *bytes);
+
 /* Residual norms of u_dev on the finest level into out_host[4]:
  * ||r_I||_2, ||r_G||_2, ||r_I||_inf, ||r_G||_inf (unscaled residuals). */
 int bcmg_residual_norm(bcmg_handle h, const double *u_dev, double *out_host);

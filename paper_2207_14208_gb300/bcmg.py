@@ -84,6 +84,7 @@ def load():
             "bcmg_dtau_opt": (i32, [i32, i32, i32, f64, f64, vp]),
             "bcmg_memory_footprint": (i32, [vp, vp]),
             "bcmg_footprint_estimate": (i32, [i32, i64, vp, vp]),
+            "bcmg_footprint": (i32, [i32, vp, vp, vp]),
             "bcmg_last_error": (C.c_char_p, []),
             "bcmg_kernel_launches": (i64, []),
             "bcmg_profile_read": (i32, [vp, vp]),
@@ -197,6 +198,15 @@ def dtau_opt(dim: int, theta: float, mode: int = DTAU_EXP, bc: int = BC_DIRICHLE
     """The library's Delta tau_OPT(theta) (Neumann: Delta tau_OPT / h)."""
     out = C.c_double()
     _check(load().bcmg_dtau_opt(int(dim), int(bc), int(mode), float(const), float(theta), C.byref(out)))
+    return out.value
+
+
+def footprint(dim: int, Ns, **opts) -> int:
+    """bcmg_footprint: the estimate with the grid size per axis (cubic)."""
+    o = default_opts(**opts)
+    arr = (C.c_int64 * len(Ns))(*[int(n) for n in Ns])
+    out = C.c_size_t()
+    _check(load().bcmg_footprint(int(dim), arr, C.byref(o), C.byref(out)))
     return out.value
 
 

@@ -1026,6 +1026,17 @@ int bcmg_memory_footprint(bcmg_handle h, int64_t *bytes) {
     });
 }
 
+int bcmg_footprint(int dim, const int64_t *N, const bcmg_opts *opts, size_t *bytes) {
+    if (!N || !bytes) return fail(BCMG_EINVAL, "null pointer");
+    if (dim != 2 && dim != 3) return fail(BCMG_EINVAL, "bad dim");
+    for (int a = 1; a < dim; ++a)
+        if (N[a] != N[0]) return fail(BCMG_EINVAL, "grids are cubic: every N[a] must equal N[0]");
+    int64_t b = 0;
+    const int rc = bcmg_footprint_estimate(dim, N[0], opts, &b);
+    if (rc == BCMG_OK) *bytes = (size_t)b;
+    return rc;
+}
+
 int bcmg_footprint_estimate(int dim, int64_t N, const bcmg_opts *opts, int64_t *bytes) {
     if (!bytes) return fail(BCMG_EINVAL, "bytes is null");
     if ((dim != 2 && dim != 3) || N < 4 || N > 65534) return fail(BCMG_EINVAL, "bad dim or N");

@@ -52,3 +52,18 @@ def test_dtau_opt_host_matches_oracle():
     # the Neumann 2D values of eq. dtauoptLFA_Neumann at theta = 0, 1/2, 1
     for th, want in [(0.0, 0.92099), (0.5, 1.28166), (1.0, 2.10663)]:
         assert abs(bcmg.dtau_opt(2, th, bcmg.DTAU_POLY, bc=1) - want) < 1e-5
+
+
+def test_footprint_per_axis_matches_estimate():
+    # bcmg_footprint (grid size per axis) is the estimate of
+    # bcmg_footprint_estimate; a host function, no GPU needed
+    from paper_2207_14208_gb300 import bcmg, build
+    if shutil.which("nvcc") is None and not build.os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    build.build()
+    for d, N in ((2, 128), (3, 64), (2, 1024)):
+        for prec in (bcmg.PREC_FP64, bcmg.PREC_MIXED):
+            assert bcmg.footprint(d, [N] * d, precision=prec) == bcmg.footprint_estimate(d, N, precision=prec) > 0
+    with pytest.raises(bcmg.BcmgError) as e:
+        bcmg.footprint(3, [64, 64, 32])
+    assert e.value.code == bcmg.EINVAL
