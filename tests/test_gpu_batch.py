@@ -359,3 +359,37 @@ def test_host_boundary_data_equals_device(bcmg):
     np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
     np.testing.assert_array_equal(out[0][2], out[1][2])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_neumann_with_reaction_matches_alone(bcmg, prec):
+    # Neumann rows and the reaction term (c u - Lap u = f, Sec. 4.2 Test2N)
+    # through the batched kernels: the same results as each solve alone
+    B = bcmg
+    p = B.PREC_FP64 if prec == "fp64" else B.PREC_MIXED
+    probs = [(2, N, W.phi_star(N, 0.1, k, 0.3)) for N, k in ((64, 5), (96, 4), (128, 6))]
+
+    def make(d, N, phi):
+        f, _ = W.manufactured(d, N)
+        s = B.Solver(d, N, torch.from_numpy(phi).cuda(), torch.from_numpy(f).cuda(), precision=p,
+                     bc=B.BC_NEUMANN, reaction=1.0)
+        Q = s.ghost_points()
+        s.set_boundary_values((torch.sin(3.0 * Q[:, 0]) * torch.cos(2.0 * Q[:, 1])).contiguous())
+        return s, torch.zeros((N + 1) ** d, dtype=torch.float64, device="cuda")
+
+    alone = []
+    for d, N, phi in probs:
+        s, u = make(d, N, phi)
+        c, rel = s.solve(u, 1e-10, 80)
+        torch.cuda.synchronize()
+        alone.append((c, u.cpu().numpy(), s.cls(0)))
+        s.close()
+    pairs = [make(d, N, phi) for d, N, phi in probs]
+    cyc, rel, st = B.solve_batch([s for s, _ in pairs], [u for _, u in pairs], 1e-10, 80)
+    torch.cuda.synchronize()
+    for (c0, u0, cls), (s, u), c, r, status in zip(alone, pairs, cyc, rel, st):
+        assert status == B.OK and r <= 1e-10
+        assert abs(c - c0) <= (1 if prec == "fp64" else 3)
+        act = np.isin(cls, [B.INTERIOR, B.GHOST])
+        assert np.abs(u.cpu().numpy()[act] - u0[act]).max() <= 1e-9 * np.abs(u0[act]).max()
+        s.close()
