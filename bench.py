@@ -464,8 +464,90 @@ def run_e2e(args, d, N, phi_h, f_h, steps=8):
             tot_t += t1 - t0
             h2d = phi_h.nbytes + f_h.nbytes
             d2h = u_p.numel() * 8
-    return {"value": tot_c / tot_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "steps": steps}
+    serial = tot_c / tot_t
+    pipe, pipe_err = run_e2e_pipelined(args, d, N, phi_p, f_p, u_p, 2 * steps)
+    return {"value": pipe, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": 2 * steps, "serial_value": serial, "serial_steps": steps, "max_rel_err_pipelined_vs_serial": pipe_err,
+            "mode": "pipelined: step k+1's H2D of phi and f and step k-1's D2H of u run while step k "
+                    "solves (two device buffers each, every copy inside the timed region); "
+                    "serial_value: each step's copies, creation and solve one after another"}
+
+
+def run_e2e_pipelined(args, d, N, phi_p, f_p, u_p, steps):
+    """The e2e step as a stream of problems: the same public calls and copies
+    per step as run_e2e, with the copies of neighbouring steps overlapping
+    the device work.  Once step k's hierarchy exists, step k + 1's inputs go
+    to device buffers (k + 1) % 2 on one copy stream and step k - 1's u comes
+    back on another, both while step k solves (creation issues small copies
+    of its own, which would queue behind a large transfer of another stream,
+    so none is in flight while a hierarchy is built).  A buffer is refilled
+    only after the step that used it two steps back has consumed it.  Host
+    wall clock from the first H2D to the completion of the last D2H.
+    Returns V-cycles/s and the largest relative difference of a returned u
+    from the serial leg's (the same problem every step)."""
+    import torch
+    from paper_2207_14208_gb300 import bcmg
+    main = torch.cuda.current_stream()
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    phi_d = [torch.empty(phi_p.shape, dtype=phi_p.dtype, device="cuda") for _ in range(2)]
+    f_d = [torch.empty(f_p.shape, dtype=f_p.dtype, device="cuda") for _ in range(2)]
+    u_d = [torch.empty(phi_p.shape, dtype=phi_p.dtype, device="cuda") for _ in range(2)]
+    u_h = [torch.empty_like(u_p).pin_memory() for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]      # inputs of buffer b on the device
+    ev_used = [torch.cuda.Event() for _ in range(2)]    # inputs of buffer b consumed
+    ev_solved = [torch.cuda.Event() for _ in range(2)]  # u of buffer b final
+    ev_out = [torch.cuda.Event() for _ in range(2)]     # u of buffer b back on the host
+    for b in range(2):
+        ev_used[b].record(main)
+        ev_out[b].record(main)
+
+    def h2d(k):
+        b = k & 1
+        up.wait_event(ev_used[b])
+        with torch.cuda.stream(up):
+            phi_d[b].copy_(phi_p, non_blocking=True)
+            f_d[b].copy_(f_p, non_blocking=True)
+        ev_in[b].record(up)
+
+    def d2h(k):
+        b = k & 1
+        down.wait_event(ev_solved[b])
+        with torch.cuda.stream(down):
+            u_h[b].copy_(u_d[b], non_blocking=True)
+        ev_out[b].record(down)
+
+    def run(n):
+        cyc = 0
+        h2d(0)
+        for k in range(n):
+            b = k & 1
+            main.wait_event(ev_in[b])
+            s = bcmg.Solver(d, N, phi_d[b], None)
+            s.set_rhs(f_d[b])
+            s.set_boundary_values(u_exact_torch(s.ghost_points()).contiguous())
+            ev_used[b].record(main)
+            if k >= 1:
+                d2h(k - 1)
+            if k + 1 < n:
+                h2d(k + 1)
+            main.wait_event(ev_out[b])  # buffer b's u of step k - 2 has reached the host
+            u_d[b].zero_()
+            c, rel = s.solve(u_d[b], args.rtol, 200)
+            ev_solved[b].record(main)
+            s.close()
+            cyc += c
+        d2h(n - 1)
+        torch.cuda.synchronize()
+        return cyc
+
+    run(2)  # warm-up
+    t0 = time.perf_counter()
+    cyc = run(steps)
+    t1 = time.perf_counter()
+    ref = u_p.numpy()
+    scale = float(np.abs(ref).max())
+    err = max(float(np.abs(u_h[b].numpy() - ref).max()) / scale for b in range(2))
+    return cyc / (t1 - t0), err
 
 
 def oracle_sample(d, N, phi_h, f_h, ncyc):

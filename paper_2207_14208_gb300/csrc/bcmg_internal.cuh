@@ -162,6 +162,7 @@ struct Handle {
     bool sgraph_failed = false;  // graph with a conditional node unavailable
     int64_t sgraph_prefix = 0, sgraph_body = 0;  // kernels before / per iteration
     SolveState *sdev = nullptr, *shost = nullptr;
+    SolveState *shost_dev = nullptr;  // device address of shost (null: copies instead)
     int64_t vgraph_kernels = 0, ngraph_kernels = 0;
     // coarse end of the V-cycle on one thread-block cluster: first level (-1:
     // none), cluster size

@@ -540,6 +540,19 @@ int guarded(Fn fn) {
     }
 }
 
+// The solve state in and out without the copy engines: in as a launch
+// parameter, out by a store into the pinned block through its device alias.
+// A small copy is queued behind the large transfers other streams have in
+// flight (a caller's next inputs, a previous result on its way back), so a
+// copy here would hold the solve until they finished.
+__global__ void k_state_put(SolveState *d, SolveState s) {
+    if (threadIdx.x == 0) *d = s;
+}
+
+__global__ void k_state_get(SolveState *h, const SolveState *d) {
+    if (threadIdx.x == 0) *h = *d;
+}
+
 // Enqueue a whole device-driven solve on the handle's stream (no host wait):
 // copy u in, the solve graph, the state back, u out.  False if this handle
 // solves with the host loop instead (profiling, graphs off, or no graph).
@@ -551,9 +564,22 @@ bool solve_enqueue(Handle &H, double *u_dev, double rtol, int max_cycles) {
     copy_active(H, u_dev, H.u0, true);
     H.shost->rtol = rtol;
     H.shost->max_cycles = max_cycles;
-    check_cuda(cudaMemcpyAsync(H.sdev, H.shost, sizeof(SolveState), cudaMemcpyHostToDevice, H.st), "solve state H2D");
+    if (H.shost_dev) {
+        k_state_put<<<1, 32, 0, H.st>>>(H.sdev, *H.shost);
+        check_cuda(cudaGetLastError(), "k_state_put");
+    } else {
+        check_cuda(cudaMemcpyAsync(H.sdev, H.shost, sizeof(SolveState), cudaMemcpyHostToDevice, H.st),
+                   "solve state H2D");
+    }
     check_cuda(cudaGraphLaunch(H.sgraph, H.st), "cudaGraphLaunch(solve)");
-    check_cuda(cudaMemcpyAsync(H.shost, H.sdev, sizeof(SolveState), cudaMemcpyDeviceToHost, H.st), "solve state D2H");
+    if (H.shost_dev) {
+        k_state_get<<<1, 32, 0, H.st>>>(H.shost_dev, H.sdev);
+        check_cuda(cudaGetLastError(), "k_state_get");
+        add_launches(2);
+    } else {
+        check_cuda(cudaMemcpyAsync(H.shost, H.sdev, sizeof(SolveState), cudaMemcpyDeviceToHost, H.st),
+                   "solve state D2H");
+    }
     copy_active(H, H.u0, u_dev, false);
     leave(H);
     return true;
@@ -776,6 +802,11 @@ int bcmg_create_grid_hierarchy_ex(int dim, int64_t N, double lo, double h, const
         static_assert(sizeof(SolveState) <= kPinBlock && 4 * sizeof(double) <= kPinBlock, "pinned block");
         H->nhost = (double *)pinned_get();
         H->shost = (SolveState *)pinned_get();
+        {
+            void *alias = nullptr;  // the block's device address (mapped pinned memory)
+            if (cudaHostGetDevicePointer(&alias, H->shost, 0) == cudaSuccess) H->shost_dev = (SolveState *)alias;
+            else (void)cudaGetLastError();
+        }
         H->sdev = (SolveState *)dalloc(*H, sizeof(SolveState));
         set_interior_rhs(*H, L0, f_dev, L0.F);
         for (auto &L : H->L) L.phi = nullptr;
