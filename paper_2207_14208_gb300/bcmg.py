@@ -94,6 +94,7 @@ def load():
             "bcmg_selftest_div_wsum": (i32, [i32, vp, i64, vp]),
             "bcmg_num_levels": (i32, [vp, vp]),
             "bcmg_level_info": (i32, [vp, i32, vp]),
+            "bcmg_level_lists": (i32, [vp, i32, vp]),
             "bcmg_get_class": (i32, [vp, i32, vp]),
             "bcmg_get_ghosts": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
             "bcmg_get_band": (i32, [vp, i32, vp]),
@@ -400,6 +401,14 @@ class Solver:
         keys = ["N", "n", "nn", "n_interior", "n_ghost", "n_band", "n_boxdir", "n_clamped",
                 "n_fallback", "n_active"]
         return dict(zip(keys, (int(v) for v in out)))
+
+    def lists(self, l: int = 0) -> dict:
+        """Sizes of the parts of the level's interior list: red rows, black
+        rows with a neighbour that is not interior (ghost or box edge),
+        black rows whose neighbours are all interior."""
+        out = np.zeros(3, dtype=np.int64)
+        _check(self.lib.bcmg_level_lists(self.h, l, _hptr(out)))
+        return dict(zip(["red", "black_near", "black_inner"], (int(v) for v in out)))
 
     def cls(self, l: int = 0) -> np.ndarray:
         out = np.zeros(self.info(l)["nn"], dtype=np.uint8)

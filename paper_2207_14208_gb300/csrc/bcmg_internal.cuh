@@ -72,6 +72,7 @@ struct Level {
     uint8_t *cls = nullptr;
     int64_t nint = 0, nbox = 0, ng = 0, nb = 0, nclamp = 0, nfall = 0, nact = 0;
     int64_t nred = 0;            // red interior nodes (head of ilist)
+    int64_t nbn = 0;             // black interior nodes next to a ghost or box-edge node (next in ilist)
     uint32_t *ilist = nullptr;  // nint interior node indices, red then black
     // GS-LEX order only: interior nodes grouped by hyperplane p = i + j (+ k),
     // hyperplane p at hlist[hoff[p] .. hoff[p + 1])
@@ -223,7 +224,9 @@ constexpr int kExtCap = 32;  // terms per band node of the expanded extension
 // the mixed-precision refinement) ----------------------------------------
 // Fs: the level's scaled right-hand side (the cycle), or null (a caller's F)
 template <typename T> void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs = nullptr);
-template <typename T> void residual(Handle &H, Level &L, const T *u, const T *F, T *r);
+// after_rb: u comes straight from a red-black smoothing step of this level
+// (black rows whose neighbours are all interior then hold a zero residual)
+template <typename T> void residual(Handle &H, Level &L, const T *u, const T *F, T *r, bool after_rb = false);
 template <typename T> void extend(Handle &H, Level &L, T *a);
 // early_ok: the fine level's residual (and band extension) are the launches
 // right before
@@ -236,7 +239,8 @@ template <typename T> void prolong(Handle &H, Level &Lf, Level &Lc, const T *ec,
 template <typename T> void coarsest_correct(Handle &H, Level &L, T *u, const T *F);
 // finest-level residual r = F - A u and its four norms (out4, device);
 // ctl 1 / 2 also enqueue the solve's start / per-cycle check on cond
-void residual_norms(Handle &H, const double *u, double *out4, int ctl = 0, unsigned long long cond = 0);
+void residual_norms(Handle &H, const double *u, double *out4, int ctl = 0, unsigned long long cond = 0,
+                    bool after_rb = false);
 int64_t norm_parts(const Level &L);  // block partials residual_norms writes
 // ghost weights of every level; the levels of the cluster tail and their tables
 void setup_cycle(Handle &H);

@@ -408,6 +408,13 @@ void enqueue_norms(Handle &H) {
     residual_norms(H, H.u0, H.nout);
 }
 
+// The norms after a cycle may take the residual's after-smoothing form: an
+// FP64 cycle ends with a red-black smoothing step of the finest level (a
+// refinement step ends with its correction instead)
+bool norms_after_rb(const Handle &H) {
+    return H.o.precision == BCMG_PREC_FP64 && H.o.ordering == BCMG_ORDER_RB && H.o.nu2 > 0 && H.L.size() > 1;
+}
+
 // add the device time of the profiled sweeps of the last completed cycle
 void profile_collect(Handle &H) {
     if (!H.o.profile) return;
@@ -427,7 +434,7 @@ void profile_collect(Handle &H) {
 void solve_body(Handle &H) {
     if (H.o.precision == BCMG_PREC_MIXED) mixed_step_enqueue(H, H.u0);
     else vcycle_enqueue(H, 0, H.u0);
-    enqueue_norms(H);
+    residual_norms(H, H.u0, H.nout, 0, 0, norms_after_rb(H));
 }
 
 void run_vcycle_norms(Handle &H) {
@@ -486,7 +493,7 @@ cudaGraphExec_t build_solve_graph(Handle &H) {
         H.captured = 0;
         if (H.o.precision == BCMG_PREC_MIXED) mixed_step_enqueue(H, H.u0);
         else vcycle_enqueue(H, 0, H.u0);
-        residual_norms(H, H.u0, H.nout, 2, (unsigned long long)cond);
+        residual_norms(H, H.u0, H.nout, 2, (unsigned long long)cond, norms_after_rb(H));
         H.sgraph_body = H.captured;
         capturing = false;
         check_cuda(cudaStreamEndCapture(H.st, &body), "end capture solve body");
@@ -1154,6 +1161,16 @@ int bcmg_level_info(bcmg_handle h, int level, int64_t *out) {
         Level &L = level_of(H, level);
         if (!out) throw Error{BCMG_EINVAL, "null pointer"};
         int64_t v[10] = {L.N, L.n, L.nn, L.nint, L.ng, L.nb, L.nbox, L.nclamp, L.nfall, L.nact};
+        std::memcpy(out, v, sizeof(v));
+    });
+}
+
+int bcmg_level_lists(bcmg_handle h, int level, int64_t *out) {
+    return guarded([&] {
+        Handle &H = *checked(h);
+        Level &L = level_of(H, level);
+        if (!out) throw Error{BCMG_EINVAL, "null pointer"};
+        const int64_t v[3] = {L.nred, L.nbn, L.nint - L.nred - L.nbn};
         std::memcpy(out, v, sizeof(v));
     });
 }

@@ -312,11 +312,17 @@ __device__ void norm_tail(const NormTail &nt, const double *part) {
 // r = F - A u on the interior rows (eq. Laph); with part != null also the
 // block's norm partials (slot = block).  NPT rows per thread (strided by the
 // block size): with norm partials the squares are summed in the thread first
-// (one FMA per row), so the warp reduction's FP64 adds are shared by NPT rows
+// (one FMA per row), so the warp reduction's FP64 adds are shared by NPT rows.
+// Rows from nfull on are black rows whose neighbours are all interior,
+// right after a red-black smoothing step: the black sweep solved their
+// equations from the red values, and the ghost relaxation after it changed
+// no neighbour of theirs, so their residual is zero (up to the sweep's
+// rounding) and is stored as such, with no loads and no arithmetic.
 template <int D, typename T, int NPT>
 __global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict__ ilist, int64_t nint,
-                                                     const T *__restrict__ u, const T *__restrict__ F,
-                                                     T *__restrict__ r, G2 G, double *__restrict__ part) {
+                                                     int64_t nfull, const T *__restrict__ u,
+                                                     const T *__restrict__ F, T *__restrict__ r, G2 G,
+                                                     double *__restrict__ part) {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * NPT + threadIdx.x;
     int64_t X[NPT];
 #pragma unroll
@@ -329,8 +335,9 @@ __global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict_
     long long mxb = 0;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
-        if (i0 + (int64_t)j * blockDim.x < nint) {
-            const T v = residual_int<D, T>(X[j], u, F, G);
+        const int64_t i = i0 + (int64_t)j * blockDim.x;
+        if (i < nint) {
+            const T v = i < nfull ? residual_int<D, T>(X[j], u, F, G) : T(0);
             r[pos(X[j], G.lay)] = v;
             s2 = fma((double)v, (double)v, s2);
             mxb = max(mxb, abs_bits((double)v));
@@ -1035,7 +1042,7 @@ void vcycle_t(Handle &H, int l, T *u) {
     }
     Level &B = H.L[l + 1];
     smooth<T>(H, A, u, Arr<T>::F(A), H.o.nu1, Arr<T>::Fs(A));
-    residual<T>(H, A, u, Arr<T>::F(A), Arr<T>::r(A));
+    residual<T>(H, A, u, Arr<T>::F(A), Arr<T>::r(A), H.o.ordering == BCMG_ORDER_RB && H.o.nu1 > 0);
     extend<T>(H, A, Arr<T>::r(A));
     restrict_to<T>(H, A, B, Arr<T>::r(A), Arr<T>::F(B), Arr<T>::u(B), true, Arr<T>::Fs(B));
     // two-grid correction scheme (Sec. 2.1): the level-1 problem solved by
@@ -1306,8 +1313,9 @@ void smooth(Handle &H, Level &L, T *u, const T *F, int nsteps, const T *Fs) {
 // returns the number of norm partials written
 template <typename T>
 static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, double *part,
-                             NormTail nt = NormTail{}) {
+                             NormTail nt = NormTail{}, bool after_rb = false) {
     const G2 G = g2_of(L);
+    const int64_t nfull = after_rb ? L.nred + L.nbn : L.nint;
     // with norm partials, kNormRows interior rows per thread; with the norm
     // tail, full-size ghost blocks (the last one reduces every partial)
     constexpr int kNormRows = 4;
@@ -1318,14 +1326,14 @@ static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, 
     nt.nparts = ni + nblk(L.ng, bg);
     if (L.d == 3) {
         launch(H, "k_residual_int", part ? k_residual_int<3, T, kNormRows> : k_residual_int<3, T, 1>, (unsigned)ni,
-               bi, (const uint32_t *)L.ilist, L.nint, u, F, r, G, part);
+               bi, (const uint32_t *)L.ilist, L.nint, nfull, u, F, r, G, part);
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<3, T, true> : k_residual_gh<3, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
                ni, nt, (int)(ni > 0));
     } else {
         launch(H, "k_residual_int", part ? k_residual_int<2, T, kNormRows> : k_residual_int<2, T, 1>, (unsigned)ni,
-               bi, (const uint32_t *)L.ilist, L.nint, u, F, r, G, part);
+               bi, (const uint32_t *)L.ilist, L.nint, nfull, u, F, r, G, part);
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<2, T, true> : k_residual_gh<2, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
@@ -1335,8 +1343,8 @@ static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, 
 }
 
 template <typename T>
-void residual(Handle &H, Level &L, const T *u, const T *F, T *r) {
-    residual_impl<T>(H, L, u, F, r, nullptr);
+void residual(Handle &H, Level &L, const T *u, const T *F, T *r, bool after_rb) {
+    residual_impl<T>(H, L, u, F, r, nullptr, NormTail{}, after_rb);
 }
 
 template <typename T>
@@ -1409,7 +1417,7 @@ void coarsest_correct(Handle &H, Level &L, T *u, const T *F) {
 // last block of the ghost residual kernel reduces the block partials and
 // runs the control; without, a single-block reduction and a separate
 // control launch follow.
-void residual_norms(Handle &H, const double *u, double *out4, int ctl, unsigned long long cond) {
+void residual_norms(Handle &H, const double *u, double *out4, int ctl, unsigned long long cond, bool after_rb) {
     Level &L = H.L[0];
     if (L.ng > 0) {
         NormTail nt{};
@@ -1418,10 +1426,10 @@ void residual_norms(Handle &H, const double *u, double *out4, int ctl, unsigned 
         nt.nout = out4;
         nt.st = H.sdev;
         nt.cond = (cudaGraphConditionalHandle)cond;
-        residual_impl<double>(H, L, u, L.F, L.r, H.npart, nt);
+        residual_impl<double>(H, L, u, L.F, L.r, H.npart, nt, after_rb);
         return;
     }
-    const int64_t parts = residual_impl<double>(H, L, u, L.F, L.r, H.npart);
+    const int64_t parts = residual_impl<double>(H, L, u, L.F, L.r, H.npart, NormTail{}, after_rb);
     launch(H, "k_norm_final", k_norm_final, 1u, 1024u, (const double *)H.npart, parts, out4);
     if (ctl == 1) solve_init_enqueue(H, cond);
     else if (ctl == 2) solve_check_enqueue(H, cond);
@@ -1637,13 +1645,13 @@ int selftest_div_wsum(int fp32, const double *a_host, int64_t n, double *out_hos
 }
 
 template void smooth<double>(Handle &, Level &, double *, const double *, int, const double *);
-template void residual<double>(Handle &, Level &, const double *, const double *, double *);
+template void residual<double>(Handle &, Level &, const double *, const double *, double *, bool);
 template void extend<double>(Handle &, Level &, double *);
 template void restrict_to<double>(Handle &, Level &, Level &, const double *, double *, double *, bool, double *);
 template void prolong<double>(Handle &, Level &, Level &, const double *, double *, bool);
 template void coarsest_correct<double>(Handle &, Level &, double *, const double *);
 template void smooth<float>(Handle &, Level &, float *, const float *, int, const float *);
-template void residual<float>(Handle &, Level &, const float *, const float *, float *);
+template void residual<float>(Handle &, Level &, const float *, const float *, float *, bool);
 template void extend<float>(Handle &, Level &, float *);
 template void restrict_to<float>(Handle &, Level &, Level &, const float *, float *, float *, bool, float *);
 template void prolong<float>(Handle &, Level &, Level &, const float *, float *, bool);

@@ -221,7 +221,12 @@ __device__ __forceinline__ bool neg_d(double x) {
 // flags of every list the set-up compacts (red / black interior, box-edge
 // Dirichlet, ghost, active), one thread per node on a (x-blocks, j, k) grid
 // (no index division).
-enum : uint8_t { kFlRed = 1, kFlBlack = 2, kFlBox = 4, kFlGhost = 8, kFlAct = 16 };
+// list flags of a node; a black interior node with a neighbour that is not
+// interior (a ghost or a box-edge node) is listed apart from the other black
+// ones (kFlBNear, kFlBlack), so that the cycle's residual after a smoothing
+// step finds the black rows whose residual the ghost relaxation may have
+// changed at the head of the black part
+enum : uint8_t { kFlRed = 1, kFlBlack = 2, kFlBox = 4, kFlGhost = 8, kFlAct = 16, kFlBNear = 32 };
 
 // One launch classifies every candidate level.  Level l reads the finest
 // phi at stride 2^l (the injection, Sec. 2.1) and, for l > 0, stores its
@@ -304,7 +309,15 @@ __global__ void __launch_bounds__(128) k_classify(ClassBatch B) {
         const uint8_t c = neg_d(pc) ? (edge ? CL_BOXDIR : CL_INTERIOR) : (gh ? CL_GHOST : CL_INACTIVE);
         C.cls[lin] = c;
         uint8_t fl = 0;
-        if (c == CL_INTERIOR) fl = ((par0 ^ (uint8_t)(q & 1)) == 0 ? kFlRed : kFlBlack) | kFlAct;
+        if (c == CL_INTERIOR && (par0 ^ (uint8_t)(q & 1)) != 0) {
+            // black: listed apart unless every neighbour is interior (off the
+            // box edge with phi < 0: the test above, whose edge neighbours
+            // read as phi = 1), i.e. when a ghost or a box-edge node is next
+            // to it
+            bool all_int = neg_d(ax) & neg_d(bx) & neg_d(ay) & neg_d(by);
+            if (D == 3) all_int = all_int & (k - 1 > 0) & neg_d(pz[q]) & (k + 1 < N) & neg_d(pz[q + 2]);
+            fl = (all_int ? kFlBlack : kFlBNear) | kFlAct;
+        } else if (c == CL_INTERIOR) fl = kFlRed | kFlAct;
         else if (c == CL_GHOST) fl = kFlGhost | kFlAct;
         else if (c == CL_BOXDIR) fl = kFlBox;
         C.flags[lin] = fl;
@@ -1286,7 +1299,8 @@ __global__ void k_hp_scatter(const uint32_t *__restrict__ ilist, int64_t nint, G
 
 struct LevelScratch {
     uint8_t *flags = nullptr, *fband = nullptr;
-    uint32_t *red = nullptr, *black = nullptr;
+    uint32_t *red = nullptr, *black = nullptr;  // black: every neighbour interior
+    uint32_t *bnear = nullptr;                  // black next to a ghost or box-edge node
     uint32_t *act = nullptr;  // active list of a coarse level (round 1)
     int64_t nact = 0;
     unsigned long long *cnt = nullptr;  // clamp / fall-back counters
@@ -1384,11 +1398,17 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             add_list(it, kFlAct, &S[l].act, true);
             items.push_back(it);
         }
+        for (int l = 0; l < nc; ++l) {
+            CompactItem it = compact_item(S[l].flags, H.L[l].nn);
+            add_list(it, kFlBNear, &S[l].bnear, true);
+            items.push_back(it);
+        }
         run_compaction(H, items);
         for (int l = 0; l < nc; ++l) {
             Level &L = H.L[l];
             L.nred = items[l].total[0];
-            L.nint = L.nred + items[l].total[1];
+            L.nbn = items[2 * nc - 1 + l].total[0];
+            L.nint = L.nred + L.nbn + items[l].total[1];
             L.nbox = items[l].total[2];
             L.ng = items[l].total[3];
             if (l > 0) S[l].nact = items[nc + l - 1].total[0];
@@ -1476,7 +1496,8 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         // no zero-fill
         L.ilist = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(L.nint, 1), false, false);
         lists.add(s.red, L.ilist, sizeof(uint32_t) * (size_t)L.nred);
-        lists.add(s.black, L.ilist + L.nred, sizeof(uint32_t) * (size_t)(L.nint - L.nred));
+        lists.add(s.bnear, L.ilist + L.nred, sizeof(uint32_t) * (size_t)L.nbn);
+        lists.add(s.black, L.ilist + L.nred + L.nbn, sizeof(uint32_t) * (size_t)(L.nint - L.nred - L.nbn));
         int64_t ng1 = std::max<int64_t>(L.ng, 1);
         L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1, false, false);
         L.gxi = (double *)dalloc(H, sizeof(double) * 3 * ng1);
