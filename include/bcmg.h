@@ -262,8 +262,10 @@ int bcmg_solve(bcmg_handle h, double *u_dev, double rtol, int max_cycles, int *c
  * hierarchies (levels aligned by depth), in a CUDA graph whose loop runs
  * while any solve is unfinished; a finished hierarchy's work is skipped.
  * The launch shape (block size, items per thread) is measured once per
- * batch shape on the first call (an autotuner; it runs batched cycles on
- * the hierarchies' working copies only).  Per node the arithmetic is that
+ * batch shape class on the first call of that class (an autotuner; it runs
+ * batched cycles on the hierarchies' working copies only); a class is the
+ * device, dimension and precision with the number of hierarchies and their
+ * total rows each rounded up to a power of two.  Per node the arithmetic is that
  * of bcmg_solve; the coarse levels and the norm reduction sum in another
  * order, so results agree with bcmg_solve alone to rounding (and a cycle
  * count within a few cycles of it), not bit for bit.  The work is ordered

@@ -1428,7 +1428,17 @@ int64_t batch_solve(const std::vector<Handle *> &hs, cudaStream_t st, double rto
         for (auto &L : H->L) nodes += L.nint + L.ng;
     int dev = 0;
     check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
-    const auto key = std::make_tuple(dev, hs[0]->d, (int)(hs[0]->o.precision == BCMG_PREC_MIXED), (int64_t)n, nodes);
+    // batches of similar size share a tuned shape: the count of hierarchies
+    // and their rows are keyed rounded up to powers of two (a stream of
+    // batches that all differ, as a server forms them, is tuned once per
+    // size class, not once per batch)
+    auto pow2 = [](int64_t v) {
+        int64_t p = 1;
+        while (p < v) p <<= 1;
+        return p;
+    };
+    const auto key =
+        std::make_tuple(dev, hs[0]->d, (int)(hs[0]->o.precision == BCMG_PREC_MIXED), pow2(n), pow2(nodes));
     int64_t launched = 0;
     Shape shape;
     {
