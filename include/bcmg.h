@@ -383,15 +383,14 @@ int bcmg_num_levels(bcmg_handle h, int *levels);
  * (0 on other levels). */
 int bcmg_level_info(bcmg_handle h, int level, int64_t *out_host);
 
-/* out_host[3]: how the level's interior list is ordered for the cycle:
- * red rows ((i + j [+ k]) even) first, then black rows with a neighbour
- * that is not interior (a ghost or a box-edge node), then the black rows
- * whose 2d neighbours are all interior.  The counts of the three parts.
- * After a red-black smoothing step (red sweep, black sweep, ghost
- * relaxation, Sec. 2.1 with eq. rel for the ghosts) the residual of a row
- * of the third part is zero up to rounding, so the cycle's residual
- * computes the first two parts only and stores zero in the third (no
- * counterpart in the paper).  Errors: EINVAL. */
+/* out_host[3]: the level's interior rows by their part in the cycle's
+ * residual: red rows ((i + j [+ k]) even), black rows with a neighbour that
+ * is not interior (a ghost or a box-edge node), and the black rows whose 2d
+ * neighbours are all interior.  After a red-black smoothing step (red
+ * sweep, black sweep, ghost relaxation, Sec. 2.1 with eq. rel for the
+ * ghosts) the residual of a row of the third part is zero up to rounding,
+ * so the cycle's residual computes the first two parts only and stores zero
+ * in the third (no counterpart in the paper).  Errors: EINVAL. */
 int bcmg_level_lists(bcmg_handle h, int level, int64_t *out_host);
 
 /* n^dim node classes (BCMG_CLASS_*) of a level. */

@@ -72,8 +72,10 @@ struct Level {
     uint8_t *cls = nullptr;
     int64_t nint = 0, nbox = 0, ng = 0, nb = 0, nclamp = 0, nfall = 0, nact = 0;
     int64_t nred = 0;            // red interior nodes (head of ilist)
-    int64_t nbn = 0;             // black interior nodes next to a ghost or box-edge node (next in ilist)
-    uint32_t *ilist = nullptr;  // nint interior node indices, red then black
+    int64_t nbn = 0;             // black interior nodes next to a ghost or box-edge node
+    uint32_t *ilist = nullptr;  // nint interior node indices, red then black (each part sorted)
+    uint32_t *bnear = nullptr;  // the nbn black nodes next to a ghost or box-edge node, sorted
+    uint32_t *bmask = nullptr;  // bit j set: black entry ilist[nred + j] is in bnear
     // GS-LEX order only: interior nodes grouped by hyperplane p = i + j (+ k),
     // hyperplane p at hlist[hoff[p] .. hoff[p + 1])
     uint32_t *hlist = nullptr;

@@ -313,35 +313,53 @@ __device__ void norm_tail(const NormTail &nt, const double *part) {
 // block's norm partials (slot = block).  NPT rows per thread (strided by the
 // block size): with norm partials the squares are summed in the thread first
 // (one FMA per row), so the warp reduction's FP64 adds are shared by NPT rows.
-// Rows from nfull on are black rows whose neighbours are all interior,
-// right after a red-black smoothing step: the black sweep solved their
-// equations from the red values, and the ghost relaxation after it changed
-// no neighbour of theirs, so their residual is zero (up to the sweep's
-// rounding) and is stored as such, with no loads and no arithmetic.
+// With after != 0 (right after a red-black smoothing step of the level) the
+// black rows whose neighbours are all interior are not computed: the black
+// sweep solved their equations from the red values and the ghost relaxation
+// after it changed no neighbour of theirs, so their residual is zero (up to
+// the sweep's rounding) and is stored as such, with no loads and no
+// arithmetic.  The other black rows (bit set in bmask) are computed from
+// their own sorted list bnear, in the grid's first nbn rows (their loads are
+// scattered along the boundary: started first, they overlap the rest).
 template <int D, typename T, int NPT>
-__global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict__ ilist, int64_t nint,
-                                                     int64_t nfull, const T *__restrict__ u,
-                                                     const T *__restrict__ F, T *__restrict__ r, G2 G,
-                                                     double *__restrict__ part) {
+__global__ void __launch_bounds__(kT) k_residual_int(const uint32_t *__restrict__ ilist, int64_t nint, int64_t nred,
+                                                     const uint32_t *__restrict__ bmask,
+                                                     const uint32_t *__restrict__ bnear, int64_t nbn, int after,
+                                                     const T *__restrict__ u, const T *__restrict__ F,
+                                                     T *__restrict__ r, G2 G, double *__restrict__ part) {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * NPT + threadIdx.x;
+    const int64_t rows = after ? nint + nbn : nint;
     int64_t X[NPT];
+    int mode[NPT];  // 0 nothing, 1 computed, 2 zero
+    const int64_t head = after ? nbn : 0;  // rows of bnear before the list's
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         const int64_t i = i0 + (int64_t)j * blockDim.x;
-        X[j] = i < nint ? ilist[i] : 0;
+        mode[j] = 0;
+        X[j] = 0;
+        if (i < head) {
+            X[j] = bnear[i];
+            mode[j] = 1;
+        } else if (i < rows) {
+            const int64_t k = i - head;
+            X[j] = ilist[k];
+            mode[j] = 1;
+            if (after && k >= nred) {
+                const int64_t b = k - nred;
+                mode[j] = ((bmask[b >> 5] >> (b & 31)) & 1u) ? 0 : 2;
+            }
+        }
     }
     pdl_begin();
     double s2 = 0.0;
     long long mxb = 0;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
-        const int64_t i = i0 + (int64_t)j * blockDim.x;
-        if (i < nint) {
-            const T v = i < nfull ? residual_int<D, T>(X[j], u, F, G) : T(0);
-            r[pos(X[j], G.lay)] = v;
-            s2 = fma((double)v, (double)v, s2);
-            mxb = max(mxb, abs_bits((double)v));
-        }
+        if (mode[j] == 0) continue;
+        const T v = mode[j] == 1 ? residual_int<D, T>(X[j], u, F, G) : T(0);
+        r[pos(X[j], G.lay)] = v;
+        s2 = fma((double)v, (double)v, s2);
+        mxb = max(mxb, abs_bits((double)v));
     }
     if (part) block_partials(s2, mxb, part, blockIdx.x, true);
 }
@@ -1315,25 +1333,27 @@ template <typename T>
 static int64_t residual_impl(Handle &H, Level &L, const T *u, const T *F, T *r, double *part,
                              NormTail nt = NormTail{}, bool after_rb = false) {
     const G2 G = g2_of(L);
-    const int64_t nfull = after_rb ? L.nred + L.nbn : L.nint;
+    const int64_t rows = after_rb ? L.nint + L.nbn : L.nint;
     // with norm partials, kNormRows interior rows per thread; with the norm
     // tail, full-size ghost blocks (the last one reduces every partial)
     constexpr int kNormRows = 4;
     const int npt = part ? kNormRows : 1;
-    const int bi = bs_for(H, (L.nint + npt - 1) / npt), bg = nt.mode ? kT : bs_for(H, L.ng);
-    const int64_t ni = nblk(L.nint, bi * npt);
+    const int bi = bs_for(H, (rows + npt - 1) / npt), bg = nt.mode ? kT : bs_for(H, L.ng);
+    const int64_t ni = nblk(rows, bi * npt);
     const T *gw = Arr<T>::gw(L);
     nt.nparts = ni + nblk(L.ng, bg);
     if (L.d == 3) {
         launch(H, "k_residual_int", part ? k_residual_int<3, T, kNormRows> : k_residual_int<3, T, 1>, (unsigned)ni,
-               bi, (const uint32_t *)L.ilist, L.nint, nfull, u, F, r, G, part);
+               bi, (const uint32_t *)L.ilist, L.nint, L.nred, (const uint32_t *)L.bmask,
+               (const uint32_t *)L.bnear, L.nbn, (int)after_rb, u, F, r, G, part);
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<3, T, true> : k_residual_gh<3, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
                ni, nt, (int)(ni > 0));
     } else {
         launch(H, "k_residual_int", part ? k_residual_int<2, T, kNormRows> : k_residual_int<2, T, 1>, (unsigned)ni,
-               bi, (const uint32_t *)L.ilist, L.nint, nfull, u, F, r, G, part);
+               bi, (const uint32_t *)L.ilist, L.nint, L.nred, (const uint32_t *)L.bmask,
+               (const uint32_t *)L.bnear, L.nbn, (int)after_rb, u, F, r, G, part);
         if (L.ng == 0) return ni;
         launch(H, "k_residual_gh", nt.mode > 1 ? k_residual_gh<2, T, true> : k_residual_gh<2, T, false>,
                nblk(L.ng, bg), bg, (const uint32_t *)L.gidx, (const uint16_t *)L.gcode, gw, L.ng, u, F, r, G, part,
@@ -1436,7 +1456,7 @@ void residual_norms(Handle &H, const double *u, double *out4, int ctl, unsigned 
 }
 
 // an upper bound of the block partials residual_norms writes (64-thread blocks)
-int64_t norm_parts(const Level &L) { return (int64_t)nblk(L.nint, 64) + nblk(L.ng, 64); }
+int64_t norm_parts(const Level &L) { return (int64_t)nblk(L.nint + L.nbn, 64) + nblk(L.ng, 64); }
 
 // V(nu1, nu2) cycle from level l down (Sec. 2.1 with gamma = 1); u is the
 // level's unknown (finest: the working copy, coarse: the correction).

@@ -222,10 +222,9 @@ __device__ __forceinline__ bool neg_d(double x) {
 // Dirichlet, ghost, active), one thread per node on a (x-blocks, j, k) grid
 // (no index division).
 // list flags of a node; a black interior node with a neighbour that is not
-// interior (a ghost or a box-edge node) is listed apart from the other black
-// ones (kFlBNear, kFlBlack), so that the cycle's residual after a smoothing
-// step finds the black rows whose residual the ghost relaxation may have
-// changed at the head of the black part
+// interior (a ghost or a box-edge node) is also listed apart (kFlBNear), so
+// that the cycle's residual after a smoothing step finds the black rows
+// whose residual the ghost relaxation may have changed
 enum : uint8_t { kFlRed = 1, kFlBlack = 2, kFlBox = 4, kFlGhost = 8, kFlAct = 16, kFlBNear = 32 };
 
 // One launch classifies every candidate level.  Level l reads the finest
@@ -316,7 +315,7 @@ __global__ void __launch_bounds__(128) k_classify(ClassBatch B) {
             // to it
             bool all_int = neg_d(ax) & neg_d(bx) & neg_d(ay) & neg_d(by);
             if (D == 3) all_int = all_int & (k - 1 > 0) & neg_d(pz[q]) & (k + 1 < N) & neg_d(pz[q + 2]);
-            fl = (all_int ? kFlBlack : kFlBNear) | kFlAct;
+            fl = kFlBlack | (all_int ? 0 : kFlBNear) | kFlAct;
         } else if (c == CL_INTERIOR) fl = kFlRed | kFlAct;
         else if (c == CL_GHOST) fl = kFlGhost | kFlAct;
         else if (c == CL_BOXDIR) fl = kFlBox;
@@ -324,6 +323,32 @@ __global__ void __launch_bounds__(128) k_classify(ClassBatch B) {
         p += s2;
         lin += sz;
     }
+}
+
+// bit j of bits: black entry j (blist[j]) has the kFlBNear flag; a warp
+// writes one word (every thread reaches the ballot).  Every level in one
+// launch: the blocks of level q start at blk0[q].
+constexpr int kNearMax = 32;  // levels of one launch
+struct NearLevel {
+    const uint32_t *blist;
+    const uint8_t *flags;
+    uint32_t *bits;
+    int64_t nb, blk0;
+};
+struct NearBatch {
+    int nl;
+    NearLevel lv[kNearMax];
+};
+
+__global__ void __launch_bounds__(256) k_near_bits(NearBatch B) {
+    int q = 0;
+    for (int k = 1; k < B.nl; ++k)
+        if ((int64_t)blockIdx.x >= B.lv[k].blk0) q = k;
+    const NearLevel &L = B.lv[q];
+    const int64_t j = ((int64_t)blockIdx.x - L.blk0) * blockDim.x + threadIdx.x;
+    const bool near = j < L.nb && (L.flags[L.blist[j]] & kFlBNear) != 0;
+    const unsigned w = __ballot_sync(0xffffffffu, near);
+    if ((threadIdx.x & 31) == 0 && j < L.nb) L.bits[j >> 5] = w;
 }
 
 // ---------------------------------------------------------------- ghosts
@@ -1299,8 +1324,7 @@ __global__ void k_hp_scatter(const uint32_t *__restrict__ ilist, int64_t nint, G
 
 struct LevelScratch {
     uint8_t *flags = nullptr, *fband = nullptr;
-    uint32_t *red = nullptr, *black = nullptr;  // black: every neighbour interior
-    uint32_t *bnear = nullptr;                  // black next to a ghost or box-edge node
+    uint32_t *red = nullptr, *black = nullptr;
     uint32_t *act = nullptr;  // active list of a coarse level (round 1)
     int64_t nact = 0;
     unsigned long long *cnt = nullptr;  // clamp / fall-back counters
@@ -1400,7 +1424,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         }
         for (int l = 0; l < nc; ++l) {
             CompactItem it = compact_item(S[l].flags, H.L[l].nn);
-            add_list(it, kFlBNear, &S[l].bnear, true);
+            add_list(it, kFlBNear, &H.L[l].bnear, false);
             items.push_back(it);
         }
         run_compaction(H, items);
@@ -1408,7 +1432,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
             Level &L = H.L[l];
             L.nred = items[l].total[0];
             L.nbn = items[2 * nc - 1 + l].total[0];
-            L.nint = L.nred + L.nbn + items[l].total[1];
+            L.nint = L.nred + items[l].total[1];
             L.nbox = items[l].total[2];
             L.ng = items[l].total[3];
             if (l > 0) S[l].nact = items[nc + l - 1].total[0];
@@ -1496,8 +1520,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         // no zero-fill
         L.ilist = (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>(L.nint, 1), false, false);
         lists.add(s.red, L.ilist, sizeof(uint32_t) * (size_t)L.nred);
-        lists.add(s.bnear, L.ilist + L.nred, sizeof(uint32_t) * (size_t)L.nbn);
-        lists.add(s.black, L.ilist + L.nred + L.nbn, sizeof(uint32_t) * (size_t)(L.nint - L.nred - L.nbn));
+        lists.add(s.black, L.ilist + L.nred, sizeof(uint32_t) * (size_t)(L.nint - L.nred));
         int64_t ng1 = std::max<int64_t>(L.ng, 1);
         L.gcode = (uint16_t *)dalloc(H, sizeof(uint16_t) * ng1, false, false);
         L.gxi = (double *)dalloc(H, sizeof(double) * 3 * ng1);
@@ -1522,6 +1545,25 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         gblocks += nblocks(L.ng, 128);
     }
     lists.flush();
+    // which black entries are listed apart (one bit each, from the flags)
+    {
+        if (keep > kNearMax) throw Error{BCMG_EINVAL, "too many levels"};
+        NearBatch nbt{};
+        int64_t blk = 0;
+        for (int l = 0; l < keep; ++l) {
+            Level &L = H.L[l];
+            const int64_t nb = L.nint - L.nred;
+            L.bmask =
+                (uint32_t *)dalloc(H, sizeof(uint32_t) * (size_t)std::max<int64_t>((nb + 31) / 32, 1), false, false);
+            nbt.lv[nbt.nl++] = NearLevel{L.ilist + L.nred, S[l].flags, L.bmask, nb, blk};
+            blk += nblocks(nb, 256);
+        }
+        if (blk > 0) {
+            k_near_bits<<<(unsigned)blk, 256, 0, H.st>>>(nbt);
+            count_launch(H);
+        }
+        check_cuda(cudaGetLastError(), "k_near_bits");
+    }
     LevelTab *tab_d = (LevelTab *)dalloc(H, sizeof(LevelTab) * keep, true);
     check_cuda(cudaMemcpyAsync(tab_d, tab.data(), sizeof(LevelTab) * keep, cudaMemcpyHostToDevice, H.st), "tab");
     if (gblocks > 0) {
