@@ -1325,7 +1325,7 @@ __global__ void k_hp_scatter(const uint32_t *__restrict__ ilist, int64_t nint, G
 struct LevelScratch {
     uint8_t *flags = nullptr, *fband = nullptr;
     uint32_t *red = nullptr, *black = nullptr;
-    uint32_t *act = nullptr;  // active list of a coarse level (round 1)
+    uint32_t *act = nullptr;  // active list of a coarse level (pass 1)
     int64_t nact = 0;
     unsigned long long *cnt = nullptr;  // clamp / fall-back counters
     int64_t *ecnt = nullptr;
@@ -1402,7 +1402,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         }
         flush();
     }
-    // round 1: counts of every list on every candidate level (one sync)
+    // pass 1: counts of every list on every candidate level (one sync)
     {
         std::vector<CompactItem> items;
         for (int l = 0; l < nc; ++l) {
@@ -1510,7 +1510,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
     uint8_t *fb_next = (uint8_t *)dalloc(H, fb_bytes, true);
     // the ghost counters of every level (two each) and the extension's
     // overflow flags and longest rows (two ints per level), contiguous, so
-    // that round 3 reads them back with one copy
+    // that pass 3 reads them back with one copy
     char *ctr = (char *)dalloc(H, (sizeof(unsigned long long) * 2 + sizeof(int) * 2) * (size_t)keep, true);
     for (int l = 0; l < keep; ++l) {
         Level &L = H.L[l];
@@ -1588,7 +1588,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
                        "active list");
         coarsest_on_side();
     }
-    // round 2: band lists on every level (and the active list of a finest
+    // pass 2: band lists on every level (and the active list of a finest
     // level that is also the coarsest) (one sync)
     {
         std::vector<CompactItem> items;
@@ -1624,7 +1624,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         if (ell && L.nb > 0) {
             L.ecnt = (uint8_t *)dalloc(H, (size_t)nb1, false, false);
             // expansion scratch with kExtCap slots; the resident copy keeps
-            // only the slots the level's longest row needs (see round 3)
+            // only the slots the level's longest row needs (see pass 3)
             L.eg = (uint32_t *)dalloc(H, sizeof(uint32_t) * kExtCap * nb1, true, false);
             L.ew = (double *)dalloc(H, sizeof(double) * kExtCap * nb1, true, false);
         }
@@ -1660,7 +1660,7 @@ void setup_hierarchy(Handle &H, const double *phi0) {
         }
     }
     check_cuda(cudaGetLastError(), "band set-up");
-    // round 3: clamp / fall-back counters and ELL overflows (one sync)
+    // pass 3: clamp / fall-back counters and ELL overflows (one sync)
     {
         int64_t *hc = pinned_scratch(H, 3 * (size_t)keep + 2);
         check_cuda(cudaMemcpyAsync(hc, ctr, (sizeof(int64_t) * 2 + sizeof(int) * 2) * (size_t)keep,
