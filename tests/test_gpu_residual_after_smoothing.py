@@ -100,4 +100,7 @@ def test_list_split_matches_classes(bcmg, name, d, N, mk):
         want = _expected_lists(s.cls(l), d, n, B)
         assert (got["red"], got["black_near"], got["black_inner"]) == want, (l, got, want)
         assert sum(want) == s.info(l)["n_interior"]
+    with pytest.raises(B.BcmgError) as e:
+        s.lists(s._num_levels())
+    assert e.value.code == B.EINVAL
     s.close()
