@@ -245,6 +245,41 @@ def test_nonconvergence_reported(bcmg):
     assert e.value.code == B.ENONFINITE
 
 
+@pytest.mark.parametrize("d,N", [(2, 32), (2, 64), (3, 16)])
+def test_box_domain_without_ghosts(bcmg, d, N):
+    # phi < 0 everywhere: no ghost on any level, the box edge is the
+    # Dirichlet boundary (its values are taken from u); the cycle, the solve
+    # (whose norms then have no ghost rows) and the box values left untouched
+    B = bcmg
+    phi = -np.ones((N + 1) ** d)
+    f, us = W.manufactured(d, N)
+    s, o = pair(B, d, N, phi, f)
+    assert s.ghost_count() == 0 and o.ghosts(0)["idx"].size == 0
+    o.set_rhs(f, np.zeros(0))
+    cls = o.cls(0)
+    box, act = cls == O.BOXDIR, cls == O.INTERIOR
+    u0 = np.where(box, us, 0.0)
+    ug = dev(u0)
+    s.vcycle(ug, 1)
+    uo = o.vcycle(u0, 1)
+    assert np.abs(host(ug)[act] - uo[act]).max() <= REL * np.abs(uo[act]).max()
+    np.testing.assert_array_equal(host(ug)[~act], u0[~act])
+    ug = dev(u0)
+    cyc, rel = s.solve(ug, 1e-10, 100)
+    uo, co, _ = o.solve(u0, 1e-10, 100)
+    assert abs(cyc - co) <= 1 and rel <= 1e-10
+    err = np.abs(host(ug)[act] - us[act]).max()
+    # second order (Sec. 4): the error against u* shrinks about fourfold per
+    # halving of h; checked between the two 2D sizes
+    _box_err[(d, N)] = err
+    if d == 2 and (2, 32) in _box_err and (2, 64) in _box_err:
+        ratio = _box_err[(2, 32)] / _box_err[(2, 64)]
+        assert 3.0 < ratio < 5.0, ratio
+
+
+_box_err = {}
+
+
 # mid-size 3D cases (more than 2^18 interior nodes on the finest level), two
 # V-cycles from a random start
 MCASES = [("ellipsoid176", 3, 176, W.phi_ellipsoid), ("spheres192", 3, 192, W.phi_spheres)]
